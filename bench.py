@@ -1,0 +1,295 @@
+#!/usr/bin/env python
+"""Throughput of sound reachable-set bounds: domain-steps per second on one B300.
+
+A step is one pass of the whole bound computation over the batched workload: every domain's
+Taylor-model seed, the per-layer back-substitution chains and concretisations, the controller
+Taylor model, the dynamics, the FP64 boxes of every horizon step and the hull over domains.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (default): 6-state stable linear dynamics, ReLU controller 6-64-64-3 (FP32 weights),
+the initial box split into a uniform 4^6 = 4096 sub-box grid, horizon 10, chord slopes.
+Prints one JSON line on rank 0.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2605_25346_b300 import workloads as wl  # noqa: E402
+
+METRIC = "sound-bound domain-steps/s (1e-5 rel vs FP64 oracle)"
+UNIT = "domain-steps/s"
+L2_BYTES = 126 * 2 ** 20
+FP32_LANES_PER_SM = 128
+SMS = 148
+
+
+def fused_flops_per_domain_step(widths):
+    """Algorithmic FLOPs (2 per multiply-add) of one domain-step of the forward pass.
+
+    Per target layer l: chain levels m = l-1..1 cost n_l*n_m*(3 + n_{m-1}) MACs (intercepts
+    Lambda^+ d, Lambda^- d, Lambda_s b and the product Lambda_s W_m); the concretisation costs
+    n_l*n*(n + 3) MACs (Lambda P, Lambda c, the remainder interval); the dynamics cost
+    n*(n+m)*(n + 3) MACs (P', c', I').
+    """
+    n, m, L = widths[0], widths[-1], len(widths) - 1
+    mac = 0
+    for l in range(1, L + 1):
+        for mm in range(l - 1, 0, -1):
+            mac += widths[l] * widths[mm] * (3 + widths[mm - 1])
+        mac += widths[l] * n * (n + 3)
+    mac += n * (n + m) * (n + 3)
+    return 2 * mac
+
+
+def workload(rank=0):
+    p = wl.quad6_batched()
+    if rank:
+        # weak scaling: every rank bounds its own 4096 sub-boxes (a shifted copy of the grid)
+        p.lo = p.lo + 0.01 * rank
+        p.hi = p.hi + 0.01 * rank
+    return p
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_baseline(prob, target_s=10.0, max_domains=None):
+    """Time the FP64 oracle, as it stands, on a bounded sample of the workload's domains."""
+    from oracle import reach as orc
+    D = prob.D if max_domains is None else min(prob.D, max_domains)
+    sub = prob.subset(np.arange(D))
+    times = []
+    t_end = time.perf_counter() + target_s
+    while True:
+        t0 = time.perf_counter()
+        orc.reach(sub)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() >= t_end or len(times) >= 10:
+            break
+    t = statistics.mean(times)
+    return {"value": D * prob.H / t, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{D} of {prob.D} domains x H={prob.H}, {len(times)} repetitions, mean {t:.3f} s"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    from oracle import reach as orc
+    prob = workload()
+    sample = 512
+    sub = prob.subset(np.arange(sample))
+    for _ in range(args.warmup):
+        orc.reach(sub)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        orc.reach(sub)
+        times.append(time.perf_counter() - t0)
+    t = statistics.mean(times)
+    val = sample * prob.H / t
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "quad6 6-64-64-3, 4^6 sub-boxes, H=10 (oracle step: 512-domain sample)",
+                       "domains": sample, "horizon": prob.H},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+                             "sample": f"{sample} of {prob.D} domains x H={prob.H} per step"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2605_25346_b300 import api
+
+    prob = workload(rank)
+    D, H, n = prob.D, prob.H, prob.n
+    stream = torch.cuda.Stream()
+    r = api.Reach(local, stream=stream).load(prob)
+    dev = f"cuda:{local}"
+    lo = torch.empty(D, H + 1, n, dtype=torch.float64, device=dev)
+    hi = torch.empty_like(lo)
+    hl = torch.empty(H + 1, n, dtype=torch.float64, device=dev)
+    hh = torch.empty_like(hl)
+    st = torch.empty(D, dtype=torch.int32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    P = api._ptr
+
+    def step(hull=True):
+        r._c(r.lib.dr_compute_bounds(r.ctx, P(lo), P(hi), P(hl) if hull else None, P(hh) if hull else None, P(st), 1))
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        l0 = r.launches()
+        with ClockSampler(local) as clk:
+            torch.cuda.synchronize()
+            t_wall = time.perf_counter()
+            for i in range(args.steps):
+                flush.zero_()  # L2 flush between timed steps (outside the events)
+                ev[i][0].record(stream)
+                step()
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            t_wall = time.perf_counter() - t_wall
+        launches = r.launches() - l0
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        # the dominant kernel alone (no hull launch), for the roofline
+        kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            kev[i][0].record(stream)
+            step(hull=False)
+            kev[i][1].record(stream)
+        torch.cuda.synchronize()
+        k_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
+
+    ms = statistics.mean(step_ms)
+    ms_t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    value = world * D * H / (ms * 1e-3)
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    hlo = np.empty((D, H + 1, n))
+    hhi = np.empty_like(hlo)
+    hhl = np.empty((H + 1, n))
+    hhh = np.empty_like(hhl)
+    hst = np.empty(D, dtype=np.uint32)
+    lo0 = np.ascontiguousarray(prob.lo)
+    hi0 = np.ascontiguousarray(prob.hi)
+
+    def e2e_step():
+        r._c(r.lib.dr_set_boxes(r.ctx, D, P(lo0), P(hi0), 0))
+        r._c(r.lib.dr_compute_bounds(r.ctx, P(hlo), P(hhi), P(hhl), P(hhh), P(hst), 0))
+
+    for _ in range(2):
+        e2e_step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    h2d = 2 * D * n * 8
+    d2h = 2 * D * (H + 1) * n * 8 + 2 * (H + 1) * n * 8 + 4 * D
+
+    flops = fused_flops_per_domain_step(prob.widths) * D * H
+    clock = clk.summary()
+    peak_mhz = 2032.0
+    peak = SMS * FP32_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12
+    achieved = flops / (k_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_fused_forward", "kernel_ms": k_ms,
+            "peak_basis": "148 SMs x 128 FP32 lanes x 2 FLOP x 2032 MHz (FMA issue rate at max SM clock)",
+            "algorithmic_flops_per_launch": flops}
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            cpu = oracle_baseline(prob, target_s=10.0)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": "quad6 6-64-64-3, 4^6 = 4096 sub-boxes, H=10, chord slopes",
+                           "domains_per_gpu": D, "horizon": H, "l2": "flushed between timed steps",
+                           "parallelism": f"domains sharded, {world} independent shard(s)"},
+                "e2e": {"value": world * D * H / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": int(launches),
+                "wall_ms_per_step_incl_flush": 1e3 * t_wall / args.steps,
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clock}
+        print(json.dumps(line), flush=True)
+    r.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * diffreach.h -- C ABI of the B300 (sm_103a) reachability library.
+ *
+ * The library bounds the reachable sets of the discrete-time closed loop
+ *     x_{t+1} = A x_t + B pi(x_t) + e,      pi = ReLU MLP with L affine layers,
+ * over a horizon H, for D independent domains (input sub-boxes or branch domains),
+ * with the paper's fixed-shape linear Taylor model (TM) x = c + P zeta + r,
+ * zeta in [-1,1]^n, r in [I_lo, I_hi] (Sec. IV-A), certified through the
+ * controller by shared-slope CROWN back-substitution (Thm. 2, Sec. IV-C) over a
+ * TM input (Thm. 3 and its proof in App. B), propagated stepwise as in Alg. 2
+ * with the closed-loop remark of Sec. IV-E, and concretised with EvalInt
+ * (Alg. 2).  The differentiable objective is the tube-volume proxy
+ * V_d = sum_{t=1..H} sum_i width(box_{t,i}) of Sec. V-A; slopes are refined by
+ * projected gradient ("gradient-based refinement", Sec. VI-A, Table I).
+ *
+ * Conventions for every entry point:
+ *  - The return value is DR_OK (0) or a negative DR_ERR_* code; dr_last_error()
+ *    returns a message for the last failing call on that context.
+ *  - Host inputs are copied during the call; the caller keeps ownership.
+ *    Device pointers (flag on_device != 0) must be device memory of the context's
+ *    device, stay valid until the context's stream has completed the call, and are
+ *    only read (inputs) or written (outputs).
+ *  - All device work is ordered on the context's CUDA stream.  Calls that return
+ *    results into host memory synchronise that stream before returning.
+ *  - Arrays are dense, C order, without padding.  Shapes are given in brackets.
+ *  - There is no CPU fallback: without a usable sm_103a device dr_create fails.
+ */
+#ifndef DIFFREACH_H
+#define DIFFREACH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define DR_OK 0
+#define DR_ERR_ARG (-1)       /* invalid argument (null pointer, negative size, bad enum) */
+#define DR_ERR_SHAPE (-2)     /* shapes inconsistent or beyond the supported limits       */
+#define DR_ERR_STATE (-3)     /* call order: e.g. bounds before controller/dynamics/boxes  */
+#define DR_ERR_OOM (-4)       /* device allocation failed or the memory cap was exceeded   */
+#define DR_ERR_CUDA (-5)      /* a CUDA runtime call failed                                */
+#define DR_ERR_TIMEOUT (-6)   /* a bounded device-side wait expired                        */
+#define DR_ERR_NONFINITE (-7) /* non-finite input values                                   */
+
+/* element types of controller parameters */
+#define DR_F32 0
+#define DR_F64 1
+
+/* slope rules for unstable ReLUs, lower alpha*z, upper alpha*z + max(-alpha*l, (1-alpha)*u) */
+#define DR_SLOPE_ADAPTIVE 0 /* alpha = 1 if u >= -l else 0                          */
+#define DR_SLOPE_CHORD 1    /* alpha = u / (u - l)                                   */
+#define DR_SLOPE_ZERO 2     /* alpha = 0                                             */
+#define DR_SLOPE_USER 3     /* alpha from dr_set_alpha / dr_optimize_slopes          */
+
+/* arithmetic of the back-substitution chain Lambda <- Lambda diag(s) W */
+#define DR_PREC_AUTO 0   /* fused FP32 kernel for narrow controllers, tensor cores otherwise */
+#define DR_PREC_SIMT 1   /* FP32 on CUDA cores                                              */
+#define DR_PREC_TF32X3 2 /* FP32-accurate 3xTF32 split on tcgen05 tensor cores              */
+
+/* per-domain status bits written by dr_compute_bounds */
+#define DR_STATUS_NONFINITE 1u  /* some bound is inf/nan                                     */
+#define DR_STATUS_INFEASIBLE 2u /* a split left l > u: the domain is empty, bounds vacuous   */
+
+typedef struct dr_ctx dr_ctx;
+
+/* One ReLU split of a branch domain: at step t (0-based), hidden layer `layer`
+ * (1-based, 1..L-1) and neuron `neuron` (0-based) the domain only contains states
+ * with sign * z >= 0 (sign = +1 or -1). */
+typedef struct dr_split {
+    int32_t t;
+    int32_t layer;
+    int32_t neuron;
+    int32_t sign;
+} dr_split;
+
+typedef struct dr_options {
+    int32_t slope_mode;    /* DR_SLOPE_*, default DR_SLOPE_CHORD                                */
+    int32_t precision;     /* DR_PREC_*, default DR_PREC_AUTO                                   */
+    double margin_rho;     /* outward margin rho: every FP32 concretisation is widened by
+                              rho * S, S the L1 magnitude of its summed terms; default 2^-22   */
+    int64_t chunk_domains; /* domains per device pass (bounds scratch memory); 0 = automatic    */
+    int64_t mem_cap_bytes; /* cap on library-owned device memory; 0 = no cap                    */
+    int32_t reserved[8];
+} dr_options;
+
+/* Create a context on `device` whose work is ordered on `cuda_stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  Fails with DR_ERR_CUDA if the device is missing
+ * or is not compute capability 10.3.  *out receives the context. */
+int dr_create(dr_ctx** out, int device, void* cuda_stream);
+
+/* Release the context and all device memory it owns (after draining its stream). */
+void dr_destroy(dr_ctx* ctx);
+
+/* Controller pi: L affine layers; widths[0..L] = (n, n_1, ..., n_{L-1}, m).
+ * W[l] points to n_{l+1} x n_l row-major values (layer l+1), b[l] to n_{l+1} values,
+ * both host memory of element type `dtype` (DR_F32 or DR_F64).  The device computes in
+ * FP32 (values are rounded once).  ReLU follows every layer but the last. */
+int dr_load_controller(dr_ctx* ctx, int L, const int32_t* widths, const void* const* W,
+                       const void* const* b, int dtype);
+
+/* Dynamics x' = A x + B u + e: A [n x n], B [n x m], e [n] (NULL = 0), host FP64.
+ * n and m must match the controller's input and output widths. */
+int dr_load_dynamics(dr_ctx* ctx, int n, int m, const double* A, const double* B, const double* e);
+
+/* D initial boxes [lo, hi] (each [D x n], FP64, lo <= hi), host (on_device = 0) or device.
+ * Resets the slopes (alpha), the split list and the multipliers (beta). */
+int dr_set_boxes(dr_ctx* ctx, int64_t D, const double* lo, const double* hi, int on_device);
+
+/* Branch-domain splits in CSR form: domain d owns s[row_ptr[d] .. row_ptr[d+1]), sorted
+ * by (t, layer).  row_ptr [D+1] (row_ptr[0] = 0, non-decreasing), s [nnz], beta [nnz]
+ * multipliers >= 0 (NULL = all 0); host memory.  Every concretisation after a split's own
+ * layer uses the Lagrangian dual min_zeta p^T zeta >= -|p - sum beta_k g_k|_1 - sum beta_k h_k
+ * of the split constraints g_k^T zeta + h_k >= 0. */
+int dr_set_splits(dr_ctx* ctx, const int64_t* row_ptr, const dr_split* s, const float* beta);
+
+/* Horizon H >= 1 (number of controller/dynamics steps). */
+int dr_set_horizon(dr_ctx* ctx, int H);
+
+/* Options (copied).  NULL restores the defaults. */
+int dr_set_options(dr_ctx* ctx, const dr_options* opt);
+
+/* Bounds for all domains and steps (Alg. 2):
+ *   lo, hi          [D x (H+1) x n]  box of every domain and step (step 0 = the input box)
+ *   hull_lo/hull_hi [(H+1) x n]      min/max over domains without DR_STATUS_INFEASIBLE
+ *   status          [D]              DR_STATUS_* bits
+ * Any output may be NULL.  out_on_device selects device (1) or host (0) outputs.
+ * Boxes are FP64, concretised in FP64 from the FP64 TM and pushed outward. */
+int dr_compute_bounds(dr_ctx* ctx, double* lo, double* hi, double* hull_lo, double* hull_hi,
+                      uint32_t* status, int out_on_device);
+
+/* Per-domain tube-volume proxy V_d of the last dr_compute_bounds / dr_optimize_slopes
+ * (Sec. V-A), [D] FP64. */
+int dr_get_objective(dr_ctx* ctx, double* V, int on_device);
+
+/* Projected-gradient refinement: alpha <- clip(alpha - lr_alpha dV/dalpha, 0, 1),
+ * beta <- max(beta - lr_beta dV/dbeta, 0), keeping per domain the best (alpha, beta, V).
+ * If no slopes were set, they start at the CHORD slopes.  V_out [steps+1] (host, may be
+ * NULL) receives sum_d best V_d after each evaluation.  Afterwards the context holds the
+ * best slopes and multipliers and slope mode DR_SLOPE_USER. */
+int dr_optimize_slopes(dr_ctx* ctx, int steps, double lr_alpha, double lr_beta, double* V_out);
+
+/* Reverse-mode gradient of sum_d sum_{t,i} (w_hi * hi - w_lo * lo) at the current slopes
+ * (DR_SLOPE_USER; CHORD slopes if none were set):
+ *   dV_dlo, dV_dhi [D x (H+1) x n] FP64 upstream weights (NULL = -1 and +1 on steps 1..H,
+ *   i.e. the gradient of V); dalpha [D x H x hidden] FP32; dbeta [nnz] FP32.
+ * Pointers are host memory unless on_device != 0. */
+int dr_backward(dr_ctx* ctx, const double* dV_dlo, const double* dV_dhi, float* dalpha, float* dbeta,
+                int on_device);
+
+/* Slopes alpha [D x H x hidden] FP32 (hidden = n_1 + ... + n_{L-1}, layers concatenated);
+ * only unstable neurons read them.  dr_set_alpha switches the slope mode to DR_SLOPE_USER. */
+int dr_get_alpha(dr_ctx* ctx, float* alpha, int on_device);
+int dr_set_alpha(dr_ctx* ctx, const float* alpha, int on_device);
+
+/* Split multipliers beta [nnz] FP32. */
+int dr_get_beta(dr_ctx* ctx, float* beta, int on_device);
+
+/* Number of kernels this context has launched (monotone counter, for accounting). */
+int64_t dr_kernel_launches(const dr_ctx* ctx);
+
+/* Message of the last failing call on ctx (or of the last failing dr_create when ctx is
+ * NULL).  The pointer stays valid until the next call on the same context. */
+const char* dr_last_error(const dr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIFFREACH_H */

@@ -221,8 +221,9 @@ def reach(prob, alpha: Optional[torch.Tensor] = None, beta: Optional[torch.Tenso
                     negm[dom[sg < 0], j[sg < 0]] = True
                     l = torch.where(posm & (l < 0), torch.zeros_like(l), l)
                     u = torch.where(negm & (u > 0), torch.zeros_like(u), u)
-                    bad = (l > u).any(-1)
-                    status = torch.where(bad, status | STATUS_INFEASIBLE, status)
+                # l > u (after clipping, or from a dual certificate) proves the domain empty
+                bad = (l > u).any(-1)
+                status = torch.where(bad, status | STATUS_INFEASIBLE, status)
                 al = alpha[:, t, offs[ell - 1]:offs[ell]] if mode == MODE_USER else None
                 s, d, a_used, unstable, br = relax(l, u, al, mode)
                 if record is not None:
@@ -258,6 +259,7 @@ def reach(prob, alpha: Optional[torch.Tensor] = None, beta: Optional[torch.Tenso
             record.append(pp > 0)
         los.append(c + Ilo - pm.abs().sum(-1) - w[:, None])
         his.append(c + Ihi + pp.abs().sum(-1) + w[:, None])
+        status = torch.where((los[-1] > his[-1]).any(-1), status | STATUS_INFEASIBLE, status)
 
     lo = torch.stack(los, dim=1)
     hi = torch.stack(his, dim=1)

@@ -1,0 +1,167 @@
+"""Python front end of the CUDA library: marshals a ``workloads.Problem`` across the C ABI.
+
+Device memory and streams come from PyTorch; every step of the bound computation runs in
+the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check
+
+_MODE = {0: _lib.DR_SLOPE_ADAPTIVE, 1: _lib.DR_SLOPE_CHORD, 2: _lib.DR_SLOPE_ZERO, 3: _lib.DR_SLOPE_USER}
+
+
+def _ptr(a) -> ctypes.c_void_p:
+    if isinstance(a, torch.Tensor):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Reach:
+    """One library context (one device, one stream) holding a loaded problem."""
+
+    def __init__(self, device: int = 0, stream: Optional[torch.cuda.Stream] = None):
+        self.lib = _lib.load()
+        self.ctx = ctypes.c_void_p()
+        self.stream = stream
+        s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+        code = self.lib.dr_create(ctypes.byref(self.ctx), device, s)
+        if code != _lib.DR_OK:
+            raise _lib.DiffReachError(code, self.lib.dr_last_error(None).decode())
+        self.device = device
+        self.prob = None
+
+    def close(self):
+        if self.ctx:
+            self.lib.dr_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _c(self, code):
+        return check(self.ctx, code)
+
+    # ---- problem upload -------------------------------------------------------------------
+    def set_options(self, mode: Optional[int] = None, precision: int = _lib.DR_PREC_AUTO, rho: Optional[float] = None,
+                    chunk: int = 0, mem_cap: int = 0):
+        o = _lib.dr_options()
+        o.slope_mode = _MODE[mode] if mode is not None else _lib.DR_SLOPE_CHORD
+        o.precision = precision
+        o.margin_rho = 2.0 ** -22 if rho is None else rho
+        o.chunk_domains = chunk
+        o.mem_cap_bytes = mem_cap
+        self._c(self.lib.dr_set_options(self.ctx, ctypes.byref(o)))
+
+    def load(self, prob, mode: Optional[int] = None, rho: Optional[float] = None, precision: int = _lib.DR_PREC_AUTO,
+             boxes_on_device: bool = False):
+        self.prob = prob
+        widths = np.asarray(prob.widths, dtype=np.int32)
+        self._keep = [np.ascontiguousarray(w, dtype=np.float64) for w in prob.W] + \
+                     [np.ascontiguousarray(b, dtype=np.float64) for b in prob.b]
+        L = prob.L
+        Wp = (ctypes.c_void_p * L)(*[x.ctypes.data for x in self._keep[:L]])
+        bp = (ctypes.c_void_p * L)(*[x.ctypes.data for x in self._keep[L:]])
+        self._c(self.lib.dr_set_horizon(self.ctx, prob.H))
+        self._c(self.lib.dr_load_controller(self.ctx, L, _ptr(widths), Wp, bp, _lib.DR_F64))
+        A = np.ascontiguousarray(prob.A, dtype=np.float64)
+        B = np.ascontiguousarray(prob.B, dtype=np.float64)
+        e = np.ascontiguousarray(prob.e, dtype=np.float64)
+        self._c(self.lib.dr_load_dynamics(self.ctx, prob.n, prob.m, _ptr(A), _ptr(B), _ptr(e)))
+        m0 = prob.mode if mode is None else mode
+        m0 = 1 if m0 == 3 else m0  # user slopes are installed with set_alpha after the boxes
+        self.set_options(m0, precision, rho)
+        if boxes_on_device:
+            lo = torch.as_tensor(prob.lo, dtype=torch.float64, device=f"cuda:{self.device}").contiguous()
+            hi = torch.as_tensor(prob.hi, dtype=torch.float64, device=f"cuda:{self.device}").contiguous()
+            self._c(self.lib.dr_set_boxes(self.ctx, prob.D, _ptr(lo), _ptr(hi), 1))
+            torch.cuda.synchronize()
+        else:
+            lo = np.ascontiguousarray(prob.lo, dtype=np.float64)
+            hi = np.ascontiguousarray(prob.hi, dtype=np.float64)
+            self._c(self.lib.dr_set_boxes(self.ctx, prob.D, _ptr(lo), _ptr(hi), 0))
+        if prob.splits is not None:
+            self.set_splits(prob.splits, prob.beta)
+        # dr_set_boxes resets the slope mode to the default; restore the requested one
+        self.set_options(m0, precision, rho)
+        return self
+
+    def set_splits(self, splits, beta=None):
+        nnz = splits.nnz
+        rec = np.zeros((max(nnz, 1), 4), dtype=np.int32)
+        rec[:nnz, 0] = splits.t
+        rec[:nnz, 1] = splits.layer
+        rec[:nnz, 2] = splits.neuron
+        rec[:nnz, 3] = splits.sign
+        rp = np.ascontiguousarray(splits.row_ptr, dtype=np.int64)
+        bt = None if beta is None else np.ascontiguousarray(beta, dtype=np.float32)
+        self._c(self.lib.dr_set_splits(self.ctx, _ptr(rp), _ptr(rec), None if bt is None else _ptr(bt)))
+
+    # ---- computation ---------------------------------------------------------------------
+    def bounds(self, on_device: bool = True, hull: bool = True):
+        """Boxes [D, H+1, n], hull [H+1, n] x2 and status [D] (device tensors, or numpy on host)."""
+        p = self.prob
+        D, H, n = p.D, p.H, p.n
+        if on_device:
+            dev = f"cuda:{self.device}"
+            lo = torch.empty(D, H + 1, n, dtype=torch.float64, device=dev)
+            hi = torch.empty_like(lo)
+            hl = torch.empty(H + 1, n, dtype=torch.float64, device=dev)
+            hh = torch.empty_like(hl)
+            st = torch.empty(D, dtype=torch.int32, device=dev)
+        else:
+            lo = np.empty((D, H + 1, n))
+            hi = np.empty_like(lo)
+            hl = np.empty((H + 1, n))
+            hh = np.empty_like(hl)
+            st = np.empty(D, dtype=np.uint32)
+        self._c(self.lib.dr_compute_bounds(self.ctx, _ptr(lo), _ptr(hi), _ptr(hl) if hull else None,
+                                           _ptr(hh) if hull else None, _ptr(st), 1 if on_device else 0))
+        return dict(lo=lo, hi=hi, hull_lo=hl, hull_hi=hh, status=st)
+
+    def objective(self) -> np.ndarray:
+        V = np.empty(self.prob.D)
+        self._c(self.lib.dr_get_objective(self.ctx, _ptr(V), 0))
+        return V
+
+    def get_alpha(self) -> np.ndarray:
+        p = self.prob
+        a = np.empty((p.D, p.H, p.hidden), dtype=np.float32)
+        self._c(self.lib.dr_get_alpha(self.ctx, _ptr(a), 0))
+        return a
+
+    def set_alpha(self, alpha):
+        a = np.ascontiguousarray(alpha, dtype=np.float32)
+        self._c(self.lib.dr_set_alpha(self.ctx, _ptr(a), 0))
+
+    def get_beta(self) -> np.ndarray:
+        p = self.prob
+        nnz = p.splits.nnz if p.splits is not None else 0
+        b = np.empty(max(nnz, 1), dtype=np.float32)
+        self._c(self.lib.dr_get_beta(self.ctx, _ptr(b), 0))
+        return b[:nnz]
+
+    def backward(self, on_device: bool = False):
+        p = self.prob
+        nnz = p.splits.nnz if p.splits is not None else 0
+        ga = np.empty((p.D, p.H, p.hidden), dtype=np.float32)
+        gb = np.empty(max(nnz, 1), dtype=np.float32)
+        self._c(self.lib.dr_backward(self.ctx, None, None, _ptr(ga), _ptr(gb), 0))
+        return ga, gb[:nnz]
+
+    def optimize(self, steps: int, lr_alpha: float, lr_beta: float = 0.0):
+        hist = np.empty(steps + 1)
+        self._c(self.lib.dr_optimize_slopes(self.ctx, steps, lr_alpha, lr_beta, _ptr(hist)))
+        return hist
+
+    def launches(self) -> int:
+        return int(self.lib.dr_kernel_launches(self.ctx))

@@ -1,0 +1,646 @@
+// Host side of the C ABI declared in include/diffreach.h: context, uploads, launch logic.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/diffreach.h"
+#include "common.cuh"
+#include "fused_fwd.cuh"
+
+
+struct dr_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int64_t launches = 0;
+    size_t owned = 0;
+
+    bool has_ctrl = false;
+    NetDesc net{};
+    float* dW = nullptr;
+    float* db = nullptr;
+
+    bool has_dyn = false;
+    double* dA = nullptr;
+    double* dB = nullptr;
+    double* de = nullptr;
+
+    int64_t D = 0;
+    double* dlo0 = nullptr;
+    double* dhi0 = nullptr;
+
+    int64_t nnz = 0;
+    int64_t* dsp_row = nullptr;
+    SplitRec* dsp = nullptr;
+    float* dbeta = nullptr;
+
+    int H = 0;
+    dr_options opt{};
+
+    float* dalpha = nullptr;  // [D][H][hidden]
+    bool alpha_set = false;
+
+    // library-owned outputs / scratch
+    double* dout_lo = nullptr;
+    double* dout_hi = nullptr;
+    double* dV = nullptr;
+    uint32_t* dstatus = nullptr;
+    double* dhull = nullptr;
+    double* dtape = nullptr;
+    size_t tape_bytes = 0;
+    size_t out_bytes = 0;
+};
+
+static thread_local std::string g_create_err;
+
+static int fail(dr_ctx* c, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_create_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                                       \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return fail(ctx, DR_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+static void dev_free(dr_ctx* c, void*& p, size_t bytes) {
+    if (p) {
+        cudaFree(p);
+        c->owned -= std::min(c->owned, bytes);
+        p = nullptr;
+    }
+}
+
+template <typename T>
+static int dev_alloc(dr_ctx* c, T*& p, size_t count) {
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    if (c->opt.mem_cap_bytes > 0 && c->owned + bytes > (size_t)c->opt.mem_cap_bytes)
+        return fail(c, DR_ERR_OOM, "allocation of %zu bytes exceeds the memory cap (%lld bytes, %zu owned)", bytes,
+                    (long long)c->opt.mem_cap_bytes, c->owned);
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, DR_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    c->owned += bytes;
+    p = reinterpret_cast<T*>(q);
+    return DR_OK;
+}
+
+#define TRY(x)                 \
+    do {                       \
+        int r_ = (x);          \
+        if (r_ != DR_OK) return r_; \
+    } while (0)
+
+static dr_options default_options() {
+    dr_options o;
+    memset(&o, 0, sizeof(o));
+    o.slope_mode = DR_SLOPE_CHORD;
+    o.precision = DR_PREC_AUTO;
+    o.margin_rho = std::ldexp(1.0, -22);
+    o.chunk_domains = 0;
+    o.mem_cap_bytes = 0;
+    return o;
+}
+
+// ------------------------------------------------------------------------------------------------
+// fused-path layout
+// ------------------------------------------------------------------------------------------------
+
+static FusedLayout fused_layout(const NetDesc& N) {
+    FusedLayout Y;
+    memset(&Y, 0, sizeof(Y));
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = (off + 15) & ~size_t(15);
+        const size_t r = off;
+        off += bytes;
+        return (int)r;
+    };
+    const int n = N.n, m = N.m;
+    for (int l = 0; l < N.L; ++l) Y.Ws[l] = take(sizeof(float) * N.w[l + 1] * odd_ld(N.w[l]));
+    int nb = 0;
+    for (int l = 0; l < N.L; ++l) nb += N.w[l + 1];
+    Y.bs = take(sizeof(float) * nb);
+    Y.A = take(sizeof(double) * n * n);
+    Y.B = take(sizeof(double) * n * m);
+    Y.e = take(sizeof(double) * n);
+    Y.c = take(sizeof(double) * n);
+    Y.P = take(sizeof(double) * n * n);
+    Y.Ilo = take(sizeof(double) * n);
+    Y.Ihi = take(sizeof(double) * n);
+    Y.v = take(sizeof(double) * n);
+    Y.w = take(sizeof(double) * 2);
+    Y.cn = take(sizeof(double) * n);
+    Y.Pn = take(sizeof(double) * std::max(n * n, 64));
+    Y.Ilon = take(sizeof(double) * n);
+    Y.Ihin = take(sizeof(double) * n);
+    Y.cf = take(sizeof(float) * n);
+    Y.Pf = take(sizeof(float) * n * n);
+    Y.Ilof = take(sizeof(float) * n);
+    Y.Ihif = take(sizeof(float) * n);
+    Y.vf = take(sizeof(float) * (n + 1));
+    const int hid = std::max(N.hidden, 1);
+    Y.hl = take(sizeof(float) * hid);
+    Y.hu = take(sizeof(float) * hid);
+    Y.hs = take(sizeof(float) * hid);
+    Y.hd = take(sizeof(float) * hid);
+    Y.klo = take(sizeof(float) * N.maxw);
+    Y.khi = take(sizeof(float) * N.maxw);
+    // per-domain chain buffers: target l, after level m the matrix is n_l x odd_ld(n_{m-1})
+    size_t lam = 1;
+    for (int l = 2; l <= N.L; ++l)
+        for (int k = 0; k <= l - 2; ++k) lam = std::max(lam, (size_t)N.w[l] * odd_ld(N.w[k]));
+    Y.lam0 = take(sizeof(float) * lam);
+    Y.lam1 = take(sizeof(float) * lam);
+    Y.G = take(sizeof(float) * N.maxw * odd_ld(n));
+    Y.a = take(sizeof(float) * N.maxw);
+    Y.Rlo = take(sizeof(float) * N.maxw);
+    Y.Rhi = take(sizeof(float) * N.maxw);
+    Y.S = take(sizeof(float) * N.maxw);
+    Y.cu = take(sizeof(float) * m);
+    Y.Iulo = take(sizeof(float) * m);
+    Y.Iuhi = take(sizeof(float) * m);
+    Y.misc = take(sizeof(int) * 4);
+    Y.total = (int)((off + 15) & ~size_t(15));
+    return Y;
+}
+
+static const int kMaxSmem = 227 * 1024;
+
+static bool fused_fits(const NetDesc& N) { return fused_layout(N).total <= kMaxSmem; }
+
+static int fused_threads(const NetDesc& N) { return N.maxw <= 64 ? 128 : 256; }
+
+// ------------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------------
+
+extern "C" {
+
+int dr_create(dr_ctx** out, int device, void* cuda_stream) {
+    if (!out) return fail(nullptr, DR_ERR_ARG, "dr_create: out is NULL");
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || count <= device || device < 0)
+        return fail(nullptr, DR_ERR_CUDA, "dr_create: no CUDA device %d (%s)", device,
+                    e == cudaSuccess ? "not present" : cudaGetErrorString(e));
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) return fail(nullptr, DR_ERR_CUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(e));
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(nullptr, DR_ERR_CUDA, "dr_create: device %d is sm_%d%d, this library is built for sm_103a", device,
+                    prop.major, prop.minor);
+    dr_ctx* c = new dr_ctx();
+    c->device = device;
+    c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    c->opt = default_options();
+    *out = c;
+    return DR_OK;
+}
+
+static void free_outputs(dr_ctx* c) {
+    const size_t ob = c->out_bytes;
+    dev_free(c, (void*&)c->dout_lo, ob);
+    dev_free(c, (void*&)c->dout_hi, ob);
+    dev_free(c, (void*&)c->dV, sizeof(double) * c->D);
+    dev_free(c, (void*&)c->dstatus, sizeof(uint32_t) * c->D);
+    dev_free(c, (void*&)c->dhull, sizeof(double) * 2 * (c->H + 1) * std::max(c->net.n, 1));
+    dev_free(c, (void*&)c->dtape, c->tape_bytes);
+    c->out_bytes = 0;
+    c->tape_bytes = 0;
+}
+
+void dr_destroy(dr_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    free_outputs(c);
+    cudaFree(c->dW);
+    cudaFree(c->db);
+    cudaFree(c->dA);
+    cudaFree(c->dB);
+    cudaFree(c->de);
+    cudaFree(c->dlo0);
+    cudaFree(c->dhi0);
+    cudaFree(c->dsp_row);
+    cudaFree(c->dsp);
+    cudaFree(c->dbeta);
+    cudaFree(c->dalpha);
+    delete c;
+}
+
+const char* dr_last_error(const dr_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+int64_t dr_kernel_launches(const dr_ctx* c) { return c ? c->launches : 0; }
+
+int dr_set_options(dr_ctx* c, const dr_options* o) {
+    if (!c) return DR_ERR_ARG;
+    dr_options n = o ? *o : default_options();
+    if (n.slope_mode < 0 || n.slope_mode > 3) return fail(c, DR_ERR_ARG, "slope_mode %d out of range", n.slope_mode);
+    if (n.precision < 0 || n.precision > 2) return fail(c, DR_ERR_ARG, "precision %d out of range", n.precision);
+    if (!(n.margin_rho >= 0.0) || n.margin_rho > 1e-2) return fail(c, DR_ERR_ARG, "margin_rho %g out of range", n.margin_rho);
+    if (n.chunk_domains < 0 || n.mem_cap_bytes < 0) return fail(c, DR_ERR_ARG, "negative chunk or memory cap");
+    if (n.slope_mode == DR_SLOPE_USER && !c->alpha_set && c->D > 0)
+        return fail(c, DR_ERR_STATE, "DR_SLOPE_USER requires dr_set_alpha first");
+    c->opt = n;
+    return DR_OK;
+}
+
+int dr_load_controller(dr_ctx* c, int L, const int32_t* widths, const void* const* W, const void* const* b, int dtype) {
+    if (!c || !widths || !W || !b) return fail(c, DR_ERR_ARG, "dr_load_controller: NULL argument");
+    if (L < 1 || L > DR_MAXL) return fail(c, DR_ERR_SHAPE, "L = %d outside 1..%d", L, DR_MAXL);
+    if (dtype != DR_F32 && dtype != DR_F64) return fail(c, DR_ERR_ARG, "dtype %d", dtype);
+    if (c->has_dyn && (widths[0] != c->net.n || widths[L] != c->net.m))
+        return fail(c, DR_ERR_SHAPE, "controller widths (%d..%d) do not match dynamics (n=%d, m=%d)", widths[0],
+                    widths[L], c->net.n, c->net.m);
+    NetDesc N{};
+    N.L = L;
+    int64_t nw = 0, nb = 0;
+    N.maxw = 0;
+    for (int l = 0; l <= L; ++l) {
+        if (widths[l] < 1 || widths[l] > 4096) return fail(c, DR_ERR_SHAPE, "width[%d] = %d", l, widths[l]);
+        N.w[l] = widths[l];
+        if (l >= 1) N.maxw = std::max(N.maxw, widths[l]);
+    }
+    N.hidden = 0;
+    for (int l = 1; l < L; ++l) {
+        N.hoff[l] = N.hidden;
+        N.hidden += widths[l];
+    }
+    N.hoff[L] = N.hidden;
+    for (int l = 0; l < L; ++l) {
+        N.Woff[l] = nw;
+        N.boff[l] = nb;
+        nw += (int64_t)widths[l + 1] * widths[l];
+        nb += widths[l + 1];
+    }
+    N.n = widths[0];
+    N.m = widths[L];
+    N.H = c->H;
+    std::vector<float> hw(nw), hb(nb);
+    for (int l = 0; l < L; ++l) {
+        const int64_t cnt = (int64_t)widths[l + 1] * widths[l];
+        for (int64_t i = 0; i < cnt; ++i) {
+            const double x = dtype == DR_F64 ? ((const double*)W[l])[i] : ((const float*)W[l])[i];
+            if (!std::isfinite(x)) return fail(c, DR_ERR_NONFINITE, "non-finite weight in layer %d", l + 1);
+            hw[N.Woff[l] + i] = (float)x;
+        }
+        for (int i = 0; i < widths[l + 1]; ++i) {
+            const double x = dtype == DR_F64 ? ((const double*)b[l])[i] : ((const float*)b[l])[i];
+            if (!std::isfinite(x)) return fail(c, DR_ERR_NONFINITE, "non-finite bias in layer %d", l + 1);
+            hb[N.boff[l] + i] = (float)x;
+        }
+    }
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    dev_free(c, (void*&)c->dW, 0);
+    dev_free(c, (void*&)c->db, 0);
+    TRY(dev_alloc(c, c->dW, nw));
+    TRY(dev_alloc(c, c->db, nb));
+    CUDA_TRY(c, cudaMemcpyAsync(c->dW, hw.data(), nw * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->db, hb.data(), nb * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const int oldH = c->H;
+    c->net = N;
+    c->net.H = oldH;
+    c->has_ctrl = true;
+    if (c->dalpha) {
+        dev_free(c, (void*&)c->dalpha, 0);
+        c->alpha_set = false;
+    }
+    return DR_OK;
+}
+
+int dr_load_dynamics(dr_ctx* c, int n, int m, const double* A, const double* B, const double* e) {
+    if (!c || !A || !B) return fail(c, DR_ERR_ARG, "dr_load_dynamics: NULL argument");
+    if (n < 1 || m < 1 || n > 64 || m > 64) return fail(c, DR_ERR_SHAPE, "n = %d, m = %d (supported 1..64)", n, m);
+    if (c->has_ctrl && (c->net.n != n || c->net.m != m))
+        return fail(c, DR_ERR_SHAPE, "dynamics (n=%d, m=%d) do not match controller (n=%d, m=%d)", n, m, c->net.n, c->net.m);
+    for (int i = 0; i < n * n; ++i)
+        if (!std::isfinite(A[i])) return fail(c, DR_ERR_NONFINITE, "non-finite A");
+    for (int i = 0; i < n * m; ++i)
+        if (!std::isfinite(B[i])) return fail(c, DR_ERR_NONFINITE, "non-finite B");
+    std::vector<double> he(n, 0.0);
+    if (e)
+        for (int i = 0; i < n; ++i) {
+            if (!std::isfinite(e[i])) return fail(c, DR_ERR_NONFINITE, "non-finite e");
+            he[i] = e[i];
+        }
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    dev_free(c, (void*&)c->dA, 0);
+    dev_free(c, (void*&)c->dB, 0);
+    dev_free(c, (void*&)c->de, 0);
+    TRY(dev_alloc(c, c->dA, (size_t)n * n));
+    TRY(dev_alloc(c, c->dB, (size_t)n * m));
+    TRY(dev_alloc(c, c->de, (size_t)n));
+    CUDA_TRY(c, cudaMemcpyAsync(c->dA, A, sizeof(double) * n * n, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->dB, B, sizeof(double) * n * m, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->de, he.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (!c->has_ctrl) {
+        c->net.n = n;
+        c->net.m = m;
+    }
+    c->has_dyn = true;
+    return DR_OK;
+}
+
+static void clear_domain_state(dr_ctx* c) {
+    free_outputs(c);
+    dev_free(c, (void*&)c->dsp_row, 0);
+    dev_free(c, (void*&)c->dsp, 0);
+    dev_free(c, (void*&)c->dbeta, 0);
+    dev_free(c, (void*&)c->dalpha, 0);
+    c->nnz = 0;
+    c->alpha_set = false;
+    if (c->opt.slope_mode == DR_SLOPE_USER) c->opt.slope_mode = DR_SLOPE_CHORD;
+}
+
+int dr_set_boxes(dr_ctx* c, int64_t D, const double* lo, const double* hi, int on_device) {
+    if (!c) return DR_ERR_ARG;
+    if (D < 0) return fail(c, DR_ERR_ARG, "D = %lld", (long long)D);
+    if (D > 0 && (!lo || !hi)) return fail(c, DR_ERR_ARG, "dr_set_boxes: NULL lo/hi");
+    if (!c->has_ctrl && !c->has_dyn) return fail(c, DR_ERR_STATE, "load the controller or dynamics before the boxes");
+    const int n = c->net.n;
+    if (!on_device)
+        for (int64_t i = 0; i < D * n; ++i) {
+            if (!std::isfinite(lo[i]) || !std::isfinite(hi[i])) return fail(c, DR_ERR_NONFINITE, "non-finite box");
+            if (lo[i] > hi[i]) return fail(c, DR_ERR_ARG, "box %lld has lo > hi", (long long)(i / n));
+        }
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    clear_domain_state(c);
+    dev_free(c, (void*&)c->dlo0, 0);
+    dev_free(c, (void*&)c->dhi0, 0);
+    c->D = D;
+    TRY(dev_alloc(c, c->dlo0, (size_t)D * n));
+    TRY(dev_alloc(c, c->dhi0, (size_t)D * n));
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (D > 0) {
+        CUDA_TRY(c, cudaMemcpyAsync(c->dlo0, lo, sizeof(double) * D * n, k, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(c->dhi0, hi, sizeof(double) * D * n, k, c->stream));
+    }
+    if (!on_device) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return DR_OK;
+}
+
+int dr_set_splits(dr_ctx* c, const int64_t* row_ptr, const dr_split* s, const float* beta) {
+    if (!c || !row_ptr) return fail(c, DR_ERR_ARG, "dr_set_splits: NULL row_ptr");
+    if (!c->has_ctrl) return fail(c, DR_ERR_STATE, "load the controller before the splits");
+    const int64_t D = c->D;
+    if (row_ptr[0] != 0) return fail(c, DR_ERR_ARG, "row_ptr[0] must be 0");
+    for (int64_t d = 0; d < D; ++d)
+        if (row_ptr[d + 1] < row_ptr[d]) return fail(c, DR_ERR_ARG, "row_ptr decreases at %lld", (long long)d);
+    const int64_t nnz = row_ptr[D];
+    if (nnz > 0 && !s) return fail(c, DR_ERR_ARG, "NULL split array with nnz = %lld", (long long)nnz);
+    if (nnz > (int64_t)0x7fffffff) return fail(c, DR_ERR_SHAPE, "too many splits");
+    const int L = c->net.L;
+    for (int64_t d = 0; d < D; ++d) {
+        for (int64_t k = row_ptr[d]; k < row_ptr[d + 1]; ++k) {
+            const dr_split& r = s[k];
+            if (r.layer < 1 || r.layer > L - 1) return fail(c, DR_ERR_ARG, "split %lld: layer %d not hidden", (long long)k, r.layer);
+            if (r.neuron < 0 || r.neuron >= c->net.w[r.layer])
+                return fail(c, DR_ERR_ARG, "split %lld: neuron %d out of range", (long long)k, r.neuron);
+            if (r.t < 0) return fail(c, DR_ERR_ARG, "split %lld: t = %d", (long long)k, r.t);
+            if (r.sign != 1 && r.sign != -1) return fail(c, DR_ERR_ARG, "split %lld: sign %d", (long long)k, r.sign);
+            if (k > row_ptr[d]) {
+                const dr_split& q = s[k - 1];
+                if (q.t > r.t || (q.t == r.t && q.layer > r.layer))
+                    return fail(c, DR_ERR_ARG, "splits of domain %lld not sorted by (t, layer)", (long long)d);
+            }
+            if (beta && !(beta[k] >= 0.f && std::isfinite(beta[k])))
+                return fail(c, DR_ERR_ARG, "beta[%lld] must be finite and >= 0", (long long)k);
+        }
+    }
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    dev_free(c, (void*&)c->dsp_row, 0);
+    dev_free(c, (void*&)c->dsp, 0);
+    dev_free(c, (void*&)c->dbeta, 0);
+    TRY(dev_alloc(c, c->dsp_row, (size_t)D + 1));
+    TRY(dev_alloc(c, c->dsp, (size_t)nnz));
+    TRY(dev_alloc(c, c->dbeta, (size_t)nnz));
+    CUDA_TRY(c, cudaMemcpyAsync(c->dsp_row, row_ptr, sizeof(int64_t) * (D + 1), cudaMemcpyHostToDevice, c->stream));
+    if (nnz) {
+        static_assert(sizeof(dr_split) == sizeof(SplitRec), "split layout");
+        CUDA_TRY(c, cudaMemcpyAsync(c->dsp, s, sizeof(SplitRec) * nnz, cudaMemcpyHostToDevice, c->stream));
+        if (beta) CUDA_TRY(c, cudaMemcpyAsync(c->dbeta, beta, sizeof(float) * nnz, cudaMemcpyHostToDevice, c->stream));
+        else CUDA_TRY(c, cudaMemsetAsync(c->dbeta, 0, sizeof(float) * nnz, c->stream));
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->nnz = nnz;
+    return DR_OK;
+}
+
+int dr_set_horizon(dr_ctx* c, int H) {
+    if (!c) return DR_ERR_ARG;
+    if (H < 1 || H > 100000) return fail(c, DR_ERR_ARG, "H = %d", H);
+    if (H != c->H) {
+        free_outputs(c);
+        dev_free(c, (void*&)c->dalpha, 0);
+        c->alpha_set = false;
+        if (c->opt.slope_mode == DR_SLOPE_USER) c->opt.slope_mode = DR_SLOPE_CHORD;
+    }
+    c->H = H;
+    c->net.H = H;
+    return DR_OK;
+}
+
+static int check_ready(dr_ctx* c) {
+    if (!c->has_ctrl) return fail(c, DR_ERR_STATE, "controller not loaded");
+    if (!c->has_dyn) return fail(c, DR_ERR_STATE, "dynamics not loaded");
+    if (c->H < 1) return fail(c, DR_ERR_STATE, "horizon not set");
+    if (c->net.n != c->net.w[0] || c->net.m != c->net.w[c->net.L]) return fail(c, DR_ERR_SHAPE, "controller/dynamics mismatch");
+    return DR_OK;
+}
+
+static int ensure_outputs(dr_ctx* c) {
+    const int n = c->net.n;
+    const size_t ob = sizeof(double) * (size_t)c->D * (c->H + 1) * n;
+    if (c->dout_lo && c->out_bytes == ob) return DR_OK;
+    free_outputs(c);
+    TRY(dev_alloc(c, c->dout_lo, ob / sizeof(double)));
+    TRY(dev_alloc(c, c->dout_hi, ob / sizeof(double)));
+    c->out_bytes = ob;
+    TRY(dev_alloc(c, c->dV, (size_t)c->D));
+    TRY(dev_alloc(c, c->dstatus, (size_t)c->D));
+    TRY(dev_alloc(c, c->dhull, 2 * (size_t)(c->H + 1) * n));
+    return DR_OK;
+}
+
+static int tape_stride(const NetDesc& N) { return N.n * N.n + 4 * N.n + 2; }
+
+static int ensure_tape(dr_ctx* c) {
+    const size_t tb = sizeof(double) * (size_t)c->D * c->H * tape_stride(c->net);
+    if (c->dtape && c->tape_bytes == tb) return DR_OK;
+    dev_free(c, (void*&)c->dtape, c->tape_bytes);
+    TRY(dev_alloc(c, c->dtape, tb / sizeof(double)));
+    c->tape_bytes = tb;
+    return DR_OK;
+}
+
+// Forward pass over all domains into the library-owned buffers (optionally recording the tape
+// and the slopes in effect).
+static int run_forward(dr_ctx* c, int mode, float* alpha_used, bool tape) {
+    NetDesc N = c->net;
+    N.H = c->H;
+    if (c->D == 0) return DR_OK;
+    if (!fused_fits(N) || c->opt.precision == DR_PREC_TF32X3)
+        return fail(c, DR_ERR_SHAPE, "controller too wide for the fused kernel (%d bytes of shared memory)",
+                    fused_layout(N).total);
+    if (mode == DR_SLOPE_USER && !c->dalpha) return fail(c, DR_ERR_STATE, "no slopes set");
+    if (tape) TRY(ensure_tape(c));
+    FusedArgs a;
+    memset(&a, 0, sizeof(a));
+    a.net = N;
+    a.lay = fused_layout(N);
+    a.W = c->dW;
+    a.b = c->db;
+    a.A = c->dA;
+    a.B = c->dB;
+    a.e = c->de;
+    a.lo0 = c->dlo0;
+    a.hi0 = c->dhi0;
+    a.sp_row = c->nnz ? c->dsp_row : nullptr;
+    a.sp = c->dsp;
+    a.beta = c->dbeta;
+    a.alpha = c->dalpha;
+    a.mode = mode;
+    a.rho = (float)c->opt.margin_rho;
+    a.lo = c->dout_lo;
+    a.hi = c->dout_hi;
+    a.V = c->dV;
+    a.status = c->dstatus;
+    a.alpha_used = alpha_used;
+    a.tape = tape ? c->dtape : nullptr;
+    a.tape_stride = tape_stride(N);
+    const int nt = fused_threads(N);
+    const int smem = a.lay.total;
+    const int64_t chunk = 1 << 20;
+    for (int64_t d0 = 0; d0 < c->D; d0 += chunk) {
+        a.d0 = d0;
+        const int64_t nd = std::min(chunk, c->D - d0);
+        if (nt == 128) {
+            CUDA_TRY(c, cudaFuncSetAttribute(k_fused_forward<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            k_fused_forward<128><<<(unsigned)nd, 128, smem, c->stream>>>(a);
+        } else {
+            CUDA_TRY(c, cudaFuncSetAttribute(k_fused_forward<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            k_fused_forward<256><<<(unsigned)nd, 256, smem, c->stream>>>(a);
+        }
+        CUDA_TRY(c, cudaGetLastError());
+        c->launches++;
+    }
+    return DR_OK;
+}
+
+int dr_compute_bounds(dr_ctx* c, double* lo, double* hi, double* hull_lo, double* hull_hi, uint32_t* status,
+                      int out_on_device) {
+    if (!c) return DR_ERR_ARG;
+    TRY(check_ready(c));
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    TRY(ensure_outputs(c));
+    if (c->opt.slope_mode == DR_SLOPE_USER && !c->alpha_set) return fail(c, DR_ERR_STATE, "DR_SLOPE_USER without slopes");
+    TRY(run_forward(c, c->opt.slope_mode, nullptr, false));
+    const int n = c->net.n, H = c->H;
+    const int TN = (H + 1) * n;
+    if (c->D > 0 && (hull_lo || hull_hi)) {
+        k_hull<<<TN, 256, 0, c->stream>>>(c->dout_lo, c->dout_hi, c->dstatus, c->D, TN, c->dhull, c->dhull + TN);
+        CUDA_TRY(c, cudaGetLastError());
+        c->launches++;
+    }
+    const size_t ob = sizeof(double) * (size_t)c->D * TN;
+    const cudaMemcpyKind k = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (c->D > 0) {
+        if (lo) CUDA_TRY(c, cudaMemcpyAsync(lo, c->dout_lo, ob, k, c->stream));
+        if (hi) CUDA_TRY(c, cudaMemcpyAsync(hi, c->dout_hi, ob, k, c->stream));
+        if (status) CUDA_TRY(c, cudaMemcpyAsync(status, c->dstatus, sizeof(uint32_t) * c->D, k, c->stream));
+        if (hull_lo) CUDA_TRY(c, cudaMemcpyAsync(hull_lo, c->dhull, sizeof(double) * TN, k, c->stream));
+        if (hull_hi) CUDA_TRY(c, cudaMemcpyAsync(hull_hi, c->dhull + TN, sizeof(double) * TN, k, c->stream));
+    }
+    if (!out_on_device) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return DR_OK;
+}
+
+int dr_get_objective(dr_ctx* c, double* V, int on_device) {
+    if (!c || !V) return fail(c, DR_ERR_ARG, "dr_get_objective: NULL");
+    if (!c->dV) return fail(c, DR_ERR_STATE, "no bounds computed yet");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    CUDA_TRY(c, cudaMemcpyAsync(V, c->dV, sizeof(double) * c->D, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                c->stream));
+    if (!on_device) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return DR_OK;
+}
+
+static int ensure_alpha(dr_ctx* c) {
+    if (c->dalpha) return DR_OK;
+    return dev_alloc(c, c->dalpha, (size_t)c->D * c->H * std::max(c->net.hidden, 1));
+}
+
+int dr_get_alpha(dr_ctx* c, float* alpha, int on_device) {
+    if (!c || !alpha) return fail(c, DR_ERR_ARG, "dr_get_alpha: NULL");
+    TRY(check_ready(c));
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    const size_t cnt = (size_t)c->D * c->H * c->net.hidden;
+    if (!c->alpha_set) {
+        // the slopes in effect for the current mode
+        TRY(ensure_outputs(c));
+        TRY(ensure_alpha(c));
+        TRY(run_forward(c, c->opt.slope_mode, c->dalpha, false));
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(alpha, c->dalpha, sizeof(float) * cnt, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return DR_OK;
+}
+
+int dr_set_alpha(dr_ctx* c, const float* alpha, int on_device) {
+    if (!c || !alpha) return fail(c, DR_ERR_ARG, "dr_set_alpha: NULL");
+    TRY(check_ready(c));
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    TRY(ensure_alpha(c));
+    const size_t cnt = (size_t)c->D * c->H * c->net.hidden;
+    if (!on_device)
+        for (size_t i = 0; i < cnt; ++i)
+            if (!(alpha[i] >= 0.f && alpha[i] <= 1.f)) return fail(c, DR_ERR_ARG, "alpha[%zu] = %g outside [0, 1]", i, alpha[i]);
+    CUDA_TRY(c, cudaMemcpyAsync(c->dalpha, alpha, sizeof(float) * cnt, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->alpha_set = true;
+    c->opt.slope_mode = DR_SLOPE_USER;
+    return DR_OK;
+}
+
+int dr_get_beta(dr_ctx* c, float* beta, int on_device) {
+    if (!c || (!beta && c->nnz)) return fail(c, DR_ERR_ARG, "dr_get_beta: NULL");
+    if (!c->nnz) return DR_OK;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    CUDA_TRY(c, cudaMemcpyAsync(beta, c->dbeta, sizeof(float) * c->nnz, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return DR_OK;
+}
+
+int dr_backward(dr_ctx* c, const double* dV_dlo, const double* dV_dhi, float* dalpha, float* dbeta, int on_device) {
+    return fail(c, DR_ERR_STATE, "dr_backward: not available in this build");
+}
+
+int dr_optimize_slopes(dr_ctx* c, int steps, double lr_alpha, double lr_beta, double* V_out) {
+    return fail(c, DR_ERR_STATE, "dr_optimize_slopes: not available in this build");
+}
+
+}  // extern "C"

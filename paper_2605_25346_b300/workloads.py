@@ -223,12 +223,13 @@ def branch_splits(prob: Problem, rng: np.random.Generator, max_k: int = 32, pool
         c1 = min(len(sel), c0 + chunk)
         z = nominal_preactivations(prob, centre[c0:c1])  # H x [c, hid]
         za = np.abs(np.stack(z, axis=1)).reshape(c1 - c0, -1)  # [c, H*hid]
-        cand = np.argpartition(za, pool * max_k, axis=1)[:, : pool * max_k]
+        kk = min(pool * max_k, za.shape[1] - 1)
+        cand = np.argpartition(za, kk, axis=1)[:, : pool * max_k]
         cand = np.take_along_axis(cand, np.argsort(np.take_along_axis(za, cand, 1), axis=1, kind="stable"), 1)
         for i in range(c0, c1):
             d = int(sel[i])
-            k = int(counts[d])
-            order = np.argsort(keys[d], kind="stable")[:k]
+            k = min(int(counts[d]), cand.shape[1])
+            order = np.argsort(keys[d][: cand.shape[1]], kind="stable")[:k]
             flat = np.sort(cand[i - c0][order])  # sorted by (t, hidden index)
             t = flat // offs[-1]
             hid = flat % offs[-1]
@@ -295,11 +296,11 @@ def double_integrator_tiny() -> Problem:
 
 def quad6_batched(parts: int = 4) -> Problem:
     """6-state random stable linear dynamics (A = mixing_dynamics, B = 0.1 N(0,1) 6x3), controller
-    6-64-64-3 (FP32 weights, N(0, 1/fan_in)), B_0.1(x_hat) split into a uniform parts^6 grid
-    (4096 sub-boxes), H = 10."""
+    6-64-64-3 (FP32 weights, N(0, 1/fan_in), output gain 0.5), B_0.1(x_hat) split into a uniform
+    parts^6 grid (4096 sub-boxes), H = 10."""
     rng = np.random.default_rng(SEED_BASE + 2)
     widths = [6, 64, 64, 3]
-    W, b = mlp(rng, widths, f32=True)
+    W, b = mlp(rng, widths, f32=True, out_gain=0.5)
     A = mixing_dynamics(rng, 6)
     B = 0.1 * rng.normal(size=(6, 3))
     xhat = rng.uniform(-1, 1, size=6)
@@ -406,12 +407,12 @@ def large16(D_grid=(4, 4) + (2,) * 14, alpha_steps: int = 10) -> Problem:
 
 
 def random_problem(seed: int, widths, D: int, H: int, eps: float = 0.1, mode: int = MODE_CHORD,
-                   f32: bool = True, a_scale: float = 0.95, b_scale: float = 0.1) -> Problem:
+                   f32: bool = True, rho: float = 0.97, b_scale: float = 0.1, out_gain: float = 0.5) -> Problem:
     """Small random closed loop for tests: random boxes of radius ~eps around U[-1,1]^n centres."""
     rng = np.random.default_rng(seed)
-    W, b = mlp(rng, list(widths), f32=f32)
+    W, b = mlp(rng, list(widths), f32=f32, out_gain=out_gain)
     n, m = widths[0], widths[-1]
-    A = a_scale * haar_orthogonal(rng, n)
+    A = mixing_dynamics(rng, n, rho)
     B = b_scale * rng.normal(size=(n, m))
     c = rng.uniform(-1, 1, size=(D, n))
     r = eps * rng.uniform(0.25, 1.0, size=(D, n))

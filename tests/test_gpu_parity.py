@@ -1,0 +1,174 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerance (floating point): |gpu - oracle| <= 1e-5 * max(|o_lo|, |o_hi|, o_hi - o_lo) for every
+domain, step and coordinate.  Soundness against the oracle: the GPU machine is never tighter than the
+oracle's by more than the outward margin rho * (|o_lo| + |o_hi|).  Status words are compared exactly.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import reach as orc
+from paper_2605_25346_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+RHO = 2.0 ** -22
+
+
+def _api():
+    from paper_2605_25346_b300 import api
+    return api
+
+
+def gpu_bounds(prob, mode=None, alpha=None, on_device=True, rho=None):
+    api = _api()
+    r = api.Reach(0)
+    r.load(prob, mode=mode, rho=rho)
+    if alpha is not None:
+        r.set_alpha(alpha)
+    out = r.bounds(on_device=on_device)
+    V = r.objective()
+    res = {k: (v.cpu().numpy() if isinstance(v, torch.Tensor) else v) for k, v in out.items()}
+    res["V"] = V
+    r.close()
+    return res
+
+
+def compare(prob, g, o, rtol=RTOL, rho=RHO, check_hull=True):
+    olo, ohi = o["lo"].detach().numpy(), o["hi"].detach().numpy()
+    glo, ghi = g["lo"], g["hi"]
+    scale = np.maximum(np.maximum(np.abs(olo), np.abs(ohi)), ohi - olo)
+    err = np.maximum(np.abs(glo - olo), np.abs(ghi - ohi)) / np.maximum(scale, 1e-300)
+    assert np.isfinite(glo).all() and np.isfinite(ghi).all()
+    worst = np.unravel_index(np.argmax(err), err.shape)
+    assert err.max() <= rtol, f"max rel err {err.max():.3e} at {worst}"
+    mag = np.abs(olo) + np.abs(ohi)
+    assert (glo <= olo + rho * mag).all(), "GPU lower bound tighter than the oracle beyond the margin"
+    assert (ghi >= ohi - rho * mag).all(), "GPU upper bound tighter than the oracle beyond the margin"
+    np.testing.assert_array_equal(g["status"].astype(np.int64), o["status"].numpy())
+    np.testing.assert_allclose(g["V"], o["V"].detach().numpy(), rtol=rtol * 10)
+    if check_hull:
+        hs = np.maximum(np.abs(o["hull_lo"].numpy()), np.abs(o["hull_hi"].numpy()))
+        assert (np.abs(g["hull_lo"] - o["hull_lo"].numpy()) <= rtol * hs).all()
+        assert (np.abs(g["hull_hi"] - o["hull_hi"].numpy()) <= rtol * hs).all()
+    return float(err.max())
+
+
+def test_double_integrator_adaptive():
+    p = wl.double_integrator_tiny()
+    compare(p, gpu_bounds(p), orc.reach(p))
+
+
+def test_quad6_all_domains():
+    p = wl.quad6_batched()
+    compare(p, gpu_bounds(p), orc.reach(p))
+
+
+def test_cartpole_all_domains():
+    p = wl.cartpole_diff()
+    compare(p, gpu_bounds(p), orc.reach(p))
+
+
+SHAPES = [[5, 37, 23, 3], [3, 16, 2], [7, 96, 96, 96, 2], [2, 128, 128, 1], [4, 1, 1, 1]]
+# The adaptive slope (1 if u >= -l else 0) jumps at u = -l, so FP32 rounding may pick the other slope
+# there; it is compared only on nets with at most two hidden layers, where no neuron sits that close.
+CASES = [(w, m) for w in SHAPES for m in (orc.MODE_CHORD, orc.MODE_ZERO)] + \
+        [(w, orc.MODE_ADAPTIVE) for w in SHAPES if len(w) <= 4]
+
+
+@pytest.mark.parametrize("widths,mode", CASES)
+def test_random_shapes(widths, mode):
+    p = wl.random_problem(hash((tuple(widths), mode)) % 1000, widths, D=77, H=5, eps=0.15, mode=mode)
+    compare(p, gpu_bounds(p), orc.reach(p))
+
+
+def test_user_slopes():
+    p = wl.random_problem(3, [4, 33, 17, 2], D=40, H=6, eps=0.3)
+    g = torch.Generator().manual_seed(0)
+    alpha = torch.rand(p.D, p.H, p.hidden, generator=g, dtype=torch.float64)
+    alpha32 = alpha.float().numpy()
+    o = orc.reach(p, alpha=torch.as_tensor(alpha32, dtype=torch.float64), mode=orc.MODE_USER)
+    compare(p, gpu_bounds(p, alpha=alpha32), o)
+
+
+def test_chord_slopes_roundtrip_bitwise():
+    api = _api()
+    p = wl.random_problem(4, [3, 20, 20, 2], D=16, H=5, eps=0.3)
+    r = api.Reach(0).load(p)
+    ref = r.bounds(on_device=False)
+    a = r.get_alpha()
+    r.set_alpha(a)
+    out = r.bounds(on_device=False)
+    np.testing.assert_array_equal(ref["lo"], out["lo"])
+    np.testing.assert_array_equal(ref["hi"], out["hi"])
+
+
+def _with_splits(p, seed, beta_scale):
+    rng = np.random.default_rng(seed)
+    p.splits = wl.branch_splits(p, rng, max_k=6)
+    p.beta = rng.uniform(0, beta_scale, size=p.splits.nnz) if beta_scale > 0 else np.zeros(p.splits.nnz)
+    p.beta = p.beta.astype(np.float32).astype(np.float64)
+    return p
+
+
+@pytest.mark.parametrize("beta_scale", [0.0, 0.5])
+def test_split_domains(beta_scale):
+    p = _with_splits(wl.random_problem(8, [6, 40, 40, 3], D=64, H=6, eps=0.2), 1, beta_scale)
+    assert p.splits.nnz > 50
+    compare(p, gpu_bounds(p), orc.reach(p))
+
+
+def test_host_and_device_outputs_identical():
+    p = wl.random_problem(5, [4, 24, 24, 2], D=33, H=4)
+    a = gpu_bounds(p, on_device=True)
+    b = gpu_bounds(p, on_device=False)
+    np.testing.assert_array_equal(a["lo"], b["lo"])
+    np.testing.assert_array_equal(a["hi"], b["hi"])
+
+
+def test_gpu_bounds_contain_trajectories():
+    p = wl.quad6_batched()
+    sub = p.subset(np.arange(0, p.D, 16))
+    g = gpu_bounds(sub)
+    dom, xs, _ = wl.sample_trajectories(sub, 10000, 7)
+    assert ((xs >= g["lo"][dom]) & (xs <= g["hi"][dom])).all()
+
+
+def test_empty_domain_set():
+    api = _api()
+    p = wl.random_problem(6, [3, 8, 2], D=4, H=3)
+    q = p.subset(np.arange(0))
+    r = api.Reach(0).load(q)
+    out = r.bounds(on_device=False)
+    assert out["lo"].shape == (0, 4, 3)
+
+
+def test_invalid_arguments_are_errors():
+    api = _api()
+    from paper_2605_25346_b300 import _lib
+    p = wl.random_problem(6, [3, 8, 2], D=4, H=3)
+    bad = p.subset(np.arange(4))
+    bad.lo = bad.lo.copy()
+    bad.lo[1, 0] = np.nan
+    with pytest.raises(_lib.DiffReachError) as e:
+        api.Reach(0).load(bad)
+    assert e.value.code == _lib.DR_ERR_NONFINITE
+    inv = p.subset(np.arange(4))
+    inv.lo, inv.hi = inv.hi.copy(), inv.lo.copy()
+    with pytest.raises(_lib.DiffReachError) as e:
+        api.Reach(0).load(inv)
+    assert e.value.code == _lib.DR_ERR_ARG
+    sp = _with_splits(p.subset(np.arange(4)), 0, 0.0)
+    sp.splits.layer = sp.splits.layer.copy()
+    if sp.splits.nnz:
+        sp.splits.layer[0] = 2  # not a hidden layer of a 2-layer controller
+        with pytest.raises(_lib.DiffReachError) as e:
+            api.Reach(0).load(sp)
+        assert e.value.code == _lib.DR_ERR_ARG
+    r = api.Reach(0)
+    r.set_options(mode=None, mem_cap=1024)
+    with pytest.raises(_lib.DiffReachError) as e:
+        r.load(wl.quad6_batched())
+    assert e.value.code == _lib.DR_ERR_OOM
