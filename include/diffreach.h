@@ -141,11 +141,13 @@ int dr_get_objective(dr_ctx* ctx, double* V, int on_device);
  * best slopes and multipliers and slope mode DR_SLOPE_USER. */
 int dr_optimize_slopes(dr_ctx* ctx, int steps, double lr_alpha, double lr_beta, double* V_out);
 
-/* Reverse-mode gradient of sum_d sum_{t,i} (w_hi * hi - w_lo * lo) at the current slopes
- * (DR_SLOPE_USER; CHORD slopes if none were set):
- *   dV_dlo, dV_dhi [D x (H+1) x n] FP64 upstream weights (NULL = -1 and +1 on steps 1..H,
- *   i.e. the gradient of V); dalpha [D x H x hidden] FP32; dbeta [nnz] FP32.
- * Pointers are host memory unless on_device != 0. */
+/* Reverse-mode gradient of the scalar sum_{d,t,i} (g_lo[d,t,i] * lo[d,t,i] + g_hi[d,t,i] * hi[d,t,i])
+ * at the current slopes (DR_SLOPE_USER; the slopes of the current mode otherwise, with dalpha 0):
+ *   dV_dlo, dV_dhi [D x (H+1) x n] FP64 upstream gradients g_lo, g_hi of the boxes (NULL for both =
+ *   the tube-volume proxy V, i.e. g_lo = -1 and g_hi = +1 on steps 1..H; one NULL = zeros);
+ *   dalpha [D x H x hidden] FP32; dbeta [nnz] FP32.  Step 0 (the input box) carries no gradient.
+ * Pointers are host memory unless on_device != 0.  Recomputes the forward pass with a per-step tape
+ * (library-owned, D*H*(n^2+4n+2) doubles) and runs the fused reverse sweep. */
 int dr_backward(dr_ctx* ctx, const double* dV_dlo, const double* dV_dhi, float* dalpha, float* dbeta,
                 int on_device);
 
@@ -154,8 +156,9 @@ int dr_backward(dr_ctx* ctx, const double* dV_dlo, const double* dV_dhi, float* 
 int dr_get_alpha(dr_ctx* ctx, float* alpha, int on_device);
 int dr_set_alpha(dr_ctx* ctx, const float* alpha, int on_device);
 
-/* Split multipliers beta [nnz] FP32. */
+/* Split multipliers beta [nnz] FP32 (>= 0). */
 int dr_get_beta(dr_ctx* ctx, float* beta, int on_device);
+int dr_set_beta(dr_ctx* ctx, const float* beta, int on_device);
 
 /* Number of kernels this context has launched (monotone counter, for accounting). */
 int64_t dr_kernel_launches(const dr_ctx* ctx);

@@ -20,7 +20,7 @@ DR_STATUS_NONFINITE, DR_STATUS_INFEASIBLE = 1, 2
 EXPORTS = [
     "dr_create", "dr_destroy", "dr_load_controller", "dr_load_dynamics", "dr_set_boxes", "dr_set_splits",
     "dr_set_horizon", "dr_set_options", "dr_compute_bounds", "dr_get_objective", "dr_optimize_slopes",
-    "dr_backward", "dr_get_alpha", "dr_set_alpha", "dr_get_beta", "dr_kernel_launches", "dr_last_error",
+    "dr_backward", "dr_get_alpha", "dr_set_alpha", "dr_get_beta", "dr_set_beta", "dr_kernel_launches", "dr_last_error",
 ]
 
 
@@ -62,6 +62,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dr_get_alpha": (i32, [vp, fp, i32]),
         "dr_set_alpha": (i32, [vp, fp, i32]),
         "dr_get_beta": (i32, [vp, fp, i32]),
+        "dr_set_beta": (i32, [vp, fp, i32]),
         "dr_kernel_launches": (i64, [vp]),
         "dr_last_error": (ctypes.c_char_p, [vp]),
     }

@@ -150,12 +150,23 @@ class Reach:
         self._c(self.lib.dr_get_beta(self.ctx, _ptr(b), 0))
         return b[:nnz]
 
-    def backward(self, on_device: bool = False):
+    def set_beta(self, beta):
+        b = np.ascontiguousarray(beta, dtype=np.float32)
+        self._c(self.lib.dr_set_beta(self.ctx, _ptr(b), 0))
+
+    def backward(self, wlo=None, whi=None):
+        """dV/dalpha [D, H, hidden] and dV/dbeta [nnz] at the current slopes (host numpy).
+
+        wlo/whi: optional upstream gradients [D, H+1, n] of the lower/upper bounds (default: the
+        tube-volume proxy, -1/+1 on steps 1..H)."""
         p = self.prob
         nnz = p.splits.nnz if p.splits is not None else 0
         ga = np.empty((p.D, p.H, p.hidden), dtype=np.float32)
         gb = np.empty(max(nnz, 1), dtype=np.float32)
-        self._c(self.lib.dr_backward(self.ctx, None, None, _ptr(ga), _ptr(gb), 0))
+        wl = None if wlo is None else np.ascontiguousarray(wlo, dtype=np.float64)
+        wh = None if whi is None else np.ascontiguousarray(whi, dtype=np.float64)
+        self._c(self.lib.dr_backward(self.ctx, None if wl is None else _ptr(wl), None if wh is None else _ptr(wh),
+                                     _ptr(ga), _ptr(gb), 0))
         return ga, gb[:nnz]
 
     def optimize(self, steps: int, lr_alpha: float, lr_beta: float = 0.0):
@@ -165,3 +176,42 @@ class Reach:
 
     def launches(self) -> int:
         return int(self.lib.dr_kernel_launches(self.ctx))
+
+
+class BoundsFunction(torch.autograd.Function):
+    """Differentiable bounds: (alpha, beta) -> (lo, hi), backward through the library's adjoint.
+
+    alpha [D, H, hidden] float32 and beta [nnz] float32 are CUDA tensors; lo/hi [D, H+1, n]
+    float64.  The backward pass hands torch's upstream gradients of lo and hi to dr_backward.
+    """
+
+    @staticmethod
+    def forward(ctx, reach: "Reach", alpha: torch.Tensor, beta: torch.Tensor):
+        a = alpha.detach().to(torch.float32).contiguous()
+        reach._c(reach.lib.dr_set_alpha(reach.ctx, _ptr(a), 1))
+        if beta.numel():
+            b = beta.detach().to(torch.float32).contiguous()
+            reach._c(reach.lib.dr_set_beta(reach.ctx, _ptr(b), 1))
+        out = reach.bounds(on_device=True, hull=False)
+        ctx.reach = reach
+        ctx.shapes = (alpha.shape, beta.shape)
+        return out["lo"], out["hi"]
+
+    @staticmethod
+    def backward(ctx, glo, ghi):
+        r = ctx.reach
+        p = r.prob
+        dev = f"cuda:{r.device}"
+        zeros = torch.zeros(p.D, p.H + 1, p.n, dtype=torch.float64, device=dev)
+        wlo = (glo if glo is not None else zeros).to(torch.float64).contiguous()
+        whi = (ghi if ghi is not None else zeros).to(torch.float64).contiguous()
+        ga = torch.empty(ctx.shapes[0], dtype=torch.float32, device=dev)
+        gb = torch.empty(max(1, ctx.shapes[1].numel()), dtype=torch.float32, device=dev)
+        torch.cuda.synchronize()
+        r._c(r.lib.dr_backward(r.ctx, _ptr(wlo), _ptr(whi), _ptr(ga), _ptr(gb), 1))
+        return None, ga, gb[: ctx.shapes[1].numel()].reshape(ctx.shapes[1])
+
+
+def bounds(reach: "Reach", alpha: torch.Tensor, beta: torch.Tensor):
+    """(lo, hi) with autograd through the CUDA adjoint (see BoundsFunction)."""
+    return BoundsFunction.apply(reach, alpha, beta)

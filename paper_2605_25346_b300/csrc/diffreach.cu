@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <limits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -11,7 +12,8 @@
 
 #include "../../include/diffreach.h"
 #include "common.cuh"
-#include "fused_fwd.cuh"
+#include "fused_core.cuh"
+#include "fused_bwd.cuh"
 
 
 struct dr_ctx {
@@ -55,6 +57,15 @@ struct dr_ctx {
     double* dtape = nullptr;
     size_t tape_bytes = 0;
     size_t out_bytes = 0;
+    // refinement / adjoint scratch
+    float* dgalpha = nullptr;
+    float* dgbeta = nullptr;
+    float* dbest_alpha = nullptr;
+    float* dbest_beta = nullptr;
+    double* dbestV = nullptr;
+    double* dVhist = nullptr;
+    double* dwlo = nullptr;
+    double* dwhi = nullptr;
 };
 
 static thread_local std::string g_create_err;
@@ -122,7 +133,7 @@ static dr_options default_options() {
 // fused-path layout
 // ------------------------------------------------------------------------------------------------
 
-static FusedLayout fused_layout(const NetDesc& N) {
+static FusedLayout fused_layout(const NetDesc& N, bool backward = false) {
     FusedLayout Y;
     memset(&Y, 0, sizeof(Y));
     size_t off = 0;
@@ -160,6 +171,13 @@ static FusedLayout fused_layout(const NetDesc& N) {
     Y.hu = take(sizeof(float) * hid);
     Y.hs = take(sizeof(float) * hid);
     Y.hd = take(sizeof(float) * hid);
+    if (backward) {
+        Y.hl0 = take(sizeof(float) * hid);
+        Y.hu0 = take(sizeof(float) * hid);
+    } else {
+        Y.hl0 = Y.hl;
+        Y.hu0 = Y.hu;
+    }
     Y.klo = take(sizeof(float) * N.maxw);
     Y.khi = take(sizeof(float) * N.maxw);
     // per-domain chain buffers: target l, after level m the matrix is n_l x odd_ld(n_{m-1})
@@ -177,6 +195,41 @@ static FusedLayout fused_layout(const NetDesc& N) {
     Y.Iulo = take(sizeof(float) * m);
     Y.Iuhi = take(sizeof(float) * m);
     Y.misc = take(sizeof(int) * 4);
+    if (backward) {
+        Y.vsnap = take(sizeof(float) * (N.L + 1) * (n + 1));
+        size_t lv = 1, gl = (size_t)N.maxw * odd_ld(n);
+        for (int l = 2; l <= N.L; ++l) {
+            lv = std::max(lv, (size_t)lev_offset(N, l, l - 1));
+            for (int k = 1; k <= l - 2; ++k) gl = std::max(gl, (size_t)N.w[l] * odd_ld(N.w[k]));
+        }
+        Y.lev = take(sizeof(float) * lv);
+        Y.gc = take(sizeof(double) * n);
+        Y.gP = take(sizeof(double) * n * n);
+        Y.gIlo = take(sizeof(double) * n);
+        Y.gIhi = take(sizeof(double) * n);
+        Y.gcn = take(sizeof(double) * n);
+        Y.gPn = take(sizeof(double) * n * n);
+        Y.gIlon = take(sizeof(double) * n);
+        Y.gIhin = take(sizeof(double) * n);
+        Y.gPu = take(sizeof(double) * m * n);
+        Y.gcu = take(sizeof(double) * m);
+        Y.gIulo = take(sizeof(double) * m);
+        Y.gIuhi = take(sizeof(double) * m);
+        Y.gv = take(sizeof(double) * n);
+        Y.gw = take(sizeof(double) * 2);
+        Y.gs = take(sizeof(float) * hid);
+        Y.gd = take(sizeof(float) * hid);
+        Y.gl = take(sizeof(float) * hid);
+        Y.gu = take(sizeof(float) * hid);
+        Y.gG = take(sizeof(float) * N.maxw * odd_ld(n));
+        Y.ga = take(sizeof(float) * N.maxw);
+        Y.gklo = take(sizeof(float) * N.maxw);
+        Y.gkhi = take(sizeof(float) * N.maxw);
+        Y.gRlo = take(sizeof(float) * N.maxw);
+        Y.gRhi = take(sizeof(float) * N.maxw);
+        Y.gL0 = take(sizeof(float) * gl);
+        Y.gL1 = take(sizeof(float) * gl);
+    }
     Y.total = (int)((off + 15) & ~size_t(15));
     return Y;
 }
@@ -223,6 +276,14 @@ static void free_outputs(dr_ctx* c) {
     dev_free(c, (void*&)c->dstatus, sizeof(uint32_t) * c->D);
     dev_free(c, (void*&)c->dhull, sizeof(double) * 2 * (c->H + 1) * std::max(c->net.n, 1));
     dev_free(c, (void*&)c->dtape, c->tape_bytes);
+    dev_free(c, (void*&)c->dgalpha, 0);
+    dev_free(c, (void*&)c->dgbeta, 0);
+    dev_free(c, (void*&)c->dbest_alpha, 0);
+    dev_free(c, (void*&)c->dbest_beta, 0);
+    dev_free(c, (void*&)c->dbestV, 0);
+    dev_free(c, (void*&)c->dVhist, 0);
+    dev_free(c, (void*&)c->dwlo, 0);
+    dev_free(c, (void*&)c->dwhi, 0);
     c->out_bytes = 0;
     c->tape_bytes = 0;
 }
@@ -635,12 +696,158 @@ int dr_get_beta(dr_ctx* c, float* beta, int on_device) {
     return DR_OK;
 }
 
+int dr_set_beta(dr_ctx* c, const float* beta, int on_device) {
+    if (!c || (!beta && c->nnz)) return fail(c, DR_ERR_ARG, "dr_set_beta: NULL");
+    if (!c->nnz) return DR_OK;
+    if (!on_device)
+        for (int64_t k = 0; k < c->nnz; ++k)
+            if (!(beta[k] >= 0.f && std::isfinite(beta[k]))) return fail(c, DR_ERR_ARG, "beta[%lld] must be finite and >= 0", (long long)k);
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    CUDA_TRY(c, cudaMemcpyAsync(c->dbeta, beta, sizeof(float) * c->nnz, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return DR_OK;
+}
+
+static int launch_backward(dr_ctx* c, int mode, const double* wlo, const double* whi, float* galpha, float* gbeta) {
+    NetDesc N = c->net;
+    N.H = c->H;
+    if (c->D == 0) return DR_OK;
+    FusedArgs a;
+    memset(&a, 0, sizeof(a));
+    a.net = N;
+    a.lay = fused_layout(N, true);
+    if (a.lay.total > kMaxSmem)
+        return fail(c, DR_ERR_SHAPE, "controller too wide for the fused reverse kernel (%d bytes of shared memory)", a.lay.total);
+    a.W = c->dW;
+    a.b = c->db;
+    a.A = c->dA;
+    a.B = c->dB;
+    a.e = c->de;
+    a.lo0 = c->dlo0;
+    a.hi0 = c->dhi0;
+    a.sp_row = c->nnz ? c->dsp_row : nullptr;
+    a.sp = c->dsp;
+    a.beta = c->dbeta;
+    a.alpha = c->dalpha;
+    a.mode = mode;
+    a.rho = (float)c->opt.margin_rho;
+    a.tape = c->dtape;
+    a.tape_stride = tape_stride(N);
+    a.wlo = wlo;
+    a.whi = whi;
+    a.dalpha = galpha;
+    a.dbeta = gbeta;
+    const int nt = fused_threads(N);
+    const int smem = a.lay.total;
+    const int64_t chunk = 1 << 20;
+    for (int64_t d0 = 0; d0 < c->D; d0 += chunk) {
+        a.d0 = d0;
+        const int64_t nd = std::min(chunk, c->D - d0);
+        if (nt == 128) {
+            CUDA_TRY(c, cudaFuncSetAttribute(k_fused_backward<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            k_fused_backward<128><<<(unsigned)nd, 128, smem, c->stream>>>(a);
+        } else {
+            CUDA_TRY(c, cudaFuncSetAttribute(k_fused_backward<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            k_fused_backward<256><<<(unsigned)nd, 256, smem, c->stream>>>(a);
+        }
+        CUDA_TRY(c, cudaGetLastError());
+        c->launches++;
+    }
+    return DR_OK;
+}
+
+static int ensure_grad_buffers(dr_ctx* c) {
+    const size_t na = (size_t)c->D * c->H * std::max(c->net.hidden, 1);
+    if (!c->dgalpha) TRY(dev_alloc(c, c->dgalpha, na));
+    if (!c->dgbeta) TRY(dev_alloc(c, c->dgbeta, (size_t)std::max<int64_t>(c->nnz, 1)));
+    return DR_OK;
+}
+
 int dr_backward(dr_ctx* c, const double* dV_dlo, const double* dV_dhi, float* dalpha, float* dbeta, int on_device) {
-    return fail(c, DR_ERR_STATE, "dr_backward: not available in this build");
+    if (!c) return DR_ERR_ARG;
+    TRY(check_ready(c));
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    TRY(ensure_outputs(c));
+    TRY(ensure_grad_buffers(c));
+    const int mode = c->alpha_set ? DR_SLOPE_USER : c->opt.slope_mode;
+    const size_t nw = (size_t)c->D * (c->H + 1) * c->net.n;
+    const double* wlo = nullptr;
+    const double* whi = nullptr;
+    if (dV_dlo || dV_dhi) {
+        if (!c->dwlo) TRY(dev_alloc(c, c->dwlo, nw));
+        if (!c->dwhi) TRY(dev_alloc(c, c->dwhi, nw));
+        const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        if (dV_dlo) CUDA_TRY(c, cudaMemcpyAsync(c->dwlo, dV_dlo, sizeof(double) * nw, k, c->stream));
+        else CUDA_TRY(c, cudaMemsetAsync(c->dwlo, 0, sizeof(double) * nw, c->stream));
+        if (dV_dhi) CUDA_TRY(c, cudaMemcpyAsync(c->dwhi, dV_dhi, sizeof(double) * nw, k, c->stream));
+        else CUDA_TRY(c, cudaMemsetAsync(c->dwhi, 0, sizeof(double) * nw, c->stream));
+        wlo = c->dwlo;
+        whi = c->dwhi;
+    }
+    TRY(run_forward(c, mode, nullptr, true));
+    TRY(launch_backward(c, mode, wlo, whi, c->dgalpha, c->dgbeta));
+    const size_t na = (size_t)c->D * c->H * c->net.hidden;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (dalpha && na) CUDA_TRY(c, cudaMemcpyAsync(dalpha, c->dgalpha, sizeof(float) * na, k, c->stream));
+    if (dbeta && c->nnz) CUDA_TRY(c, cudaMemcpyAsync(dbeta, c->dgbeta, sizeof(float) * c->nnz, k, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return DR_OK;
 }
 
 int dr_optimize_slopes(dr_ctx* c, int steps, double lr_alpha, double lr_beta, double* V_out) {
-    return fail(c, DR_ERR_STATE, "dr_optimize_slopes: not available in this build");
+    if (!c) return DR_ERR_ARG;
+    if (steps < 0 || !(lr_alpha >= 0.0) || !(lr_beta >= 0.0)) return fail(c, DR_ERR_ARG, "steps/learning rates out of range");
+    TRY(check_ready(c));
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    TRY(ensure_outputs(c));
+    TRY(ensure_grad_buffers(c));
+    if (c->D == 0) return DR_OK;
+    const int64_t per_dom = (int64_t)c->H * c->net.hidden;
+    const size_t na = (size_t)c->D * per_dom;
+    if (!c->alpha_set) {
+        TRY(ensure_alpha(c));
+        TRY(run_forward(c, DR_SLOPE_CHORD, c->dalpha, false));  // start at the chord slopes
+        c->alpha_set = true;
+    }
+    if (!c->dbest_alpha) TRY(dev_alloc(c, c->dbest_alpha, std::max<size_t>(na, 1)));
+    if (!c->dbest_beta) TRY(dev_alloc(c, c->dbest_beta, (size_t)std::max<int64_t>(c->nnz, 1)));
+    if (!c->dbestV) TRY(dev_alloc(c, c->dbestV, (size_t)c->D));
+    dev_free(c, (void*&)c->dVhist, 0);
+    TRY(dev_alloc(c, c->dVhist, (size_t)steps + 1));
+    {
+        std::vector<double> inf(c->D, std::numeric_limits<double>::infinity());
+        CUDA_TRY(c, cudaMemcpyAsync(c->dbestV, inf.data(), sizeof(double) * c->D, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+    const int64_t* sp_row = c->nnz ? c->dsp_row : nullptr;
+    for (int it = 0; it <= steps; ++it) {
+        TRY(run_forward(c, DR_SLOPE_USER, nullptr, it < steps));
+        k_keep_best<<<(unsigned)c->D, 128, 0, c->stream>>>(c->dV, c->dbestV, c->dalpha, c->dbest_alpha, c->dbeta,
+                                                          c->dbest_beta, sp_row, per_dom);
+        k_sum<<<1, 256, 0, c->stream>>>(c->dbestV, c->D, c->dVhist + it);
+        CUDA_TRY(c, cudaGetLastError());
+        c->launches += 2;
+        if (it == steps) break;
+        TRY(launch_backward(c, DR_SLOPE_USER, nullptr, nullptr, c->dgalpha, c->dgbeta));
+        if (na) {
+            k_pgd<<<1184, 256, 0, c->stream>>>(c->dalpha, c->dgalpha, (int64_t)na, (float)lr_alpha, 0.f, 1.f);
+            c->launches++;
+        }
+        if (c->nnz && lr_beta > 0.0) {
+            k_pgd<<<1184, 256, 0, c->stream>>>(c->dbeta, c->dgbeta, c->nnz, (float)lr_beta, 0.f, INFINITY);
+            c->launches++;
+        }
+        CUDA_TRY(c, cudaGetLastError());
+    }
+    // install the best slopes and multipliers and leave their bounds in the output buffers
+    if (na) CUDA_TRY(c, cudaMemcpyAsync(c->dalpha, c->dbest_alpha, sizeof(float) * na, cudaMemcpyDeviceToDevice, c->stream));
+    if (c->nnz) CUDA_TRY(c, cudaMemcpyAsync(c->dbeta, c->dbest_beta, sizeof(float) * c->nnz, cudaMemcpyDeviceToDevice, c->stream));
+    c->opt.slope_mode = DR_SLOPE_USER;
+    TRY(run_forward(c, DR_SLOPE_USER, nullptr, false));
+    if (V_out) CUDA_TRY(c, cudaMemcpyAsync(V_out, c->dVhist, sizeof(double) * (steps + 1), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return DR_OK;
 }
 
 }  // extern "C"

@@ -1,0 +1,387 @@
+// Fused reverse sweep (adjoint) of the per-domain forward pass: dV/dalpha and dV/dbeta.
+//
+// Objective sum_{t,i} (g_lo lo_{t,i} + g_hi hi_{t,i}); the tube-volume proxy of Sec. V-A is
+// g_lo = -1, g_hi = +1.  One CTA owns one domain.  Steps are reversed t = H-1..0; each step is recomputed
+// from its tape entry (FP64 TM, dual state, split cursor) and then differentiated in exactly
+// the reverse order of the forward: EvalInt, dynamics, then for each target layer
+// l = L..1 the relaxation, split records, concretisation, input projection and the
+// back-substitution chain (Lambda matrices recomputed per target, not stored per step).
+// Subgradient conventions: |0|' = 0, Lambda^+/- have zero slope at 0, the intercept
+// max(-alpha l, (1-alpha) u) takes the first branch on a tie.  The outward margin is treated
+// as a constant.
+#pragma once
+#include "fused_core.cuh"
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_fused_backward(const FusedArgs a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const NetDesc& N = a.net;
+    const FusedLayout& Y = a.lay;
+    const Dom s = make_dom(sm, Y);
+    const int tid = threadIdx.x;
+    const int64_t dom = a.d0 + blockIdx.x;
+    const int n = N.n, m = N.m, L = N.L, H = N.H, gld = odd_ld(n);
+    double* gc = SMD(Y.gc);
+    double* gP = SMD(Y.gP);
+    double* gIlo = SMD(Y.gIlo);
+    double* gIhi = SMD(Y.gIhi);
+    double* gcn = SMD(Y.gcn);
+    double* gPn = SMD(Y.gPn);
+    double* gIlon = SMD(Y.gIlon);
+    double* gIhin = SMD(Y.gIhin);
+    double* gPu = SMD(Y.gPu);
+    double* gcu = SMD(Y.gcu);
+    double* gIulo = SMD(Y.gIulo);
+    double* gIuhi = SMD(Y.gIuhi);
+    double* gv = SMD(Y.gv);
+    double* gw = SMD(Y.gw);
+    float* gs = SMF(Y.gs);
+    float* gd = SMF(Y.gd);
+    float* gl = SMF(Y.gl);
+    float* gu = SMF(Y.gu);
+    float* gG = SMF(Y.gG);
+    float* ga = SMF(Y.ga);
+    float* gklo = SMF(Y.gklo);
+    float* gkhi = SMF(Y.gkhi);
+    float* gRlo = SMF(Y.gRlo);
+    float* gRhi = SMF(Y.gRhi);
+    float* vsnap = SMF(Y.vsnap);
+    float* lev = SMF(Y.lev);
+
+    load_params<NT>(s, a);
+    for (int idx = tid; idx < n * n; idx += NT) gPn[idx] = 0.0;
+    for (int i = tid; i < n; i += NT) {
+        gcn[i] = 0.0;
+        gIlon[i] = 0.0;
+        gIhin[i] = 0.0;
+        gv[i] = 0.0;
+    }
+    if (tid == 0) gw[0] = 0.0;
+    const int64_t sp_end = a.sp_row ? a.sp_row[dom + 1] : 0;
+    __syncthreads();
+
+    for (int t = H - 1; t >= 0; --t) {
+        // ---- recompute step t from its tape entry
+        const double* tp = a.tape + (dom * H + t) * (int64_t)a.tape_stride;
+        for (int idx = tid; idx < n * n; idx += NT) s.P[idx] = tp[idx];
+        for (int i = tid; i < n; i += NT) {
+            s.c[i] = tp[n * n + i];
+            s.Ilo[i] = tp[n * n + n + i];
+            s.Ihi[i] = tp[n * n + 2 * n + i];
+            s.v[i] = tp[n * n + 3 * n + i];
+        }
+        if (tid == 0) {
+            s.wv[0] = tp[n * n + 4 * n];
+            s.misc[0] = (int)tp[n * n + 4 * n + 1];
+            s.misc[1] = 0;
+        }
+        __syncthreads();
+        const int cursor0 = s.misc[0];
+        tm_view<NT>(s, n);
+        controller_pass<NT>(s, N, a, dom, sp_end, t, vsnap);
+        dynamics<NT>(s, N);
+
+        // ---- EvalInt of box t+1 (uses the dual state after step t)
+        const int64_t wrow = (dom * (H + 1) + t + 1) * n;
+        for (int i = tid; i < n; i += NT) {
+            const double wl = a.wlo ? a.wlo[wrow + i] : -1.0;
+            const double wh = a.whi ? a.whi[wrow + i] : 1.0;
+            gcn[i] += wl + wh;
+            gIlon[i] += wl;
+            gIhin[i] += wh;
+            for (int k = 0; k < n; ++k) {
+                const double x = s.Pn[i * n + k];
+                gPn[i * n + k] += -wl * sgnd(x - s.v[k]) + wh * sgnd(x + s.v[k]);
+            }
+        }
+        for (int k = tid; k < n; k += NT) {
+            double acc = 0.0;
+            for (int i = 0; i < n; ++i) {
+                const double wl = a.wlo ? a.wlo[wrow + i] : -1.0;
+                const double wh = a.whi ? a.whi[wrow + i] : 1.0;
+                const double x = s.Pn[i * n + k];
+                acc += wl * sgnd(x - s.v[k]) + wh * sgnd(x + s.v[k]);
+            }
+            gv[k] += acc;
+        }
+        if (tid == 0) {
+            double acc = 0.0;
+            for (int i = 0; i < n; ++i) {
+                const double wl = a.wlo ? a.wlo[wrow + i] : -1.0;
+                const double wh = a.whi ? a.whi[wrow + i] : 1.0;
+                acc += wh - wl;
+            }
+            gw[0] += acc;
+        }
+        __syncthreads();
+
+        // ---- dynamics reverse: TM_t and controller-TM adjoints
+        for (int idx = tid; idx < n * n; idx += NT) {
+            const int j = idx / n, k = idx - j * n;
+            double acc = 0.0;
+            for (int i = 0; i < n; ++i) acc += s.A[i * n + j] * gPn[i * n + k];
+            gP[idx] = acc;
+        }
+        for (int idx = tid; idx < m * n; idx += NT) {
+            const int j = idx / n, k = idx - j * n;
+            double acc = 0.0;
+            for (int i = 0; i < n; ++i) acc += s.B[i * m + j] * gPn[i * n + k];
+            gPu[idx] = acc;
+        }
+        for (int j = tid; j < n; j += NT) {
+            double c_ = 0.0, lo_ = 0.0, hi_ = 0.0;
+            for (int i = 0; i < n; ++i) {
+                const double x = s.A[i * n + j];
+                c_ += x * gcn[i];
+                lo_ += posd(x) * gIlon[i] + negd(x) * gIhin[i];
+                hi_ += posd(x) * gIhin[i] + negd(x) * gIlon[i];
+            }
+            gc[j] = c_;
+            gIlo[j] = lo_;
+            gIhi[j] = hi_;
+        }
+        for (int j = tid; j < m; j += NT) {
+            double c_ = 0.0, lo_ = 0.0, hi_ = 0.0;
+            for (int i = 0; i < n; ++i) {
+                const double x = s.B[i * m + j];
+                c_ += x * gcn[i];
+                lo_ += posd(x) * gIlon[i] + negd(x) * gIhin[i];
+                hi_ += posd(x) * gIhin[i] + negd(x) * gIlon[i];
+            }
+            gcu[j] = c_;
+            gIulo[j] = lo_;
+            gIuhi[j] = hi_;
+        }
+        for (int j = tid; j < N.hidden; j += NT) {
+            gs[j] = 0.f;
+            gd[j] = 0.f;
+        }
+        __syncthreads();
+
+        // ---- targets in reverse order
+        for (int ell = L; ell >= 1; --ell) {
+            const int rows = N.w[ell];
+            int ld;
+            const float* cur = chain<NT>(s, N, ell, lev, &ld);
+            if (ell < L) {
+                for (int k = tid; k <= n; k += NT) s.vf[k] = vsnap[ell * (n + 1) + k];
+                __syncthreads();
+            }
+            project<NT>(s, N, ell, cur, ld, a.rho, false);
+            const float* vb = vsnap + ell * (n + 1);
+            if (ell == L) {
+                for (int i = tid; i < rows; i += NT) {
+                    const float c_ = (float)gcu[i], dl = (float)(gIulo[i] - gIuhi[i]);
+                    ga[i] = c_;
+                    gklo[i] = 0.5f * c_ + 0.5f * dl;
+                    gkhi[i] = 0.5f * c_ - 0.5f * dl;
+                    gRlo[i] = (float)gIulo[i];
+                    gRhi[i] = (float)gIuhi[i];
+                    for (int k = 0; k < n; ++k) gG[i * gld + k] = (float)gPu[i * n + k];
+                }
+                __syncthreads();
+            } else {
+                const int ho = N.hoff[ell];
+                // relaxation reverse (post-clip bounds), then the clip
+                for (int j = tid; j < rows; j += NT) {
+                    const float l = s.hl[ho + j], u = s.hu[ho + j];
+                    const float g_s = gs[ho + j], g_d = gd[ho + j];
+                    float g_l = 0.f, g_u = 0.f, g_a = 0.f;
+                    if (l < 0.f && u > 0.f) {
+                        const float user = a.mode == DR_SLOPE_USER_K ? a.alpha[(dom * H + t) * (int64_t)N.hidden + ho + j] : 0.f;
+                        const float al = slope_of(a.mode, l, u, user);
+                        const bool br = (-al * l) >= ((1.f - al) * u);
+                        g_a = g_s + g_d * (br ? -l : -u);
+                        if (br) g_l = g_d * (-al);
+                        else g_u = g_d * (1.f - al);
+                        if (a.mode == DR_SLOPE_CHORD_K) {
+                            const float den = u - l;
+                            g_l += g_a * u / (den * den);
+                            g_u += g_a * (-l) / (den * den);
+                        }
+                    }
+                    if (a.dalpha) a.dalpha[(dom * H + t) * (int64_t)N.hidden + ho + j] = (a.mode == DR_SLOPE_USER_K) ? g_a : 0.f;
+                    if (s.hl0[ho + j] != l) g_l = 0.f;  // clipped by a split
+                    if (s.hu0[ho + j] != u) g_u = 0.f;
+                    gl[ho + j] = g_l;
+                    gu[ho + j] = g_u;
+                    ga[j] = 0.f;
+                    gklo[j] = 0.f;
+                    gkhi[j] = 0.f;
+                    gRlo[j] = 0.f;
+                    gRhi[j] = 0.f;
+                    for (int k = 0; k < n; ++k) gG[j * gld + k] = 0.f;
+                }
+                __syncthreads();
+                // split records of (t, ell): v += beta sign G_j, w += beta h (adjoint of the updated dual)
+                if (tid == 0 && a.sp_row) {
+                    for (int cpos = cursor0; cpos < sp_end; ++cpos) {
+                        const SplitRec r = a.sp[cpos];
+                        if (r.t > t) break;
+                        if (r.t != t || r.layer != ell) continue;
+                        const int j = r.neuron;
+                        const float bt = a.beta ? a.beta[cpos] : 0.f;
+                        const float hh = split_h(s, j, r.sign, a.rho);
+                        double gb = gw[0] * (double)hh;
+                        for (int k = 0; k < n; ++k) gb += gv[k] * (double)r.sign * (double)s.G[j * gld + k];
+                        if (a.dbeta) a.dbeta[cpos] = (float)gb;
+                        if (bt != 0.f) {
+                            for (int k = 0; k < n; ++k) gG[j * gld + k] += (float)((double)bt * (double)r.sign * gv[k]);
+                            const float hb = (float)((double)bt * gw[0]);
+                            if (r.sign > 0) {
+                                ga[j] += hb;
+                                gkhi[j] += hb;
+                                gRhi[j] += hb;
+                            } else {
+                                ga[j] -= hb;
+                                gklo[j] -= hb;
+                                gRlo[j] -= hb;
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+                // concretisation reverse (dual vector as seen by this layer)
+                for (int i = tid; i < rows; i += NT) {
+                    const float g_l = gl[ho + i], g_u = gu[ho + i];
+                    ga[i] += g_l + g_u;
+                    gklo[i] += g_l;
+                    gkhi[i] += g_u;
+                    gRlo[i] += g_l;
+                    gRhi[i] += g_u;
+                    for (int k = 0; k < n; ++k) {
+                        const float x = s.G[i * gld + k];
+                        gG[i * gld + k] += -g_l * sgnf(x - vb[k]) + g_u * sgnf(x + vb[k]);
+                    }
+                }
+                for (int k = tid; k < n; k += NT) {
+                    double acc = 0.0;
+                    for (int i = 0; i < rows; ++i) {
+                        const float x = s.G[i * gld + k];
+                        acc += (double)(gl[ho + i] * sgnf(x - vb[k]) + gu[ho + i] * sgnf(x + vb[k]));
+                    }
+                    gv[k] += acc;
+                }
+                if (tid == 0) {
+                    double acc = 0.0;
+                    for (int i = 0; i < rows; ++i) acc += (double)(gu[ho + i] - gl[ho + i]);
+                    gw[0] += acc;
+                }
+                __syncthreads();
+            }
+            // ---- input projection reverse: TM adjoints and Lambda_x adjoint
+            for (int idx = tid; idx < n * n; idx += NT) {
+                const int j = idx / n, k = idx - j * n;
+                double acc = 0.0;
+                for (int i = 0; i < rows; ++i) acc += (double)(cur[i * ld + j] * gG[i * gld + k]);
+                gP[idx] += acc;
+            }
+            for (int j = tid; j < n; j += NT) {
+                double c_ = 0.0, lo_ = 0.0, hi_ = 0.0;
+                for (int i = 0; i < rows; ++i) {
+                    const float x = cur[i * ld + j];
+                    c_ += (double)(x * ga[i]);
+                    lo_ += (double)(gRlo[i] * posf(x) + gRhi[i] * negf(x));
+                    hi_ += (double)(gRlo[i] * negf(x) + gRhi[i] * posf(x));
+                }
+                gc[j] += c_;
+                gIlo[j] += lo_;
+                gIhi[j] += hi_;
+            }
+            float* gLprev = SMF(Y.gL0);  // adjoint of Lambda^(0) = Lambda_x
+            const int xld = odd_ld(n);
+            if (ell > 1) {
+                for (int idx = tid; idx < rows * n; idx += NT) {
+                    const int i = idx / n, j = idx - i * n;
+                    const float x = cur[i * ld + j];
+                    float acc = ga[i] * s.cf[j];
+                    for (int k = 0; k < n; ++k) acc = fmaf(gG[i * gld + k], s.Pf[j * n + k], acc);
+                    acc += gRlo[i] * (x > 0.f ? s.Ilof[j] : (x < 0.f ? s.Ihif[j] : 0.f));
+                    acc += gRhi[i] * (x > 0.f ? s.Ihif[j] : (x < 0.f ? s.Ilof[j] : 0.f));
+                    gLprev[i * xld + j] = acc;
+                }
+            }
+            __syncthreads();
+            // ---- chain reverse, levels mm = 1 .. ell-1
+            int prev_ld = xld;
+            int buf = 1;
+            for (int mm = 1; mm <= ell - 1; ++mm) {
+                const int K = N.w[mm], NN = N.w[mm - 1];
+                const float* Wm = s.W(mm - 1);
+                const int wld = odd_ld(NN);
+                const float* Lm = (mm == ell - 1) ? s.W(ell - 1) : (lev + lev_offset(N, ell, mm));
+                const int lmld = odd_ld(K);
+                const float* sl = s.hs + N.hoff[mm];
+                const float* dl = s.hd + N.hoff[mm];
+                const float* bm = s.bs + N.boff[mm - 1];
+                float* gLnext = SMF(buf ? Y.gL1 : Y.gL0);
+                // column j of Lambda_s adjoint: sum_k gLprev[i][k] W_m[j][k] + (gklo_i + gkhi_i) b_m[j]
+                for (int j = tid; j < K; j += NT) {
+                    float acc_s = 0.f, acc_d = 0.f;
+                    for (int i = 0; i < rows; ++i) {
+                        float gls = (gklo[i] + gkhi[i]) * bm[j];
+                        const float* pr = gLprev + i * prev_ld;
+                        for (int k = 0; k < NN; ++k) gls = fmaf(pr[k], Wm[j * wld + k], gls);
+                        const float x = Lm[i * lmld + j];
+                        acc_s = fmaf(gls, x, acc_s);
+                        acc_d += gkhi[i] * posf(x) + gklo[i] * negf(x);
+                        if (mm < ell - 1) {
+                            gLnext[i * lmld + j] = gls * sl[j] + gkhi[i] * (x > 0.f ? dl[j] : 0.f) + gklo[i] * (x < 0.f ? dl[j] : 0.f);
+                        }
+                    }
+                    gs[N.hoff[mm] + j] += acc_s;
+                    gd[N.hoff[mm] + j] += acc_d;
+                }
+                __syncthreads();
+                gLprev = gLnext;
+                prev_ld = lmld;
+                buf ^= 1;
+            }
+        }
+        // ---- TM_t adjoint becomes the incoming adjoint of the previous step
+        for (int idx = tid; idx < n * n; idx += NT) gPn[idx] = gP[idx];
+        for (int i = tid; i < n; i += NT) {
+            gcn[i] = gc[i];
+            gIlon[i] = gIlo[i];
+            gIhin[i] = gIhi[i];
+        }
+        __syncthreads();
+    }
+}
+
+// Keep-best per domain: if V improved, remember the slopes and multipliers.
+__global__ void k_keep_best(const double* __restrict__ V, double* __restrict__ bestV, const float* __restrict__ alpha,
+                            float* __restrict__ best_alpha, const float* __restrict__ beta, float* __restrict__ best_beta,
+                            const int64_t* __restrict__ sp_row, int64_t per_dom) {
+    const int64_t d = blockIdx.x;
+    __shared__ int better;
+    if (threadIdx.x == 0) {
+        better = V[d] < bestV[d];
+        if (better) bestV[d] = V[d];
+    }
+    __syncthreads();
+    if (!better) return;
+    for (int64_t i = threadIdx.x; i < per_dom; i += blockDim.x) best_alpha[d * per_dom + i] = alpha[d * per_dom + i];
+    if (sp_row)
+        for (int64_t k = sp_row[d] + threadIdx.x; k < sp_row[d + 1]; k += blockDim.x) best_beta[k] = beta[k];
+}
+
+// Projected gradient step: x <- clip(x - lr g, lo, hi).
+__global__ void k_pgd(float* __restrict__ x, const float* __restrict__ g, int64_t cnt, float lr, float lo, float hi) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = fminf(fmaxf(x[i] - lr * g[i], lo), hi);
+}
+
+// Sum of D values into out[0] (single block, deterministic order per thread then tree).
+__global__ void k_sum(const double* __restrict__ v, int64_t D, double* __restrict__ out) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < D; i += blockDim.x) acc += v[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0];
+}
