@@ -160,6 +160,50 @@ int dr_set_alpha(dr_ctx* ctx, const float* alpha, int on_device);
 int dr_get_beta(dr_ctx* ctx, float* beta, int on_device);
 int dr_set_beta(dr_ctx* ctx, const float* beta, int on_device);
 
+/* ---- allocation-free slope gradient ----------------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that cannot allocate
+ * device memory, e.g. code running inside a custom memory pool or a real-time loop that forbids
+ * cudaMalloc/cudaFree (which may synchronise the device), or a host that owns all GPU memory
+ * itself.  It computes the same gradient as dr_backward (dV/dalpha of the tube-volume proxy at
+ * user slopes, without split constraints) using only caller-owned inputs and outputs plus a
+ * fixed scratch array that the library reserves statically on every device that loads it.
+ *
+ * All pointers in dr_static_args are device memory of the current device; nothing is copied and
+ * nothing is allocated.  Layouts: W packs the L layers one after another, layer l+1 as an
+ * n_{l+1} x n_l row-major FP32 block; b packs the biases the same way; A [n x n], B [n x m],
+ * e [n] (may be NULL) FP64; lo/hi [D x n] FP64; alpha and dalpha [D x H x hidden] FP32; V [D]
+ * FP64 (may be NULL).  Work is ordered on `stream` (NULL = legacy default stream).
+ *
+ * Limits: D*H*(n^2 + 4n + 2) doubles of scratch must fit DR_STATIC_SCRATCH_BYTES (8 MiB), and
+ * the controller must fit the fused kernels (widths up to a few hundred); larger problems are
+ * rejected with DR_ERR_SHAPE and a message, before any device work.
+ * The first call on a device looks up the scratch address (cudaGetSymbolAddress); make that
+ * first call before capturing a stream into a graph.  Every call shares the same scratch array:
+ * calls that overlap on the GPU (other streams, other threads) race and must be serialised by
+ * the caller.  Each call overwrites the scratch before reading it, so no clearing is needed. */
+#define DR_STATIC_SCRATCH_BYTES (8u << 20)
+
+typedef struct dr_static_args {
+    int32_t L;
+    int32_t widths[9]; /* n_0 .. n_L */
+    const float* W;
+    const float* b;
+    const double* A;
+    const double* B;
+    const double* e;
+    int64_t D;
+    int32_t H;
+    const double* lo;
+    const double* hi;
+    const float* alpha;
+    double margin_rho; /* same meaning as dr_options.margin_rho; 0 selects the default 2^-22 */
+    float* dalpha;
+    double* V;
+    void* stream;
+} dr_static_args;
+
+int dr_slope_gradient_static(const dr_static_args* args);
+
 /* Number of kernels this context has launched (monotone counter, for accounting). */
 int64_t dr_kernel_launches(const dr_ctx* ctx);
 

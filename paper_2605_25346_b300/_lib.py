@@ -21,11 +21,20 @@ EXPORTS = [
     "dr_create", "dr_destroy", "dr_load_controller", "dr_load_dynamics", "dr_set_boxes", "dr_set_splits",
     "dr_set_horizon", "dr_set_options", "dr_compute_bounds", "dr_get_objective", "dr_optimize_slopes",
     "dr_backward", "dr_get_alpha", "dr_set_alpha", "dr_get_beta", "dr_set_beta", "dr_kernel_launches", "dr_last_error",
+    "dr_slope_gradient_static",
 ]
 
 
 class dr_split(ctypes.Structure):
     _fields_ = [("t", ctypes.c_int32), ("layer", ctypes.c_int32), ("neuron", ctypes.c_int32), ("sign", ctypes.c_int32)]
+
+
+class dr_static_args(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("widths", ctypes.c_int32 * 9), ("W", ctypes.c_void_p), ("b", ctypes.c_void_p),
+                ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("e", ctypes.c_void_p), ("D", ctypes.c_int64),
+                ("H", ctypes.c_int32), ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p), ("alpha", ctypes.c_void_p),
+                ("margin_rho", ctypes.c_double), ("dalpha", ctypes.c_void_p), ("V", ctypes.c_void_p),
+                ("stream", ctypes.c_void_p)]
 
 
 class dr_options(ctypes.Structure):
@@ -65,6 +74,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dr_set_beta": (i32, [vp, fp, i32]),
         "dr_kernel_launches": (i64, [vp]),
         "dr_last_error": (ctypes.c_char_p, [vp]),
+        "dr_slope_gradient_static": (i32, [ctypes.POINTER(dr_static_args)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

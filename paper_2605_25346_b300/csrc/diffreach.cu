@@ -851,3 +851,123 @@ int dr_optimize_slopes(dr_ctx* c, int steps, double lr_alpha, double lr_beta, do
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// Allocation-free slope gradient (dr_slope_gradient_static): the reverse sweep with its tape in a
+// statically reserved device array instead of context-owned memory.
+// ------------------------------------------------------------------------------------------------
+
+#include <mutex>
+
+static __device__ __align__(256) double g_static_tape[DR_STATIC_SCRATCH_BYTES / sizeof(double)];
+
+static std::mutex g_static_mu;
+static double* g_static_tape_ptr[64];  // device address of g_static_tape, per device ordinal
+static bool g_static_ready[64];
+
+// Host code cannot use g_static_tape directly (it names a host-side shadow); look up the device
+// address once per device, with that device current.
+static int static_tape_ptr(int dev, double** out) {
+    if (dev < 0 || dev >= 64) return fail(nullptr, DR_ERR_CUDA, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ready[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_tape);
+        if (e != cudaSuccess) return fail(nullptr, DR_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+        g_static_tape_ptr[dev] = reinterpret_cast<double*>(p);
+        g_static_ready[dev] = true;
+    }
+    *out = g_static_tape_ptr[dev];
+    return DR_OK;
+}
+
+extern "C" int dr_slope_gradient_static(const dr_static_args* s) {
+    if (!s) return fail(nullptr, DR_ERR_ARG, "dr_slope_gradient_static: args is NULL");
+    if (s->L < 1 || s->L > DR_MAXL) return fail(nullptr, DR_ERR_SHAPE, "L = %d outside 1..%d", s->L, DR_MAXL);
+    if (!s->W || !s->b || !s->A || !s->B || !s->lo || !s->hi || !s->alpha || !s->dalpha)
+        return fail(nullptr, DR_ERR_ARG, "dr_slope_gradient_static: NULL device pointer");
+    if (s->D < 0 || s->H < 1) return fail(nullptr, DR_ERR_ARG, "D = %lld, H = %d", (long long)s->D, s->H);
+    if (!(s->margin_rho >= 0.0) || s->margin_rho > 1e-2) return fail(nullptr, DR_ERR_ARG, "margin_rho %g", s->margin_rho);
+    NetDesc N{};
+    N.L = s->L;
+    N.maxw = 0;
+    int64_t nw = 0, nb = 0;
+    for (int l = 0; l <= s->L; ++l) {
+        if (s->widths[l] < 1 || s->widths[l] > 4096) return fail(nullptr, DR_ERR_SHAPE, "width[%d] = %d", l, s->widths[l]);
+        N.w[l] = s->widths[l];
+        if (l >= 1) N.maxw = std::max(N.maxw, s->widths[l]);
+    }
+    for (int l = 1; l < s->L; ++l) {
+        N.hoff[l] = N.hidden;
+        N.hidden += N.w[l];
+    }
+    N.hoff[s->L] = N.hidden;
+    for (int l = 0; l < s->L; ++l) {
+        N.Woff[l] = nw;
+        N.boff[l] = nb;
+        nw += (int64_t)N.w[l + 1] * N.w[l];
+        nb += N.w[l + 1];
+    }
+    N.n = N.w[0];
+    N.m = N.w[s->L];
+    N.H = s->H;
+    if (N.n > 64 || N.m > 64) return fail(nullptr, DR_ERR_SHAPE, "n = %d, m = %d (supported 1..64)", N.n, N.m);
+    const double need = (double)s->D * s->H * tape_stride(N) * sizeof(double);
+    if (need > (double)DR_STATIC_SCRATCH_BYTES)
+        return fail(nullptr, DR_ERR_SHAPE,
+                    "dr_slope_gradient_static: needs %.0f bytes of scratch for D=%lld, H=%d, n=%d; the static limit is %u bytes",
+                    need, (long long)s->D, s->H, N.n, (unsigned)DR_STATIC_SCRATCH_BYTES);
+    const FusedLayout fwd = fused_layout(N, false), bwd = fused_layout(N, true);
+    if (bwd.total > kMaxSmem) return fail(nullptr, DR_ERR_SHAPE, "controller too wide for the fused kernels");
+    if (s->D == 0) return DR_OK;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(nullptr, DR_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    double* tape = nullptr;
+    TRY(static_tape_ptr(dev, &tape));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(s->stream);
+
+    FusedArgs a;
+    memset(&a, 0, sizeof(a));
+    a.net = N;
+    a.W = s->W;
+    a.b = s->b;
+    a.A = s->A;
+    a.B = s->B;
+    a.e = s->e;
+    a.lo0 = s->lo;
+    a.hi0 = s->hi;
+    a.alpha = s->alpha;
+    a.mode = DR_SLOPE_USER_K;
+    a.rho = (float)(s->margin_rho > 0.0 ? s->margin_rho : std::ldexp(1.0, -22));
+    a.V = s->V;
+    a.tape = tape;
+    a.tape_stride = tape_stride(N);
+    a.dalpha = s->dalpha;
+    const int nt = fused_threads(N);
+    const int64_t chunk = 1 << 20;
+    for (int pass = 0; pass < 2; ++pass) {
+        a.lay = pass == 0 ? fwd : bwd;
+        const int smem = a.lay.total;
+        for (int64_t d0 = 0; d0 < s->D; d0 += chunk) {
+            a.d0 = d0;
+            const unsigned nd = (unsigned)std::min(chunk, s->D - d0);
+            if (pass == 0 && nt == 128) {
+                CUDA_TRY(nullptr, cudaFuncSetAttribute(k_fused_forward<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                k_fused_forward<128><<<nd, 128, smem, st>>>(a);
+            } else if (pass == 0) {
+                CUDA_TRY(nullptr, cudaFuncSetAttribute(k_fused_forward<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                k_fused_forward<256><<<nd, 256, smem, st>>>(a);
+            } else if (nt == 128) {
+                CUDA_TRY(nullptr, cudaFuncSetAttribute(k_fused_backward<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                k_fused_backward<128><<<nd, 128, smem, st>>>(a);
+            } else {
+                CUDA_TRY(nullptr, cudaFuncSetAttribute(k_fused_backward<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                k_fused_backward<256><<<nd, 256, smem, st>>>(a);
+            }
+            CUDA_TRY(nullptr, cudaGetLastError());
+        }
+        a.V = nullptr;
+    }
+    return DR_OK;
+}
