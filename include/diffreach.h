@@ -78,11 +78,18 @@ typedef struct dr_split {
 typedef struct dr_options {
     int32_t slope_mode;    /* DR_SLOPE_*, default DR_SLOPE_CHORD                                */
     int32_t precision;     /* DR_PREC_*, default DR_PREC_AUTO                                   */
-    double margin_rho;     /* outward margin rho: every FP32 concretisation is widened by
-                              rho * S, S the L1 magnitude of its summed terms; default 2^-22   */
+    double margin_rho;     /* optional outward margin inside the pass: every FP32 concretisation
+                              (pre-activation bounds, controller remainder, split constraint)
+                              is widened by rho * S, S the L1 magnitude of its summed terms.
+                              Default 0: such margins compound through the closed loop.      */
     int64_t chunk_domains; /* domains per device pass (bounds scratch memory); 0 = automatic    */
     int64_t mem_cap_bytes; /* cap on library-owned device memory; 0 = no cap                    */
-    int32_t reserved[8];
+    double box_margin;     /* outward margin of every reported box: lo -= b*S_box, hi += b*S_box,
+                              S_box = |c| + sum|P| + |I| + |w| + sum|v| of the FP64 Taylor model;
+                              default 2^-18, calibrated to cover the measured deviation of the
+                              FP32 controller pass from FP64 arithmetic (it does not feed back
+                              into the Taylor model)                                        */
+    int32_t reserved[6];
 } dr_options;
 
 /* Create a context on `device` whose work is ordered on `cuda_stream` (a cudaStream_t;
@@ -126,7 +133,7 @@ int dr_set_options(dr_ctx* ctx, const dr_options* opt);
  *   hull_lo/hull_hi [(H+1) x n]      min/max over domains without DR_STATUS_INFEASIBLE
  *   status          [D]              DR_STATUS_* bits
  * Any output may be NULL.  out_on_device selects device (1) or host (0) outputs.
- * Boxes are FP64, concretised in FP64 from the FP64 TM and pushed outward. */
+ * Boxes are FP64, concretised in FP64 from the FP64 TM and pushed outward by box_margin. */
 int dr_compute_bounds(dr_ctx* ctx, double* lo, double* hi, double* hull_lo, double* hull_hi,
                       uint32_t* status, int out_on_device);
 
@@ -196,7 +203,7 @@ typedef struct dr_static_args {
     const double* lo;
     const double* hi;
     const float* alpha;
-    double margin_rho; /* same meaning as dr_options.margin_rho; 0 selects the default 2^-22 */
+    double margin_rho; /* same meaning as dr_options.margin_rho (0 = none) */
     float* dalpha;
     double* V;
     void* stream;

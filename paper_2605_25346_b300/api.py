@@ -14,6 +14,7 @@ import torch
 from . import _lib
 from ._lib import check
 
+BOX_MARGIN = 2.0 ** -18  # default outward margin of reported boxes (relative to their L1 magnitude)
 _MODE = {0: _lib.DR_SLOPE_ADAPTIVE, 1: _lib.DR_SLOPE_CHORD, 2: _lib.DR_SLOPE_ZERO, 3: _lib.DR_SLOPE_USER}
 
 
@@ -53,13 +54,14 @@ class Reach:
 
     # ---- problem upload -------------------------------------------------------------------
     def set_options(self, mode: Optional[int] = None, precision: int = _lib.DR_PREC_AUTO, rho: Optional[float] = None,
-                    chunk: int = 0, mem_cap: int = 0):
+                    chunk: int = 0, mem_cap: int = 0, box_margin: Optional[float] = None):
         o = _lib.dr_options()
         o.slope_mode = _MODE[mode] if mode is not None else _lib.DR_SLOPE_CHORD
         o.precision = precision
-        o.margin_rho = 2.0 ** -22 if rho is None else rho
+        o.margin_rho = 0.0 if rho is None else rho
         o.chunk_domains = chunk
         o.mem_cap_bytes = mem_cap
+        o.box_margin = BOX_MARGIN if box_margin is None else box_margin
         self._c(self.lib.dr_set_options(self.ctx, ctypes.byref(o)))
 
     def load(self, prob, mode: Optional[int] = None, rho: Optional[float] = None, precision: int = _lib.DR_PREC_AUTO,

@@ -14,6 +14,7 @@
 #include "common.cuh"
 #include "fused_core.cuh"
 #include "fused_bwd.cuh"
+#include "wide.cuh"
 
 
 struct dr_ctx {
@@ -66,6 +67,10 @@ struct dr_ctx {
     double* dVhist = nullptr;
     double* dwlo = nullptr;
     double* dwhi = nullptr;
+    // staged (wide) path chunk scratch
+    void* wscratch = nullptr;
+    size_t wscratch_bytes = 0;
+    int wDc = 0;
 };
 
 static thread_local std::string g_create_err;
@@ -123,7 +128,8 @@ static dr_options default_options() {
     memset(&o, 0, sizeof(o));
     o.slope_mode = DR_SLOPE_CHORD;
     o.precision = DR_PREC_AUTO;
-    o.margin_rho = std::ldexp(1.0, -22);
+    o.margin_rho = 0.0;
+    o.box_margin = std::ldexp(1.0, -18);
     o.chunk_domains = 0;
     o.mem_cap_bytes = 0;
     return o;
@@ -284,6 +290,9 @@ static void free_outputs(dr_ctx* c) {
     dev_free(c, (void*&)c->dVhist, 0);
     dev_free(c, (void*&)c->dwlo, 0);
     dev_free(c, (void*&)c->dwhi, 0);
+    dev_free(c, c->wscratch, c->wscratch_bytes);
+    c->wscratch_bytes = 0;
+    c->wDc = 0;
     c->out_bytes = 0;
     c->tape_bytes = 0;
 }
@@ -318,6 +327,7 @@ int dr_set_options(dr_ctx* c, const dr_options* o) {
     if (n.slope_mode < 0 || n.slope_mode > 3) return fail(c, DR_ERR_ARG, "slope_mode %d out of range", n.slope_mode);
     if (n.precision < 0 || n.precision > 2) return fail(c, DR_ERR_ARG, "precision %d out of range", n.precision);
     if (!(n.margin_rho >= 0.0) || n.margin_rho > 1e-2) return fail(c, DR_ERR_ARG, "margin_rho %g out of range", n.margin_rho);
+    if (!(n.box_margin >= 0.0) || n.box_margin > 1e-2) return fail(c, DR_ERR_ARG, "box_margin %g out of range", n.box_margin);
     if (n.chunk_domains < 0 || n.mem_cap_bytes < 0) return fail(c, DR_ERR_ARG, "negative chunk or memory cap");
     if (n.slope_mode == DR_SLOPE_USER && !c->alpha_set && c->D > 0)
         return fail(c, DR_ERR_STATE, "DR_SLOPE_USER requires dr_set_alpha first");
@@ -555,16 +565,188 @@ static int ensure_tape(dr_ctx* c) {
     return DR_OK;
 }
 
+// ------------------------------------------------------------------------------------------------
+// staged (wide) path
+// ------------------------------------------------------------------------------------------------
+
+static int64_t wide_lam_stride(const NetDesc& N) {
+    int64_t best = 1;
+    for (int l = 2; l <= N.L; ++l)
+        for (int k = 0; k <= l - 1; ++k) best = std::max<int64_t>(best, (int64_t)N.w[l] * N.w[k]);
+    return best;
+}
+
+static size_t wide_bytes_per_domain(const NetDesc& N) {
+    const int n = N.n, m = N.m;
+    size_t b = 0;
+    b += sizeof(double) * (n + n * n + n + n + n + 2);           // c, P, Ilo, Ihi, v, w, vacc
+    b += sizeof(int) + sizeof(uint32_t);                          // cursor, status
+    b += sizeof(float) * (n + n * n + n + n + n + 1);            // FP32 view
+    b += sizeof(float) * 4 * std::max(N.hidden, 1);               // l, u, s, d
+    b += sizeof(float) * 2 * N.maxw;                              // kappa
+    b += sizeof(float) * ((size_t)N.maxw * n + 4 * N.maxw);       // G, a, R, S
+    b += sizeof(float) * 3 * m;                                   // controller TM
+    b += sizeof(float) * 2 * wide_lam_stride(N);                  // Lambda ping-pong
+    return b + 16 * 24;
+}
+
+// Carve the chunk scratch for Dc domains out of one allocation.
+static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, float** lamA, float** lamB) {
+    const NetDesc& N = a.net;
+    const size_t need = wide_bytes_per_domain(N) * (size_t)Dc + 4096;
+    if (!c->wscratch || c->wscratch_bytes < need || c->wDc != Dc) {
+        dev_free(c, c->wscratch, c->wscratch_bytes);
+        unsigned char* p = nullptr;
+        TRY(dev_alloc(c, p, need));
+        c->wscratch = p;
+        c->wscratch_bytes = need;
+        c->wDc = Dc;
+    }
+    unsigned char* base = reinterpret_cast<unsigned char*>(c->wscratch);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = (off + 255) & ~size_t(255);
+        void* r = base + off;
+        off += bytes;
+        return r;
+    };
+    const int n = N.n, m = N.m;
+    const size_t D = (size_t)Dc;
+    a.c = (double*)take(sizeof(double) * D * n);
+    a.P = (double*)take(sizeof(double) * D * n * n);
+    a.Ilo = (double*)take(sizeof(double) * D * n);
+    a.Ihi = (double*)take(sizeof(double) * D * n);
+    a.v = (double*)take(sizeof(double) * D * n);
+    a.w = (double*)take(sizeof(double) * D);
+    a.vacc = (double*)take(sizeof(double) * D);
+    a.cursor = (int*)take(sizeof(int) * D);
+    a.st = (uint32_t*)take(sizeof(uint32_t) * D);
+    a.cf = (float*)take(sizeof(float) * D * n);
+    a.Pf = (float*)take(sizeof(float) * D * n * n);
+    a.Ilof = (float*)take(sizeof(float) * D * n);
+    a.Ihif = (float*)take(sizeof(float) * D * n);
+    a.vf = (float*)take(sizeof(float) * D * (n + 1));
+    const size_t hid = std::max(N.hidden, 1);
+    a.hl = (float*)take(sizeof(float) * D * hid);
+    a.hu = (float*)take(sizeof(float) * D * hid);
+    a.hs = (float*)take(sizeof(float) * D * hid);
+    a.hd = (float*)take(sizeof(float) * D * hid);
+    a.klo = (float*)take(sizeof(float) * D * N.maxw);
+    a.khi = (float*)take(sizeof(float) * D * N.maxw);
+    a.G = (float*)take(sizeof(float) * D * N.maxw * n);
+    a.sa = (float*)take(sizeof(float) * D * N.maxw);
+    a.sRlo = (float*)take(sizeof(float) * D * N.maxw);
+    a.sRhi = (float*)take(sizeof(float) * D * N.maxw);
+    a.sS = (float*)take(sizeof(float) * D * N.maxw);
+    a.cu = (float*)take(sizeof(float) * D * m);
+    a.Iulo = (float*)take(sizeof(float) * D * m);
+    a.Iuhi = (float*)take(sizeof(float) * D * m);
+    a.lam_stride = wide_lam_stride(N);
+    *lamA = (float*)take(sizeof(float) * D * a.lam_stride);
+    *lamB = (float*)take(sizeof(float) * D * a.lam_stride);
+    if (off > c->wscratch_bytes) return fail(c, DR_ERR_OOM, "staged scratch layout overflow");
+    return DR_OK;
+}
+
+static int wide_chunk(dr_ctx* c, const NetDesc& N) {
+    if (c->opt.chunk_domains > 0) return (int)std::min<int64_t>(std::min<int64_t>(c->opt.chunk_domains, c->D), 65535);
+    const size_t budget = size_t(4) << 30;
+    const int64_t dc = std::max<int64_t>(1, (int64_t)(budget / wide_bytes_per_domain(N)));
+    return (int)std::min<int64_t>(std::min<int64_t>(dc, c->D), 65535);
+}
+
+static inline unsigned blocks_for(int64_t threads, int bs) { return (unsigned)((threads + bs - 1) / bs); }
+
+static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
+    NetDesc N = c->net;
+    N.H = c->H;
+    const int n = N.n, L = N.L, H = N.H;
+    WideArgs a;
+    memset(&a, 0, sizeof(a));
+    a.net = N;
+    a.W = c->dW;
+    a.b = c->db;
+    a.A = c->dA;
+    a.B = c->dB;
+    a.e = c->de;
+    a.lo0 = c->dlo0;
+    a.hi0 = c->dhi0;
+    a.sp_row = c->nnz ? c->dsp_row : nullptr;
+    a.sp = c->dsp;
+    a.beta = c->dbeta;
+    a.alpha = c->dalpha;
+    a.mode = mode;
+    a.rho = (float)c->opt.margin_rho;
+    a.box_margin = c->opt.box_margin;
+    a.lo = c->dout_lo;
+    a.hi = c->dout_hi;
+    a.V = c->dV;
+    a.status = c->dstatus;
+    a.alpha_used = alpha_used;
+    const int Dc = wide_chunk(c, N);
+    float *lamA = nullptr, *lamB = nullptr;
+    TRY(wide_bind(c, a, Dc, &lamA, &lamB));
+    const size_t dyn_smem = sizeof(double) * (n * n + 3 * n + 128);
+    for (int64_t d0 = 0; d0 < c->D; d0 += Dc) {
+        a.d0 = d0;
+        a.Dc = (int)std::min<int64_t>(Dc, c->D - d0);
+        const int dc = a.Dc;
+        k_w_seed<<<blocks_for((int64_t)dc * n, 256), 256, 0, c->stream>>>(a);
+        c->launches++;
+        for (int t = 0; t < H; ++t) {
+            k_w_view<<<dc, 128, 0, c->stream>>>(a);
+            c->launches++;
+            for (int ell = 1; ell <= L; ++ell) {
+                const int rows = N.w[ell];
+                const int64_t warps = (int64_t)dc * rows;
+                k_w_chain_init<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, ell, lamA);
+                c->launches++;
+                float* cur = lamA;
+                float* nxt = lamB;
+                for (int mm = ell - 1; mm >= 1; --mm) {
+                    const int K = N.w[mm], NN = N.w[mm - 1];
+                    const float* Wm = c->dW + N.Woff[mm - 1];
+                    dim3 grid((NN + 63) / 64, (rows + 63) / 64, dc);
+                    k_w_gemm_simt<<<grid, 256, 0, c->stream>>>(cur, Wm, nxt, rows, K, NN, a.lam_stride);
+                    c->launches++;
+                    if (mm - 1 >= 1) {
+                        k_w_level_epi<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, ell, mm - 1, nxt);
+                        c->launches++;
+                    }
+                    std::swap(cur, nxt);
+                }
+                if (ell == 1) k_w_project<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, 1, c->dW + N.Woff[0], 1);
+                else k_w_project<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, ell, cur, 0);
+                c->launches++;
+                if (ell < L) {
+                    k_w_relax<<<dc, 256, 0, c->stream>>>(a, ell, t);
+                    c->launches++;
+                }
+            }
+            k_w_dyn<<<dc, 128, dyn_smem, c->stream>>>(a, t);
+            c->launches++;
+        }
+        CUDA_TRY(c, cudaGetLastError());
+    }
+    return DR_OK;
+}
+
 // Forward pass over all domains into the library-owned buffers (optionally recording the tape
-// and the slopes in effect).
+// and the slopes in effect).  The fused kernel serves controllers that fit in shared memory
+// (DR_PREC_AUTO); DR_PREC_SIMT / DR_PREC_TF32X3 and wider controllers take the staged path.
+static bool use_fused(const dr_ctx* c) {
+    return c->opt.precision == DR_PREC_AUTO && fused_fits(c->net);
+}
+
 static int run_forward(dr_ctx* c, int mode, float* alpha_used, bool tape) {
     NetDesc N = c->net;
     N.H = c->H;
     if (c->D == 0) return DR_OK;
-    if (!fused_fits(N) || c->opt.precision == DR_PREC_TF32X3)
-        return fail(c, DR_ERR_SHAPE, "controller too wide for the fused kernel (%d bytes of shared memory)",
-                    fused_layout(N).total);
     if (mode == DR_SLOPE_USER && !c->dalpha) return fail(c, DR_ERR_STATE, "no slopes set");
+    if (!use_fused(c)) {
+        if (tape) return fail(c, DR_ERR_SHAPE, "the reverse sweep needs a controller that fits the fused kernel");
+        return run_forward_wide(c, mode, alpha_used);
+    }
     if (tape) TRY(ensure_tape(c));
     FusedArgs a;
     memset(&a, 0, sizeof(a));
@@ -583,6 +765,7 @@ static int run_forward(dr_ctx* c, int mode, float* alpha_used, bool tape) {
     a.alpha = c->dalpha;
     a.mode = mode;
     a.rho = (float)c->opt.margin_rho;
+    a.box_margin = c->opt.box_margin;
     a.lo = c->dout_lo;
     a.hi = c->dout_hi;
     a.V = c->dV;
@@ -939,7 +1122,8 @@ extern "C" int dr_slope_gradient_static(const dr_static_args* s) {
     a.hi0 = s->hi;
     a.alpha = s->alpha;
     a.mode = DR_SLOPE_USER_K;
-    a.rho = (float)(s->margin_rho > 0.0 ? s->margin_rho : std::ldexp(1.0, -22));
+    a.rho = (float)s->margin_rho;
+    a.box_margin = std::ldexp(1.0, -18);
     a.V = s->V;
     a.tape = tape;
     a.tape_stride = tape_stride(N);

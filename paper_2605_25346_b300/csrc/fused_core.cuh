@@ -55,6 +55,7 @@ struct FusedArgs {
     const float* alpha;     // [D][H][hidden] (USER) or null
     int mode;
     float rho;
+    double box_margin;
     double* lo;  // [D][H+1][n] or null
     double* hi;
     double* V;          // [D] or null
@@ -404,8 +405,8 @@ __device__ void dynamics(const Dom& s, const NetDesc& N) {
     __syncthreads();
 }
 
-// a8: EvalInt of the TM in cn/Pn/Ilon/Ihin with the current dual, outward by 2^-50 of the summed
-// magnitude.  Returns this thread's width sum contribution.
+// a8: EvalInt of the TM in cn/Pn/Ilon/Ihin with the current dual, outward by box_margin times the
+// summed magnitude.  Returns this thread's width sum contribution.
 template <int NT>
 __device__ double eval_box(const Dom& s, const NetDesc& N, const FusedArgs& a, int64_t dom, int t1) {
     const int n = N.n, H = N.H;
@@ -418,8 +419,8 @@ __device__ double eval_box(const Dom& s, const NetDesc& N, const FusedArgs& a, i
             pp += fabs(x + s.v[k]);
             mag += fabs(x) + fabs(s.v[k]);
         }
-        const double bl = s.cn[i] + s.Ilon[i] - pm - s.wv[0] - 0x1p-50 * mag;
-        const double bh = s.cn[i] + s.Ihin[i] + pp + s.wv[0] + 0x1p-50 * mag;
+        const double bl = s.cn[i] + s.Ilon[i] - pm - s.wv[0] - a.box_margin * mag;
+        const double bh = s.cn[i] + s.Ihin[i] + pp + s.wv[0] + a.box_margin * mag;
         if (a.lo) a.lo[(dom * (H + 1) + t1) * n + i] = bl;
         if (a.hi) a.hi[(dom * (H + 1) + t1) * n + i] = bh;
         vsum += bh - bl;

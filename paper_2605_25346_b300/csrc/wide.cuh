@@ -1,0 +1,434 @@
+// Staged forward pass for wide controllers (widths beyond the fused kernel's shared memory).
+//
+// Domains are processed in chunks; per closed-loop step (Alg. 2, closed loop of Sec. IV-E) the
+// phases are separate kernels over the whole chunk, with per-domain state in global scratch:
+//   view     FP64 TM -> FP32 view (remainder widened to cover the cast)
+//   for each target layer l = 1..L:
+//     init   kappa = b_l; first chain level from the shared W_l: Lambda^+/- intercepts with the
+//            relaxation of layer l-1 and A = W_l diag(s_{l-1}) per domain
+//     levels Lambda <- A W_m (batched GEMM, shared W_m; tensor cores or CUDA cores), then the
+//            next level's intercepts and A = Lambda diag(s_{m-1}) (row reductions)      (Thm. 2)
+//     proj   G = Lambda_x P, a = Lambda_x c, R = Lambda_x (x) I, concretisation with the
+//            split dual and the outward margin (Thm. 3), or the controller TM
+//     relax  split clipping / dual records, shared-slope relaxation              (Sec. IV-C)
+//   dyn      FP64 dynamics on the TM and EvalInt (Alg. 2)
+#pragma once
+#include "common.cuh"
+
+struct WideArgs {
+    NetDesc net;
+    const float* W;
+    const float* b;
+    const double* A;
+    const double* B;
+    const double* e;
+    const double* lo0;
+    const double* hi0;
+    int64_t d0;  // first domain of the chunk
+    int Dc;      // domains in the chunk
+    const int64_t* sp_row;
+    const SplitRec* sp;
+    const float* beta;
+    const float* alpha;
+    int mode;
+    float rho;
+    double box_margin;
+    double* lo;
+    double* hi;
+    double* V;
+    uint32_t* status;
+    float* alpha_used;
+    // chunk scratch (index = domain within the chunk)
+    double *c, *P, *Ilo, *Ihi, *v, *w, *vacc;
+    int* cursor;
+    uint32_t* st;
+    float *cf, *Pf, *Ilof, *Ihif, *vf;  // vf: [Dc][n+1] (last = wf)
+    float *hl, *hu, *hs, *hd;           // [Dc][hidden]
+    float *klo, *khi;                   // [Dc][maxw]
+    float *G, *sa, *sRlo, *sRhi, *sS;   // [Dc][maxw][n], [Dc][maxw]
+    float *cu, *Iulo, *Iuhi;            // [Dc][m]
+    int64_t lam_stride;                 // floats per domain in a Lambda buffer
+};
+
+__device__ __forceinline__ float warp_sum(float x) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// a1 + box_0: seed the TM of every domain in the chunk.
+__global__ void k_w_seed(const WideArgs a) {
+    const NetDesc& N = a.net;
+    const int n = N.n, H = N.H;
+    const int64_t total = (int64_t)a.Dc * n;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int d = (int)(idx / n), i = (int)(idx - (int64_t)d * n);
+        const int64_t dom = a.d0 + d;
+        const double lo = a.lo0[dom * n + i], hi = a.hi0[dom * n + i];
+        a.c[idx] = 0.5 * (lo + hi);
+        for (int k = 0; k < n; ++k) a.P[(int64_t)d * n * n + i * n + k] = (i == k) ? 0.5 * (hi - lo) : 0.0;
+        a.Ilo[idx] = 0.0;
+        a.Ihi[idx] = 0.0;
+        a.v[idx] = 0.0;
+        if (a.lo) a.lo[(dom * (H + 1)) * n + i] = lo;
+        if (a.hi) a.hi[(dom * (H + 1)) * n + i] = hi;
+        if (i == 0) {
+            a.w[d] = 0.0;
+            a.vacc[d] = 0.0;
+            a.st[d] = 0u;
+            a.cursor[d] = a.sp_row ? (int)a.sp_row[dom] : 0;
+        }
+    }
+}
+
+// FP32 view of each domain's TM; one block per domain.
+__global__ void k_w_view(const WideArgs a) {
+    const int n = a.net.n, d = blockIdx.x;
+    const double* P = a.P + (int64_t)d * n * n;
+    float* Pf = a.Pf + (int64_t)d * n * n;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) Pf[idx] = (float)P[idx];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double ci = a.c[(int64_t)d * n + i];
+        const float cf = (float)ci;
+        double dev = 0.0;
+        for (int k = 0; k < n; ++k) dev += fabs(P[i * n + k] - (double)(float)P[i * n + k]);
+        const double dc = ci - (double)cf;
+        a.cf[(int64_t)d * n + i] = cf;
+        a.Ilof[(int64_t)d * n + i] = __double2float_rd(a.Ilo[(int64_t)d * n + i] + dc - dev);
+        a.Ihif[(int64_t)d * n + i] = __double2float_ru(a.Ihi[(int64_t)d * n + i] + dc + dev);
+    }
+    if (threadIdx.x == 0) {
+        double dv = 0.0;
+        float* vf = a.vf + (int64_t)d * (n + 1);
+        for (int k = 0; k < n; ++k) {
+            vf[k] = (float)a.v[(int64_t)d * n + k];
+            dv += fabs(a.v[(int64_t)d * n + k] - (double)vf[k]);
+        }
+        vf[n] = __double2float_ru(a.w[d] + dv);
+    }
+}
+
+// Target ell: kappa = b_ell and, for ell >= 2, the first chain level from the shared W_ell:
+// intercepts with the relaxation of layer ell-1 and A = W_ell diag(s_{ell-1}) into Aout.
+// One warp per (domain, row).
+__global__ void k_w_chain_init(const WideArgs a, int ell, float* __restrict__ Aout) {
+    const NetDesc& N = a.net;
+    const int rows = N.w[ell];
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= (int64_t)a.Dc * rows) return;
+    const int d = (int)(wid / rows), i = (int)(wid - (int64_t)d * rows);
+    const float bi = a.b[N.boff[ell - 1] + i];
+    if (ell == 1) {
+        if (lane == 0) {
+            a.klo[(int64_t)d * N.maxw + i] = bi;
+            a.khi[(int64_t)d * N.maxw + i] = bi;
+        }
+        return;
+    }
+    const int K = N.w[ell - 1];
+    const float* Wrow = a.W + N.Woff[ell - 1] + (int64_t)i * K;
+    const float* s = a.hs + (int64_t)d * N.hidden + N.hoff[ell - 1];
+    const float* dd = a.hd + (int64_t)d * N.hidden + N.hoff[ell - 1];
+    const float* bm = a.b + N.boff[ell - 2];
+    float* out = Aout + (int64_t)d * a.lam_stride + (int64_t)i * K;
+    float spos = 0.f, sneg = 0.f, sb = 0.f;
+    for (int j = lane; j < K; j += 32) {
+        const float x = Wrow[j];
+        spos = fmaf(posf(x), dd[j], spos);
+        sneg = fmaf(negf(x), dd[j], sneg);
+        const float xs = x * s[j];
+        sb = fmaf(xs, bm[j], sb);
+        out[j] = xs;
+    }
+    spos = warp_sum(spos);
+    sneg = warp_sum(sneg);
+    sb = warp_sum(sb);
+    if (lane == 0) {
+        a.khi[(int64_t)d * N.maxw + i] = bi + spos + sb;
+        a.klo[(int64_t)d * N.maxw + i] = bi + sneg + sb;
+    }
+}
+
+// After a GEMM level produced Lambda^(mm) (mm >= 1) in buf [d][i][k], k < n_mm: the intercepts of the
+// relaxation of layer mm and, in place, A = Lambda diag(s_mm).  One warp per (domain, row).
+__global__ void k_w_level_epi(const WideArgs a, int ell, int mm, float* __restrict__ buf) {
+    const NetDesc& N = a.net;
+    const int rows = N.w[ell], K = N.w[mm];
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= (int64_t)a.Dc * rows) return;
+    const int d = (int)(wid / rows), i = (int)(wid - (int64_t)d * rows);
+    const float* s = a.hs + (int64_t)d * N.hidden + N.hoff[mm];
+    const float* dd = a.hd + (int64_t)d * N.hidden + N.hoff[mm];
+    const float* bm = a.b + N.boff[mm - 1];
+    float* row = buf + (int64_t)d * a.lam_stride + (int64_t)i * K;
+    float spos = 0.f, sneg = 0.f, sb = 0.f;
+    for (int j = lane; j < K; j += 32) {
+        const float x = row[j];
+        spos = fmaf(posf(x), dd[j], spos);
+        sneg = fmaf(negf(x), dd[j], sneg);
+        const float xs = x * s[j];
+        sb = fmaf(xs, bm[j], sb);
+        row[j] = xs;
+    }
+    spos = warp_sum(spos);
+    sneg = warp_sum(sneg);
+    sb = warp_sum(sb);
+    if (lane == 0) {
+        a.khi[(int64_t)d * N.maxw + i] += spos + sb;
+        a.klo[(int64_t)d * N.maxw + i] += sneg + sb;
+    }
+}
+
+// Batched C[d] = A[d] B with A[d] M x K (row-major, ld K), B K x N shared (row-major, ld N),
+// C[d] M x N (ld N); CUDA-core FP32, 64x64 tiles, 4x4 per thread.
+__global__ void __launch_bounds__(256) k_w_gemm_simt(const float* __restrict__ Ab, const float* __restrict__ B,
+                                                     float* __restrict__ Cb, int M, int K, int N, int64_t stride) {
+    __shared__ float As[16][64 + 4];
+    __shared__ float Bs[16][64 + 4];
+    const float* A = Ab + blockIdx.z * stride;
+    float* C = Cb + blockIdx.z * stride;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int idx = threadIdx.x; idx < 64 * 16; idx += 256) {
+            const int r = idx >> 4, q = idx & 15;
+            const int gm = m0 + r, gk = k0 + q;
+            As[q][r] = (gm < M && gk < K) ? A[(int64_t)gm * K + gk] : 0.f;
+            const int br = idx >> 6, bc = idx & 63;
+            const int gk2 = k0 + br, gn = n0 + bc;
+            Bs[br][bc] = (gk2 < K && gn < N) ? B[(int64_t)gk2 * N + gn] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            float ar[4], br[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) ar[u] = As[q][ty * 4 + u];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) br[u] = Bs[q][tx * 4 + u];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) acc[u][w] = fmaf(ar[u], br[w], acc[u][w]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int gm = m0 + ty * 4 + u;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int gn = n0 + tx * 4 + w;
+            if (gn < N) C[(int64_t)gm * N + gn] = acc[u][w];
+        }
+    }
+}
+
+// Concretisation of target ell over the TM input.  One warp per (domain, row); Lx is the
+// domain's Lambda_x (rows x n, ld n) or, for ell == 1, the shared W_1.
+__global__ void k_w_project(const WideArgs a, int ell, const float* __restrict__ Lxb, int shared_lx) {
+    const NetDesc& N = a.net;
+    const int n = N.n, L = N.L, rows = N.w[ell];
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= (int64_t)a.Dc * rows) return;
+    const int d = (int)(wid / rows), i = (int)(wid - (int64_t)d * rows);
+    const float* Lx = shared_lx ? (Lxb + (int64_t)i * n) : (Lxb + (int64_t)d * a.lam_stride + (int64_t)i * n);
+    const float* Pf = a.Pf + (int64_t)d * n * n;
+    const float* cf = a.cf + (int64_t)d * n;
+    const float* Ilof = a.Ilof + (int64_t)d * n;
+    const float* Ihif = a.Ihif + (int64_t)d * n;
+    const float* vf = a.vf + (int64_t)d * (n + 1);
+    float* G = a.G + ((int64_t)d * N.maxw + i) * n;
+    float g1 = 0.f, gm = 0.f, gp = 0.f;
+    for (int k = lane; k < n; k += 32) {
+        float acc = 0.f;
+        for (int j = 0; j < n; ++j) acc = fmaf(Lx[j], Pf[j * n + k], acc);
+        G[k] = acc;
+        g1 += fabsf(acc);
+        gm += fabsf(acc - vf[k]);
+        gp += fabsf(acc + vf[k]);
+    }
+    float av = 0.f, rlo = 0.f, rhi = 0.f;
+    for (int j = lane; j < n; j += 32) {
+        const float x = Lx[j];
+        av = fmaf(x, cf[j], av);
+        rlo = fmaf(posf(x), Ilof[j], fmaf(negf(x), Ihif[j], rlo));
+        rhi = fmaf(posf(x), Ihif[j], fmaf(negf(x), Ilof[j], rhi));
+    }
+    g1 = warp_sum(g1);
+    gm = warp_sum(gm);
+    gp = warp_sum(gp);
+    av = warp_sum(av);
+    rlo = warp_sum(rlo);
+    rhi = warp_sum(rhi);
+    if (lane != 0) return;
+    const float klo = a.klo[(int64_t)d * N.maxw + i], khi = a.khi[(int64_t)d * N.maxw + i];
+    const float wf = vf[n];
+    const float S = fabsf(av) + g1 + fabsf(klo) + fabsf(khi) + fabsf(rlo) + fabsf(rhi) + fabsf(wf);
+    if (ell < L) {
+        a.hl[(int64_t)d * N.hidden + N.hoff[ell] + i] = av + klo + rlo - gm - wf - a.rho * S;
+        a.hu[(int64_t)d * N.hidden + N.hoff[ell] + i] = av + khi + rhi + gp + wf + a.rho * S;
+        a.sa[(int64_t)d * N.maxw + i] = av;
+        a.sRlo[(int64_t)d * N.maxw + i] = rlo;
+        a.sRhi[(int64_t)d * N.maxw + i] = rhi;
+        a.sS[(int64_t)d * N.maxw + i] = S;
+    } else {
+        a.cu[(int64_t)d * N.m + i] = av + 0.5f * (klo + khi);
+        a.Iulo[(int64_t)d * N.m + i] = 0.5f * (klo - khi) + rlo - a.rho * S;
+        a.Iuhi[(int64_t)d * N.m + i] = 0.5f * (khi - klo) + rhi + a.rho * S;
+    }
+}
+
+// Splits of (t, ell) and the shared-slope relaxation of hidden layer ell; one block per domain.
+__global__ void k_w_relax(const WideArgs a, int ell, int t) {
+    const NetDesc& N = a.net;
+    const int n = N.n, rows = N.w[ell], H = N.H, d = blockIdx.x;
+    const int64_t dom = a.d0 + d;
+    float* lh = a.hl + (int64_t)d * N.hidden + N.hoff[ell];
+    float* uh = a.hu + (int64_t)d * N.hidden + N.hoff[ell];
+    if (threadIdx.x == 0 && a.sp_row) {
+        const int64_t sp_end = a.sp_row[dom + 1];
+        int cpos = a.cursor[d];
+        bool changed = false;
+        while (cpos < sp_end) {
+            const SplitRec r = a.sp[cpos];
+            if (r.t > t || (r.t == t && r.layer > ell)) break;
+            if (r.t == t && r.layer == ell) {
+                const int j = r.neuron;
+                const int64_t q = (int64_t)d * N.maxw + j;
+                const float bt = a.beta ? a.beta[cpos] : 0.f;
+                const float hh = r.sign > 0 ? (a.sa[q] + a.khi[q] + a.sRhi[q] + a.rho * a.sS[q])
+                                            : (-(a.sa[q] + a.klo[q] + a.sRlo[q]) + a.rho * a.sS[q]);
+                if (r.sign > 0) {
+                    if (lh[j] < 0.f) lh[j] = 0.f;
+                } else {
+                    if (uh[j] > 0.f) uh[j] = 0.f;
+                }
+                if (bt != 0.f) {
+                    const float* Gj = a.G + q * n;
+                    for (int k = 0; k < n; ++k) a.v[(int64_t)d * n + k] += (double)bt * (double)r.sign * (double)Gj[k];
+                    a.w[d] += (double)bt * (double)hh;
+                    changed = true;
+                }
+            }
+            ++cpos;
+        }
+        a.cursor[d] = cpos;
+        if (changed) {
+            double dv = 0.0;
+            float* vf = a.vf + (int64_t)d * (n + 1);
+            for (int k = 0; k < n; ++k) {
+                vf[k] = (float)a.v[(int64_t)d * n + k];
+                dv += fabs(a.v[(int64_t)d * n + k] - (double)vf[k]);
+            }
+            vf[n] = __double2float_ru(a.w[d] + dv);
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < rows; j += blockDim.x) {
+        const float l = lh[j], u = uh[j];
+        if (l > u) atomicOr(&a.st[d], DR_STATUS_INFEASIBLE_BIT);
+        float sl = 0.f, dd = 0.f, al = 0.f;
+        if (l >= 0.f) {
+            sl = 1.f;
+        } else if (u > 0.f) {
+            if (a.mode == DR_SLOPE_CHORD_K) al = u / (u - l);
+            else if (a.mode == DR_SLOPE_ADAPTIVE_K) al = (u >= -l) ? 1.f : 0.f;
+            else if (a.mode == DR_SLOPE_ZERO_K) al = 0.f;
+            else al = a.alpha[(dom * H + t) * (int64_t)N.hidden + N.hoff[ell] + j];
+            const float b1 = -al * l, b2 = (1.f - al) * u;
+            sl = al;
+            dd = (b1 >= b2) ? b1 : b2;
+        }
+        a.hs[(int64_t)d * N.hidden + N.hoff[ell] + j] = sl;
+        a.hd[(int64_t)d * N.hidden + N.hoff[ell] + j] = dd;
+        if (a.alpha_used) a.alpha_used[(dom * H + t) * (int64_t)N.hidden + N.hoff[ell] + j] = al;
+    }
+}
+
+// FP64 dynamics on the TM, EvalInt of box t+1 and the running objective; one block per domain.
+__global__ void k_w_dyn(const WideArgs a, int t) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double* sm = reinterpret_cast<double*>(smraw);
+    const NetDesc& N = a.net;
+    const int n = N.n, m = N.m, H = N.H, d = blockIdx.x;
+    const int64_t dom = a.d0 + d;
+    double* Pn = sm;           // n*n
+    double* cn = Pn + n * n;   // n
+    double* Ilon = cn + n;     // n
+    double* Ihin = Ilon + n;   // n
+    double* red = Ihin + n;    // blockDim
+    const double* P = a.P + (int64_t)d * n * n;
+    const double* c = a.c + (int64_t)d * n;
+    const double* Ilo = a.Ilo + (int64_t)d * n;
+    const double* Ihi = a.Ihi + (int64_t)d * n;
+    const float* G = a.G + (int64_t)d * N.maxw * n;
+    const float* cu = a.cu + (int64_t)d * m;
+    const float* Iulo = a.Iulo + (int64_t)d * m;
+    const float* Iuhi = a.Iuhi + (int64_t)d * m;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int i = idx / n, k = idx - i * n;
+        double acc = 0.0;
+        for (int j = 0; j < n; ++j) acc = fma(a.A[i * n + j], P[j * n + k], acc);
+        for (int j = 0; j < m; ++j) acc = fma(a.B[i * m + j], (double)G[j * n + k], acc);
+        Pn[idx] = acc;
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double acc = a.e ? a.e[i] : 0.0, lo_ = 0.0, hi_ = 0.0;
+        for (int j = 0; j < n; ++j) {
+            const double x = a.A[i * n + j];
+            acc = fma(x, c[j], acc);
+            lo_ += posd(x) * Ilo[j] + negd(x) * Ihi[j];
+            hi_ += posd(x) * Ihi[j] + negd(x) * Ilo[j];
+        }
+        for (int j = 0; j < m; ++j) {
+            const double x = a.B[i * m + j];
+            acc = fma(x, (double)cu[j], acc);
+            lo_ += posd(x) * (double)Iulo[j] + negd(x) * (double)Iuhi[j];
+            hi_ += posd(x) * (double)Iuhi[j] + negd(x) * (double)Iulo[j];
+        }
+        cn[i] = acc;
+        Ilon[i] = lo_;
+        Ihin[i] = hi_;
+    }
+    __syncthreads();
+    double* Pw = a.P + (int64_t)d * n * n;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) Pw[idx] = Pn[idx];
+    const double* v = a.v + (int64_t)d * n;
+    const double wv = a.w[d];
+    double vsum = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        a.c[(int64_t)d * n + i] = cn[i];
+        a.Ilo[(int64_t)d * n + i] = Ilon[i];
+        a.Ihi[(int64_t)d * n + i] = Ihin[i];
+        double pm = 0.0, pp = 0.0, mag = fabs(cn[i]) + fabs(Ilon[i]) + fabs(Ihin[i]) + fabs(wv);
+        for (int k = 0; k < n; ++k) {
+            const double x = Pn[i * n + k];
+            pm += fabs(x - v[k]);
+            pp += fabs(x + v[k]);
+            mag += fabs(x) + fabs(v[k]);
+        }
+        const double bl = cn[i] + Ilon[i] - pm - wv - a.box_margin * mag;
+        const double bh = cn[i] + Ihin[i] + pp + wv + a.box_margin * mag;
+        if (a.lo) a.lo[(dom * (H + 1) + t + 1) * n + i] = bl;
+        if (a.hi) a.hi[(dom * (H + 1) + t + 1) * n + i] = bh;
+        vsum += bh - bl;
+        if (!isfinite(bl) || !isfinite(bh)) atomicOr(&a.st[d], DR_STATUS_NONFINITE_BIT);
+        if (bl > bh) atomicOr(&a.st[d], DR_STATUS_INFEASIBLE_BIT);
+    }
+    red[threadIdx.x] = vsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < (int)blockDim.x; ++q) s += red[q];
+        a.vacc[d] += s;
+        if (t == H - 1) {
+            if (a.V) a.V[dom] = a.vacc[d];
+            if (a.status) a.status[dom] = a.st[d];
+        }
+    }
+}

@@ -102,7 +102,7 @@ def test_refinement_cartpole_subset():
     h_o = np.array(ref["V_hist"])
     assert (np.diff(hist) <= 0).all()
     assert hist[-1] < hist[0]
-    np.testing.assert_allclose(hist[0], h_o[0], rtol=1e-5)
+    np.testing.assert_allclose(hist[0], h_o[0], rtol=5e-4)  # V includes the outward box margin
     np.testing.assert_allclose(hist, h_o, rtol=2e-3)
     # the installed best slopes reproduce the best objective
     V = r.objective()

@@ -2,7 +2,9 @@
 
 Tolerance (floating point): |gpu - oracle| <= 1e-5 * max(|o_lo|, |o_hi|, o_hi - o_lo) for every
 domain, step and coordinate.  Soundness against the oracle: the GPU machine is never tighter than the
-oracle's by more than the outward margin rho * (|o_lo| + |o_hi|).  Status words are compared exactly.
+oracle's, i.e. g_lo <= o_lo and g_hi >= o_hi (the reported boxes carry the outward margin 2^-18 of
+their L1 magnitude, sized to cover the FP32 pass's deviation from FP64).  Status words are compared
+exactly.
 """
 import numpy as np
 import pytest
@@ -14,7 +16,7 @@ from paper_2605_25346_b300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 RTOL = 1e-5
-RHO = 2.0 ** -22
+RHO = 0.0  # no slack: the GPU machine must enclose the oracle's box
 
 
 def _api():
@@ -22,10 +24,12 @@ def _api():
     return api
 
 
-def gpu_bounds(prob, mode=None, alpha=None, on_device=True, rho=None):
+def gpu_bounds(prob, mode=None, alpha=None, on_device=True, rho=None, precision=0, chunk=0):
     api = _api()
     r = api.Reach(0)
-    r.load(prob, mode=mode, rho=rho)
+    r.load(prob, mode=mode, rho=rho, precision=precision)
+    if chunk:
+        r.set_options(mode=prob.mode if mode is None else mode, precision=precision, rho=rho, chunk=chunk)
     if alpha is not None:
         r.set_alpha(alpha)
     out = r.bounds(on_device=on_device)
@@ -48,7 +52,8 @@ def compare(prob, g, o, rtol=RTOL, rho=RHO, check_hull=True):
     assert (glo <= olo + rho * mag).all(), "GPU lower bound tighter than the oracle beyond the margin"
     assert (ghi >= ohi - rho * mag).all(), "GPU upper bound tighter than the oracle beyond the margin"
     np.testing.assert_array_equal(g["status"].astype(np.int64), o["status"].numpy())
-    np.testing.assert_allclose(g["V"], o["V"].detach().numpy(), rtol=rtol * 10)
+    # V sums box widths, which carry the outward box margin (about 2 * 2^-18 * |centre| per entry)
+    np.testing.assert_allclose(g["V"], o["V"].detach().numpy(), rtol=5e-4)
     if check_hull:
         hs = np.maximum(np.abs(o["hull_lo"].numpy()), np.abs(o["hull_hi"].numpy()))
         assert (np.abs(g["hull_lo"] - o["hull_lo"].numpy()) <= rtol * hs).all()
@@ -172,3 +177,38 @@ def test_invalid_arguments_are_errors():
     with pytest.raises(_lib.DiffReachError) as e:
         r.load(wl.quad6_batched())
     assert e.value.code == _lib.DR_ERR_OOM
+
+
+# ---- staged path (per-phase kernels over domain chunks; wide controllers) -----------------------
+STAGED = 1  # DR_PREC_SIMT: staged path with the CUDA-core chain GEMM
+
+
+@pytest.mark.parametrize("cfg", [2, 3])
+def test_staged_path_narrow_configs(cfg):
+    p = wl.CONFIGS[cfg]()
+    sub = p.subset(np.arange(0, p.D, 4))
+    compare(sub, gpu_bounds(sub, precision=STAGED, chunk=97), orc.reach(sub))
+
+
+@pytest.mark.parametrize("widths,mode", [([5, 37, 23, 3], orc.MODE_CHORD), ([7, 96, 96, 96, 2], orc.MODE_ZERO),
+                                         ([3, 70, 130, 65, 2], orc.MODE_CHORD)])
+def test_staged_path_random_shapes(widths, mode):
+    p = wl.random_problem(hash(tuple(widths)) % 1000, widths, D=45, H=4, eps=0.15, mode=mode)
+    compare(p, gpu_bounds(p, precision=STAGED, chunk=16), orc.reach(p))
+
+
+@pytest.mark.parametrize("beta_scale", [0.0, 0.02])
+def test_branch12_split_domains(beta_scale):
+    idx = np.arange(0, 65536, 1021)[:64]
+    p = wl.quadrotor_branch(only=idx)
+    if beta_scale > 0:
+        p.beta = np.random.default_rng(5).uniform(0, beta_scale, size=p.splits.nnz).astype(np.float32).astype(np.float64)
+    assert p.splits.nnz > 500
+    # (multipliers of order 0.5 make the split dual itself diverge over 30 steps; 0.02 keeps it finite)
+    compare(p, gpu_bounds(p), orc.reach(p))
+
+
+def test_large16_subset():
+    p = wl.large16()
+    sub = p.subset(np.arange(0, p.D, p.D // 8))
+    compare(sub, gpu_bounds(sub), orc.reach(sub))
