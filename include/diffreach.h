@@ -211,6 +211,13 @@ typedef struct dr_static_args {
 
 int dr_slope_gradient_static(const dr_static_args* args);
 
+/* FP32-accurate matrix product on the tensor cores: C [M x N] = A [M x K] * BT [N x K]^T, all FP32
+ * row-major device arrays, computed as the 3xTF32 split A_hi B_hi + A_hi B_lo + A_lo B_hi with FP32
+ * accumulation (tcgen05.mma kind::tf32, TMA-staged operands).  This is the contraction the chain
+ * Lambda <- (Lambda diag(s)) W of Thm. 2 runs on; exposed for testing and reuse.  Uses temporary
+ * device memory; synchronises `stream`.  DR_ERR_TIMEOUT if a bounded pipeline wait expired. */
+int dr_tf32x3_gemm(int M, int N, int K, const float* A, const float* BT, float* C, void* stream);
+
 /* Number of kernels this context has launched (monotone counter, for accounting). */
 int64_t dr_kernel_launches(const dr_ctx* ctx);
 

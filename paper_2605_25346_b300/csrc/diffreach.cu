@@ -15,6 +15,7 @@
 #include "fused_core.cuh"
 #include "fused_bwd.cuh"
 #include "wide.cuh"
+#include "tc_gemm.cuh"
 
 
 struct dr_ctx {
@@ -1034,6 +1035,109 @@ int dr_optimize_slopes(dr_ctx* c, int steps, double lr_alpha, double lr_beta, do
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// tensor-core GEMM plumbing
+// ------------------------------------------------------------------------------------------------
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+static int get_encoder(dr_ctx* c) {
+    if (g_encode) return DR_OK;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+        return fail(c, DR_ERR_CUDA, "cuTensorMapEncodeTiled unavailable (%s)", cudaGetErrorString(e));
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return DR_OK;
+}
+
+// 2D FP32 tensor map over rows x ldk (K contiguous), box 32 x box_rows, 128-byte swizzle.
+static int make_map(dr_ctx* c, CUtensorMap* map, const float* ptr, int64_t rows, int ldk, int box_rows) {
+    if ((reinterpret_cast<uintptr_t>(ptr) & 15) || (ldk % tc::BK)) return fail(c, DR_ERR_ARG, "tensor map alignment");
+    cuuint64_t dims[2] = {(cuuint64_t)ldk, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ldk * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptr), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(c, DR_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return DR_OK;
+}
+
+static int tc_bn(int N) { return N > 128 ? 256 : (N > 64 ? 128 : (N > 32 ? 64 : (N > 16 ? 32 : 16))); }
+
+template <int BN>
+static int launch_tc_gemm_bn(dr_ctx* c, const CUtensorMap* m, float* C, int R, int K, int N, int ldc, int* err,
+                             cudaStream_t st) {
+    const int smem = tc::smem_bytes(BN);
+    CUDA_TRY(c, cudaFuncSetAttribute(tc::k_tc_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    dim3 grid((R + tc::BM - 1) / tc::BM, (N + BN - 1) / BN);
+    tc::k_tc_gemm<BN><<<grid, 128, smem, st>>>(m[0], m[1], m[2], m[3], C, R, K, N, ldc, err);
+    CUDA_TRY(c, cudaGetLastError());
+    if (c) c->launches++;
+    return DR_OK;
+}
+
+// C [R x N] (ld ldc) = A B with A given as TF32 parts Ah/Al [R][ldk] and B as BTh/BTl [N][ldk].
+static int tc_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* BTh, const float* BTl, float* C, int R, int K,
+                   int N, int ldk, int ldc, int* err, cudaStream_t st) {
+    TRY(get_encoder(c));
+    const int BN = tc_bn(N);
+    CUtensorMap m[4];
+    TRY(make_map(c, &m[0], Ah, R, ldk, tc::BM));
+    TRY(make_map(c, &m[1], Al, R, ldk, tc::BM));
+    TRY(make_map(c, &m[2], BTh, N, ldk, BN));
+    TRY(make_map(c, &m[3], BTl, N, ldk, BN));
+    switch (BN) {
+        case 256: return launch_tc_gemm_bn<256>(c, m, C, R, K, N, ldc, err, st);
+        case 128: return launch_tc_gemm_bn<128>(c, m, C, R, K, N, ldc, err, st);
+        case 64: return launch_tc_gemm_bn<64>(c, m, C, R, K, N, ldc, err, st);
+        case 32: return launch_tc_gemm_bn<32>(c, m, C, R, K, N, ldc, err, st);
+        default: return launch_tc_gemm_bn<16>(c, m, C, R, K, N, ldc, err, st);
+    }
+}
+
+static inline int round_up32(int x) { return (x + 31) & ~31; }
+
+// Utility entry: FP32-accurate C = A B^T on tensor cores (temporary device buffers).
+extern "C" int dr_tf32x3_gemm(int M, int N, int K, const float* A, const float* BT, float* C, void* stream) {
+    if (M < 0 || N < 0 || K < 1 || !A || !BT || !C) return fail(nullptr, DR_ERR_ARG, "dr_tf32x3_gemm: bad arguments");
+    if (M == 0 || N == 0) return DR_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int ldk = round_up32(K);
+    float *Ah = nullptr, *Al = nullptr, *Bh = nullptr, *Bl = nullptr;
+    int* err = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(Ah);
+        cudaFree(Al);
+        cudaFree(Bh);
+        cudaFree(Bl);
+        cudaFree(err);
+    };
+    if (cudaMalloc(&Ah, sizeof(float) * (size_t)M * ldk) != cudaSuccess || cudaMalloc(&Al, sizeof(float) * (size_t)M * ldk) != cudaSuccess ||
+        cudaMalloc(&Bh, sizeof(float) * (size_t)N * ldk) != cudaSuccess || cudaMalloc(&Bl, sizeof(float) * (size_t)N * ldk) != cudaSuccess ||
+        cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+        cleanup();
+        cudaGetLastError();
+        return fail(nullptr, DR_ERR_OOM, "dr_tf32x3_gemm: allocation failed");
+    }
+    cudaMemsetAsync(err, 0, sizeof(int), st);
+    tc::k_split_tf32<<<1184, 256, 0, st>>>(A, K, M, K, ldk, Ah, Al);
+    tc::k_split_tf32<<<1184, 256, 0, st>>>(BT, K, N, K, ldk, Bh, Bl);
+    int rc = tc_gemm(nullptr, Ah, Al, Bh, Bl, C, M, K, N, ldk, N, err, st);
+    int herr = 0;
+    if (rc == DR_OK) {
+        cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = fail(nullptr, DR_ERR_CUDA, "dr_tf32x3_gemm: %s", cudaGetErrorString(e));
+        else if (herr) rc = fail(nullptr, DR_ERR_TIMEOUT, "dr_tf32x3_gemm: a pipeline wait timed out");
+    }
+    cleanup();
+    return rc;
+}
 
 // ------------------------------------------------------------------------------------------------
 // Allocation-free slope gradient (dr_slope_gradient_static): the reverse sweep with its tape in a

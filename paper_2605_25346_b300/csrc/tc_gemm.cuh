@@ -1,0 +1,253 @@
+// FP32-accurate GEMM on the 5th-generation tensor cores: C = A B with A [R x K] (rows of all
+// domains stacked) and B [K x N] shared, as the split product A_hi B_hi + A_hi B_lo + A_lo B_hi of
+// TF32 parts (3xTF32), accumulated in FP32 in tensor memory.
+//
+//   - A_hi/A_lo [R][ldk] and BT_hi/BT_lo [N][ldk] (B transposed, K contiguous) are FP32 arrays whose
+//     values are TF32-representable; ldk is a multiple of 32 and the padding columns are zero.
+//   - One CTA computes a 128 x BN tile over the whole K range.  Thread 0 issues the TMA loads
+//     (cp.async.bulk.tensor, 128-byte swizzle, 32-float K chunks), thread 32 issues tcgen05.mma
+//     (kind::tf32, M = 128, N = BN, K = 8 per instruction) from the single accumulator in TMEM,
+//     and all four warps drain TMEM (tcgen05.ld 32x32b) into C [R][ldc].
+//   - Stages are handed over with mbarriers (TMA complete_tx for "full", tcgen05.commit for
+//     "empty").  Every wait is bounded by a clock budget; on expiry the kernel raises *err, stops
+//     issuing, drains its own copies (bounded), frees TMEM and returns.
+#pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cstdint>
+
+namespace tc {
+
+constexpr int BM = 128;
+constexpr int BK = 32;  // floats per K chunk: one 128-byte swizzle row
+constexpr long long kWaitCycles = 4000000000ll;  // about 2 s at 2 GHz
+
+__host__ __device__ constexpr int stage_bytes(int bn) { return 2 * BM * BK * 4 + 2 * bn * BK * 4; }
+__host__ __device__ constexpr int stages_for(int bn) { return bn >= 256 ? 2 : (bn >= 128 ? 3 : 4); }
+__host__ __device__ constexpr int tmem_cols(int bn) { return bn <= 32 ? 32 : (bn <= 64 ? 64 : (bn <= 128 ? 128 : 256)); }
+__host__ __device__ constexpr int smem_bytes(int bn) { return stages_for(bn) * stage_bytes(bn) + 1024 + 256; }
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait on an mbarrier phase; false when the clock budget ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity)) {
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand in the 128-byte swizzle layout written by TMA
+// (8-row groups of 128-byte rows, 1024 bytes apart).  Bits: start address >> 4 [0,14), leading
+// offset >> 4 [16,30) (unused for this layout), stride offset >> 4 [32,46), version 1 [46,48),
+// layout type 2 = 128-byte swizzle [61,64).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor of kind::tf32: D = F32 [4,6), A = B = TF32 [7,10) [10,13), both K-major,
+// N >> 3 [17,23), M >> 4 [24,29).
+__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+                                                    const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
+                                                    float* __restrict__ C, int R, int K, int N, int ldc, int* __restrict__ err) {
+    constexpr int S = stages_for(BN);
+    constexpr int SB = stage_bytes(BN);
+    constexpr int TC = tmem_cols(BN);
+    constexpr uint32_t IDESC = idesc_tf32(BM, BN);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + S * SB);
+    uint64_t* empty = full + S;
+    uint64_t* accum = empty + S;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(accum + 1);
+    int* abort_flag = reinterpret_cast<int*>(tmem_holder + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int nk = (K + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mAh)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mBh)) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)), "r"(TC)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    if (threadIdx.x == 0) {
+        // ---- TMA producer
+        int issued = 0;
+        for (int kc = 0; kc < nk; ++kc) {
+            const int s = kc % S;
+            if (kc >= S && !mbar_wait(&empty[s], ((kc / S) - 1) & 1)) {
+                atomicExch(err, 1);
+                *(volatile int*)abort_flag = 1;
+                break;
+            }
+            if (*(volatile int*)abort_flag) break;
+            unsigned char* st = base + s * SB;
+            mbar_expect_tx(&full[s], SB);
+            tma_load_2d(st, &mAh, &full[s], kc * BK, m0);
+            tma_load_2d(st + BM * BK * 4, &mAl, &full[s], kc * BK, m0);
+            tma_load_2d(st + 2 * BM * BK * 4, &mBh, &full[s], kc * BK, n0);
+            tma_load_2d(st + 2 * BM * BK * 4 + BN * BK * 4, &mBl, &full[s], kc * BK, n0);
+            ++issued;
+        }
+        // drain: every issued stage must have landed before the CTA may exit
+        for (int kc = (issued > S ? issued - S : 0); kc < issued; ++kc) {
+            if (!mbar_wait(&full[kc % S], (kc / S) & 1)) {
+                atomicExch(err, 1);
+                break;
+            }
+        }
+    } else if (threadIdx.x == 32) {
+        // ---- MMA issuer
+        bool ok = true;
+        for (int kc = 0; kc < nk; ++kc) {
+            const int s = kc % S;
+            if (!mbar_wait(&full[s], (kc / S) & 1)) {
+                atomicExch(err, 1);
+                *(volatile int*)abort_flag = 1;
+                ok = false;
+                break;
+            }
+            fence_after();
+            const uint32_t sa = smem_u32(base + s * SB);
+            const uint64_t ah = sw128_desc(sa), al = sw128_desc(sa + BM * BK * 4);
+            const uint64_t bh = sw128_desc(sa + 2 * BM * BK * 4), bl = sw128_desc(sa + 2 * BM * BK * 4 + BN * BK * 4);
+#pragma unroll
+            for (int kk = 0; kk < BK / 8; ++kk) {
+                const uint64_t o = (uint64_t)(kk * 32) >> 4;  // 8 TF32 values = 32 bytes along K
+                mma_tf32(tmem, ah + o, bh + o, IDESC, (kc | kk) ? 1u : 0u);
+                mma_tf32(tmem, ah + o, bl + o, IDESC, 1u);
+                mma_tf32(tmem, al + o, bh + o, IDESC, 1u);
+            }
+            mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(accum);
+        else mbar_expect_tx(accum, 0);  // complete the phase so the epilogue does not wait out its budget
+    }
+    __syncwarp();
+    // ---- epilogue: warp w drains TMEM lanes 32w..32w+31 (one output row per thread)
+    const bool have = mbar_wait(accum, 0);
+    fence_after();
+    if (!have) atomicExch(err, 1);
+    if (have && !*(volatile int*)abort_flag) {
+        const int row = m0 + warp * 32 + lane;
+        float v[32];
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (row < R) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int col = n0 + c0 + j;
+                    if (c0 + j < BN && col < N) C[(int64_t)row * ldc + col] = v[j];
+                }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC) : "memory");
+    }
+}
+
+// TF32 part of x with round-to-nearest (ties away), as an FP32 value whose low 13 bits are zero.
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Split rows of X [R][K] (ld ldx) into TF32 parts H/L [R][ldk] with zero padding in K..ldk-1.
+__global__ void k_split_tf32(const float* __restrict__ X, int ldx, int R, int K, int ldk, float* __restrict__ Hh,
+                             float* __restrict__ Ll) {
+    const int64_t total = (int64_t)R * ldk;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = idx / ldk;
+        const int k = (int)(idx - r * ldk);
+        const float x = k < K ? X[r * ldx + k] : 0.f;
+        const float h = tf32_rna(x);
+        Hh[idx] = h;
+        Ll[idx] = tf32_rna(x - h);
+    }
+}
+
+}  // namespace tc
