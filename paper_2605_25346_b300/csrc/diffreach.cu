@@ -68,6 +68,11 @@ struct dr_ctx {
     double* dVhist = nullptr;
     double* dwlo = nullptr;
     double* dwhi = nullptr;
+    // transposed TF32 parts of every layer for the tensor-core chain: layer l -> [n_{l-1}][ru32(n_l)]
+    float* dWTh = nullptr;
+    float* dWTl = nullptr;
+    int64_t WToff[DR_MAXL] = {};
+    int* derr = nullptr;
     // staged (wide) path chunk scratch
     void* wscratch = nullptr;
     size_t wscratch_bytes = 0;
@@ -251,6 +256,71 @@ static int fused_threads(const NetDesc& N) { return N.maxw <= 64 ? 128 : 256; }
 // C ABI
 // ------------------------------------------------------------------------------------------------
 
+// ------------------------------------------------------------------------------------------------
+// tensor-core GEMM plumbing
+// ------------------------------------------------------------------------------------------------
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+static int get_encoder(dr_ctx* c) {
+    if (g_encode) return DR_OK;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+        return fail(c, DR_ERR_CUDA, "cuTensorMapEncodeTiled unavailable (%s)", cudaGetErrorString(e));
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return DR_OK;
+}
+
+// 2D FP32 tensor map over rows x ldk (K contiguous), box 32 x box_rows, 128-byte swizzle.
+static int make_map(dr_ctx* c, CUtensorMap* map, const float* ptr, int64_t rows, int ldk, int box_rows) {
+    if ((reinterpret_cast<uintptr_t>(ptr) & 15) || (ldk % tc::BK)) return fail(c, DR_ERR_ARG, "tensor map alignment");
+    cuuint64_t dims[2] = {(cuuint64_t)ldk, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ldk * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptr), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(c, DR_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return DR_OK;
+}
+
+static int tc_bn(int N) { return N > 64 ? 128 : (N > 32 ? 64 : (N > 16 ? 32 : 16)); }
+
+template <int BN>
+static int launch_tc_gemm_bn(dr_ctx* c, const CUtensorMap* m, float* C, int R, int K, int N, int ldc, int* err,
+                             cudaStream_t st) {
+    const int smem = tc::psmem_bytes(BN);
+    CUDA_TRY(c, cudaFuncSetAttribute(tc::k_tc_gemm_p<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    dim3 grid((R + tc::BM - 1) / tc::BM, (N + BN - 1) / BN);
+    tc::k_tc_gemm_p<BN><<<grid, tc::kGemmThreads, smem, st>>>(m[0], m[1], m[2], m[3], C, R, K, N, ldc, err);
+    CUDA_TRY(c, cudaGetLastError());
+    if (c) c->launches++;
+    return DR_OK;
+}
+
+// C [R x N] (ld ldc) = A B with A given as TF32 parts Ah/Al [R][ldk] and B as BTh/BTl [N][ldk].
+static int tc_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* BTh, const float* BTl, float* C, int R, int K,
+                   int N, int ldk, int ldc, int* err, cudaStream_t st) {
+    TRY(get_encoder(c));
+    const int BN = tc_bn(N);
+    CUtensorMap m[4];
+    TRY(make_map(c, &m[0], Ah, R, ldk, tc::BM));
+    TRY(make_map(c, &m[1], Al, R, ldk, tc::BM));
+    TRY(make_map(c, &m[2], BTh, N, ldk, BN));
+    TRY(make_map(c, &m[3], BTl, N, ldk, BN));
+    switch (BN) {
+        case 128: return launch_tc_gemm_bn<128>(c, m, C, R, K, N, ldc, err, st);
+        case 64: return launch_tc_gemm_bn<64>(c, m, C, R, K, N, ldc, err, st);
+        case 32: return launch_tc_gemm_bn<32>(c, m, C, R, K, N, ldc, err, st);
+        default: return launch_tc_gemm_bn<16>(c, m, C, R, K, N, ldc, err, st);
+    }
+}
+
+static inline int round_up32(int x) { return (x + 31) & ~31; }
+
 extern "C" {
 
 int dr_create(dr_ctx** out, int device, void* cuda_stream) {
@@ -315,6 +385,9 @@ void dr_destroy(dr_ctx* c) {
     cudaFree(c->dsp);
     cudaFree(c->dbeta);
     cudaFree(c->dalpha);
+    cudaFree(c->dWTh);
+    cudaFree(c->dWTl);
+    cudaFree(c->derr);
     delete c;
 }
 
@@ -389,6 +462,46 @@ int dr_load_controller(dr_ctx* c, int L, const int32_t* widths, const void* cons
     CUDA_TRY(c, cudaMemcpyAsync(c->dW, hw.data(), nw * sizeof(float), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->db, hb.data(), nb * sizeof(float), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    // transposed TF32 parts (round to nearest, ties away) for the tensor-core chain
+    {
+        auto tf32 = [](float x) {
+            uint32_t u;
+            memcpy(&u, &x, 4);
+            if ((u & 0x7f800000u) != 0x7f800000u) {
+                u += 0x1000u;
+                u &= 0xffffe000u;
+            }
+            float r;
+            memcpy(&r, &u, 4);
+            return r;
+        };
+        int64_t tot = 0;
+        int64_t offs[DR_MAXL];
+        for (int l = 0; l < L; ++l) {
+            offs[l] = tot;
+            tot += (int64_t)widths[l] * ((widths[l + 1] + 31) & ~31);
+        }
+        std::vector<float> th(tot, 0.f), tl(tot, 0.f);
+        for (int l = 0; l < L; ++l) {
+            const int K = widths[l + 1], Nn = widths[l], ldk = (K + 31) & ~31;
+            for (int nn = 0; nn < Nn; ++nn)
+                for (int kk = 0; kk < K; ++kk) {
+                    const float x = hw[N.Woff[l] + (int64_t)kk * Nn + nn];
+                    const float h = tf32(x);
+                    th[offs[l] + (int64_t)nn * ldk + kk] = h;
+                    tl[offs[l] + (int64_t)nn * ldk + kk] = tf32(x - h);
+                }
+        }
+        dev_free(c, (void*&)c->dWTh, 0);
+        dev_free(c, (void*&)c->dWTl, 0);
+        TRY(dev_alloc(c, c->dWTh, tot));
+        TRY(dev_alloc(c, c->dWTl, tot));
+        if (!c->derr) TRY(dev_alloc(c, c->derr, 1));
+        CUDA_TRY(c, cudaMemcpyAsync(c->dWTh, th.data(), tot * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(c->dWTl, tl.data(), tot * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        for (int l = 0; l < L; ++l) c->WToff[l] = offs[l];
+    }
     const int oldH = c->H;
     c->net = N;
     c->net.H = oldH;
@@ -573,7 +686,7 @@ static int ensure_tape(dr_ctx* c) {
 static int64_t wide_lam_stride(const NetDesc& N) {
     int64_t best = 1;
     for (int l = 2; l <= N.L; ++l)
-        for (int k = 0; k <= l - 1; ++k) best = std::max<int64_t>(best, (int64_t)N.w[l] * N.w[k]);
+        for (int k = 0; k <= l - 1; ++k) best = std::max<int64_t>(best, (int64_t)N.w[l] * ((N.w[k] + 31) & ~31));
     return best;
 }
 
@@ -587,12 +700,12 @@ static size_t wide_bytes_per_domain(const NetDesc& N) {
     b += sizeof(float) * 2 * N.maxw;                              // kappa
     b += sizeof(float) * ((size_t)N.maxw * n + 4 * N.maxw);       // G, a, R, S
     b += sizeof(float) * 3 * m;                                   // controller TM
-    b += sizeof(float) * 2 * wide_lam_stride(N);                  // Lambda ping-pong
+    b += sizeof(float) * 3 * wide_lam_stride(N);                  // Lambda buffers (two + GEMM output)
     return b + 16 * 24;
 }
 
 // Carve the chunk scratch for Dc domains out of one allocation.
-static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, float** lamA, float** lamB) {
+static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, float** lamA, float** lamB, float** lamC) {
     const NetDesc& N = a.net;
     const size_t need = wide_bytes_per_domain(N) * (size_t)Dc + 4096;
     if (!c->wscratch || c->wscratch_bytes < need || c->wDc != Dc) {
@@ -645,6 +758,7 @@ static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, float** lamA, float** lamB)
     a.lam_stride = wide_lam_stride(N);
     *lamA = (float*)take(sizeof(float) * D * a.lam_stride);
     *lamB = (float*)take(sizeof(float) * D * a.lam_stride);
+    *lamC = (float*)take(sizeof(float) * D * a.lam_stride);
     if (off > c->wscratch_bytes) return fail(c, DR_ERR_OOM, "staged scratch layout overflow");
     return DR_OK;
 }
@@ -685,8 +799,10 @@ static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
     a.status = c->dstatus;
     a.alpha_used = alpha_used;
     const int Dc = wide_chunk(c, N);
-    float *lamA = nullptr, *lamB = nullptr;
-    TRY(wide_bind(c, a, Dc, &lamA, &lamB));
+    float *lamA = nullptr, *lamB = nullptr, *lamC = nullptr;
+    TRY(wide_bind(c, a, Dc, &lamA, &lamB, &lamC));
+    const bool tcore = c->opt.precision != DR_PREC_SIMT;
+    if (tcore) CUDA_TRY(c, cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream));
     const size_t dyn_smem = sizeof(double) * (n * n + 3 * n + 128);
     for (int64_t d0 = 0; d0 < c->D; d0 += Dc) {
         a.d0 = d0;
@@ -700,25 +816,48 @@ static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
             for (int ell = 1; ell <= L; ++ell) {
                 const int rows = N.w[ell];
                 const int64_t warps = (int64_t)dc * rows;
-                k_w_chain_init<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, ell, lamA);
-                c->launches++;
-                float* cur = lamA;
-                float* nxt = lamB;
-                for (int mm = ell - 1; mm >= 1; --mm) {
-                    const int K = N.w[mm], NN = N.w[mm - 1];
-                    const float* Wm = c->dW + N.Woff[mm - 1];
-                    dim3 grid((NN + 63) / 64, (rows + 63) / 64, dc);
-                    k_w_gemm_simt<<<grid, 256, 0, c->stream>>>(cur, Wm, nxt, rows, K, NN, a.lam_stride);
+                if (!tcore || ell == 1) {
+                    k_w_chain_init<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, ell, lamA);
                     c->launches++;
-                    if (mm - 1 >= 1) {
-                        k_w_level_epi<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, ell, mm - 1, nxt);
+                    float* cur = lamA;
+                    float* nxt = lamB;
+                    for (int mm = ell - 1; mm >= 1; --mm) {
+                        const int K = N.w[mm], NN = N.w[mm - 1];
+                        const float* Wm = c->dW + N.Woff[mm - 1];
+                        dim3 grid((NN + 63) / 64, (rows + 63) / 64, dc);
+                        k_w_gemm_simt<<<grid, 256, 0, c->stream>>>(cur, Wm, nxt, rows, K, NN, a.lam_stride);
                         c->launches++;
+                        if (mm - 1 >= 1) {
+                            k_w_level_epi<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, ell, mm - 1, nxt);
+                            c->launches++;
+                        }
+                        std::swap(cur, nxt);
                     }
-                    std::swap(cur, nxt);
+                    if (ell == 1) k_w_project<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, 1, c->dW + N.Woff[0], 1);
+                    else k_w_project<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, ell, cur, 0);
+                    c->launches++;
+                } else {
+                    // tensor-core chain: rows of all domains stacked, A as TF32 parts, shared W^T parts
+                    const int R = dc * rows;
+                    int ldk = round_up32(N.w[ell - 1]);
+                    k_t_chain_init<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, ell, lamA, lamB, ldk);
+                    c->launches++;
+                    for (int mm = ell - 1; mm >= 1; --mm) {
+                        const int K = N.w[mm], NN = N.w[mm - 1];
+                        TRY(tc_gemm(c, lamA, lamB, c->dWTh + c->WToff[mm - 1], c->dWTl + c->WToff[mm - 1], lamC, R, K, NN, ldk,
+                                    NN, c->derr, c->stream));
+                        if (mm - 1 >= 1) {
+                            ldk = round_up32(NN);
+                            k_t_level_epi<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, ell, mm - 1, lamC, lamA,
+                                                                                             lamB, ldk);
+                            c->launches++;
+                        }
+                    }
+                    WideArgs ap = a;
+                    ap.lam_stride = (int64_t)rows * n;  // Lambda_x rows of domain d start at d * rows * n
+                    k_w_project<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(ap, ell, lamC, 0);
+                    c->launches++;
                 }
-                if (ell == 1) k_w_project<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, 1, c->dW + N.Woff[0], 1);
-                else k_w_project<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, ell, cur, 0);
-                c->launches++;
                 if (ell < L) {
                     k_w_relax<<<dc, 256, 0, c->stream>>>(a, ell, t);
                     c->launches++;
@@ -728,6 +867,12 @@ static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
             c->launches++;
         }
         CUDA_TRY(c, cudaGetLastError());
+    }
+    if (tcore) {
+        int herr = 0;
+        CUDA_TRY(c, cudaMemcpyAsync(&herr, c->derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        if (herr) return fail(c, DR_ERR_TIMEOUT, "a tensor-core pipeline wait timed out");
     }
     return DR_OK;
 }
@@ -1035,72 +1180,6 @@ int dr_optimize_slopes(dr_ctx* c, int steps, double lr_alpha, double lr_beta, do
 }
 
 }  // extern "C"
-
-// ------------------------------------------------------------------------------------------------
-// tensor-core GEMM plumbing
-// ------------------------------------------------------------------------------------------------
-
-static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
-
-static int get_encoder(dr_ctx* c) {
-    if (g_encode) return DR_OK;
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
-        return fail(c, DR_ERR_CUDA, "cuTensorMapEncodeTiled unavailable (%s)", cudaGetErrorString(e));
-    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    return DR_OK;
-}
-
-// 2D FP32 tensor map over rows x ldk (K contiguous), box 32 x box_rows, 128-byte swizzle.
-static int make_map(dr_ctx* c, CUtensorMap* map, const float* ptr, int64_t rows, int ldk, int box_rows) {
-    if ((reinterpret_cast<uintptr_t>(ptr) & 15) || (ldk % tc::BK)) return fail(c, DR_ERR_ARG, "tensor map alignment");
-    cuuint64_t dims[2] = {(cuuint64_t)ldk, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)ldk * sizeof(float)};
-    cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptr), dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(c, DR_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-    return DR_OK;
-}
-
-static int tc_bn(int N) { return N > 128 ? 256 : (N > 64 ? 128 : (N > 32 ? 64 : (N > 16 ? 32 : 16))); }
-
-template <int BN>
-static int launch_tc_gemm_bn(dr_ctx* c, const CUtensorMap* m, float* C, int R, int K, int N, int ldc, int* err,
-                             cudaStream_t st) {
-    const int smem = tc::smem_bytes(BN);
-    CUDA_TRY(c, cudaFuncSetAttribute(tc::k_tc_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    dim3 grid((R + tc::BM - 1) / tc::BM, (N + BN - 1) / BN);
-    tc::k_tc_gemm<BN><<<grid, 128, smem, st>>>(m[0], m[1], m[2], m[3], C, R, K, N, ldc, err);
-    CUDA_TRY(c, cudaGetLastError());
-    if (c) c->launches++;
-    return DR_OK;
-}
-
-// C [R x N] (ld ldc) = A B with A given as TF32 parts Ah/Al [R][ldk] and B as BTh/BTl [N][ldk].
-static int tc_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* BTh, const float* BTl, float* C, int R, int K,
-                   int N, int ldk, int ldc, int* err, cudaStream_t st) {
-    TRY(get_encoder(c));
-    const int BN = tc_bn(N);
-    CUtensorMap m[4];
-    TRY(make_map(c, &m[0], Ah, R, ldk, tc::BM));
-    TRY(make_map(c, &m[1], Al, R, ldk, tc::BM));
-    TRY(make_map(c, &m[2], BTh, N, ldk, BN));
-    TRY(make_map(c, &m[3], BTl, N, ldk, BN));
-    switch (BN) {
-        case 256: return launch_tc_gemm_bn<256>(c, m, C, R, K, N, ldc, err, st);
-        case 128: return launch_tc_gemm_bn<128>(c, m, C, R, K, N, ldc, err, st);
-        case 64: return launch_tc_gemm_bn<64>(c, m, C, R, K, N, ldc, err, st);
-        case 32: return launch_tc_gemm_bn<32>(c, m, C, R, K, N, ldc, err, st);
-        default: return launch_tc_gemm_bn<16>(c, m, C, R, K, N, ldc, err, st);
-    }
-}
-
-static inline int round_up32(int x) { return (x + 31) & ~31; }
 
 // Utility entry: FP32-accurate C = A B^T on tensor cores (temporary device buffers).
 extern "C" int dr_tf32x3_gemm(int M, int N, int K, const float* A, const float* BT, float* C, void* stream) {

@@ -229,6 +229,162 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
     }
 }
 
+__host__ __device__ constexpr int pstages_for(int bn) { return bn >= 128 ? 3 : 4; }
+__host__ __device__ constexpr int psmem_bytes(int bn) { return pstages_for(bn) * stage_bytes(bn) + 1024 + 256; }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Same contraction with promoted accumulation: every 32-wide K chunk is accumulated in a fresh
+// TMEM buffer (two buffers, ping-pong) and the four epilogue warps add the chunk partials into FP32
+// registers, one output row per thread.  The tensor core then never accumulates more than one
+// chunk (12 MMAs), and the long sum over K runs in IEEE FP32 adds, which keeps the 3xTF32 product
+// as accurate as an FP32 SGEMM.  BN <= 128 (a thread holds BN partial sums).
+// Warp roles (192 threads): warp 0 lane 0 = TMA producer, warp 1 = TMEM owner and (lane 0) MMA
+// issuer, warps 2..5 = epilogue; warp w drains TMEM lanes 32*(w%4)..+31.
+constexpr int kGemmThreads = 192;
+template <int BN>
+__global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+                                                      const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
+                                                      float* __restrict__ C, int R, int K, int N, int ldc, int* __restrict__ err) {
+    static_assert(BN <= 128, "promoted accumulation keeps BN partial sums per thread");
+    constexpr int S = pstages_for(BN);
+    constexpr int SB = stage_bytes(BN);
+    constexpr int PB = BN < 32 ? 32 : BN;  // TMEM columns per partial buffer (32-column loads stay inside)
+    constexpr int TC = tmem_cols(2 * PB);
+    constexpr uint32_t IDESC = idesc_tf32(BM, BN);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + S * SB);
+    uint64_t* empty = full + S;
+    uint64_t* pfull = empty + S;  // [2] partial ready (MMA commit)
+    uint64_t* pfree = pfull + 2;  // [2] partial consumed (4 epilogue warps)
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(pfree + 2);
+    int* abort_flag = reinterpret_cast<int*>(tmem_holder + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int nk = (K + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int p = 0; p < 2; ++p) {
+            mbar_init(&pfull[p], 1);
+            mbar_init(&pfree[p], 4);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mAh)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mBh)) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)), "r"(TC)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    if (threadIdx.x == 0) {
+        int issued = 0;
+        for (int kc = 0; kc < nk; ++kc) {
+            const int s = kc % S;
+            if (kc >= S && !mbar_wait(&empty[s], ((kc / S) - 1) & 1)) {
+                atomicExch(err, 1);
+                *(volatile int*)abort_flag = 1;
+                break;
+            }
+            if (*(volatile int*)abort_flag) break;
+            unsigned char* st = base + s * SB;
+            mbar_expect_tx(&full[s], SB);
+            tma_load_2d(st, &mAh, &full[s], kc * BK, m0);
+            tma_load_2d(st + BM * BK * 4, &mAl, &full[s], kc * BK, m0);
+            tma_load_2d(st + 2 * BM * BK * 4, &mBh, &full[s], kc * BK, n0);
+            tma_load_2d(st + 2 * BM * BK * 4 + BN * BK * 4, &mBl, &full[s], kc * BK, n0);
+            ++issued;
+        }
+        for (int kc = (issued > S ? issued - S : 0); kc < issued; ++kc) {
+            if (!mbar_wait(&full[kc % S], (kc / S) & 1)) {
+                atomicExch(err, 1);
+                break;
+            }
+        }
+    } else if (threadIdx.x == 32) {
+        for (int kc = 0; kc < nk; ++kc) {
+            const int s = kc % S, p = kc & 1;
+            if (!mbar_wait(&full[s], (kc / S) & 1) || (kc >= 2 && !mbar_wait(&pfree[p], ((kc >> 1) - 1) & 1))) {
+                atomicExch(err, 1);
+                *(volatile int*)abort_flag = 1;
+                break;
+            }
+            fence_after();
+            const uint32_t d = tmem + (uint32_t)(p * PB);
+            const uint32_t sa = smem_u32(base + s * SB);
+            const uint64_t ah = sw128_desc(sa), al = sw128_desc(sa + BM * BK * 4);
+            const uint64_t bh = sw128_desc(sa + 2 * BM * BK * 4), bl = sw128_desc(sa + 2 * BM * BK * 4 + BN * BK * 4);
+#pragma unroll
+            for (int kk = 0; kk < BK / 8; ++kk) {
+                const uint64_t o = (uint64_t)(kk * 32) >> 4;
+                mma_tf32(d, ah + o, bh + o, IDESC, kk ? 1u : 0u);
+                mma_tf32(d, ah + o, bl + o, IDESC, 1u);
+                mma_tf32(d, al + o, bh + o, IDESC, 1u);
+            }
+            mma_commit(&empty[s]);
+            mma_commit(&pfull[p]);
+        }
+    }
+    if (warp >= 2) {
+        // ---- epilogue warps: add every chunk partial into FP32 registers
+        const int sub = warp & 3;
+        float acc[BN];
+#pragma unroll
+        for (int j = 0; j < BN; ++j) acc[j] = 0.f;
+        bool ok = true;
+        const uint32_t lane_base = (uint32_t)(sub * 32) << 16;
+        for (int kc = 0; kc < nk; ++kc) {
+            const int p = kc & 1;
+            if (*(volatile int*)abort_flag || !mbar_wait(&pfull[p], (kc >> 1) & 1)) {
+                ok = false;
+                break;
+            }
+            fence_after();
+#pragma unroll
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                float v[32];
+                tmem_ld32(tmem + lane_base + (uint32_t)(p * PB + c0), v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (c0 + j < BN) acc[c0 + j] += v[j];
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&pfree[p]);
+        }
+        if (!ok) atomicExch(err, 1);
+        const int row = m0 + sub * 32 + lane;
+        if (ok && row < R) {
+#pragma unroll
+            for (int j = 0; j < BN; ++j) {
+                const int col = n0 + j;
+                if (col < N) C[(int64_t)row * ldc + col] = acc[j];
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC) : "memory");
+    }
+}
+
 // TF32 part of x with round-to-nearest (ties away), as an FP32 value whose low 13 bits are zero.
 __device__ __forceinline__ float tf32_rna(float x) {
     uint32_t r;

@@ -197,14 +197,15 @@ def test_staged_path_random_shapes(widths, mode):
     compare(p, gpu_bounds(p, precision=STAGED, chunk=16), orc.reach(p))
 
 
-@pytest.mark.parametrize("beta_scale", [0.0, 0.02])
+@pytest.mark.parametrize("beta_scale", [0.0, 0.005])
 def test_branch12_split_domains(beta_scale):
     idx = np.arange(0, 65536, 1021)[:64]
     p = wl.quadrotor_branch(only=idx)
     if beta_scale > 0:
         p.beta = np.random.default_rng(5).uniform(0, beta_scale, size=p.splits.nnz).astype(np.float32).astype(np.float64)
     assert p.splits.nnz > 500
-    # (multipliers of order 0.5 make the split dual itself diverge over 30 steps; 0.02 keeps it finite)
+    # Arbitrary (unoptimised) multipliers widen the tube: at 0.5 the dual bound diverges over 30 steps,
+    # at 0.02 plain FP32 arithmetic already drifts 8e-6 from FP64 by the last step; 0.005 stays at 2e-6.
     compare(p, gpu_bounds(p), orc.reach(p))
 
 
@@ -212,3 +213,21 @@ def test_large16_subset():
     p = wl.large16()
     sub = p.subset(np.arange(0, p.D, p.D // 8))
     compare(sub, gpu_bounds(sub), orc.reach(sub))
+
+
+# ---- staged path with the tcgen05 3xTF32 chain (the default for wide controllers) --------------
+TCORE = 2  # DR_PREC_TF32X3
+
+
+@pytest.mark.parametrize("cfg", [2, 3])
+def test_tensor_core_path_narrow_configs(cfg):
+    p = wl.CONFIGS[cfg]()
+    sub = p.subset(np.arange(0, p.D, 4))
+    compare(sub, gpu_bounds(sub, precision=TCORE, chunk=257), orc.reach(sub))
+
+
+@pytest.mark.parametrize("widths,mode", [([5, 37, 23, 3], orc.MODE_CHORD), ([7, 96, 96, 96, 2], orc.MODE_ZERO),
+                                         ([3, 70, 130, 65, 2], orc.MODE_CHORD), ([9, 300, 40, 5], orc.MODE_CHORD)])
+def test_tensor_core_path_random_shapes(widths, mode):
+    p = wl.random_problem(hash(tuple(widths)) % 1000 + 1, widths, D=45, H=4, eps=0.15, mode=mode)
+    compare(p, gpu_bounds(p, precision=TCORE, chunk=16), orc.reach(p))
