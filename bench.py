@@ -53,6 +53,73 @@ def fused_flops_per_domain_step(widths):
     return 2 * mac
 
 
+def measure_refinement(local):
+    """Slope refinement on the cart-pole workload (1024 sub-boxes, H=20, 20 projected-gradient steps):
+    batched over all domains vs the plain per-domain form (one domain per call) on a sample."""
+    from paper_2605_25346_b300 import api
+    p = wl.cartpole_diff()
+    r = api.Reach(local).load(p)
+    r.optimize(1, 0.1, 0.0)  # warm-up (also compiles/loads every kernel)
+    r.close()
+    r = api.Reach(local).load(p)
+    torch.cuda.synchronize()
+    l0 = r.launches()
+    t0 = time.perf_counter()
+    hist = r.optimize(p.alpha_steps, 0.1, 0.0)
+    tb = time.perf_counter() - t0
+    launches = r.launches() - l0
+    Vb = r.objective()
+    r.close()
+    sample = 8
+    tp, Vp = 0.0, []
+    for d in range(sample):
+        q = p.subset([d])
+        rr = api.Reach(local).load(q)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rr.optimize(p.alpha_steps, 0.1, 0.0)
+        tp += time.perf_counter() - t0
+        Vp.append(rr.objective()[0])
+        rr.close()
+    gap = float(np.max(np.abs(np.array(Vp) - Vb[:sample]) / np.abs(Vb[:sample])))
+    return {"workload": "cart-pole 4-128-128-2, 1024 sub-boxes, H=20, 20 steps, lr 0.1",
+            "alpha_opt_steps_per_s": p.alpha_steps / tb, "batched_domains_per_s": p.D / tb,
+            "plain_domains_per_s": sample / tp, "plain_sample_domains": sample,
+            "batched_over_plain": (p.D / tb) / (sample / tp), "max_rel_V_gap_batched_vs_plain": gap,
+            "V_first": float(hist[0]), "V_best": float(hist[-1]), "gpu_launches": int(launches)}
+
+
+def measure_wide(local, reps=2):
+    """Throughput of the staged tcgen05 path on domain samples of the two wide workloads."""
+    from paper_2605_25346_b300 import api
+    out = {}
+    peak_tf32 = None
+    try:
+        import json as _json
+        mp = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peak_tf32 = mp["bf16_tflops"] * 1.1 / 2.25  # nominal TF32/BF16 ratio
+    except Exception:
+        peak_tf32 = 1800.0 * 1.1 / 2.25
+    for name, prob in (("branch12 12-256x3-4, 4096 of 65536 branch domains, H=30",
+                        wl.quadrotor_branch(only=np.arange(4096))),
+                       ("large16 16-512x4-8, 2048 of 262144 sub-boxes, H=50", wl.large16().subset(np.arange(2048)))):
+        r = api.Reach(local).load(prob)
+        r.bounds(on_device=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            r.bounds(on_device=True)
+        torch.cuda.synchronize()
+        t = (time.perf_counter() - t0) / reps
+        fl = fused_flops_per_domain_step(prob.widths) * prob.D * prob.H
+        out[name] = {"domain_steps_per_s": prob.D * prob.H / t, "ms_per_pass": 1e3 * t,
+                     "fp32eq_tflops_whole_pass": fl / t / 1e12,
+                     "fp32eq_peak_tflops": peak_tf32 / 3.0,
+                     "frac_of_fp32eq_tensor_peak": fl / t / 1e12 / (peak_tf32 / 3.0)}
+        r.close()
+    return out
+
+
 def workload(rank=0):
     p = wl.quad6_batched()
     if rank:
@@ -170,6 +237,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the refinement and wide-controller measurements")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -274,6 +342,10 @@ def main():
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             cpu = oracle_baseline(prob, target_s=10.0)
+        extras = {}
+        if not args.no_extras and world == 1:
+            extras["refinement"] = measure_refinement(local)
+            extras["wide"] = measure_wide(local)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
@@ -284,7 +356,7 @@ def main():
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": int(launches),
                 "wall_ms_per_step_incl_flush": 1e3 * t_wall / args.steps,
-                "roofline": roof, "cpu_baseline": cpu, "clocks": clock}
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clock, "extras": extras}
         print(json.dumps(line), flush=True)
     r.close()
     if world > 1:
