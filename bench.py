@@ -139,7 +139,8 @@ class ClockSampler:
     def __init__(self, index=0):
         self.index = index
         self.proc = None
-        self.lines = []
+        self.lines = []  # (host time, csv line)
+        self.window = (0.0, float("inf"))
 
     def __enter__(self):
         try:
@@ -148,13 +149,20 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t_end = time.time() + 5.0  # nvidia-smi needs a moment before its first sample
+            while not self.lines and time.time() < t_end:
+                time.sleep(0.05)
         except OSError:
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, start, end):
+        """Restrict the summary to samples taken in [start, end] (host time)."""
+        self.window = (start, end)
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -167,7 +175,8 @@ class ClockSampler:
     def summary(self):
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = [ln for ts, ln in self.lines if self.window[0] - 0.15 <= ts <= self.window[1] + 0.15]
+        for ln in lines:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -269,7 +278,7 @@ def main():
     def step(hull=True):
         r._c(r.lib.dr_compute_bounds(r.ctx, P(lo), P(hi), P(hl) if hull else None, P(hh) if hull else None, P(st), 1))
 
-    with torch.cuda.stream(stream):
+    with torch.cuda.stream(stream), ClockSampler(local) as clk:
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
@@ -277,16 +286,17 @@ def main():
             dist.barrier()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         l0 = r.launches()
-        with ClockSampler(local) as clk:
-            torch.cuda.synchronize()
-            t_wall = time.perf_counter()
-            for i in range(args.steps):
-                flush.zero_()  # L2 flush between timed steps (outside the events)
-                ev[i][0].record(stream)
-                step()
-                ev[i][1].record(stream)
-            torch.cuda.synchronize()
-            t_wall = time.perf_counter() - t_wall
+        torch.cuda.synchronize()
+        h0 = time.time()
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps (outside the events)
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+        clk.mark(h0, time.time())
         launches = r.launches() - l0
         step_ms = [a.elapsed_time(b) for a, b in ev]
         # the dominant kernel alone (no hull launch), for the roofline

@@ -14,6 +14,7 @@
 #include "common.cuh"
 #include "fused_core.cuh"
 #include "fused_bwd.cuh"
+#include "fused_multi.cuh"
 #include "wide.cuh"
 #include "tc_gemm.cuh"
 
@@ -246,7 +247,82 @@ static FusedLayout fused_layout(const NetDesc& N, bool backward = false) {
     return Y;
 }
 
+static MultiLayout multi_layout(const NetDesc& N, int G) {
+    MultiLayout Y;
+    memset(&Y, 0, sizeof(Y));
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = (off + 15) & ~size_t(15);
+        const size_t r = off;
+        off += bytes;
+        return (int)r;
+    };
+    const int n = N.n, m = N.m;
+    for (int l = 0; l < N.L; ++l) Y.Ws[l] = take(sizeof(float) * N.w[l + 1] * odd_ld(N.w[l]));
+    int nb = 0;
+    for (int l = 0; l < N.L; ++l) nb += N.w[l + 1];
+    Y.bs = take(sizeof(float) * nb);
+    Y.A = take(sizeof(double) * n * n);
+    Y.B = take(sizeof(double) * n * m);
+    Y.e = take(sizeof(double) * n);
+    Y.dom0 = (int)((off + 15) & ~size_t(15));
+    size_t d = 0;
+    auto dtake = [&](size_t bytes) {
+        d = (d + 15) & ~size_t(15);
+        const size_t r = d;
+        d += bytes;
+        return (int)r;
+    };
+    Y.c = dtake(sizeof(double) * n);
+    Y.P = dtake(sizeof(double) * n * n);
+    Y.Ilo = dtake(sizeof(double) * n);
+    Y.Ihi = dtake(sizeof(double) * n);
+    Y.v = dtake(sizeof(double) * n);
+    Y.w = dtake(sizeof(double) * 2);
+    Y.cn = dtake(sizeof(double) * n);
+    Y.Pn = dtake(sizeof(double) * n * n);
+    Y.Ilon = dtake(sizeof(double) * n);
+    Y.Ihin = dtake(sizeof(double) * n);
+    Y.red = dtake(sizeof(double) * (n + 1));
+    Y.cf = dtake(sizeof(float) * n);
+    Y.Pf = dtake(sizeof(float) * n * n);
+    Y.Ilof = dtake(sizeof(float) * n);
+    Y.Ihif = dtake(sizeof(float) * n);
+    Y.vf = dtake(sizeof(float) * (n + 1));
+    const int hid = std::max(N.hidden, 1);
+    Y.hl = dtake(sizeof(float) * hid);
+    Y.hu = dtake(sizeof(float) * hid);
+    Y.hs = dtake(sizeof(float) * hid);
+    Y.hd = dtake(sizeof(float) * hid);
+    Y.klo = dtake(sizeof(float) * N.maxw);
+    Y.khi = dtake(sizeof(float) * N.maxw);
+    size_t lam = 1;
+    for (int l = 2; l <= N.L; ++l)
+        for (int k = 0; k <= l - 2; ++k) lam = std::max(lam, (size_t)N.w[l] * odd_ld(N.w[k]));
+    Y.lam0 = dtake(sizeof(float) * lam);
+    Y.lam1 = dtake(sizeof(float) * lam);
+    Y.G = dtake(sizeof(float) * N.maxw * odd_ld(n));
+    Y.a = dtake(sizeof(float) * N.maxw);
+    Y.Rlo = dtake(sizeof(float) * N.maxw);
+    Y.Rhi = dtake(sizeof(float) * N.maxw);
+    Y.S = dtake(sizeof(float) * N.maxw);
+    Y.cu = dtake(sizeof(float) * m);
+    Y.Iulo = dtake(sizeof(float) * m);
+    Y.Iuhi = dtake(sizeof(float) * m);
+    Y.misc = dtake(sizeof(int) * 4);
+    Y.stride = (int)((d + 15) & ~size_t(15));
+    Y.total = Y.dom0 + G * Y.stride;
+    return Y;
+}
+
 static const int kMaxSmem = 227 * 1024;
+
+// Domains per CTA of the grouped forward kernel: the largest of 8, 4, 2, 1 that fits.
+static int multi_group(const NetDesc& N) {
+    for (int G = 8; G > 1; G >>= 1)
+        if (multi_layout(N, G).total <= kMaxSmem) return G;
+    return 1;
+}
 
 static bool fused_fits(const NetDesc& N) { return fused_layout(N).total <= kMaxSmem; }
 
@@ -892,6 +968,56 @@ static int run_forward(dr_ctx* c, int mode, float* alpha_used, bool tape) {
     if (!use_fused(c)) {
         if (tape) return fail(c, DR_ERR_SHAPE, "the reverse sweep needs a controller that fits the fused kernel");
         return run_forward_wide(c, mode, alpha_used);
+    }
+    if (!tape && multi_layout(N, 1).total <= kMaxSmem) {
+        // grouped kernel: G domains per CTA
+        const int G = multi_group(N);
+        MultiArgs a;
+        memset(&a, 0, sizeof(a));
+        a.net = N;
+        a.lay = multi_layout(N, G);
+        a.W = c->dW;
+        a.b = c->db;
+        a.A = c->dA;
+        a.B = c->dB;
+        a.e = c->de;
+        a.lo0 = c->dlo0;
+        a.hi0 = c->dhi0;
+        a.D = c->D;
+        a.sp_row = c->nnz ? c->dsp_row : nullptr;
+        a.sp = c->dsp;
+        a.beta = c->dbeta;
+        a.alpha = c->dalpha;
+        a.mode = mode;
+        a.rho = (float)c->opt.margin_rho;
+        a.box_margin = c->opt.box_margin;
+        a.lo = c->dout_lo;
+        a.hi = c->dout_hi;
+        a.V = c->dV;
+        a.status = c->dstatus;
+        a.alpha_used = alpha_used;
+        const int smem = a.lay.total;
+        const unsigned grid = (unsigned)((c->D + G - 1) / G);
+        switch (G) {
+            case 8:
+                CUDA_TRY(c, cudaFuncSetAttribute(k_fused_forward_multi<256, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                k_fused_forward_multi<256, 8><<<grid, 256, smem, c->stream>>>(a);
+                break;
+            case 4:
+                CUDA_TRY(c, cudaFuncSetAttribute(k_fused_forward_multi<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                k_fused_forward_multi<256, 4><<<grid, 256, smem, c->stream>>>(a);
+                break;
+            case 2:
+                CUDA_TRY(c, cudaFuncSetAttribute(k_fused_forward_multi<256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                k_fused_forward_multi<256, 2><<<grid, 256, smem, c->stream>>>(a);
+                break;
+            default:
+                CUDA_TRY(c, cudaFuncSetAttribute(k_fused_forward_multi<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                k_fused_forward_multi<256, 1><<<grid, 256, smem, c->stream>>>(a);
+        }
+        CUDA_TRY(c, cudaGetLastError());
+        c->launches++;
+        return DR_OK;
     }
     if (tape) TRY(ensure_tape(c));
     FusedArgs a;

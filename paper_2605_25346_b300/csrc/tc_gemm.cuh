@@ -328,12 +328,18 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CU
             const uint32_t sa = smem_u32(base + s * SB);
             const uint64_t ah = sw128_desc(sa), al = sw128_desc(sa + BM * BK * 4);
             const uint64_t bh = sw128_desc(sa + 2 * BM * BK * 4), bl = sw128_desc(sa + 2 * BM * BK * 4 + BN * BK * 4);
+            // small cross terms first, the large hi*hi terms last: the tensor core's accumulation
+            // rounds toward zero relative to the running magnitude, so fewer steps at full size
 #pragma unroll
             for (int kk = 0; kk < BK / 8; ++kk) {
                 const uint64_t o = (uint64_t)(kk * 32) >> 4;
-                mma_tf32(d, ah + o, bh + o, IDESC, kk ? 1u : 0u);
-                mma_tf32(d, ah + o, bl + o, IDESC, 1u);
+                mma_tf32(d, ah + o, bl + o, IDESC, kk ? 1u : 0u);
                 mma_tf32(d, al + o, bh + o, IDESC, 1u);
+            }
+#pragma unroll
+            for (int kk = 0; kk < BK / 8; ++kk) {
+                const uint64_t o = (uint64_t)(kk * 32) >> 4;
+                mma_tf32(d, ah + o, bh + o, IDESC, 1u);
             }
             mma_commit(&empty[s]);
             mma_commit(&pfull[p]);
