@@ -89,7 +89,10 @@ typedef struct dr_options {
                               default 2^-18, calibrated to cover the measured deviation of the
                               FP32 controller pass from FP64 arithmetic (it does not feed back
                               into the Taylor model)                                        */
-    int32_t reserved[6];
+    int32_t tuning;        /* 0 = pick the fused kernel's launch shape by timing the candidates on
+                              first use (cached per architecture and widths; file DR_TUNE_CACHE
+                              if set), 1 = no search                                          */
+    int32_t reserved[5];
 } dr_options;
 
 /* Create a context on `device` whose work is ordered on `cuda_stream` (a cudaStream_t;

@@ -40,7 +40,8 @@ class dr_static_args(ctypes.Structure):
 class dr_options(ctypes.Structure):
     _fields_ = [("slope_mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("margin_rho", ctypes.c_double),
                 ("chunk_domains", ctypes.c_int64), ("mem_cap_bytes", ctypes.c_int64),
-                ("box_margin", ctypes.c_double), ("reserved", ctypes.c_int32 * 6)]
+                ("box_margin", ctypes.c_double), ("tuning", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 _lib = None

@@ -3,6 +3,8 @@
 
 #include <algorithm>
 #include <limits>
+#include <map>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -265,6 +267,21 @@ static MultiLayout multi_layout(const NetDesc& N, int G) {
     Y.A = take(sizeof(double) * n * n);
     Y.B = take(sizeof(double) * n * m);
     Y.e = take(sizeof(double) * n);
+    {
+        size_t chain = 4, bsz = 4, esz = 2;
+        for (int l = 2; l <= N.L; ++l) {
+            for (int mm = l - 1; mm >= 1; --mm) chain = std::max(chain, (size_t)G * N.w[l] * odd_ld(N.w[mm - 1]));
+            if (N.w[l - 2] <= 16) {
+                chain = std::max(chain, (size_t)N.w[l] * ru4(G * N.w[l - 2]));
+                bsz = std::max(bsz, (size_t)N.w[l - 1] * ru4(G * N.w[l - 2]));
+            }
+            esz = std::max(esz, (size_t)N.w[l - 1] * G * 2);
+        }
+        Y.chA = take(sizeof(float) * chain);
+        Y.chB = take(sizeof(float) * chain);
+        Y.Bs = take(sizeof(float) * bsz);
+        Y.E = take(sizeof(float) * esz);
+    }
     Y.dom0 = (int)((off + 15) & ~size_t(15));
     size_t d = 0;
     auto dtake = [&](size_t bytes) {
@@ -296,11 +313,6 @@ static MultiLayout multi_layout(const NetDesc& N, int G) {
     Y.hd = dtake(sizeof(float) * hid);
     Y.klo = dtake(sizeof(float) * N.maxw);
     Y.khi = dtake(sizeof(float) * N.maxw);
-    size_t lam = 1;
-    for (int l = 2; l <= N.L; ++l)
-        for (int k = 0; k <= l - 2; ++k) lam = std::max(lam, (size_t)N.w[l] * odd_ld(N.w[k]));
-    Y.lam0 = dtake(sizeof(float) * lam);
-    Y.lam1 = dtake(sizeof(float) * lam);
     Y.G = dtake(sizeof(float) * N.maxw * odd_ld(n));
     Y.a = dtake(sizeof(float) * N.maxw);
     Y.Rlo = dtake(sizeof(float) * N.maxw);
@@ -317,12 +329,6 @@ static MultiLayout multi_layout(const NetDesc& N, int G) {
 
 static const int kMaxSmem = 227 * 1024;
 
-// Domains per CTA of the grouped forward kernel: the largest of 8, 4, 2, 1 that fits.
-static int multi_group(const NetDesc& N) {
-    for (int G = 8; G > 1; G >>= 1)
-        if (multi_layout(N, G).total <= kMaxSmem) return G;
-    return 1;
-}
 
 static bool fused_fits(const NetDesc& N) { return fused_layout(N).total <= kMaxSmem; }
 
@@ -396,6 +402,133 @@ static int tc_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* BTh
 }
 
 static inline int round_up32(int x) { return (x + 31) & ~31; }
+
+// ------------------------------------------------------------------------------------------------
+// grouped fused kernel: launch variants and the autotuner
+// ------------------------------------------------------------------------------------------------
+
+struct MultiVariant {
+    int threads, group;
+};
+static const MultiVariant kMultiVariants[] = {{256, 8}, {512, 8}, {256, 4}, {512, 4}, {128, 2}, {256, 2}, {128, 1}};
+static const int kNumMultiVariants = (int)(sizeof(kMultiVariants) / sizeof(kMultiVariants[0]));
+
+template <int NT, int G>
+static int launch_multi_t(dr_ctx* c, MultiArgs a) {
+    a.lay = multi_layout(a.net, G);
+    const int smem = a.lay.total;
+    if (smem > kMaxSmem) return fail(c, DR_ERR_SHAPE, "grouped variant does not fit shared memory");
+    CUDA_TRY(c, cudaFuncSetAttribute(k_fused_forward_multi<NT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    k_fused_forward_multi<NT, G><<<(unsigned)((a.D + G - 1) / G), NT, smem, c->stream>>>(a);
+    CUDA_TRY(c, cudaGetLastError());
+    c->launches++;
+    return DR_OK;
+}
+
+static int launch_multi(dr_ctx* c, const MultiArgs& a, int v) {
+    switch (v) {
+        case 0: return launch_multi_t<256, 8>(c, a);
+        case 1: return launch_multi_t<512, 8>(c, a);
+        case 2: return launch_multi_t<256, 4>(c, a);
+        case 3: return launch_multi_t<512, 4>(c, a);
+        case 4: return launch_multi_t<128, 2>(c, a);
+        case 5: return launch_multi_t<256, 2>(c, a);
+        default: return launch_multi_t<128, 1>(c, a);
+    }
+}
+
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune_cache;
+static bool g_tune_file_loaded = false;
+
+static std::string tune_key(const NetDesc& N, int dev) {
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, dev);
+    std::string k = std::string("sm") + std::to_string(prop.major) + std::to_string(prop.minor) + ":";
+    for (int l = 0; l <= N.L; ++l) k += std::to_string(N.w[l]) + (l < N.L ? "-" : "");
+    return k;
+}
+
+// Tuning cache file (optional): one "key variant" pair per line, path from DR_TUNE_CACHE.
+static void tune_file_load() {
+    if (g_tune_file_loaded) return;
+    g_tune_file_loaded = true;
+    const char* path = getenv("DR_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    char key[512];
+    int v;
+    while (fscanf(f, "%511s %d", key, &v) == 2)
+        if (v >= 0 && v < kNumMultiVariants) g_tune_cache[key] = v;
+    fclose(f);
+}
+
+static void tune_file_store() {
+    const char* path = getenv("DR_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = fopen(path, "w");
+    if (!f) return;
+    for (const auto& kv : g_tune_cache) fprintf(f, "%s %d\n", kv.first.c_str(), kv.second);
+    fclose(f);
+}
+
+// Pick the fastest fitting (threads, domains per CTA) variant for this controller shape: each
+// candidate runs once on a sample of up to 2048 domains and 2 steps (CUDA events on the context's
+// stream), the winner is cached per (architecture, widths).  dr_options.tuning = 1 disables the
+// search and takes the first fitting variant with the largest group.
+static int tuned_variant(dr_ctx* c, const MultiArgs& a, int* out) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_file_load();
+    const std::string key = tune_key(a.net, c->device);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+        *out = it->second;
+        return DR_OK;
+    }
+    int first_fit = -1;
+    for (int v = 0; v < kNumMultiVariants; ++v)
+        if (multi_layout(a.net, kMultiVariants[v].group).total <= kMaxSmem) {
+            first_fit = v;
+            break;
+        }
+    if (first_fit < 0) return fail(c, DR_ERR_SHAPE, "no grouped variant fits shared memory");
+    if (c->opt.tuning == 1 || c->D == 0) {
+        *out = first_fit;
+        return DR_OK;
+    }
+    MultiArgs t = a;
+    t.D = std::min<int64_t>(a.D, 2048);
+    t.net.H = std::min(a.net.H, 2);
+    t.V = nullptr;
+    t.status = nullptr;
+    t.alpha_used = nullptr;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(c, cudaEventCreate(&e0));
+    CUDA_TRY(c, cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bestv = first_fit;
+    for (int v = 0; v < kNumMultiVariants; ++v) {
+        if (multi_layout(a.net, kMultiVariants[v].group).total > kMaxSmem) continue;
+        TRY(launch_multi(c, t, v));  // warm-up
+        CUDA_TRY(c, cudaEventRecord(e0, c->stream));
+        TRY(launch_multi(c, t, v));
+        CUDA_TRY(c, cudaEventRecord(e1, c->stream));
+        CUDA_TRY(c, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CUDA_TRY(c, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            bestv = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g_tune_cache[key] = bestv;
+    tune_file_store();
+    *out = bestv;
+    return DR_OK;
+}
 
 extern "C" {
 
@@ -970,12 +1103,10 @@ static int run_forward(dr_ctx* c, int mode, float* alpha_used, bool tape) {
         return run_forward_wide(c, mode, alpha_used);
     }
     if (!tape && multi_layout(N, 1).total <= kMaxSmem) {
-        // grouped kernel: G domains per CTA
-        const int G = multi_group(N);
+        // grouped kernel: G domains per CTA, (threads, G) chosen by the autotuner
         MultiArgs a;
         memset(&a, 0, sizeof(a));
         a.net = N;
-        a.lay = multi_layout(N, G);
         a.W = c->dW;
         a.b = c->db;
         a.A = c->dA;
@@ -996,27 +1127,9 @@ static int run_forward(dr_ctx* c, int mode, float* alpha_used, bool tape) {
         a.V = c->dV;
         a.status = c->dstatus;
         a.alpha_used = alpha_used;
-        const int smem = a.lay.total;
-        const unsigned grid = (unsigned)((c->D + G - 1) / G);
-        switch (G) {
-            case 8:
-                CUDA_TRY(c, cudaFuncSetAttribute(k_fused_forward_multi<256, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-                k_fused_forward_multi<256, 8><<<grid, 256, smem, c->stream>>>(a);
-                break;
-            case 4:
-                CUDA_TRY(c, cudaFuncSetAttribute(k_fused_forward_multi<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-                k_fused_forward_multi<256, 4><<<grid, 256, smem, c->stream>>>(a);
-                break;
-            case 2:
-                CUDA_TRY(c, cudaFuncSetAttribute(k_fused_forward_multi<256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-                k_fused_forward_multi<256, 2><<<grid, 256, smem, c->stream>>>(a);
-                break;
-            default:
-                CUDA_TRY(c, cudaFuncSetAttribute(k_fused_forward_multi<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-                k_fused_forward_multi<256, 1><<<grid, 256, smem, c->stream>>>(a);
-        }
-        CUDA_TRY(c, cudaGetLastError());
-        c->launches++;
+        int variant = 0;
+        TRY(tuned_variant(c, a, &variant));
+        TRY(launch_multi(c, a, variant));
         return DR_OK;
     }
     if (tape) TRY(ensure_tape(c));

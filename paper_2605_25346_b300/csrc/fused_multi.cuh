@@ -10,6 +10,8 @@
 struct MultiLayout {  // shared: byte offsets from the CTA base; per domain: from the domain base
     int Ws[DR_MAXL];
     int bs, A, B, e;
+    int chA, chB;  // CTA-level chain buffers (all domains of the CTA)
+    int Bs, E;     // first-level right operand [K][ldb] and intercept table [K][G] (float2)
     int dom0;    // start of the first domain's region
     int stride;  // bytes per domain region
     // per-domain offsets
@@ -50,6 +52,95 @@ struct MultiArgs {
 #define MI(g, off) reinterpret_cast<int*>(sm + Y.dom0 + (g) * Y.stride + (off))
 #define SF(off) reinterpret_cast<float*>(sm + (off))
 #define SD(off) reinterpret_cast<double*>(sm + (off))
+
+__host__ __device__ __forceinline__ int ru4(int x) { return (x + 3) & ~3; }
+
+// C [M x N] (ld ldc) = A [M x K] (ld lda) * B [K x N] (ld ldb, ldb % 4 == 0, 16-byte aligned, padding
+// columns finite): 4 x 4 register tiles, one float4 of B and four A values per k.
+template <int NT>
+__device__ __forceinline__ void gemm_shared_a(const float* __restrict__ A, int lda, const float* __restrict__ B, int ldb,
+                                              float* __restrict__ C, int ldc, int M, int K, int N) {
+    const int tilesM = (M + 3) >> 2, tilesN = (N + 3) >> 2;
+    for (int tt = threadIdx.x; tt < tilesM * tilesN; tt += NT) {
+        const int tm = tt / tilesN, tn = tt - tm * tilesN;
+        const int i0 = tm << 2, c0 = tn << 2;
+        const float* a0 = A + min(i0, M - 1) * lda;
+        const float* a1 = A + min(i0 + 1, M - 1) * lda;
+        const float* a2 = A + min(i0 + 2, M - 1) * lda;
+        const float* a3 = A + min(i0 + 3, M - 1) * lda;
+        const float* bp = B + c0;
+        float acc[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
+#pragma unroll 4
+        for (int j = 0; j < K; ++j) {
+            const float4 b = *reinterpret_cast<const float4*>(bp + j * ldb);
+            const float x[4] = {a0[j], a1[j], a2[j], a3[j]};
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                acc[r][0] = fmaf(x[r], b.x, acc[r][0]);
+                acc[r][1] = fmaf(x[r], b.y, acc[r][1]);
+                acc[r][2] = fmaf(x[r], b.z, acc[r][2]);
+                acc[r][3] = fmaf(x[r], b.w, acc[r][3]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if (i0 + r >= M) break;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (c0 + q < N) C[(i0 + r) * ldc + c0 + q] = acc[r][q];
+        }
+    }
+}
+
+// Stacked rows of all domains: C[(g*rows + i)*ldc + k] = sum_j A_g[i][j] s_g[j] B[j][k] for g < gcount,
+// A_g = Ab + g*a_gs + i*lda (a_gs = 0: one shared A), s_g = sb + g*s_gs, B [K][N] (ld ldb).  4 x 4 tiles.
+template <int NT>
+__device__ __forceinline__ void gemm_stacked_scaled(const float* __restrict__ Ab, int a_gs, int lda, const float* __restrict__ sb,
+                                                    int s_gs, const float* __restrict__ B, int ldb, float* __restrict__ C,
+                                                    int ldc, int gcount, int rows, int K, int N) {
+    const int M = gcount * rows;
+    const int tilesM = (M + 3) >> 2, tilesN = (N + 3) >> 2;
+    for (int tt = threadIdx.x; tt < tilesM * tilesN; tt += NT) {
+        const int tm = tt / tilesN, tn = tt - tm * tilesN;
+        const int i0 = tm << 2, c0 = tn << 2;
+        const float* ap[4];
+        const float* sp[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int R = min(i0 + r, M - 1), g = R / rows, i = R - g * rows;
+            ap[r] = Ab + g * a_gs + i * lda;
+            sp[r] = sb + g * s_gs;
+        }
+        const int cc[4] = {min(c0, N - 1), min(c0 + 1, N - 1), min(c0 + 2, N - 1), min(c0 + 3, N - 1)};
+        float acc[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
+#pragma unroll 2
+        for (int j = 0; j < K; ++j) {
+            const float* brow = B + j * ldb;
+            const float b[4] = {brow[cc[0]], brow[cc[1]], brow[cc[2]], brow[cc[3]]};
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float x = ap[r][j] * sp[r][j];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(x, b[q], acc[r][q]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if (i0 + r >= M) break;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (c0 + q < N) C[(i0 + r) * ldc + c0 + q] = acc[r][q];
+        }
+    }
+}
 
 template <int NT, int G>
 __global__ void __launch_bounds__(NT) k_fused_forward_multi(const MultiArgs a) {
@@ -148,52 +239,112 @@ __global__ void __launch_bounds__(NT) k_fused_forward_multi(const MultiArgs a) {
                 MF(g, Y.klo)[i] = bl[i];
                 MF(g, Y.khi)[i] = bl[i];
             }
-            // ---- a4 chain; level matrices per domain, the first level reads the shared W_ell
-            int cur_off = -1;  // -1: the shared W_ell
+            // ---- a4 chain over all domains of the CTA.  Domain g's current matrix starts at
+            // curb + g * cur_gs with row stride cur_ld (cur_gs = 0: the shared W_ell).
+            float* curb = SF(Y.Ws[ell - 1]);
+            int cur_gs = 0;
             int cur_ld = odd_ld(N.w[ell - 1]);
             int cur_cols = N.w[ell - 1];
             int buf = 0;
             __syncthreads();
             for (int mm = ell - 1; mm >= 1; --mm) {
                 const float* bm = bs + N.boff[mm - 1];
-                for (int idx = tid; idx < gcount * rows; idx += NT) {
-                    const int g = idx / rows, i = idx - g * rows;
-                    const float* row = (cur_off < 0 ? SF(Y.Ws[ell - 1]) : MF(g, cur_off)) + i * cur_ld;
-                    const float* sl = MF(g, Y.hs) + N.hoff[mm];
-                    const float* dl = MF(g, Y.hd) + N.hoff[mm];
-                    float spos = 0.f, sneg = 0.f, sb = 0.f;
-                    for (int j = 0; j < cur_cols; ++j) {
-                        const float x = row[j];
-                        spos = fmaf(posf(x), dl[j], spos);
-                        sneg = fmaf(negf(x), dl[j], sneg);
-                        sb = fmaf(x * sl[j], bm[j], sb);
-                    }
-                    MF(g, Y.khi)[i] += spos + sb;
-                    MF(g, Y.klo)[i] += sneg + sb;
-                }
                 const int K = N.w[mm], NN = N.w[mm - 1];
                 const float* Wm = SF(Y.Ws[mm - 1]);
                 const int wld = odd_ld(NN);
-                const int nxt_off = buf ? Y.lam1 : Y.lam0;
-                const int nld = odd_ld(NN);
-                for (int idx = tid; idx < gcount * rows * NN; idx += NT) {
-                    const int g = idx / (rows * NN), r = idx - g * rows * NN, i = r / NN, k = r - i * NN;
-                    const float* row = (cur_off < 0 ? SF(Y.Ws[ell - 1]) : MF(g, cur_off)) + i * cur_ld;
-                    const float* sl = MF(g, Y.hs) + N.hoff[mm];
-                    float acc = 0.f;
-                    for (int j = 0; j < K; ++j) acc = fmaf(row[j] * sl[j], Wm[j * wld + k], acc);
-                    MF(g, nxt_off)[i * nld + k] = acc;
+                float* nxt = SF(buf ? Y.chB : Y.chA);
+                const bool first = (cur_gs == 0);
+                const bool shared_a = first && NN <= 16;
+                float2* E = reinterpret_cast<float2*>(sm + Y.E);
+                if (first) {
+                    // intercept table E[j][g] = (d_gj, s_gj b_j) for the shared W_ell rows
+                    for (int idx = tid; idx < K * G; idx += NT) {
+                        const int j = idx / G, g = idx - j * G;
+                        float2 ev = make_float2(0.f, 0.f);
+                        if (g < gcount) ev = make_float2(MF(g, Y.hd)[N.hoff[mm] + j], MF(g, Y.hs)[N.hoff[mm] + j] * bm[j]);
+                        E[idx] = ev;
+                    }
                 }
-                __syncthreads();
-                cur_off = nxt_off;
-                cur_ld = nld;
+                const int ldb = ru4(G * NN);
+                if (shared_a) {
+                    // right operand [K][g*NN + k] = s_gj W_mm[j][k]; one GEMM with the shared W_ell
+                    float* Bs = SF(Y.Bs);
+                    for (int idx = tid; idx < K * ldb; idx += NT) {
+                        const int j = idx / ldb, col = idx - j * ldb;
+                        const int g = col / NN, k = col - g * NN;
+                        float val = 0.f;
+                        if (g < gcount) val = MF(g, Y.hs)[N.hoff[mm] + j] * Wm[j * wld + k];
+                        Bs[idx] = val;
+                    }
+                }
+                if (first) __syncthreads();
+                if (first) {
+                    // intercepts: thread = (row i, GQ domains); the W_ell row is loaded once for them
+                    constexpr int GQ = G < 4 ? G : 4;
+                    const int gq = G / GQ;
+                    for (int idx = tid; idx < rows * gq; idx += NT) {
+                        const int i = idx / gq, g0 = (idx - i * gq) * GQ;
+                        const float* row = curb + i * cur_ld;
+                        float sp[GQ], sn[GQ], sbv[GQ];
+#pragma unroll
+                        for (int q = 0; q < GQ; ++q) sp[q] = sn[q] = sbv[q] = 0.f;
+                        for (int j = 0; j < cur_cols; ++j) {
+                            const float x = row[j], xp = posf(x), xn = negf(x);
+#pragma unroll
+                            for (int q = 0; q < GQ; ++q) {
+                                const float2 ev = E[j * G + g0 + q];
+                                sp[q] = fmaf(xp, ev.x, sp[q]);
+                                sn[q] = fmaf(xn, ev.x, sn[q]);
+                                sbv[q] = fmaf(x, ev.y, sbv[q]);
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < GQ; ++q) {
+                            if (g0 + q < gcount) {
+                                MF(g0 + q, Y.khi)[i] += sp[q] + sbv[q];
+                                MF(g0 + q, Y.klo)[i] += sn[q] + sbv[q];
+                            }
+                        }
+                    }
+                } else {
+                    for (int idx = tid; idx < gcount * rows; idx += NT) {
+                        const int g = idx / rows, i = idx - g * rows;
+                        const float* row = curb + g * cur_gs + i * cur_ld;
+                        const float* sl = MF(g, Y.hs) + N.hoff[mm];
+                        const float* dl = MF(g, Y.hd) + N.hoff[mm];
+                        float spos = 0.f, sneg = 0.f, sb = 0.f;
+                        for (int j = 0; j < cur_cols; ++j) {
+                            const float x = row[j];
+                            spos = fmaf(posf(x), dl[j], spos);
+                            sneg = fmaf(negf(x), dl[j], sneg);
+                            sb = fmaf(x * sl[j], bm[j], sb);
+                        }
+                        MF(g, Y.khi)[i] += spos + sb;
+                        MF(g, Y.klo)[i] += sneg + sb;
+                    }
+                }
+                if (shared_a) {
+                    gemm_shared_a<NT>(curb, cur_ld, SF(Y.Bs), ldb, nxt, ldb, rows, K, G * NN);
+                    __syncthreads();
+                    curb = nxt;
+                    cur_gs = NN;
+                    cur_ld = ldb;
+                } else {
+                    const int nld = odd_ld(NN);
+                    gemm_stacked_scaled<NT>(curb, cur_gs, cur_ld, MF(0, Y.hs) + N.hoff[mm], Y.stride / 4, Wm, wld, nxt, nld,
+                                            gcount, rows, K, NN);
+                    __syncthreads();
+                    curb = nxt;
+                    cur_gs = rows * nld;
+                    cur_ld = nld;
+                }
                 cur_cols = NN;
                 buf ^= 1;
             }
             // ---- a5 / a6 concretisation
             for (int idx = tid; idx < gcount * rows * n; idx += NT) {
                 const int g = idx / (rows * n), r = idx - g * rows * n, i = r / n, k = r - i * n;
-                const float* row = (cur_off < 0 ? SF(Y.Ws[ell - 1]) : MF(g, cur_off)) + i * cur_ld;
+                const float* row = curb + g * cur_gs + i * cur_ld;
                 const float* Pf = MF(g, Y.Pf);
                 float acc = 0.f;
                 for (int j = 0; j < n; ++j) acc = fmaf(row[j], Pf[j * n + k], acc);
@@ -202,7 +353,7 @@ __global__ void __launch_bounds__(NT) k_fused_forward_multi(const MultiArgs a) {
             __syncthreads();
             for (int idx = tid; idx < gcount * rows; idx += NT) {
                 const int g = idx / rows, i = idx - g * rows;
-                const float* row = (cur_off < 0 ? SF(Y.Ws[ell - 1]) : MF(g, cur_off)) + i * cur_ld;
+                const float* row = curb + g * cur_gs + i * cur_ld;
                 const float* cf = MF(g, Y.cf);
                 const float* Ilof = MF(g, Y.Ilof);
                 const float* Ihif = MF(g, Y.Ihif);
