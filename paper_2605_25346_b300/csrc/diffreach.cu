@@ -371,21 +371,22 @@ static int make_map(dr_ctx* c, CUtensorMap* map, const float* ptr, int64_t rows,
 
 static int tc_bn(int N) { return N > 64 ? 128 : (N > 32 ? 64 : (N > 16 ? 32 : 16)); }
 
-template <int BN>
+template <int BN, bool EPI>
 static int launch_tc_gemm_bn(dr_ctx* c, const CUtensorMap* m, float* C, int R, int K, int N, int ldc, int* err,
-                             cudaStream_t st) {
+                             cudaStream_t st, const tc::ChainEpi& epi) {
     const int smem = tc::psmem_bytes(BN);
-    CUDA_TRY(c, cudaFuncSetAttribute(tc::k_tc_gemm_p<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CUDA_TRY(c, cudaFuncSetAttribute(tc::k_tc_gemm_p<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     dim3 grid((R + tc::BM - 1) / tc::BM, (N + BN - 1) / BN);
-    tc::k_tc_gemm_p<BN><<<grid, tc::kGemmThreads, smem, st>>>(m[0], m[1], m[2], m[3], C, R, K, N, ldc, err);
+    tc::k_tc_gemm_p<BN, EPI><<<grid, tc::kGemmThreads, smem, st>>>(m[0], m[1], m[2], m[3], C, R, K, N, ldc, err, epi);
     CUDA_TRY(c, cudaGetLastError());
     if (c) c->launches++;
     return DR_OK;
 }
 
-// C [R x N] (ld ldc) = A B with A given as TF32 parts Ah/Al [R][ldk] and B as BTh/BTl [N][ldk].
+// C [R x N] (ld ldc) = A B with A given as TF32 parts Ah/Al [R][ldk] and B as BTh/BTl [N][ldk]; with
+// `epi` the chain epilogue replaces the store of C.
 static int tc_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* BTh, const float* BTl, float* C, int R, int K,
-                   int N, int ldk, int ldc, int* err, cudaStream_t st) {
+                   int N, int ldk, int ldc, int* err, cudaStream_t st, const tc::ChainEpi* epi = nullptr) {
     TRY(get_encoder(c));
     const int BN = tc_bn(N);
     CUtensorMap m[4];
@@ -393,12 +394,21 @@ static int tc_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* BTh
     TRY(make_map(c, &m[1], Al, R, ldk, tc::BM));
     TRY(make_map(c, &m[2], BTh, N, ldk, BN));
     TRY(make_map(c, &m[3], BTl, N, ldk, BN));
+    tc::ChainEpi e{};
+    if (epi) e = *epi;
+#define DR_TC_CASE(bn)                                                                          \
+    case bn:                                                                                    \
+        return epi ? launch_tc_gemm_bn<bn, true>(c, m, C, R, K, N, ldc, err, st, e)             \
+                   : launch_tc_gemm_bn<bn, false>(c, m, C, R, K, N, ldc, err, st, e);
     switch (BN) {
-        case 128: return launch_tc_gemm_bn<128>(c, m, C, R, K, N, ldc, err, st);
-        case 64: return launch_tc_gemm_bn<64>(c, m, C, R, K, N, ldc, err, st);
-        case 32: return launch_tc_gemm_bn<32>(c, m, C, R, K, N, ldc, err, st);
-        default: return launch_tc_gemm_bn<16>(c, m, C, R, K, N, ldc, err, st);
+        DR_TC_CASE(128)
+        DR_TC_CASE(64)
+        DR_TC_CASE(32)
+        default:
+            return epi ? launch_tc_gemm_bn<16, true>(c, m, C, R, K, N, ldc, err, st, e)
+                       : launch_tc_gemm_bn<16, false>(c, m, C, R, K, N, ldc, err, st, e);
     }
+#undef DR_TC_CASE
 }
 
 static inline int round_up32(int x) { return (x + 31) & ~31; }
@@ -899,6 +909,16 @@ static int64_t wide_lam_stride(const NetDesc& N) {
     return best;
 }
 
+static int64_t wide_part_per_domain(const NetDesc& N) {
+    int64_t best = 1;
+    for (int l = 2; l <= N.L; ++l)
+        for (int mm = l - 1; mm >= 2; --mm) {
+            const int NN = N.w[mm - 1], bn = tc_bn(NN);
+            best = std::max<int64_t>(best, (int64_t)N.w[l] * ((NN + bn - 1) / bn));
+        }
+    return best;
+}
+
 static size_t wide_bytes_per_domain(const NetDesc& N) {
     const int n = N.n, m = N.m;
     size_t b = 0;
@@ -909,12 +929,13 @@ static size_t wide_bytes_per_domain(const NetDesc& N) {
     b += sizeof(float) * 2 * N.maxw;                              // kappa
     b += sizeof(float) * ((size_t)N.maxw * n + 4 * N.maxw);       // G, a, R, S
     b += sizeof(float) * 3 * m;                                   // controller TM
-    b += sizeof(float) * 3 * wide_lam_stride(N);                  // Lambda buffers (two + GEMM output)
+    b += sizeof(float) * 4 * wide_lam_stride(N);                  // Lambda buffers (two TF32 pairs)
+    b += sizeof(float) * 3 * wide_part_per_domain(N);             // intercept partials of fused levels
     return b + 16 * 24;
 }
 
 // Carve the chunk scratch for Dc domains out of one allocation.
-static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, float** lamA, float** lamB, float** lamC) {
+static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, float** lamA, float** lamB, float** lamC, float** lamD, float** part) {
     const NetDesc& N = a.net;
     const size_t need = wide_bytes_per_domain(N) * (size_t)Dc + 4096;
     if (!c->wscratch || c->wscratch_bytes < need || c->wDc != Dc) {
@@ -968,6 +989,8 @@ static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, float** lamA, float** lamB,
     *lamA = (float*)take(sizeof(float) * D * a.lam_stride);
     *lamB = (float*)take(sizeof(float) * D * a.lam_stride);
     *lamC = (float*)take(sizeof(float) * D * a.lam_stride);
+    *lamD = (float*)take(sizeof(float) * D * a.lam_stride);
+    *part = (float*)take(sizeof(float) * D * 3 * wide_part_per_domain(N));
     if (off > c->wscratch_bytes) return fail(c, DR_ERR_OOM, "staged scratch layout overflow");
     return DR_OK;
 }
@@ -1008,8 +1031,8 @@ static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
     a.status = c->dstatus;
     a.alpha_used = alpha_used;
     const int Dc = wide_chunk(c, N);
-    float *lamA = nullptr, *lamB = nullptr, *lamC = nullptr;
-    TRY(wide_bind(c, a, Dc, &lamA, &lamB, &lamC));
+    float *lamA = nullptr, *lamB = nullptr, *lamC = nullptr, *lamD = nullptr, *part = nullptr;
+    TRY(wide_bind(c, a, Dc, &lamA, &lamB, &lamC, &lamD, &part));
     const bool tcore = c->opt.precision != DR_PREC_SIMT;
     if (tcore) CUDA_TRY(c, cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream));
     const size_t dyn_smem = sizeof(double) * (n * n + 3 * n + 128);
@@ -1046,25 +1069,41 @@ static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
                     else k_w_project<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, ell, cur, 0);
                     c->launches++;
                 } else {
-                    // tensor-core chain: rows of all domains stacked, A as TF32 parts, shared W^T parts
+                    // tensor-core chain: rows of all domains stacked, A as TF32 parts, shared W^T parts;
+                    // levels that feed another level form the next operand in the GEMM epilogue
                     const int R = dc * rows;
                     int ldk = round_up32(N.w[ell - 1]);
                     k_t_chain_init<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, ell, lamA, lamB, ldk);
                     c->launches++;
+                    float *curh = lamA, *curl = lamB, *nxth = lamC, *nxtl = lamD;
                     for (int mm = ell - 1; mm >= 1; --mm) {
                         const int K = N.w[mm], NN = N.w[mm - 1];
-                        TRY(tc_gemm(c, lamA, lamB, c->dWTh + c->WToff[mm - 1], c->dWTl + c->WToff[mm - 1], lamC, R, K, NN, ldk,
-                                    NN, c->derr, c->stream));
+                        const float* WTh = c->dWTh + c->WToff[mm - 1];
+                        const float* WTl = c->dWTl + c->WToff[mm - 1];
                         if (mm - 1 >= 1) {
-                            ldk = round_up32(NN);
-                            k_t_level_epi<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, ell, mm - 1, lamC, lamA,
-                                                                                             lamB, ldk);
+                            tc::ChainEpi epi{};
+                            epi.hs = a.hs;
+                            epi.hd = a.hd;
+                            epi.bias = c->db + N.boff[mm - 2];
+                            epi.hidden = N.hidden;
+                            epi.hoff = N.hoff[mm - 1];
+                            epi.rows_per_dom = rows;
+                            epi.Ah = nxth;
+                            epi.Al = nxtl;
+                            epi.ldk = round_up32(NN);
+                            epi.part = part;
+                            TRY(tc_gemm(c, curh, curl, WTh, WTl, nullptr, R, K, NN, ldk, 0, c->derr, c->stream, &epi));
+                            const int ntiles = (NN + tc_bn(NN) - 1) / tc_bn(NN);
+                            k_t_partials<<<blocks_for(R, 256), 256, 0, c->stream>>>(a, ell, part, ntiles);
                             c->launches++;
+                            std::swap(curh, nxth);
+                            std::swap(curl, nxtl);
+                            ldk = round_up32(NN);
+                        } else {
+                            TRY(tc_gemm(c, curh, curl, WTh, WTl, nxth, R, K, NN, ldk, NN, c->derr, c->stream));
                         }
                     }
-                    WideArgs ap = a;
-                    ap.lam_stride = (int64_t)rows * n;  // Lambda_x rows of domain d start at d * rows * n
-                    k_w_project<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(ap, ell, lamC, 0);
+                    k_t_project<<<blocks_for(R, 256), 256, 0, c->stream>>>(a, ell, nxth);
                     c->launches++;
                 }
                 if (ell < L) {

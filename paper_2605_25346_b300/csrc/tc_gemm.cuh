@@ -230,6 +230,21 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
 }
 
 __host__ __device__ constexpr int pstages_for(int bn) { return bn >= 128 ? 3 : 4; }
+
+// Chain epilogue: the output columns are the coefficients on the activations of a hidden layer;
+// instead of storing C the epilogue forms that layer's intercept partials over its column tile
+// (sum pos(x) d, sum neg(x) d, sum x s b) and the next level's left operand x*s as TF32 parts.
+struct ChainEpi {
+    const float* hs;   // [domains][hidden] slopes
+    const float* hd;   // [domains][hidden] intercepts
+    const float* bias; // [N] bias of the layer
+    int hidden, hoff;  // row stride of hs/hd and the layer's offset
+    int rows_per_dom;  // stacked rows per domain
+    float* Ah;         // next left operand, TF32 parts [R][ldk]
+    float* Al;
+    int ldk;
+    float* part;       // [R][gridDim.y][3] partial intercepts
+};
 __host__ __device__ constexpr int psmem_bytes(int bn) { return pstages_for(bn) * stage_bytes(bn) + 1024 + 256; }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -244,10 +259,17 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // Warp roles (192 threads): warp 0 lane 0 = TMA producer, warp 1 = TMEM owner and (lane 0) MMA
 // issuer, warps 2..5 = epilogue; warp w drains TMEM lanes 32*(w%4)..+31.
 constexpr int kGemmThreads = 192;
-template <int BN>
+__device__ __forceinline__ float tf32_part_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+template <int BN, bool EPI>
 __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                                                       const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
-                                                      float* __restrict__ C, int R, int K, int N, int ldc, int* __restrict__ err) {
+                                                      float* __restrict__ C, int R, int K, int N, int ldc, int* __restrict__ err,
+                                                      const ChainEpi epi) {
     static_assert(BN <= 128, "promoted accumulation keeps BN partial sums per thread");
     constexpr int S = pstages_for(BN);
     constexpr int SB = stage_bytes(BN);
@@ -374,11 +396,59 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CU
         }
         if (!ok) atomicExch(err, 1);
         const int row = m0 + sub * 32 + lane;
-        if (ok && row < R) {
+        if constexpr (EPI) {
+            // x*s as TF32 parts, staged per warp through the (now idle) pipeline buffers as a
+            // 32 x BN tile with an odd row stride, then stored row by row with lanes across columns
+            constexpr int TLD = BN + 1;
+            float* tile = reinterpret_cast<float*>(base) + sub * 32 * TLD;
+            const bool live = ok && row < R;
+            const int rr = live ? row : (R > 0 ? R - 1 : 0);
+            const int dom = rr / epi.rows_per_dom;
+            const float* sl = epi.hs + (int64_t)dom * epi.hidden + epi.hoff;
+            const float* dl = epi.hd + (int64_t)dom * epi.hidden + epi.hoff;
+            float spos = 0.f, sneg = 0.f, sb = 0.f;
 #pragma unroll
             for (int j = 0; j < BN; ++j) {
                 const int col = n0 + j;
-                if (col < N) C[(int64_t)row * ldc + col] = acc[j];
+                float xs = 0.f;
+                if (col < N) {
+                    const float x = acc[j], dj = dl[col];
+                    xs = x * sl[col];
+                    spos = fmaf(fmaxf(x, 0.f), dj, spos);
+                    sneg = fmaf(fminf(x, 0.f), dj, sneg);
+                    sb = fmaf(xs, epi.bias[col], sb);
+                }
+                acc[j] = xs;
+            }
+            if (live) {
+                float* pp = epi.part + ((int64_t)row * gridDim.y + blockIdx.y) * 3;
+                pp[0] = spos;
+                pp[1] = sneg;
+                pp[2] = sb;
+            }
+            const int cmax = min(BN, epi.ldk - n0);  // columns of this tile inside the operand (incl. zero padding)
+            for (int part_i = 0; part_i < 2; ++part_i) {
+#pragma unroll
+                for (int j = 0; j < BN; ++j) {
+                    const float h = tf32_part_rna(acc[j]);
+                    tile[lane * TLD + j] = part_i == 0 ? h : tf32_part_rna(acc[j] - h);
+                }
+                __syncwarp();
+                float* dst = part_i == 0 ? epi.Ah : epi.Al;
+                for (int r = 0; r < 32; ++r) {
+                    const int grow = m0 + sub * 32 + r;
+                    if (!ok || grow >= R) continue;
+                    for (int j = lane; j < cmax; j += 32) dst[(int64_t)grow * epi.ldk + n0 + j] = tile[r * TLD + j];
+                }
+                __syncwarp();
+            }
+        } else if (ok && row < R) {
+            {
+#pragma unroll
+                for (int j = 0; j < BN; ++j) {
+                    const int col = n0 + j;
+                    if (col < N) C[(int64_t)row * ldc + col] = acc[j];
+                }
             }
         }
     }

@@ -519,3 +519,70 @@ __global__ void k_t_level_epi(const WideArgs a, int ell, int mm, const float* __
         a.klo[(int64_t)d * N.maxw + i] += sneg + sb;
     }
 }
+
+// Adds the per-column-tile intercept partials of a fused chain level into kappa (fixed order).
+__global__ void k_t_partials(const WideArgs a, int ell, const float* __restrict__ part, int ntiles) {
+    const NetDesc& N = a.net;
+    const int rows = N.w[ell];
+    const int64_t R = (int64_t)a.Dc * rows;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+        const int d = (int)(r / rows), i = (int)(r - (int64_t)d * rows);
+        float sp = 0.f, sn = 0.f, sb = 0.f;
+        for (int t = 0; t < ntiles; ++t) {
+            sp += part[(r * ntiles + t) * 3 + 0];
+            sn += part[(r * ntiles + t) * 3 + 1];
+            sb += part[(r * ntiles + t) * 3 + 2];
+        }
+        a.khi[(int64_t)d * N.maxw + i] += sp + sb;
+        a.klo[(int64_t)d * N.maxw + i] += sn + sb;
+    }
+}
+
+// Concretisation of target ell with one thread per (domain, row); Lambda_x rows of domain d start at
+// Lxb + d * rows * n (ld n).  Same arithmetic as k_w_project.
+__global__ void k_t_project(const WideArgs a, int ell, const float* __restrict__ Lxb) {
+    const NetDesc& N = a.net;
+    const int n = N.n, L = N.L, rows = N.w[ell];
+    const int64_t R = (int64_t)a.Dc * rows;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+        const int d = (int)(r / rows), i = (int)(r - (int64_t)d * rows);
+        const float* Lx = Lxb + r * n;
+        const float* Pf = a.Pf + (int64_t)d * n * n;
+        const float* cf = a.cf + (int64_t)d * n;
+        const float* Ilof = a.Ilof + (int64_t)d * n;
+        const float* Ihif = a.Ihif + (int64_t)d * n;
+        const float* vf = a.vf + (int64_t)d * (n + 1);
+        float* G = a.G + ((int64_t)d * N.maxw + i) * n;
+        float av = 0.f, rlo = 0.f, rhi = 0.f;
+        for (int j = 0; j < n; ++j) {
+            const float x = Lx[j];
+            av = fmaf(x, cf[j], av);
+            rlo = fmaf(posf(x), Ilof[j], fmaf(negf(x), Ihif[j], rlo));
+            rhi = fmaf(posf(x), Ihif[j], fmaf(negf(x), Ilof[j], rhi));
+        }
+        float g1 = 0.f, gm = 0.f, gp = 0.f;
+        for (int k = 0; k < n; ++k) {
+            float acc = 0.f;
+            for (int j = 0; j < n; ++j) acc = fmaf(Lx[j], Pf[j * n + k], acc);
+            G[k] = acc;
+            g1 += fabsf(acc);
+            gm += fabsf(acc - vf[k]);
+            gp += fabsf(acc + vf[k]);
+        }
+        const float klo = a.klo[(int64_t)d * N.maxw + i], khi = a.khi[(int64_t)d * N.maxw + i];
+        const float wf = vf[n];
+        const float S = fabsf(av) + g1 + fabsf(klo) + fabsf(khi) + fabsf(rlo) + fabsf(rhi) + fabsf(wf);
+        if (ell < L) {
+            a.hl[(int64_t)d * N.hidden + N.hoff[ell] + i] = av + klo + rlo - gm - wf - a.rho * S;
+            a.hu[(int64_t)d * N.hidden + N.hoff[ell] + i] = av + khi + rhi + gp + wf + a.rho * S;
+            a.sa[(int64_t)d * N.maxw + i] = av;
+            a.sRlo[(int64_t)d * N.maxw + i] = rlo;
+            a.sRhi[(int64_t)d * N.maxw + i] = rhi;
+            a.sS[(int64_t)d * N.maxw + i] = S;
+        } else {
+            a.cu[(int64_t)d * N.m + i] = av + 0.5f * (klo + khi);
+            a.Iulo[(int64_t)d * N.m + i] = 0.5f * (klo - khi) + rlo - a.rho * S;
+            a.Iuhi[(int64_t)d * N.m + i] = 0.5f * (khi - klo) + rhi + a.rho * S;
+        }
+    }
+}

@@ -55,7 +55,8 @@ def compare(prob, g, o, rtol=RTOL, rho=RHO, check_hull=True):
     # V sums box widths, which carry the outward box margin (about 2 * 2^-18 * |centre| per entry)
     np.testing.assert_allclose(g["V"], o["V"].detach().numpy(), rtol=5e-4)
     if check_hull:
-        hs = np.maximum(np.abs(o["hull_lo"].numpy()), np.abs(o["hull_hi"].numpy()))
+        hl, hh = o["hull_lo"].numpy(), o["hull_hi"].numpy()
+        hs = np.maximum(np.maximum(np.abs(hl), np.abs(hh)), hh - hl)  # the same per-entry scale as the boxes
         assert (np.abs(g["hull_lo"] - o["hull_lo"].numpy()) <= rtol * hs).all()
         assert (np.abs(g["hull_hi"] - o["hull_hi"].numpy()) <= rtol * hs).all()
     return float(err.max())
