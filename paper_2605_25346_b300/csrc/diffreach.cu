@@ -76,6 +76,9 @@ struct dr_ctx {
     float* dWTl = nullptr;
     int64_t WToff[DR_MAXL] = {};
     int* derr = nullptr;
+    // per-CTA global slabs for the fused kernels on wide controllers (tape runs)
+    unsigned char* gslab = nullptr;
+    size_t gslab_bytes = 0;
     // staged (wide) path chunk scratch
     void* wscratch = nullptr;
     size_t wscratch_bytes = 0;
@@ -582,6 +585,8 @@ static void free_outputs(dr_ctx* c) {
     dev_free(c, (void*&)c->dwhi, 0);
     dev_free(c, c->wscratch, c->wscratch_bytes);
     c->wscratch_bytes = 0;
+    dev_free(c, (void*&)c->gslab, c->gslab_bytes);
+    c->gslab_bytes = 0;
     c->wDc = 0;
     c->out_bytes = 0;
     c->tape_bytes = 0;
@@ -1125,9 +1130,26 @@ static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
     return DR_OK;
 }
 
+// Domains per launch and the slab buffer for running the fused kernels out of global memory.
+static int slab_chunk(dr_ctx* c, size_t per_cta, int64_t* chunk) {
+    const size_t budget = size_t(2) << 30;
+    int64_t ch = std::max<int64_t>(1, std::min<int64_t>(c->D, (int64_t)(budget / std::max<size_t>(per_cta, 1))));
+    ch = std::min<int64_t>(ch, 4 * 148);
+    const size_t need = (size_t)ch * per_cta;
+    if (!c->gslab || c->gslab_bytes < need) {
+        dev_free(c, (void*&)c->gslab, c->gslab_bytes);
+        c->gslab_bytes = 0;
+        TRY(dev_alloc(c, c->gslab, need));
+        c->gslab_bytes = need;
+    }
+    *chunk = ch;
+    return DR_OK;
+}
+
 // Forward pass over all domains into the library-owned buffers (optionally recording the tape
-// and the slopes in effect).  The fused kernel serves controllers that fit in shared memory
-// (DR_PREC_AUTO); DR_PREC_SIMT / DR_PREC_TF32X3 and wider controllers take the staged path.
+// and the slopes in effect).  Bounds-only passes: the fused kernels serve controllers that fit in
+// shared memory (DR_PREC_AUTO); DR_PREC_SIMT / DR_PREC_TF32X3 and wider controllers take the
+// staged path.
 static bool use_fused(const dr_ctx* c) {
     return c->opt.precision == DR_PREC_AUTO && fused_fits(c->net);
 }
@@ -1137,10 +1159,10 @@ static int run_forward(dr_ctx* c, int mode, float* alpha_used, bool tape) {
     N.H = c->H;
     if (c->D == 0) return DR_OK;
     if (mode == DR_SLOPE_USER && !c->dalpha) return fail(c, DR_ERR_STATE, "no slopes set");
-    if (!use_fused(c)) {
-        if (tape) return fail(c, DR_ERR_SHAPE, "the reverse sweep needs a controller that fits the fused kernel");
-        return run_forward_wide(c, mode, alpha_used);
-    }
+    // The tape-recording pass always runs the fused kernel; a controller whose working set exceeds
+    // shared memory runs it out of per-CTA global slabs.
+    if (!tape && !use_fused(c)) return run_forward_wide(c, mode, alpha_used);
+    const bool slab = fused_layout(N).total > kMaxSmem;
     if (!tape && multi_layout(N, 1).total <= kMaxSmem) {
         // grouped kernel: G domains per CTA, (threads, G) chosen by the autotuner
         MultiArgs a;
@@ -1198,8 +1220,14 @@ static int run_forward(dr_ctx* c, int mode, float* alpha_used, bool tape) {
     a.tape = tape ? c->dtape : nullptr;
     a.tape_stride = tape_stride(N);
     const int nt = fused_threads(N);
-    const int smem = a.lay.total;
-    const int64_t chunk = 1 << 20;
+    int smem = a.lay.total;
+    int64_t chunk = 1 << 20;
+    if (slab) {
+        a.slab_stride = ((int64_t)a.lay.total + 255) & ~int64_t(255);
+        TRY(slab_chunk(c, (size_t)a.slab_stride, &chunk));
+        a.gslab = c->gslab;
+        smem = 0;
+    }
     for (int64_t d0 = 0; d0 < c->D; d0 += chunk) {
         a.d0 = d0;
         const int64_t nd = std::min(chunk, c->D - d0);
@@ -1324,8 +1352,7 @@ static int launch_backward(dr_ctx* c, int mode, const double* wlo, const double*
     memset(&a, 0, sizeof(a));
     a.net = N;
     a.lay = fused_layout(N, true);
-    if (a.lay.total > kMaxSmem)
-        return fail(c, DR_ERR_SHAPE, "controller too wide for the fused reverse kernel (%d bytes of shared memory)", a.lay.total);
+    const bool slab = a.lay.total > kMaxSmem;
     a.W = c->dW;
     a.b = c->db;
     a.A = c->dA;
@@ -1346,8 +1373,14 @@ static int launch_backward(dr_ctx* c, int mode, const double* wlo, const double*
     a.dalpha = galpha;
     a.dbeta = gbeta;
     const int nt = fused_threads(N);
-    const int smem = a.lay.total;
-    const int64_t chunk = 1 << 20;
+    int smem = a.lay.total;
+    int64_t chunk = 1 << 20;
+    if (slab) {
+        a.slab_stride = ((int64_t)a.lay.total + 255) & ~int64_t(255);
+        TRY(slab_chunk(c, (size_t)a.slab_stride, &chunk));
+        a.gslab = c->gslab;
+        smem = 0;
+    }
     for (int64_t d0 = 0; d0 < c->D; d0 += chunk) {
         a.d0 = d0;
         const int64_t nd = std::min(chunk, c->D - d0);

@@ -14,7 +14,8 @@
 
 template <int NT>
 __global__ void __launch_bounds__(NT) k_fused_backward(const FusedArgs a) {
-    extern __shared__ __align__(16) unsigned char sm[];
+    extern __shared__ __align__(16) unsigned char sm_dyn[];
+    unsigned char* sm = a.gslab ? a.gslab + (int64_t)blockIdx.x * a.slab_stride : sm_dyn;
     const NetDesc& N = a.net;
     const FusedLayout& Y = a.lay;
     const Dom s = make_dom(sm, Y);

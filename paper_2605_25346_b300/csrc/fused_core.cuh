@@ -63,6 +63,10 @@ struct FusedArgs {
     float* alpha_used;  // [D][H][hidden] or null
     double* tape;       // [D][H][tape_stride] or null
     int tape_stride;
+    // wide controllers: the working set lives in a per-CTA slab of global memory instead of
+    // dynamic shared memory (slab of CTA b at gslab + b * slab_stride)
+    unsigned char* gslab;
+    int64_t slab_stride;
     // reverse kernel
     const double* wlo;  // [D][H+1][n] upstream gradient of lo (null: -1 on steps 1..H)
     const double* whi;  // [D][H+1][n] upstream gradient of hi (null: +1 on steps 1..H)
@@ -452,7 +456,8 @@ __device__ void controller_pass(const Dom& s, const NetDesc& N, const FusedArgs&
 
 template <int NT>
 __global__ void __launch_bounds__(NT) k_fused_forward(const FusedArgs a) {
-    extern __shared__ __align__(16) unsigned char sm[];
+    extern __shared__ __align__(16) unsigned char sm_dyn[];
+    unsigned char* sm = a.gslab ? a.gslab + (int64_t)blockIdx.x * a.slab_stride : sm_dyn;
     const NetDesc& N = a.net;
     const Dom s = make_dom(sm, a.lay);
     const int tid = threadIdx.x;
