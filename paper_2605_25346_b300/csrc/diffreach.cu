@@ -17,8 +17,8 @@
 #include "fused_core.cuh"
 #include "fused_bwd.cuh"
 #include "fused_multi.cuh"
-#include "wide.cuh"
 #include "tc_gemm.cuh"
+#include "wide.cuh"
 
 
 struct dr_ctx {
@@ -372,6 +372,14 @@ static int make_map(dr_ctx* c, CUtensorMap* map, const float* ptr, int64_t rows,
     return DR_OK;
 }
 
+// Tensor map over a blocked left operand (tc::blk_index) of R rows (padded to whole 128-row tiles)
+// and ldk columns: a 2D view [tiles * ldk/32 * 128][32], box 32 x 128, 128-byte swizzle.
+static int make_map_blocked(dr_ctx* c, CUtensorMap* map, const float* ptr, int64_t R, int ldk) {
+    const int64_t rows = ((R + tc::BM - 1) / tc::BM) * (ldk / tc::BK) * tc::BM;
+    if (rows > 0x7fffffffll) return fail(c, DR_ERR_SHAPE, "left operand too large for the tensor map (%lld rows)", (long long)R);
+    return make_map(c, map, ptr, rows, tc::BK, tc::BM);
+}
+
 static int tc_bn(int N) { return N > 64 ? 128 : (N > 32 ? 64 : (N > 16 ? 32 : 16)); }
 
 template <int BN, bool EPI>
@@ -379,22 +387,25 @@ static int launch_tc_gemm_bn(dr_ctx* c, const CUtensorMap* m, float* C, int R, i
                              cudaStream_t st, const tc::ChainEpi& epi) {
     const int smem = tc::psmem_bytes(BN);
     CUDA_TRY(c, cudaFuncSetAttribute(tc::k_tc_gemm_p<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    dim3 grid((R + tc::BM - 1) / tc::BM, (N + BN - 1) / BN);
+    // column tiles fastest: the CTAs sharing a row tile of A run together (one HBM read of A)
+    const int64_t mt = (R + tc::BM - 1) / tc::BM;
+    if (mt > 65535) return fail(c, DR_ERR_SHAPE, "too many row tiles (%lld) for one launch", (long long)mt);
+    dim3 grid((N + BN - 1) / BN, (unsigned)mt);
     tc::k_tc_gemm_p<BN, EPI><<<grid, tc::kGemmThreads, smem, st>>>(m[0], m[1], m[2], m[3], C, R, K, N, ldc, err, epi);
     CUDA_TRY(c, cudaGetLastError());
     if (c) c->launches++;
     return DR_OK;
 }
 
-// C [R x N] (ld ldc) = A B with A given as TF32 parts Ah/Al [R][ldk] and B as BTh/BTl [N][ldk]; with
-// `epi` the chain epilogue replaces the store of C.
+// C [R x N] (ld ldc) = A B with A given as TF32 parts Ah/Al (blocked layout, tc::blk_index, ldk
+// columns) and B as BTh/BTl [N][ldk]; with `epi` the chain epilogue replaces the store of C.
 static int tc_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* BTh, const float* BTl, float* C, int R, int K,
                    int N, int ldk, int ldc, int* err, cudaStream_t st, const tc::ChainEpi* epi = nullptr) {
     TRY(get_encoder(c));
     const int BN = tc_bn(N);
     CUtensorMap m[4];
-    TRY(make_map(c, &m[0], Ah, R, ldk, tc::BM));
-    TRY(make_map(c, &m[1], Al, R, ldk, tc::BM));
+    TRY(make_map_blocked(c, &m[0], Ah, R, ldk));
+    TRY(make_map_blocked(c, &m[1], Al, R, ldk));
     TRY(make_map(c, &m[2], BTh, N, ldk, BN));
     TRY(make_map(c, &m[3], BTl, N, ldk, BN));
     tc::ChainEpi e{};
@@ -940,9 +951,17 @@ static size_t wide_bytes_per_domain(const NetDesc& N) {
 }
 
 // Carve the chunk scratch for Dc domains out of one allocation.
+// Extra floats per Lambda buffer: the blocked operand layout pads the stacked rows to whole
+// 128-row tiles.
+static int64_t wide_lam_pad(const NetDesc& N) {
+    int ldk = 32;
+    for (int l = 0; l <= N.L; ++l) ldk = std::max(ldk, (N.w[l] + 31) & ~31);
+    return (int64_t)tc::BM * ldk;
+}
+
 static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, float** lamA, float** lamB, float** lamC, float** lamD, float** part) {
     const NetDesc& N = a.net;
-    const size_t need = wide_bytes_per_domain(N) * (size_t)Dc + 4096;
+    const size_t need = wide_bytes_per_domain(N) * (size_t)Dc + 4 * (sizeof(float) * wide_lam_pad(N) + 256) + 4096;
     if (!c->wscratch || c->wscratch_bytes < need || c->wDc != Dc) {
         dev_free(c, c->wscratch, c->wscratch_bytes);
         unsigned char* p = nullptr;
@@ -991,10 +1010,11 @@ static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, float** lamA, float** lamB,
     a.Iulo = (float*)take(sizeof(float) * D * m);
     a.Iuhi = (float*)take(sizeof(float) * D * m);
     a.lam_stride = wide_lam_stride(N);
-    *lamA = (float*)take(sizeof(float) * D * a.lam_stride);
-    *lamB = (float*)take(sizeof(float) * D * a.lam_stride);
-    *lamC = (float*)take(sizeof(float) * D * a.lam_stride);
-    *lamD = (float*)take(sizeof(float) * D * a.lam_stride);
+    const int64_t lam_pad = wide_lam_pad(N);
+    *lamA = (float*)take(sizeof(float) * (D * a.lam_stride + lam_pad));
+    *lamB = (float*)take(sizeof(float) * (D * a.lam_stride + lam_pad));
+    *lamC = (float*)take(sizeof(float) * (D * a.lam_stride + lam_pad));
+    *lamD = (float*)take(sizeof(float) * (D * a.lam_stride + lam_pad));
     *part = (float*)take(sizeof(float) * D * 3 * wide_part_per_domain(N));
     if (off > c->wscratch_bytes) return fail(c, DR_ERR_OOM, "staged scratch layout overflow");
     return DR_OK;
@@ -1498,6 +1518,7 @@ extern "C" int dr_tf32x3_gemm(int M, int N, int K, const float* A, const float* 
     if (M == 0 || N == 0) return DR_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int ldk = round_up32(K);
+    const int64_t Mpad = ((int64_t)M + tc::BM - 1) / tc::BM * tc::BM;  // blocked A: whole 128-row tiles
     float *Ah = nullptr, *Al = nullptr, *Bh = nullptr, *Bl = nullptr;
     int* err = nullptr;
     auto cleanup = [&]() {
@@ -1507,7 +1528,7 @@ extern "C" int dr_tf32x3_gemm(int M, int N, int K, const float* A, const float* 
         cudaFree(Bl);
         cudaFree(err);
     };
-    if (cudaMalloc(&Ah, sizeof(float) * (size_t)M * ldk) != cudaSuccess || cudaMalloc(&Al, sizeof(float) * (size_t)M * ldk) != cudaSuccess ||
+    if (cudaMalloc(&Ah, sizeof(float) * (size_t)Mpad * ldk) != cudaSuccess || cudaMalloc(&Al, sizeof(float) * (size_t)Mpad * ldk) != cudaSuccess ||
         cudaMalloc(&Bh, sizeof(float) * (size_t)N * ldk) != cudaSuccess || cudaMalloc(&Bl, sizeof(float) * (size_t)N * ldk) != cudaSuccess ||
         cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
         cleanup();
@@ -1515,8 +1536,8 @@ extern "C" int dr_tf32x3_gemm(int M, int N, int K, const float* A, const float* 
         return fail(nullptr, DR_ERR_OOM, "dr_tf32x3_gemm: allocation failed");
     }
     cudaMemsetAsync(err, 0, sizeof(int), st);
-    tc::k_split_tf32<<<1184, 256, 0, st>>>(A, K, M, K, ldk, Ah, Al);
-    tc::k_split_tf32<<<1184, 256, 0, st>>>(BT, K, N, K, ldk, Bh, Bl);
+    tc::k_split_tf32<<<1184, 256, 0, st>>>(A, K, M, K, ldk, Ah, Al, 1);
+    tc::k_split_tf32<<<1184, 256, 0, st>>>(BT, K, N, K, ldk, Bh, Bl, 0);
     int rc = tc_gemm(nullptr, Ah, Al, Bh, Bl, C, M, K, N, ldk, N, err, st);
     int herr = 0;
     if (rc == DR_OK) {

@@ -2,12 +2,14 @@
 // domains stacked) and B [K x N] shared, as the split product A_hi B_hi + A_hi B_lo + A_lo B_hi of
 // TF32 parts (3xTF32), accumulated in FP32 in tensor memory.
 //
-//   - A_hi/A_lo [R][ldk] and BT_hi/BT_lo [N][ldk] (B transposed, K contiguous) are FP32 arrays whose
-//     values are TF32-representable; ldk is a multiple of 32 and the padding columns are zero.
-//   - One CTA computes a 128 x BN tile over the whole K range.  Thread 0 issues the TMA loads
-//     (cp.async.bulk.tensor, 128-byte swizzle, 32-float K chunks), thread 32 issues tcgen05.mma
-//     (kind::tf32, M = 128, N = BN, K = 8 per instruction) from the single accumulator in TMEM,
-//     and all four warps drain TMEM (tcgen05.ld 32x32b) into C [R][ldc].
+//   - A_hi/A_lo (blocked layout, see blk_index; R padded to whole 128-row tiles) and BT_hi/BT_lo
+//     [N][ldk] (B transposed, K contiguous) are FP32 arrays whose values are TF32-representable;
+//     ldk is a multiple of 32 and the padding columns are zero.
+//   - One CTA computes a 128 x BN tile over the whole K range; the column tile is the fastest grid
+//     index, so the CTAs that share a row tile of A run together and read it once from HBM.
+//     Thread 0 issues the TMA loads (cp.async.bulk.tensor, 128-byte swizzle, 32-float K chunks),
+//     thread 32 issues tcgen05.mma (kind::tf32, M = 128, N = BN, K = 8 per instruction), and the
+//     epilogue warps drain TMEM (tcgen05.ld 32x32b).
 //   - Stages are handed over with mbarriers (TMA complete_tx for "full", tcgen05.commit for
 //     "empty").  Every wait is bounded by a clock budget; on expiry the kernel raises *err, stops
 //     issuing, drains its own copies (bounded), frees TMEM and returns.
@@ -23,9 +25,14 @@ constexpr int BK = 32;  // floats per K chunk: one 128-byte swizzle row
 constexpr long long kWaitCycles = 4000000000ll;  // about 2 s at 2 GHz
 
 __host__ __device__ constexpr int stage_bytes(int bn) { return 2 * BM * BK * 4 + 2 * bn * BK * 4; }
-__host__ __device__ constexpr int stages_for(int bn) { return bn >= 256 ? 2 : (bn >= 128 ? 3 : 4); }
 __host__ __device__ constexpr int tmem_cols(int bn) { return bn <= 32 ? 32 : (bn <= 64 ? 64 : (bn <= 128 ? 128 : 256)); }
-__host__ __device__ constexpr int smem_bytes(int bn) { return stages_for(bn) * stage_bytes(bn) + 1024 + 256; }
+
+// Left operands (A parts) live in a blocked layout: 128-row x 32-column blocks of 16 KB, stored
+// contiguously in (row tile, K chunk) order, so one TMA box is one contiguous 16 KB read and an
+// epilogue's 32 x 32 sub-block is one contiguous 4 KB write.  nk = ldk / 32 chunks per row tile.
+__host__ __device__ __forceinline__ int64_t blk_index(int64_t row, int k, int nk) {
+    return (((row >> 7) * nk + (k >> 5)) << 12) + ((row & 127) << 5) + (k & 31);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -108,127 +115,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-template <int BN>
-__global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
-                                                    const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
-                                                    float* __restrict__ C, int R, int K, int N, int ldc, int* __restrict__ err) {
-    constexpr int S = stages_for(BN);
-    constexpr int SB = stage_bytes(BN);
-    constexpr int TC = tmem_cols(BN);
-    constexpr uint32_t IDESC = idesc_tf32(BM, BN);
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* full = reinterpret_cast<uint64_t*>(base + S * SB);
-    uint64_t* empty = full + S;
-    uint64_t* accum = empty + S;
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(accum + 1);
-    int* abort_flag = reinterpret_cast<int*>(tmem_holder + 1);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-    const int nk = (K + BK - 1) / BK;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < S; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
-        }
-        mbar_init(accum, 1);
-        *abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mAh)) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mBh)) : "memory");
-    }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)), "r"(TC)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    fence_before();
-    __syncthreads();
-    fence_after();
-    const uint32_t tmem = *tmem_holder;
-
-    if (threadIdx.x == 0) {
-        // ---- TMA producer
-        int issued = 0;
-        for (int kc = 0; kc < nk; ++kc) {
-            const int s = kc % S;
-            if (kc >= S && !mbar_wait(&empty[s], ((kc / S) - 1) & 1)) {
-                atomicExch(err, 1);
-                *(volatile int*)abort_flag = 1;
-                break;
-            }
-            if (*(volatile int*)abort_flag) break;
-            unsigned char* st = base + s * SB;
-            mbar_expect_tx(&full[s], SB);
-            tma_load_2d(st, &mAh, &full[s], kc * BK, m0);
-            tma_load_2d(st + BM * BK * 4, &mAl, &full[s], kc * BK, m0);
-            tma_load_2d(st + 2 * BM * BK * 4, &mBh, &full[s], kc * BK, n0);
-            tma_load_2d(st + 2 * BM * BK * 4 + BN * BK * 4, &mBl, &full[s], kc * BK, n0);
-            ++issued;
-        }
-        // drain: every issued stage must have landed before the CTA may exit
-        for (int kc = (issued > S ? issued - S : 0); kc < issued; ++kc) {
-            if (!mbar_wait(&full[kc % S], (kc / S) & 1)) {
-                atomicExch(err, 1);
-                break;
-            }
-        }
-    } else if (threadIdx.x == 32) {
-        // ---- MMA issuer
-        bool ok = true;
-        for (int kc = 0; kc < nk; ++kc) {
-            const int s = kc % S;
-            if (!mbar_wait(&full[s], (kc / S) & 1)) {
-                atomicExch(err, 1);
-                *(volatile int*)abort_flag = 1;
-                ok = false;
-                break;
-            }
-            fence_after();
-            const uint32_t sa = smem_u32(base + s * SB);
-            const uint64_t ah = sw128_desc(sa), al = sw128_desc(sa + BM * BK * 4);
-            const uint64_t bh = sw128_desc(sa + 2 * BM * BK * 4), bl = sw128_desc(sa + 2 * BM * BK * 4 + BN * BK * 4);
-#pragma unroll
-            for (int kk = 0; kk < BK / 8; ++kk) {
-                const uint64_t o = (uint64_t)(kk * 32) >> 4;  // 8 TF32 values = 32 bytes along K
-                mma_tf32(tmem, ah + o, bh + o, IDESC, (kc | kk) ? 1u : 0u);
-                mma_tf32(tmem, ah + o, bl + o, IDESC, 1u);
-                mma_tf32(tmem, al + o, bh + o, IDESC, 1u);
-            }
-            mma_commit(&empty[s]);
-        }
-        if (ok) mma_commit(accum);
-        else mbar_expect_tx(accum, 0);  // complete the phase so the epilogue does not wait out its budget
-    }
-    __syncwarp();
-    // ---- epilogue: warp w drains TMEM lanes 32w..32w+31 (one output row per thread)
-    const bool have = mbar_wait(accum, 0);
-    fence_after();
-    if (!have) atomicExch(err, 1);
-    if (have && !*(volatile int*)abort_flag) {
-        const int row = m0 + warp * 32 + lane;
-        float v[32];
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            if (row < R) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int col = n0 + c0 + j;
-                    if (c0 + j < BN && col < N) C[(int64_t)row * ldc + col] = v[j];
-                }
-            }
-        }
-    }
-    fence_before();
-    __syncthreads();
-    if (warp == 1) {
-        fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC) : "memory");
-    }
-}
-
 __host__ __device__ constexpr int pstages_for(int bn) { return bn >= 128 ? 3 : 4; }
 
 // Chain epilogue: the output columns are the coefficients on the activations of a hidden layer;
@@ -285,7 +171,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CU
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(pfree + 2);
     int* abort_flag = reinterpret_cast<int*>(tmem_holder + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int nk = (K + BK - 1) / BK;
 
     if (threadIdx.x == 0) {
@@ -325,8 +211,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CU
             if (*(volatile int*)abort_flag) break;
             unsigned char* st = base + s * SB;
             mbar_expect_tx(&full[s], SB);
-            tma_load_2d(st, &mAh, &full[s], kc * BK, m0);
-            tma_load_2d(st + BM * BK * 4, &mAl, &full[s], kc * BK, m0);
+            const int ay = ((int)blockIdx.y * nk + kc) * BM;  // row of the A block in the blocked view
+            tma_load_2d(st, &mAh, &full[s], 0, ay);
+            tma_load_2d(st + BM * BK * 4, &mAl, &full[s], 0, ay);
             tma_load_2d(st + 2 * BM * BK * 4, &mBh, &full[s], kc * BK, n0);
             tma_load_2d(st + 2 * BM * BK * 4 + BN * BK * 4, &mBl, &full[s], kc * BK, n0);
             ++issued;
@@ -421,7 +308,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CU
                 acc[j] = xs;
             }
             if (live) {
-                float* pp = epi.part + ((int64_t)row * gridDim.y + blockIdx.y) * 3;
+                float* pp = epi.part + ((int64_t)row * gridDim.x + blockIdx.x) * 3;
                 pp[0] = spos;
                 pp[1] = sneg;
                 pp[2] = sb;
@@ -434,11 +321,18 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CU
                     tile[lane * TLD + j] = part_i == 0 ? h : tf32_part_rna(acc[j] - h);
                 }
                 __syncwarp();
+                // blocked layout: the warp's 32 rows of one 32-column chunk are 4 KB contiguous
                 float* dst = part_i == 0 ? epi.Ah : epi.Al;
-                for (int r = 0; r < 32; ++r) {
-                    const int grow = m0 + sub * 32 + r;
-                    if (!ok || grow >= R) continue;
-                    for (int j = lane; j < cmax; j += 32) dst[(int64_t)grow * epi.ldk + n0 + j] = tile[r * TLD + j];
+                const int enk = epi.ldk >> 5;
+                for (int c0 = 0; c0 < cmax; c0 += 32) {
+                    const int j = c0 + lane;
+                    if (j >= cmax) continue;
+                    // rows m0 + sub*32 .. +31 stay inside one 128-row block: consecutive rows are 32 apart
+                    float* col = dst + blk_index(m0 + sub * 32, n0 + j, enk);
+                    for (int r = 0; r < 32; ++r) {
+                        if (!ok || m0 + sub * 32 + r >= R) break;
+                        col[r * 32] = tile[r * TLD + j];
+                    }
                 }
                 __syncwarp();
             }
@@ -468,17 +362,19 @@ __device__ __forceinline__ float tf32_rna(float x) {
     return __uint_as_float(r);
 }
 
-// Split rows of X [R][K] (ld ldx) into TF32 parts H/L [R][ldk] with zero padding in K..ldk-1.
+// Split rows of X [R][K] (ld ldx) into TF32 parts H/L with zero padding in K..ldk-1: row-major
+// [R][ldk] (B operands) or, with `blocked`, the blocked left-operand layout.
 __global__ void k_split_tf32(const float* __restrict__ X, int ldx, int R, int K, int ldk, float* __restrict__ Hh,
-                             float* __restrict__ Ll) {
+                             float* __restrict__ Ll, int blocked) {
     const int64_t total = (int64_t)R * ldk;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = idx / ldk;
         const int k = (int)(idx - r * ldk);
         const float x = k < K ? X[r * ldx + k] : 0.f;
         const float h = tf32_rna(x);
-        Hh[idx] = h;
-        Ll[idx] = tf32_rna(x - h);
+        const int64_t o = blocked ? blk_index(r, k, ldk >> 5) : idx;
+        Hh[o] = h;
+        Ll[o] = tf32_rna(x - h);
     }
 }
 

@@ -442,7 +442,8 @@ __device__ __forceinline__ float tf32_part(float x) {
 }
 
 // First chain level of target ell >= 2 from the shared W_ell, writing A = W_ell diag(s_{ell-1}) as
-// TF32 parts Ah/Al [Dc*n_ell][ldk] (zero padded) plus kappa.  One warp per (domain, row).
+// TF32 parts Ah/Al in the blocked left-operand layout (rows Dc*n_ell, ldk zero-padded columns; see
+// tc::blk_index) plus kappa.  One warp per (domain, row).
 __global__ void k_t_chain_init(const WideArgs a, int ell, float* __restrict__ Ah, float* __restrict__ Al, int ldk) {
     const NetDesc& N = a.net;
     const int rows = N.w[ell];
@@ -456,8 +457,7 @@ __global__ void k_t_chain_init(const WideArgs a, int ell, float* __restrict__ Ah
     const float* s = a.hs + (int64_t)d * N.hidden + N.hoff[ell - 1];
     const float* dd = a.hd + (int64_t)d * N.hidden + N.hoff[ell - 1];
     const float* bm = a.b + N.boff[ell - 2];
-    float* oh = Ah + wid * ldk;
-    float* ol = Al + wid * ldk;
+    const int nk = ldk >> 5;
     float spos = 0.f, sneg = 0.f, sb = 0.f;
     for (int j = lane; j < ldk; j += 32) {
         float xs = 0.f;
@@ -469,8 +469,9 @@ __global__ void k_t_chain_init(const WideArgs a, int ell, float* __restrict__ Ah
             sb = fmaf(xs, bm[j], sb);
         }
         const float h = tf32_part(xs);
-        oh[j] = h;
-        ol[j] = tf32_part(xs - h);
+        const int64_t o = tc::blk_index(wid, j, nk);
+        Ah[o] = h;
+        Al[o] = tf32_part(xs - h);
     }
     spos = warp_sum(spos);
     sneg = warp_sum(sneg);
@@ -478,45 +479,6 @@ __global__ void k_t_chain_init(const WideArgs a, int ell, float* __restrict__ Ah
     if (lane == 0) {
         a.khi[(int64_t)d * N.maxw + i] = bi + spos + sb;
         a.klo[(int64_t)d * N.maxw + i] = bi + sneg + sb;
-    }
-}
-
-// After a GEMM level produced Lambda^(mm) (mm >= 1) in C [Dc*n_ell][n_mm]: intercepts of layer mm's
-// relaxation and the next A = Lambda diag(s_mm) as TF32 parts [..][ldk].  One warp per (domain, row).
-__global__ void k_t_level_epi(const WideArgs a, int ell, int mm, const float* __restrict__ C, float* __restrict__ Ah,
-                              float* __restrict__ Al, int ldk) {
-    const NetDesc& N = a.net;
-    const int rows = N.w[ell], K = N.w[mm];
-    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (wid >= (int64_t)a.Dc * rows) return;
-    const int d = (int)(wid / rows), i = (int)(wid - (int64_t)d * rows);
-    const float* s = a.hs + (int64_t)d * N.hidden + N.hoff[mm];
-    const float* dd = a.hd + (int64_t)d * N.hidden + N.hoff[mm];
-    const float* bm = a.b + N.boff[mm - 1];
-    const float* row = C + wid * K;
-    float* oh = Ah + wid * ldk;
-    float* ol = Al + wid * ldk;
-    float spos = 0.f, sneg = 0.f, sb = 0.f;
-    for (int j = lane; j < ldk; j += 32) {
-        float xs = 0.f;
-        if (j < K) {
-            const float x = row[j];
-            spos = fmaf(posf(x), dd[j], spos);
-            sneg = fmaf(negf(x), dd[j], sneg);
-            xs = x * s[j];
-            sb = fmaf(xs, bm[j], sb);
-        }
-        const float h = tf32_part(xs);
-        oh[j] = h;
-        ol[j] = tf32_part(xs - h);
-    }
-    spos = warp_sum(spos);
-    sneg = warp_sum(sneg);
-    sb = warp_sum(sb);
-    if (lane == 0) {
-        a.khi[(int64_t)d * N.maxw + i] += spos + sb;
-        a.klo[(int64_t)d * N.maxw + i] += sneg + sb;
     }
 }
 
