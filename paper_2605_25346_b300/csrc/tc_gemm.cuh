@@ -25,7 +25,9 @@ constexpr int BK = 32;  // floats per K chunk: one 128-byte swizzle row
 constexpr long long kWaitCycles = 4000000000ll;  // about 2 s at 2 GHz
 
 __host__ __device__ constexpr int stage_bytes(int bn) { return 2 * BM * BK * 4 + 2 * bn * BK * 4; }
-__host__ __device__ constexpr int tmem_cols(int bn) { return bn <= 32 ? 32 : (bn <= 64 ? 64 : (bn <= 128 ? 128 : 256)); }
+__host__ __device__ constexpr int tmem_cols(int cols) {
+    return cols <= 32 ? 32 : (cols <= 64 ? 64 : (cols <= 128 ? 128 : (cols <= 256 ? 256 : 512)));
+}
 
 // Left operands (A parts) live in a blocked layout: 128-row x 32-column blocks of 16 KB, stored
 // contiguously in (row tile, K chunk) order, so one TMA box is one contiguous 16 KB read and an
@@ -131,15 +133,17 @@ struct ChainEpi {
     int ldk;
     float* part;       // [R][gridDim.y][3] partial intercepts
 };
-__host__ __device__ constexpr int psmem_bytes(int bn) { return pstages_for(bn) * stage_bytes(bn) + 1024 + 256; }
+// pipeline stages, 1 KB alignment slack, 256 B of barriers, and the epilogue's per-column table
+__host__ __device__ constexpr int psmem_bytes(int bn) { return pstages_for(bn) * stage_bytes(bn) + 1024 + 256 + 16 * bn; }
+constexpr int kPartials = 3;  // TMEM partial buffers: the MMA issuer may run two chunks ahead of the epilogue
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // Same contraction with promoted accumulation: every 32-wide K chunk is accumulated in a fresh
-// TMEM buffer (two buffers, ping-pong) and the four epilogue warps add the chunk partials into FP32
-// registers, one output row per thread.  The tensor core then never accumulates more than one
+// TMEM buffer (three buffers, round robin) and the four epilogue warps add the chunk partials into
+// FP32 registers, one output row per thread.  The tensor core then never accumulates more than one
 // chunk (12 MMAs), and the long sum over K runs in IEEE FP32 adds, which keeps the 3xTF32 product
 // as accurate as an FP32 SGEMM.  BN <= 128 (a thread holds BN partial sums).
 // Warp roles (192 threads): warp 0 lane 0 = TMA producer, warp 1 = TMEM owner and (lane 0) MMA
@@ -160,16 +164,18 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CU
     constexpr int S = pstages_for(BN);
     constexpr int SB = stage_bytes(BN);
     constexpr int PB = BN < 32 ? 32 : BN;  // TMEM columns per partial buffer (32-column loads stay inside)
-    constexpr int TC = tmem_cols(2 * PB);
+    constexpr int NP = kPartials;
+    constexpr int TC = tmem_cols(NP * PB);
     constexpr uint32_t IDESC = idesc_tf32(BM, BN);
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* full = reinterpret_cast<uint64_t*>(base + S * SB);
     uint64_t* empty = full + S;
-    uint64_t* pfull = empty + S;  // [2] partial ready (MMA commit)
-    uint64_t* pfree = pfull + 2;  // [2] partial consumed (4 epilogue warps)
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(pfree + 2);
+    uint64_t* pfull = empty + S;   // [NP] partial ready (MMA commit)
+    uint64_t* pfree = pfull + NP;  // [NP] partial consumed (4 epilogue warps)
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(pfree + NP);
     int* abort_flag = reinterpret_cast<int*>(tmem_holder + 1);
+    float4* coltab = reinterpret_cast<float4*>(base + S * SB + 256);  // [BN] (s, d, bias) of the tile's columns
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int nk = (K + BK - 1) / BK;
@@ -179,7 +185,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CU
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int p = 0; p < 2; ++p) {
+        for (int p = 0; p < NP; ++p) {
             mbar_init(&pfull[p], 1);
             mbar_init(&pfree[p], 4);
         }
@@ -226,8 +232,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CU
         }
     } else if (threadIdx.x == 32) {
         for (int kc = 0; kc < nk; ++kc) {
-            const int s = kc % S, p = kc & 1;
-            if (!mbar_wait(&full[s], (kc / S) & 1) || (kc >= 2 && !mbar_wait(&pfree[p], ((kc >> 1) - 1) & 1))) {
+            const int s = kc % S, p = kc % NP;
+            if (!mbar_wait(&full[s], (kc / S) & 1) || (kc >= NP && !mbar_wait(&pfree[p], ((kc / NP) - 1) & 1))) {
                 atomicExch(err, 1);
                 *(volatile int*)abort_flag = 1;
                 break;
@@ -262,9 +268,27 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CU
         for (int j = 0; j < BN; ++j) acc[j] = 0.f;
         bool ok = true;
         const uint32_t lane_base = (uint32_t)(sub * 32) << 16;
+        // chain epilogue: when the tile's rows all belong to one domain, its columns' slope,
+        // intercept and bias are staged once in shared memory while the first chunk is computed
+        bool uniform = false;
+        if constexpr (EPI) {
+            const int dom0 = m0 / epi.rows_per_dom;
+            uniform = R > 0 && dom0 == (min(m0 + BM, R) - 1) / epi.rows_per_dom;
+            if (uniform) {
+                for (int j = threadIdx.x - 64; j < BN; j += 128) {
+                    const int col = n0 + j;
+                    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (col < N)
+                        q = make_float4(epi.hs[(int64_t)dom0 * epi.hidden + epi.hoff + col],
+                                        epi.hd[(int64_t)dom0 * epi.hidden + epi.hoff + col], epi.bias[col], 0.f);
+                    coltab[j] = q;
+                }
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");  // the four epilogue warps
+        }
         for (int kc = 0; kc < nk; ++kc) {
-            const int p = kc & 1;
-            if (*(volatile int*)abort_flag || !mbar_wait(&pfull[p], (kc >> 1) & 1)) {
+            const int p = kc % NP;
+            if (*(volatile int*)abort_flag || !mbar_wait(&pfull[p], (kc / NP) & 1)) {
                 ok = false;
                 break;
             }
@@ -294,18 +318,31 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CU
             const float* sl = epi.hs + (int64_t)dom * epi.hidden + epi.hoff;
             const float* dl = epi.hd + (int64_t)dom * epi.hidden + epi.hoff;
             float spos = 0.f, sneg = 0.f, sb = 0.f;
+            if (uniform) {
+                // padding columns carry (0, 0, 0): x*s = 0 and no intercept contribution
 #pragma unroll
-            for (int j = 0; j < BN; ++j) {
-                const int col = n0 + j;
-                float xs = 0.f;
-                if (col < N) {
-                    const float x = acc[j], dj = dl[col];
-                    xs = x * sl[col];
-                    spos = fmaf(fmaxf(x, 0.f), dj, spos);
-                    sneg = fmaf(fminf(x, 0.f), dj, sneg);
-                    sb = fmaf(xs, epi.bias[col], sb);
+                for (int j = 0; j < BN; ++j) {
+                    const float4 q = coltab[j];
+                    const float x = acc[j], xs = x * q.x;
+                    spos = fmaf(fmaxf(x, 0.f), q.y, spos);
+                    sneg = fmaf(fminf(x, 0.f), q.y, sneg);
+                    sb = fmaf(xs, q.z, sb);
+                    acc[j] = xs;
                 }
-                acc[j] = xs;
+            } else {
+#pragma unroll
+                for (int j = 0; j < BN; ++j) {
+                    const int col = n0 + j;
+                    float xs = 0.f;
+                    if (col < N) {
+                        const float x = acc[j], dj = dl[col];
+                        xs = x * sl[col];
+                        spos = fmaf(fmaxf(x, 0.f), dj, spos);
+                        sneg = fmaf(fminf(x, 0.f), dj, sneg);
+                        sb = fmaf(xs, epi.bias[col], sb);
+                    }
+                    acc[j] = xs;
+                }
             }
             if (live) {
                 float* pp = epi.part + ((int64_t)row * gridDim.x + blockIdx.x) * 3;
@@ -324,15 +361,18 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CU
                 // blocked layout: the warp's 32 rows of one 32-column chunk are 4 KB contiguous
                 float* dst = part_i == 0 ? epi.Ah : epi.Al;
                 const int enk = epi.ldk >> 5;
+                const int nr = ok ? max(0, min(32, R - (m0 + sub * 32))) : 0;  // live rows of this warp
                 for (int c0 = 0; c0 < cmax; c0 += 32) {
                     const int j = c0 + lane;
                     if (j >= cmax) continue;
                     // rows m0 + sub*32 .. +31 stay inside one 128-row block: consecutive rows are 32 apart
                     float* col = dst + blk_index(m0 + sub * 32, n0 + j, enk);
-                    for (int r = 0; r < 32; ++r) {
-                        if (!ok || m0 + sub * 32 + r >= R) break;
-                        col[r * 32] = tile[r * TLD + j];
-                    }
+                    float v[32];
+#pragma unroll
+                    for (int r = 0; r < 32; ++r) v[r] = tile[r * TLD + j];
+#pragma unroll
+                    for (int r = 0; r < 32; ++r)
+                        if (r < nr) col[r * 32] = v[r];
                 }
                 __syncwarp();
             }
