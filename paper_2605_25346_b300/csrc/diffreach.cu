@@ -391,7 +391,7 @@ static int launch_tc_gemm_bn(dr_ctx* c, const CUtensorMap* m, float* C, int R, i
     const int64_t mt = (R + tc::BM - 1) / tc::BM;
     if (mt > 65535) return fail(c, DR_ERR_SHAPE, "too many row tiles (%lld) for one launch", (long long)mt);
     dim3 grid((N + BN - 1) / BN, (unsigned)mt);
-    tc::k_tc_gemm_p<BN, EPI><<<grid, tc::kGemmThreads, smem, st>>>(m[0], m[1], m[2], m[3], C, R, K, N, ldc, err, epi);
+    tc::k_tc_gemm_p<BN, EPI><<<grid, tc::gemm_threads(BN), smem, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], C, R, K, N, ldc, err, epi);
     CUDA_TRY(c, cudaGetLastError());
     if (c) c->launches++;
     return DR_OK;
@@ -403,11 +403,19 @@ static int tc_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* BTh
                    int N, int ldk, int ldc, int* err, cudaStream_t st, const tc::ChainEpi* epi = nullptr) {
     TRY(get_encoder(c));
     const int BN = tc_bn(N);
-    CUtensorMap m[4];
+    CUtensorMap m[6];
     TRY(make_map_blocked(c, &m[0], Ah, R, ldk));
     TRY(make_map_blocked(c, &m[1], Al, R, ldk));
     TRY(make_map(c, &m[2], BTh, N, ldk, BN));
     TRY(make_map(c, &m[3], BTl, N, ldk, BN));
+    if (epi) {
+        // the chain epilogue stores the next left operand (blocked, epi->ldk columns) by TMA
+        TRY(make_map_blocked(c, &m[4], epi->Ah, R, epi->ldk));
+        TRY(make_map_blocked(c, &m[5], epi->Al, R, epi->ldk));
+    } else {
+        m[4] = m[0];
+        m[5] = m[1];
+    }
     tc::ChainEpi e{};
     if (epi) e = *epi;
 #define DR_TC_CASE(bn)                                                                          \
@@ -930,7 +938,7 @@ static int64_t wide_part_per_domain(const NetDesc& N) {
     for (int l = 2; l <= N.L; ++l)
         for (int mm = l - 1; mm >= 2; --mm) {
             const int NN = N.w[mm - 1], bn = tc_bn(NN);
-            best = std::max<int64_t>(best, (int64_t)N.w[l] * ((NN + bn - 1) / bn));
+            best = std::max<int64_t>(best, (int64_t)N.w[l] * ((NN + bn - 1) / bn) * tc::epi_groups(bn));
         }
     return best;
 }
@@ -1029,6 +1037,13 @@ static int wide_chunk(dr_ctx* c, const NetDesc& N) {
 
 static inline unsigned blocks_for(int64_t threads, int bs) { return (unsigned)((threads + bs - 1) / bs); }
 
+static void launch_t_project(dr_ctx* c, const WideArgs& a, int ell, const float* Lx, int shared_lx, int64_t R) {
+    const unsigned blocks = (unsigned)std::min<int64_t>((R + 127) / 128, (int64_t)148 * 16);
+    if (a.net.n <= 16) k_t_project<16><<<blocks, 128, 0, c->stream>>>(a, ell, Lx, shared_lx);
+    else k_t_project<64><<<blocks, 128, 0, c->stream>>>(a, ell, Lx, shared_lx);
+    c->launches++;
+}
+
 static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
     NetDesc N = c->net;
     N.H = c->H;
@@ -1073,7 +1088,10 @@ static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
             for (int ell = 1; ell <= L; ++ell) {
                 const int rows = N.w[ell];
                 const int64_t warps = (int64_t)dc * rows;
-                if (!tcore || ell == 1) {
+                if (tcore && ell == 1) {
+                    // layer 1: Lambda_x = W_1, shared by every domain
+                    launch_t_project(c, a, 1, c->dW + N.Woff[0], 1, (int64_t)dc * rows);
+                } else if (!tcore || ell == 1) {
                     k_w_chain_init<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, ell, lamA);
                     c->launches++;
                     float* cur = lamA;
@@ -1118,7 +1136,7 @@ static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
                             epi.ldk = round_up32(NN);
                             epi.part = part;
                             TRY(tc_gemm(c, curh, curl, WTh, WTl, nullptr, R, K, NN, ldk, 0, c->derr, c->stream, &epi));
-                            const int ntiles = (NN + tc_bn(NN) - 1) / tc_bn(NN);
+                            const int ntiles = (NN + tc_bn(NN) - 1) / tc_bn(NN) * tc::epi_groups(tc_bn(NN));
                             k_t_partials<<<blocks_for(R, 256), 256, 0, c->stream>>>(a, ell, part, ntiles);
                             c->launches++;
                             std::swap(curh, nxth);
@@ -1128,8 +1146,7 @@ static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
                             TRY(tc_gemm(c, curh, curl, WTh, WTl, nxth, R, K, NN, ldk, NN, c->derr, c->stream));
                         }
                     }
-                    k_t_project<<<blocks_for(R, 256), 256, 0, c->stream>>>(a, ell, nxth);
-                    c->launches++;
+                    launch_t_project(c, a, ell, nxth, 0, R);
                 }
                 if (ell < L) {
                     k_w_relax<<<dc, 256, 0, c->stream>>>(a, ell, t);

@@ -119,6 +119,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 
 __host__ __device__ constexpr int pstages_for(int bn) { return bn >= 128 ? 3 : 4; }
 
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float* v) {
+    uint32_t r[64];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 64; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// TMA tensor store of one box from shared memory (bulk-group completion).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(reinterpret_cast<uint64_t>(map)),
+                 "r"(smem_u32(src)), "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
 // Chain epilogue: the output columns are the coefficients on the activations of a hidden layer;
 // instead of storing C the epilogue forms that layer's intercept partials over its column tile
 // (sum pos(x) d, sum neg(x) d, sum x s b) and the next level's left operand x*s as TF32 parts.
@@ -146,9 +165,17 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // FP32 registers, one output row per thread.  The tensor core then never accumulates more than one
 // chunk (12 MMAs), and the long sum over K runs in IEEE FP32 adds, which keeps the 3xTF32 product
 // as accurate as an FP32 SGEMM.  BN <= 128 (a thread holds BN partial sums).
-// Warp roles (192 threads): warp 0 lane 0 = TMA producer, warp 1 = TMEM owner and (lane 0) MMA
-// issuer, warps 2..5 = epilogue; warp w drains TMEM lanes 32*(w%4)..+31.
-constexpr int kGemmThreads = 192;
+// Warp roles: warp 0 lane 0 = TMA producer, warp 1 = TMEM owner and (lane 0) MMA issuer, warps
+// 2.. = epilogue, in EG groups of four warps (EG = 2 for BN >= 64: two warps per TMEM lane
+// quadrant, each with half of the tile's columns, so each thread holds BN / EG partial sums).
+__host__ __device__ constexpr int epi_groups(int bn) { return bn >= 64 ? 2 : 1; }
+__host__ __device__ constexpr int gemm_threads(int bn) { return 64 + 128 * epi_groups(bn); }
+template <int EG>
+__device__ __forceinline__ void epi_bar() {
+    if constexpr (EG == 2) asm volatile("bar.sync 1, 256;" ::: "memory");
+    else asm volatile("bar.sync 1, 128;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ float tf32_part_rna(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -156,8 +183,9 @@ __device__ __forceinline__ float tf32_part_rna(float x) {
 }
 
 template <int BN, bool EPI>
-__global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+__global__ void __launch_bounds__(gemm_threads(BN), 1) k_tc_gemm_p(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                                                       const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
+                                                      const __grid_constant__ CUtensorMap mOh, const __grid_constant__ CUtensorMap mOl,
                                                       float* __restrict__ C, int R, int K, int N, int ldc, int* __restrict__ err,
                                                       const ChainEpi epi) {
     static_assert(BN <= 128, "promoted accumulation keeps BN partial sums per thread");
@@ -165,6 +193,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CU
     constexpr int SB = stage_bytes(BN);
     constexpr int PB = BN < 32 ? 32 : BN;  // TMEM columns per partial buffer (32-column loads stay inside)
     constexpr int NP = kPartials;
+    constexpr int EG = epi_groups(BN);
+    constexpr int BNH = BN / EG;
     constexpr int TC = tmem_cols(NP * PB);
     constexpr uint32_t IDESC = idesc_tf32(BM, BN);
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -187,7 +217,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CU
         }
         for (int p = 0; p < NP; ++p) {
             mbar_init(&pfull[p], 1);
-            mbar_init(&pfree[p], 4);
+            mbar_init(&pfree[p], 4 * EG);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -261,11 +291,14 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CU
         }
     }
     if (warp >= 2) {
-        // ---- epilogue warps: add every chunk partial into FP32 registers
+        // ---- epilogue warps: add every chunk partial into FP32 registers.  Warp w drains TMEM lane
+        // quadrant w % 4 (the quadrant a warp may access), columns [cofs, cofs + BNH) of the tile.
         const int sub = warp & 3;
-        float acc[BN];
+        const int cofs = ((warp - 2) >> 2) * BNH;
+        const int grp = (warp - 2) >> 2;
+        float acc[BNH];
 #pragma unroll
-        for (int j = 0; j < BN; ++j) acc[j] = 0.f;
+        for (int j = 0; j < BNH; ++j) acc[j] = 0.f;
         bool ok = true;
         const uint32_t lane_base = (uint32_t)(sub * 32) << 16;
         // chain epilogue: when the tile's rows all belong to one domain, its columns' slope,
@@ -275,7 +308,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CU
             const int dom0 = m0 / epi.rows_per_dom;
             uniform = R > 0 && dom0 == (min(m0 + BM, R) - 1) / epi.rows_per_dom;
             if (uniform) {
-                for (int j = threadIdx.x - 64; j < BN; j += 128) {
+                for (int j = threadIdx.x - 64; j < BN; j += 128 * EG) {
                     const int col = n0 + j;
                     float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (col < N)
@@ -284,7 +317,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CU
                     coltab[j] = q;
                 }
             }
-            asm volatile("bar.sync 1, 128;" ::: "memory");  // the four epilogue warps
+            epi_bar<EG>();
         }
         for (int kc = 0; kc < nk; ++kc) {
             const int p = kc % NP;
@@ -293,13 +326,23 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CU
                 break;
             }
             fence_after();
+            if constexpr (BNH >= 64) {
 #pragma unroll
-            for (int c0 = 0; c0 < BN; c0 += 32) {
-                float v[32];
-                tmem_ld32(tmem + lane_base + (uint32_t)(p * PB + c0), v);
+                for (int c0 = 0; c0 < BNH; c0 += 64) {
+                    float v[64];
+                    tmem_ld64(tmem + lane_base + (uint32_t)(p * PB + cofs + c0), v);
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (c0 + j < BN) acc[c0 + j] += v[j];
+                    for (int j = 0; j < 64; ++j) acc[c0 + j] += v[j];
+                }
+            } else {
+#pragma unroll
+                for (int c0 = 0; c0 < BNH; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(tmem + lane_base + (uint32_t)(p * PB + cofs + c0), v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (c0 + j < BNH) acc[c0 + j] += v[j];
+                }
             }
             fence_before();
             __syncwarp();
@@ -308,10 +351,6 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CU
         if (!ok) atomicExch(err, 1);
         const int row = m0 + sub * 32 + lane;
         if constexpr (EPI) {
-            // x*s as TF32 parts, staged per warp through the (now idle) pipeline buffers as a
-            // 32 x BN tile with an odd row stride, then stored row by row with lanes across columns
-            constexpr int TLD = BN + 1;
-            float* tile = reinterpret_cast<float*>(base) + sub * 32 * TLD;
             const bool live = ok && row < R;
             const int rr = live ? row : (R > 0 ? R - 1 : 0);
             const int dom = rr / epi.rows_per_dom;
@@ -321,8 +360,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CU
             if (uniform) {
                 // padding columns carry (0, 0, 0): x*s = 0 and no intercept contribution
 #pragma unroll
-                for (int j = 0; j < BN; ++j) {
-                    const float4 q = coltab[j];
+                for (int j = 0; j < BNH; ++j) {
+                    const float4 q = coltab[cofs + j];
                     const float x = acc[j], xs = x * q.x;
                     spos = fmaf(fmaxf(x, 0.f), q.y, spos);
                     sneg = fmaf(fminf(x, 0.f), q.y, sneg);
@@ -331,8 +370,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CU
                 }
             } else {
 #pragma unroll
-                for (int j = 0; j < BN; ++j) {
-                    const int col = n0 + j;
+                for (int j = 0; j < BNH; ++j) {
+                    const int col = n0 + cofs + j;
                     float xs = 0.f;
                     if (col < N) {
                         const float x = acc[j], dj = dl[col];
@@ -345,44 +384,87 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_p(const __grid_constant__ CU
                 }
             }
             if (live) {
-                float* pp = epi.part + ((int64_t)row * gridDim.x + blockIdx.x) * 3;
+                // partial intercepts [R][column tiles * EG][3], one entry per (tile, column group)
+                float* pp = epi.part + (((int64_t)row * gridDim.x + blockIdx.x) * EG + grp) * 3;
                 pp[0] = spos;
                 pp[1] = sneg;
                 pp[2] = sb;
             }
             const int cmax = min(BN, epi.ldk - n0);  // columns of this tile inside the operand (incl. zero padding)
-            for (int part_i = 0; part_i < 2; ++part_i) {
+            if constexpr (BN >= 32) {
+                // Both TF32 parts staged in the idle pipeline buffers as 128-row x 32-column boxes in
+                // the 128-byte swizzle layout ([part][chunk][row][16-byte unit ^ (row & 7)]); one
+                // thread then writes every box with a TMA tensor store (a box of the blocked operand
+                // is 16 KB contiguous in global memory).
+                constexpr int NCH = BN / 32;
+                const int rr = sub * 32 + lane;
+                const int nch = cmax >> 5;
 #pragma unroll
-                for (int j = 0; j < BN; ++j) {
-                    const float h = tf32_part_rna(acc[j]);
-                    tile[lane * TLD + j] = part_i == 0 ? h : tf32_part_rna(acc[j] - h);
+                for (int cl = 0; cl < BNH / 32; ++cl) {
+                    const int c = cofs / 32 + cl;  // chunk of the tile
+                    if (c < nch) {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int j = cl * 32 + u * 4;
+                            const float h0 = tf32_part_rna(acc[j]), h1 = tf32_part_rna(acc[j + 1]);
+                            const float h2 = tf32_part_rna(acc[j + 2]), h3 = tf32_part_rna(acc[j + 3]);
+                            const float4 hv = make_float4(h0, h1, h2, h3);
+                            const float4 lv = make_float4(tf32_part_rna(acc[j] - h0), tf32_part_rna(acc[j + 1] - h1),
+                                                          tf32_part_rna(acc[j + 2] - h2), tf32_part_rna(acc[j + 3] - h3));
+                            const int off = c * 16384 + rr * 128 + ((u ^ (rr & 7)) << 4);
+                            *reinterpret_cast<float4*>(base + off) = hv;
+                            *reinterpret_cast<float4*>(base + NCH * 16384 + off) = lv;
+                        }
+                    }
                 }
-                __syncwarp();
-                // blocked layout: the warp's 32 rows of one 32-column chunk are 4 KB contiguous
-                float* dst = part_i == 0 ? epi.Ah : epi.Al;
-                const int enk = epi.ldk >> 5;
-                const int nr = ok ? max(0, min(32, R - (m0 + sub * 32))) : 0;  // live rows of this warp
-                for (int c0 = 0; c0 < cmax; c0 += 32) {
-                    const int j = c0 + lane;
-                    if (j >= cmax) continue;
-                    // rows m0 + sub*32 .. +31 stay inside one 128-row block: consecutive rows are 32 apart
-                    float* col = dst + blk_index(m0 + sub * 32, n0 + j, enk);
-                    float v[32];
-#pragma unroll
-                    for (int r = 0; r < 32; ++r) v[r] = tile[r * TLD + j];
-#pragma unroll
-                    for (int r = 0; r < 32; ++r)
-                        if (r < nr) col[r * 32] = v[r];
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                epi_bar<EG>();
+                if (threadIdx.x == 64 && ok) {
+                    const int enk = epi.ldk >> 5;
+                    for (int c = 0; c < nch; ++c) {
+                        const int y = ((int)blockIdx.y * enk + (n0 >> 5) + c) * BM;
+                        tma_store_2d(&mOh, base + c * 16384, 0, y);
+                        tma_store_2d(&mOl, base + NCH * 16384 + c * 16384, 0, y);
+                    }
+                    bulk_commit();
+                    bulk_wait_read();  // the boxes are read before the CTA releases its shared memory
                 }
-                __syncwarp();
+            } else {
+                // narrow tiles (BN = 16, one column group): x*s as TF32 parts staged per warp as a
+                // 32 x BN tile with an odd row stride, stored row by row with lanes across columns
+                constexpr int TLD = BN + 1;
+                float* tile = reinterpret_cast<float*>(base) + sub * 32 * TLD;
+                for (int part_i = 0; part_i < 2; ++part_i) {
+#pragma unroll
+                    for (int j = 0; j < BN; ++j) {
+                        const float h = tf32_part_rna(acc[j]);
+                        tile[lane * TLD + j] = part_i == 0 ? h : tf32_part_rna(acc[j] - h);
+                    }
+                    __syncwarp();
+                    // blocked layout: the warp's 32 rows of one 32-column chunk are 4 KB contiguous
+                    float* dst = part_i == 0 ? epi.Ah : epi.Al;
+                    const int enk = epi.ldk >> 5;
+                    const int nr = ok ? max(0, min(32, R - (m0 + sub * 32))) : 0;  // live rows of this warp
+                    for (int c0 = 0; c0 < cmax; c0 += 32) {
+                        const int j = c0 + lane;
+                        if (j >= cmax) continue;
+                        // rows m0 + sub*32 .. +31 stay inside one 128-row block: consecutive rows are 32 apart
+                        float* col = dst + blk_index(m0 + sub * 32, n0 + j, enk);
+                        float v[32];
+#pragma unroll
+                        for (int r = 0; r < 32; ++r) v[r] = tile[r * TLD + j];
+#pragma unroll
+                        for (int r = 0; r < 32; ++r)
+                            if (r < nr) col[r * 32] = v[r];
+                    }
+                    __syncwarp();
+                }
             }
         } else if (ok && row < R) {
-            {
 #pragma unroll
-                for (int j = 0; j < BN; ++j) {
-                    const int col = n0 + j;
-                    if (col < N) C[(int64_t)row * ldc + col] = acc[j];
-                }
+            for (int j = 0; j < BNH; ++j) {
+                const int col = n0 + cofs + j;
+                if (col < N) C[(int64_t)row * ldc + col] = acc[j];
             }
         }
     }

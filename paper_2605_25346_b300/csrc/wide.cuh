@@ -501,37 +501,56 @@ __global__ void k_t_partials(const WideArgs a, int ell, const float* __restrict_
 }
 
 // Concretisation of target ell with one thread per (domain, row); Lambda_x rows of domain d start at
-// Lxb + d * rows * n (ld n).  Same arithmetic as k_w_project.
-__global__ void k_t_project(const WideArgs a, int ell, const float* __restrict__ Lxb) {
+// Lxb + d * rows * n (ld n), or, with shared_lx, every domain uses the same rows Lxb + i * n (the
+// first layer: Lambda_x = W_1 and kappa = b_1).  Same arithmetic as k_w_project.  NMAX >= n is a compile-time bound
+// so that the row lives in registers and the loops unroll.
+template <int NMAX>
+__global__ void __launch_bounds__(128) k_t_project(const WideArgs a, int ell, const float* __restrict__ Lxb, int shared_lx) {
     const NetDesc& N = a.net;
     const int n = N.n, L = N.L, rows = N.w[ell];
     const int64_t R = (int64_t)a.Dc * rows;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
         const int d = (int)(r / rows), i = (int)(r - (int64_t)d * rows);
-        const float* Lx = Lxb + r * n;
+        const float* Lx = shared_lx ? Lxb + (int64_t)i * n : Lxb + r * n;
         const float* Pf = a.Pf + (int64_t)d * n * n;
         const float* cf = a.cf + (int64_t)d * n;
         const float* Ilof = a.Ilof + (int64_t)d * n;
         const float* Ihif = a.Ihif + (int64_t)d * n;
         const float* vf = a.vf + (int64_t)d * (n + 1);
         float* G = a.G + ((int64_t)d * N.maxw + i) * n;
+        float x[NMAX];
+#pragma unroll
+        for (int j = 0; j < NMAX; ++j) x[j] = j < n ? Lx[j] : 0.f;
         float av = 0.f, rlo = 0.f, rhi = 0.f;
-        for (int j = 0; j < n; ++j) {
-            const float x = Lx[j];
-            av = fmaf(x, cf[j], av);
-            rlo = fmaf(posf(x), Ilof[j], fmaf(negf(x), Ihif[j], rlo));
-            rhi = fmaf(posf(x), Ihif[j], fmaf(negf(x), Ilof[j], rhi));
+#pragma unroll
+        for (int j = 0; j < NMAX; ++j) {
+            if (j < n) {
+                av = fmaf(x[j], cf[j], av);
+                rlo = fmaf(posf(x[j]), Ilof[j], fmaf(negf(x[j]), Ihif[j], rlo));
+                rhi = fmaf(posf(x[j]), Ihif[j], fmaf(negf(x[j]), Ilof[j], rhi));
+            }
         }
         float g1 = 0.f, gm = 0.f, gp = 0.f;
         for (int k = 0; k < n; ++k) {
             float acc = 0.f;
-            for (int j = 0; j < n; ++j) acc = fmaf(Lx[j], Pf[j * n + k], acc);
+#pragma unroll
+            for (int j = 0; j < NMAX; ++j)
+                if (j < n) acc = fmaf(x[j], Pf[j * n + k], acc);
             G[k] = acc;
             g1 += fabsf(acc);
             gm += fabsf(acc - vf[k]);
             gp += fabsf(acc + vf[k]);
         }
-        const float klo = a.klo[(int64_t)d * N.maxw + i], khi = a.khi[(int64_t)d * N.maxw + i];
+        // layer 1 has no chain: its intercepts are the bias (and kappa is recorded for the splits)
+        float klo, khi;
+        if (shared_lx) {
+            klo = khi = a.b[N.boff[0] + i];
+            a.klo[(int64_t)d * N.maxw + i] = klo;
+            a.khi[(int64_t)d * N.maxw + i] = khi;
+        } else {
+            klo = a.klo[(int64_t)d * N.maxw + i];
+            khi = a.khi[(int64_t)d * N.maxw + i];
+        }
         const float wf = vf[n];
         const float S = fabsf(av) + g1 + fabsf(klo) + fabsf(khi) + fabsf(rlo) + fabsf(rhi) + fabsf(wf);
         if (ell < L) {
