@@ -75,6 +75,7 @@ struct dr_ctx {
     float* dWTh = nullptr;
     float* dWTl = nullptr;
     int64_t WToff[DR_MAXL] = {};
+    float* dW2T = nullptr;  // W_2 transposed [n_1][n_2], FP32 (null for a one-layer controller)
     int* derr = nullptr;
     // per-CTA global slabs for the fused kernels on wide controllers (tape runs)
     unsigned char* gslab = nullptr;
@@ -382,7 +383,7 @@ static int make_map_blocked(dr_ctx* c, CUtensorMap* map, const float* ptr, int64
 
 static int tc_bn(int N) { return N > 64 ? 128 : (N > 32 ? 64 : (N > 16 ? 32 : 16)); }
 
-template <int BN, bool EPI>
+template <int BN, int EPI>
 static int launch_tc_gemm_bn(dr_ctx* c, const CUtensorMap* m, float* C, int R, int K, int N, int ldc, int* err,
                              cudaStream_t st, const tc::ChainEpi& epi) {
     const int smem = tc::psmem_bytes(BN);
@@ -408,7 +409,7 @@ static int tc_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* BTh
     TRY(make_map_blocked(c, &m[1], Al, R, ldk));
     TRY(make_map(c, &m[2], BTh, N, ldk, BN));
     TRY(make_map(c, &m[3], BTl, N, ldk, BN));
-    if (epi) {
+    if (epi && !epi->W1) {
         // the chain epilogue stores the next left operand (blocked, epi->ldk columns) by TMA
         TRY(make_map_blocked(c, &m[4], epi->Ah, R, epi->ldk));
         TRY(make_map_blocked(c, &m[5], epi->Al, R, epi->ldk));
@@ -418,17 +419,20 @@ static int tc_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* BTh
     }
     tc::ChainEpi e{};
     if (epi) e = *epi;
-#define DR_TC_CASE(bn)                                                                          \
-    case bn:                                                                                    \
-        return epi ? launch_tc_gemm_bn<bn, true>(c, m, C, R, K, N, ldc, err, st, e)             \
-                   : launch_tc_gemm_bn<bn, false>(c, m, C, R, K, N, ldc, err, st, e);
+    if (epi && epi->W1 && (BN < 32 || epi->n0 > tc::kFinalCols))
+        return fail(c, DR_ERR_SHAPE, "fused final chain level needs >= 32 columns and n <= %d", tc::kFinalCols);
+#define DR_TC_CASE(bn)                                                                                        \
+    case bn:                                                                                                  \
+        return !epi ? launch_tc_gemm_bn<bn, 0>(c, m, C, R, K, N, ldc, err, st, e)                             \
+                    : (epi->W1 ? launch_tc_gemm_bn<bn, 2>(c, m, C, R, K, N, ldc, err, st, e)                  \
+                               : launch_tc_gemm_bn<bn, 1>(c, m, C, R, K, N, ldc, err, st, e));
     switch (BN) {
         DR_TC_CASE(128)
         DR_TC_CASE(64)
         DR_TC_CASE(32)
         default:
-            return epi ? launch_tc_gemm_bn<16, true>(c, m, C, R, K, N, ldc, err, st, e)
-                       : launch_tc_gemm_bn<16, false>(c, m, C, R, K, N, ldc, err, st, e);
+            return epi ? launch_tc_gemm_bn<16, 1>(c, m, C, R, K, N, ldc, err, st, e)
+                       : launch_tc_gemm_bn<16, 0>(c, m, C, R, K, N, ldc, err, st, e);
     }
 #undef DR_TC_CASE
 }
@@ -630,6 +634,7 @@ void dr_destroy(dr_ctx* c) {
     cudaFree(c->dalpha);
     cudaFree(c->dWTh);
     cudaFree(c->dWTl);
+    cudaFree(c->dW2T);
     cudaFree(c->derr);
     delete c;
 }
@@ -737,8 +742,16 @@ int dr_load_controller(dr_ctx* c, int L, const int32_t* widths, const void* cons
         }
         dev_free(c, (void*&)c->dWTh, 0);
         dev_free(c, (void*&)c->dWTl, 0);
+        dev_free(c, (void*&)c->dW2T, 0);
         TRY(dev_alloc(c, c->dWTh, tot));
         TRY(dev_alloc(c, c->dWTl, tot));
+        if (L >= 2) {
+            std::vector<float> w2t((size_t)widths[1] * widths[2]);
+            for (int ii = 0; ii < widths[2]; ++ii)
+                for (int kk = 0; kk < widths[1]; ++kk) w2t[(size_t)kk * widths[2] + ii] = hw[N.Woff[1] + (int64_t)ii * widths[1] + kk];
+            TRY(dev_alloc(c, c->dW2T, w2t.size()));
+            CUDA_TRY(c, cudaMemcpyAsync(c->dW2T, w2t.data(), w2t.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        }
         if (!c->derr) TRY(dev_alloc(c, c->derr, 1));
         CUDA_TRY(c, cudaMemcpyAsync(c->dWTh, th.data(), tot * sizeof(float), cudaMemcpyHostToDevice, c->stream));
         CUDA_TRY(c, cudaMemcpyAsync(c->dWTl, tl.data(), tot * sizeof(float), cudaMemcpyHostToDevice, c->stream));
@@ -943,6 +956,12 @@ static int64_t wide_part_per_domain(const NetDesc& N) {
     return best;
 }
 
+// Partial Lambda_x rows per stacked row when the last chain level is fused into the GEMM epilogue.
+static int wide_lx_parts(const NetDesc& N) {
+    const int bn = tc_bn(N.w[1]);
+    return (N.w[1] + bn - 1) / bn * tc::epi_groups(bn);
+}
+
 static size_t wide_bytes_per_domain(const NetDesc& N) {
     const int n = N.n, m = N.m;
     size_t b = 0;
@@ -955,6 +974,7 @@ static size_t wide_bytes_per_domain(const NetDesc& N) {
     b += sizeof(float) * 3 * m;                                   // controller TM
     b += sizeof(float) * 4 * wide_lam_stride(N);                  // Lambda buffers (two TF32 pairs)
     b += sizeof(float) * 3 * wide_part_per_domain(N);             // intercept partials of fused levels
+    b += sizeof(float) * (size_t)N.maxw * wide_lx_parts(N) * n;   // partial Lambda_x rows of a fused final level
     return b + 16 * 24;
 }
 
@@ -967,7 +987,8 @@ static int64_t wide_lam_pad(const NetDesc& N) {
     return (int64_t)tc::BM * ldk;
 }
 
-static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, float** lamA, float** lamB, float** lamC, float** lamD, float** part) {
+static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, float** lamA, float** lamB, float** lamC, float** lamD, float** part,
+                     float** lxpart) {
     const NetDesc& N = a.net;
     const size_t need = wide_bytes_per_domain(N) * (size_t)Dc + 4 * (sizeof(float) * wide_lam_pad(N) + 256) + 4096;
     if (!c->wscratch || c->wscratch_bytes < need || c->wDc != Dc) {
@@ -1024,6 +1045,7 @@ static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, float** lamA, float** lamB,
     *lamC = (float*)take(sizeof(float) * (D * a.lam_stride + lam_pad));
     *lamD = (float*)take(sizeof(float) * (D * a.lam_stride + lam_pad));
     *part = (float*)take(sizeof(float) * D * 3 * wide_part_per_domain(N));
+    *lxpart = (float*)take(sizeof(float) * D * N.maxw * wide_lx_parts(N) * n);
     if (off > c->wscratch_bytes) return fail(c, DR_ERR_OOM, "staged scratch layout overflow");
     return DR_OK;
 }
@@ -1037,10 +1059,10 @@ static int wide_chunk(dr_ctx* c, const NetDesc& N) {
 
 static inline unsigned blocks_for(int64_t threads, int bs) { return (unsigned)((threads + bs - 1) / bs); }
 
-static void launch_t_project(dr_ctx* c, const WideArgs& a, int ell, const float* Lx, int shared_lx, int64_t R) {
+static void launch_t_project(dr_ctx* c, const WideArgs& a, int ell, const float* Lx, int shared_lx, int64_t R, int lx_parts) {
     const unsigned blocks = (unsigned)std::min<int64_t>((R + 127) / 128, (int64_t)148 * 16);
-    if (a.net.n <= 16) k_t_project<16><<<blocks, 128, 0, c->stream>>>(a, ell, Lx, shared_lx);
-    else k_t_project<64><<<blocks, 128, 0, c->stream>>>(a, ell, Lx, shared_lx);
+    if (a.net.n <= 16) k_t_project<16><<<blocks, 128, 0, c->stream>>>(a, ell, Lx, shared_lx, lx_parts);
+    else k_t_project<64><<<blocks, 128, 0, c->stream>>>(a, ell, Lx, shared_lx, lx_parts);
     c->launches++;
 }
 
@@ -1071,8 +1093,8 @@ static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
     a.status = c->dstatus;
     a.alpha_used = alpha_used;
     const int Dc = wide_chunk(c, N);
-    float *lamA = nullptr, *lamB = nullptr, *lamC = nullptr, *lamD = nullptr, *part = nullptr;
-    TRY(wide_bind(c, a, Dc, &lamA, &lamB, &lamC, &lamD, &part));
+    float *lamA = nullptr, *lamB = nullptr, *lamC = nullptr, *lamD = nullptr, *part = nullptr, *lxpart = nullptr;
+    TRY(wide_bind(c, a, Dc, &lamA, &lamB, &lamC, &lamD, &part, &lxpart));
     const bool tcore = c->opt.precision != DR_PREC_SIMT;
     if (tcore) CUDA_TRY(c, cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream));
     const size_t dyn_smem = sizeof(double) * (n * n + 3 * n + 128);
@@ -1090,7 +1112,7 @@ static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
                 const int64_t warps = (int64_t)dc * rows;
                 if (tcore && ell == 1) {
                     // layer 1: Lambda_x = W_1, shared by every domain
-                    launch_t_project(c, a, 1, c->dW + N.Woff[0], 1, (int64_t)dc * rows);
+                    launch_t_project(c, a, 1, c->dW + N.Woff[0], 1, (int64_t)dc * rows, 0);
                 } else if (!tcore || ell == 1) {
                     k_w_chain_init<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, ell, lamA);
                     c->launches++;
@@ -1113,40 +1135,62 @@ static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
                     c->launches++;
                 } else {
                     // tensor-core chain: rows of all domains stacked, A as TF32 parts, shared W^T parts;
-                    // levels that feed another level form the next operand in the GEMM epilogue
+                    // levels that feed another level form the next operand in the GEMM epilogue, and
+                    // the last level (x W_1, n columns) is folded into the epilogue of the level before
                     const int R = dc * rows;
-                    int ldk = round_up32(N.w[ell - 1]);
-                    k_t_chain_init<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, ell, lamA, lamB, ldk);
-                    c->launches++;
-                    float *curh = lamA, *curl = lamB, *nxth = lamC, *nxtl = lamD;
-                    for (int mm = ell - 1; mm >= 1; --mm) {
-                        const int K = N.w[mm], NN = N.w[mm - 1];
-                        const float* WTh = c->dWTh + c->WToff[mm - 1];
-                        const float* WTl = c->dWTl + c->WToff[mm - 1];
-                        if (mm - 1 >= 1) {
-                            tc::ChainEpi epi{};
-                            epi.hs = a.hs;
-                            epi.hd = a.hd;
-                            epi.bias = c->db + N.boff[mm - 2];
-                            epi.hidden = N.hidden;
-                            epi.hoff = N.hoff[mm - 1];
-                            epi.rows_per_dom = rows;
-                            epi.Ah = nxth;
-                            epi.Al = nxtl;
-                            epi.ldk = round_up32(NN);
-                            epi.part = part;
-                            TRY(tc_gemm(c, curh, curl, WTh, WTl, nullptr, R, K, NN, ldk, 0, c->derr, c->stream, &epi));
-                            const int ntiles = (NN + tc_bn(NN) - 1) / tc_bn(NN) * tc::epi_groups(tc_bn(NN));
-                            k_t_partials<<<blocks_for(R, 256), 256, 0, c->stream>>>(a, ell, part, ntiles);
-                            c->launches++;
-                            std::swap(curh, nxth);
-                            std::swap(curl, nxtl);
-                            ldk = round_up32(NN);
-                        } else {
-                            TRY(tc_gemm(c, curh, curl, WTh, WTl, nxth, R, K, NN, ldk, NN, c->derr, c->stream));
+                    const bool fuse_final = N.n <= tc::kFinalCols && tc_bn(N.w[1]) >= 32;
+                    const size_t chain2_smem = sizeof(float) * (size_t)N.w[1] * (16 + 2);
+                    if (ell == 2 && N.n <= 16 && chain2_smem <= 48 * 1024) {
+                        // target 2: the whole chain W_2 diag(s_1) W_1 in one SIMT pass
+                        dim3 g2((unsigned)dc, (unsigned)((rows + 127) / 128));
+                        k_t_chain2<16><<<g2, 128, chain2_smem, c->stream>>>(a, c->dW2T, lamC);
+                        c->launches++;
+                        launch_t_project(c, a, ell, lamC, 0, R, 0);
+                    } else {
+                        int ldk = round_up32(N.w[ell - 1]);
+                        k_t_chain_init<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, ell, lamA, lamB, ldk);
+                        c->launches++;
+                        float *curh = lamA, *curl = lamB, *nxth = lamC, *nxtl = lamD;
+                        int lx_parts = 0;
+                        for (int mm = ell - 1; mm >= 1; --mm) {
+                            const int K = N.w[mm], NN = N.w[mm - 1];
+                            const float* WTh = c->dWTh + c->WToff[mm - 1];
+                            const float* WTl = c->dWTl + c->WToff[mm - 1];
+                            if (mm - 1 >= 1) {
+                                const bool fin = mm == 2 && fuse_final;
+                                tc::ChainEpi epi{};
+                                epi.hs = a.hs;
+                                epi.hd = a.hd;
+                                epi.bias = c->db + N.boff[mm - 2];
+                                epi.hidden = N.hidden;
+                                epi.hoff = N.hoff[mm - 1];
+                                epi.rows_per_dom = rows;
+                                epi.Ah = nxth;
+                                epi.Al = nxtl;
+                                epi.ldk = round_up32(NN);
+                                epi.part = part;
+                                if (fin) {
+                                    epi.W1 = c->dW + N.Woff[0];
+                                    epi.n0 = N.n;
+                                    epi.lxpart = lxpart;
+                                }
+                                TRY(tc_gemm(c, curh, curl, WTh, WTl, nullptr, R, K, NN, ldk, 0, c->derr, c->stream, &epi));
+                                const int ntiles = (NN + tc_bn(NN) - 1) / tc_bn(NN) * tc::epi_groups(tc_bn(NN));
+                                k_t_partials<<<blocks_for(R, 256), 256, 0, c->stream>>>(a, ell, part, ntiles);
+                                c->launches++;
+                                if (fin) {
+                                    lx_parts = ntiles;
+                                    break;
+                                }
+                                std::swap(curh, nxth);
+                                std::swap(curl, nxtl);
+                                ldk = round_up32(NN);
+                            } else {
+                                TRY(tc_gemm(c, curh, curl, WTh, WTl, nxth, R, K, NN, ldk, NN, c->derr, c->stream));
+                            }
                         }
+                        launch_t_project(c, a, ell, lx_parts ? lxpart : nxth, 0, R, lx_parts);
                     }
-                    launch_t_project(c, a, ell, nxth, 0, R);
                 }
                 if (ell < L) {
                     k_w_relax<<<dc, 256, 0, c->stream>>>(a, ell, t);

@@ -141,19 +141,28 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 // Chain epilogue: the output columns are the coefficients on the activations of a hidden layer;
 // instead of storing C the epilogue forms that layer's intercept partials over its column tile
 // (sum pos(x) d, sum neg(x) d, sum x s b) and the next level's left operand x*s as TF32 parts.
+// With W1 set (the last level of a chain, whose columns are layer 1's activations) the epilogue
+// instead multiplies x*s by W1 [N][n0] in FP32 and writes per-tile partial rows of Lambda_x.
 struct ChainEpi {
     const float* hs;   // [domains][hidden] slopes
     const float* hd;   // [domains][hidden] intercepts
     const float* bias; // [N] bias of the layer
     int hidden, hoff;  // row stride of hs/hd and the layer's offset
     int rows_per_dom;  // stacked rows per domain
-    float* Ah;         // next left operand, TF32 parts [R][ldk]
+    float* Ah;         // next left operand, TF32 parts (blocked layout, ldk columns)
     float* Al;
     int ldk;
-    float* part;       // [R][gridDim.y][3] partial intercepts
+    float* part;       // [column tiles * column groups][3][R] partial intercepts (rows contiguous)
+    const float* W1;   // final level: W_1 [N][n0] (row-major), else null
+    int n0;            // columns of W_1 (<= kFinalCols)
+    float* lxpart;     // final level: [column tiles * column groups][n0][R] partial Lambda_x entries
 };
-// pipeline stages, 1 KB alignment slack, 256 B of barriers, and the epilogue's per-column table
-__host__ __device__ constexpr int psmem_bytes(int bn) { return pstages_for(bn) * stage_bytes(bn) + 1024 + 256 + 16 * bn; }
+constexpr int kFinalCols = 16;  // widest input layer the fused final level handles
+// pipeline stages, 1 KB alignment slack, 256 B of barriers, the epilogue's per-column table and
+// the final level's W_1 rows
+__host__ __device__ constexpr int psmem_bytes(int bn) {
+    return pstages_for(bn) * stage_bytes(bn) + 1024 + 256 + 16 * bn + 4 * kFinalCols * bn;
+}
 constexpr int kPartials = 3;  // TMEM partial buffers: the MMA issuer may run two chunks ahead of the epilogue
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -182,7 +191,8 @@ __device__ __forceinline__ float tf32_part_rna(float x) {
     return __uint_as_float(r);
 }
 
-template <int BN, bool EPI>
+// EPI: 0 = store C, 1 = chain level (next operand by TMA), 2 = final chain level (W_1 product).
+template <int BN, int EPI>
 __global__ void __launch_bounds__(gemm_threads(BN), 1) k_tc_gemm_p(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                                                       const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
                                                       const __grid_constant__ CUtensorMap mOh, const __grid_constant__ CUtensorMap mOl,
@@ -206,6 +216,7 @@ __global__ void __launch_bounds__(gemm_threads(BN), 1) k_tc_gemm_p(const __grid_
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(pfree + NP);
     int* abort_flag = reinterpret_cast<int*>(tmem_holder + 1);
     float4* coltab = reinterpret_cast<float4*>(base + S * SB + 256);  // [BN] (s, d, bias) of the tile's columns
+    float* w1tab = reinterpret_cast<float*>(coltab + BN);               // [BN][kFinalCols] W_1 rows (final level)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int nk = (K + BK - 1) / BK;
@@ -304,7 +315,14 @@ __global__ void __launch_bounds__(gemm_threads(BN), 1) k_tc_gemm_p(const __grid_
         // chain epilogue: when the tile's rows all belong to one domain, its columns' slope,
         // intercept and bias are staged once in shared memory while the first chunk is computed
         bool uniform = false;
-        if constexpr (EPI) {
+        if constexpr (EPI != 0) {
+            if constexpr (EPI == 2) {
+                for (int idx = threadIdx.x - 64; idx < BN * kFinalCols; idx += 128 * EG) {
+                    const int j = idx / kFinalCols, c = idx - j * kFinalCols;
+                    const int col = n0 + j;
+                    w1tab[idx] = (col < N && c < epi.n0) ? epi.W1[(int64_t)col * epi.n0 + c] : 0.f;
+                }
+            }
             const int dom0 = m0 / epi.rows_per_dom;
             uniform = R > 0 && dom0 == (min(m0 + BM, R) - 1) / epi.rows_per_dom;
             if (uniform) {
@@ -350,7 +368,7 @@ __global__ void __launch_bounds__(gemm_threads(BN), 1) k_tc_gemm_p(const __grid_
         }
         if (!ok) atomicExch(err, 1);
         const int row = m0 + sub * 32 + lane;
-        if constexpr (EPI) {
+        if constexpr (EPI != 0) {
             const bool live = ok && row < R;
             const int rr = live ? row : (R > 0 ? R - 1 : 0);
             const int dom = rr / epi.rows_per_dom;
@@ -384,14 +402,40 @@ __global__ void __launch_bounds__(gemm_threads(BN), 1) k_tc_gemm_p(const __grid_
                 }
             }
             if (live) {
-                // partial intercepts [R][column tiles * EG][3], one entry per (tile, column group)
-                float* pp = epi.part + (((int64_t)row * gridDim.x + blockIdx.x) * EG + grp) * 3;
-                pp[0] = spos;
-                pp[1] = sneg;
-                pp[2] = sb;
+                // partial intercepts, one set per (column tile, column group); consecutive rows are
+                // consecutive in memory, so a warp's stores coalesce
+                const int64_t t = (int64_t)blockIdx.x * EG + grp;
+                epi.part[(t * 3 + 0) * R + row] = spos;
+                epi.part[(t * 3 + 1) * R + row] = sneg;
+                epi.part[(t * 3 + 2) * R + row] = sb;
             }
             const int cmax = min(BN, epi.ldk - n0);  // columns of this tile inside the operand (incl. zero padding)
-            if constexpr (BN >= 32) {
+            if constexpr (EPI == 2) {
+                // final level: this thread's share of Lambda_x row = sum over its columns of
+                // (x*s)_j W_1[j][:], in FP32 (W_1 rows broadcast from shared memory)
+                float px[kFinalCols];
+#pragma unroll
+                for (int c = 0; c < kFinalCols; ++c) px[c] = 0.f;
+#pragma unroll
+                for (int j = 0; j < BNH; ++j) {
+                    const float xs = acc[j];
+                    const float4* w = reinterpret_cast<const float4*>(w1tab + (cofs + j) * kFinalCols);
+#pragma unroll
+                    for (int q = 0; q < kFinalCols / 4; ++q) {
+                        const float4 wv = w[q];
+                        px[4 * q] = fmaf(xs, wv.x, px[4 * q]);
+                        px[4 * q + 1] = fmaf(xs, wv.y, px[4 * q + 1]);
+                        px[4 * q + 2] = fmaf(xs, wv.z, px[4 * q + 2]);
+                        px[4 * q + 3] = fmaf(xs, wv.w, px[4 * q + 3]);
+                    }
+                }
+                if (live) {
+                    float* o = epi.lxpart + ((int64_t)blockIdx.x * EG + grp) * epi.n0 * (int64_t)R + row;
+#pragma unroll
+                    for (int c = 0; c < kFinalCols; ++c)
+                        if (c < epi.n0) o[(int64_t)c * R] = px[c];
+                }
+            } else if constexpr (BN >= 32) {
                 // Both TF32 parts staged in the idle pipeline buffers as 128-row x 32-column boxes in
                 // the 128-byte swizzle layout ([part][chunk][row][16-byte unit ^ (row & 7)]); one
                 // thread then writes every box with a TMA tensor store (a box of the blocked operand

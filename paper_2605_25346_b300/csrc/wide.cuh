@@ -482,6 +482,62 @@ __global__ void k_t_chain_init(const WideArgs a, int ell, float* __restrict__ Ah
     }
 }
 
+// Whole chain of target 2 (n <= NX) in FP32: kappa as k_t_chain_init and Lambda_x = W_2 diag(s_1) W_1.
+// Block (domain d, 128 rows of W_2), one thread per row i.  The domain's right factor
+// B[k][:] = s_1[k] W_1[k][:], d_1 and s_1*b_1 are staged in shared memory (broadcast reads), and
+// W2T = W_2 transposed [n_1][n_2] gives coalesced row loads.  Rows Lx [Dc*n_2][n].
+template <int NX>
+__global__ void __launch_bounds__(128) k_t_chain2(const WideArgs a, const float* __restrict__ W2T, float* __restrict__ Lx) {
+    extern __shared__ __align__(16) float sm2[];
+    const NetDesc& N = a.net;
+    const int rows = N.w[2], n = N.n, K = N.w[1];
+    const int d = blockIdx.x;
+    float* Bk = sm2;                  // [K][NX]
+    float* dk = Bk + (size_t)K * NX;  // [K]
+    float* sbk = dk + K;              // [K]
+    const float* s = a.hs + (int64_t)d * N.hidden + N.hoff[1];
+    const float* dd = a.hd + (int64_t)d * N.hidden + N.hoff[1];
+    const float* bm = a.b + N.boff[0];
+    const float* W1 = a.W + N.Woff[0];
+    for (int idx = threadIdx.x; idx < K * NX; idx += blockDim.x) {
+        const int k = idx / NX, c = idx - k * NX;
+        Bk[idx] = c < n ? s[k] * W1[(int64_t)k * n + c] : 0.f;
+    }
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        dk[k] = dd[k];
+        sbk[k] = s[k] * bm[k];
+    }
+    __syncthreads();
+    const int i = blockIdx.y * blockDim.x + threadIdx.x;
+    if (i >= rows) return;
+    float spos = 0.f, sneg = 0.f, sb = 0.f;
+    float px[NX];
+#pragma unroll
+    for (int c = 0; c < NX; ++c) px[c] = 0.f;
+    for (int k = 0; k < K; ++k) {
+        const float w = W2T[(int64_t)k * rows + i];
+        spos = fmaf(posf(w), dk[k], spos);
+        sneg = fmaf(negf(w), dk[k], sneg);
+        sb = fmaf(w, sbk[k], sb);
+        const float4* b4 = reinterpret_cast<const float4*>(Bk + (size_t)k * NX);
+#pragma unroll
+        for (int q = 0; q < NX / 4; ++q) {
+            const float4 bv = b4[q];
+            px[4 * q] = fmaf(w, bv.x, px[4 * q]);
+            px[4 * q + 1] = fmaf(w, bv.y, px[4 * q + 1]);
+            px[4 * q + 2] = fmaf(w, bv.z, px[4 * q + 2]);
+            px[4 * q + 3] = fmaf(w, bv.w, px[4 * q + 3]);
+        }
+    }
+    const int64_t r = (int64_t)d * rows + i;
+#pragma unroll
+    for (int c = 0; c < NX; ++c)
+        if (c < n) Lx[r * n + c] = px[c];
+    const float bi = a.b[N.boff[1] + i];
+    a.khi[(int64_t)d * N.maxw + i] = bi + spos + sb;
+    a.klo[(int64_t)d * N.maxw + i] = bi + sneg + sb;
+}
+
 // Adds the per-column-tile intercept partials of a fused chain level into kappa (fixed order).
 __global__ void k_t_partials(const WideArgs a, int ell, const float* __restrict__ part, int ntiles) {
     const NetDesc& N = a.net;
@@ -491,9 +547,9 @@ __global__ void k_t_partials(const WideArgs a, int ell, const float* __restrict_
         const int d = (int)(r / rows), i = (int)(r - (int64_t)d * rows);
         float sp = 0.f, sn = 0.f, sb = 0.f;
         for (int t = 0; t < ntiles; ++t) {
-            sp += part[(r * ntiles + t) * 3 + 0];
-            sn += part[(r * ntiles + t) * 3 + 1];
-            sb += part[(r * ntiles + t) * 3 + 2];
+            sp += part[((int64_t)t * 3 + 0) * R + r];
+            sn += part[((int64_t)t * 3 + 1) * R + r];
+            sb += part[((int64_t)t * 3 + 2) * R + r];
         }
         a.khi[(int64_t)d * N.maxw + i] += sp + sb;
         a.klo[(int64_t)d * N.maxw + i] += sn + sb;
@@ -504,8 +560,11 @@ __global__ void k_t_partials(const WideArgs a, int ell, const float* __restrict_
 // Lxb + d * rows * n (ld n), or, with shared_lx, every domain uses the same rows Lxb + i * n (the
 // first layer: Lambda_x = W_1 and kappa = b_1).  Same arithmetic as k_w_project.  NMAX >= n is a compile-time bound
 // so that the row lives in registers and the loops unroll.
+// With lx_parts > 0 the row is the sum, in order, of lx_parts partial rows stored entry-major:
+// entry j of part t at Lxb[(t*n + j)*R + r].
 template <int NMAX>
-__global__ void __launch_bounds__(128) k_t_project(const WideArgs a, int ell, const float* __restrict__ Lxb, int shared_lx) {
+__global__ void __launch_bounds__(128) k_t_project(const WideArgs a, int ell, const float* __restrict__ Lxb, int shared_lx,
+                                                   int lx_parts) {
     const NetDesc& N = a.net;
     const int n = N.n, L = N.L, rows = N.w[ell];
     const int64_t R = (int64_t)a.Dc * rows;
@@ -519,8 +578,19 @@ __global__ void __launch_bounds__(128) k_t_project(const WideArgs a, int ell, co
         const float* vf = a.vf + (int64_t)d * (n + 1);
         float* G = a.G + ((int64_t)d * N.maxw + i) * n;
         float x[NMAX];
+        if (lx_parts > 0) {
 #pragma unroll
-        for (int j = 0; j < NMAX; ++j) x[j] = j < n ? Lx[j] : 0.f;
+            for (int j = 0; j < NMAX; ++j) x[j] = 0.f;
+            for (int t = 0; t < lx_parts; ++t) {
+                const float* q = Lxb + (int64_t)t * n * R + r;
+#pragma unroll
+                for (int j = 0; j < NMAX; ++j)
+                    if (j < n) x[j] += q[(int64_t)j * R];
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < NMAX; ++j) x[j] = j < n ? Lx[j] : 0.f;
+        }
         float av = 0.f, rlo = 0.f, rhi = 0.f;
 #pragma unroll
         for (int j = 0; j < NMAX; ++j) {
