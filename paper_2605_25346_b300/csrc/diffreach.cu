@@ -84,6 +84,10 @@ struct dr_ctx {
     void* wscratch = nullptr;
     size_t wscratch_bytes = 0;
     int wDc = 0;
+    int wLanes = 0;
+    // second stream (and fork/join events) for the staged path's independent domain lanes
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 static thread_local std::string g_create_err;
@@ -636,6 +640,9 @@ void dr_destroy(dr_ctx* c) {
     cudaFree(c->dWTl);
     cudaFree(c->dW2T);
     cudaFree(c->derr);
+    if (c->aux) cudaStreamDestroy(c->aux);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
 }
 
@@ -987,19 +994,21 @@ static int64_t wide_lam_pad(const NetDesc& N) {
     return (int64_t)tc::BM * ldk;
 }
 
-static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, float** lamA, float** lamB, float** lamC, float** lamD, float** part,
-                     float** lxpart) {
+static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, int lanes, int lane, float** lamA, float** lamB, float** lamC,
+                     float** lamD, float** part, float** lxpart) {
     const NetDesc& N = a.net;
-    const size_t need = wide_bytes_per_domain(N) * (size_t)Dc + 4 * (sizeof(float) * wide_lam_pad(N) + 256) + 4096;
-    if (!c->wscratch || c->wscratch_bytes < need || c->wDc != Dc) {
+    const size_t need = (wide_bytes_per_domain(N) * (size_t)Dc + 4 * (sizeof(float) * wide_lam_pad(N) + 256) + 4096 + 255) & ~size_t(255);
+    if (!c->wscratch || c->wscratch_bytes < need * lanes || c->wDc != Dc || c->wLanes != lanes) {
         dev_free(c, c->wscratch, c->wscratch_bytes);
+        c->wscratch_bytes = 0;
         unsigned char* p = nullptr;
-        TRY(dev_alloc(c, p, need));
+        TRY(dev_alloc(c, p, need * lanes));
         c->wscratch = p;
-        c->wscratch_bytes = need;
+        c->wscratch_bytes = need * lanes;
         c->wDc = Dc;
+        c->wLanes = lanes;
     }
-    unsigned char* base = reinterpret_cast<unsigned char*>(c->wscratch);
+    unsigned char* base = reinterpret_cast<unsigned char*>(c->wscratch) + need * lane;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         off = (off + 255) & ~size_t(255);
@@ -1046,30 +1055,146 @@ static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, float** lamA, float** lamB,
     *lamD = (float*)take(sizeof(float) * (D * a.lam_stride + lam_pad));
     *part = (float*)take(sizeof(float) * D * 3 * wide_part_per_domain(N));
     *lxpart = (float*)take(sizeof(float) * D * N.maxw * wide_lx_parts(N) * n);
-    if (off > c->wscratch_bytes) return fail(c, DR_ERR_OOM, "staged scratch layout overflow");
+    if (off > need) return fail(c, DR_ERR_OOM, "staged scratch layout overflow");
     return DR_OK;
 }
 
-static int wide_chunk(dr_ctx* c, const NetDesc& N) {
+static int wide_chunk(dr_ctx* c, const NetDesc& N, int lanes) {
     if (c->opt.chunk_domains > 0) return (int)std::min<int64_t>(std::min<int64_t>(c->opt.chunk_domains, c->D), 65535);
-    const size_t budget = size_t(4) << 30;
+    const size_t budget = (size_t(4) << 30) / lanes;
     const int64_t dc = std::max<int64_t>(1, (int64_t)(budget / wide_bytes_per_domain(N)));
     return (int)std::min<int64_t>(std::min<int64_t>(dc, c->D), 65535);
 }
 
 static inline unsigned blocks_for(int64_t threads, int bs) { return (unsigned)((threads + bs - 1) / bs); }
 
-static void launch_t_project(dr_ctx* c, const WideArgs& a, int ell, const float* Lx, int shared_lx, int64_t R, int lx_parts) {
+static void launch_t_project(dr_ctx* c, const WideArgs& a, int ell, const float* Lx, int shared_lx, int64_t R, int lx_parts,
+                             cudaStream_t st) {
     const unsigned blocks = (unsigned)std::min<int64_t>((R + 127) / 128, (int64_t)148 * 16);
-    if (a.net.n <= 16) k_t_project<16><<<blocks, 128, 0, c->stream>>>(a, ell, Lx, shared_lx, lx_parts);
-    else k_t_project<64><<<blocks, 128, 0, c->stream>>>(a, ell, Lx, shared_lx, lx_parts);
+    if (a.net.n <= 16) k_t_project<16><<<blocks, 128, 0, st>>>(a, ell, Lx, shared_lx, lx_parts);
+    else k_t_project<64><<<blocks, 128, 0, st>>>(a, ell, Lx, shared_lx, lx_parts);
     c->launches++;
+}
+
+// One lane of the staged path: a chunk of domains with its own scratch, advanced on its own stream.
+struct WideLane {
+    WideArgs a;
+    float *lamA, *lamB, *lamC, *lamD, *part, *lxpart;
+    cudaStream_t st;
+    bool active;
+};
+
+// Every kernel of time step t of one lane's chunk (layers, chain, concretisation, relaxation, dynamics).
+static int wide_step(dr_ctx* c, WideLane& w, int t, bool tcore) {
+    const NetDesc& N = w.a.net;
+    const int n = N.n, L = N.L;
+    WideArgs& a = w.a;
+    const cudaStream_t st = w.st;
+    const int dc = a.Dc;
+    float *lamA = w.lamA, *lamB = w.lamB, *lamC = w.lamC, *lamD = w.lamD, *part = w.part, *lxpart = w.lxpart;
+    const size_t dyn_smem = sizeof(double) * (n * n + 3 * n + 128);
+    k_w_view<<<dc, 128, 0, st>>>(a);
+    c->launches++;
+    for (int ell = 1; ell <= L; ++ell) {
+        const int rows = N.w[ell];
+        const int64_t warps = (int64_t)dc * rows;
+        if (tcore && ell == 1) {
+            // layer 1: Lambda_x = W_1, shared by every domain
+            launch_t_project(c, a, 1, c->dW + N.Woff[0], 1, (int64_t)dc * rows, 0, st);
+        } else if (!tcore || ell == 1) {
+            k_w_chain_init<<<blocks_for(warps * 32, 256), 256, 0, st>>>(a, ell, lamA);
+            c->launches++;
+            float* cur = lamA;
+            float* nxt = lamB;
+            for (int mm = ell - 1; mm >= 1; --mm) {
+                const int K = N.w[mm], NN = N.w[mm - 1];
+                const float* Wm = c->dW + N.Woff[mm - 1];
+                dim3 grid((NN + 63) / 64, (rows + 63) / 64, dc);
+                k_w_gemm_simt<<<grid, 256, 0, st>>>(cur, Wm, nxt, rows, K, NN, a.lam_stride);
+                c->launches++;
+                if (mm - 1 >= 1) {
+                    k_w_level_epi<<<blocks_for(warps * 32, 256), 256, 0, st>>>(a, ell, mm - 1, nxt);
+                    c->launches++;
+                }
+                std::swap(cur, nxt);
+            }
+            if (ell == 1) k_w_project<<<blocks_for(warps * 32, 256), 256, 0, st>>>(a, 1, c->dW + N.Woff[0], 1);
+            else k_w_project<<<blocks_for(warps * 32, 256), 256, 0, st>>>(a, ell, cur, 0);
+            c->launches++;
+        } else {
+            // tensor-core chain: rows of all domains stacked, A as TF32 parts, shared W^T parts;
+            // levels that feed another level form the next operand in the GEMM epilogue, and
+            // the last level (x W_1, n columns) is folded into the epilogue of the level before
+            const int R = dc * rows;
+            const bool fuse_final = N.n <= tc::kFinalCols && tc_bn(N.w[1]) >= 32;
+            const size_t chain2_smem = sizeof(float) * (size_t)N.w[1] * (16 + 2);
+            if (ell == 2 && N.n <= 16 && chain2_smem <= 48 * 1024) {
+                // target 2: the whole chain W_2 diag(s_1) W_1 in one SIMT pass
+                dim3 g2((unsigned)dc, (unsigned)((rows + 127) / 128));
+                k_t_chain2<16><<<g2, 128, chain2_smem, st>>>(a, c->dW2T, lamC);
+                c->launches++;
+                launch_t_project(c, a, ell, lamC, 0, R, 0, st);
+            } else {
+                int ldk = round_up32(N.w[ell - 1]);
+                k_t_chain_init<<<blocks_for(warps * 32, 256), 256, 0, st>>>(a, ell, lamA, lamB, ldk);
+                c->launches++;
+                float *curh = lamA, *curl = lamB, *nxth = lamC, *nxtl = lamD;
+                int lx_parts = 0;
+                for (int mm = ell - 1; mm >= 1; --mm) {
+                    const int K = N.w[mm], NN = N.w[mm - 1];
+                    const float* WTh = c->dWTh + c->WToff[mm - 1];
+                    const float* WTl = c->dWTl + c->WToff[mm - 1];
+                    if (mm - 1 >= 1) {
+                        const bool fin = mm == 2 && fuse_final;
+                        tc::ChainEpi epi{};
+                        epi.hs = a.hs;
+                        epi.hd = a.hd;
+                        epi.bias = c->db + N.boff[mm - 2];
+                        epi.hidden = N.hidden;
+                        epi.hoff = N.hoff[mm - 1];
+                        epi.rows_per_dom = rows;
+                        epi.Ah = nxth;
+                        epi.Al = nxtl;
+                        epi.ldk = round_up32(NN);
+                        epi.part = part;
+                        if (fin) {
+                            epi.W1 = c->dW + N.Woff[0];
+                            epi.n0 = N.n;
+                            epi.lxpart = lxpart;
+                        }
+                        TRY(tc_gemm(c, curh, curl, WTh, WTl, nullptr, R, K, NN, ldk, 0, c->derr, st, &epi));
+                        const int ntiles = (NN + tc_bn(NN) - 1) / tc_bn(NN) * tc::epi_groups(tc_bn(NN));
+                        k_t_partials<<<blocks_for(R, 256), 256, 0, st>>>(a, ell, part, ntiles);
+                        c->launches++;
+                        if (fin) {
+                            lx_parts = ntiles;
+                            break;
+                        }
+                        std::swap(curh, nxth);
+                        std::swap(curl, nxtl);
+                        ldk = round_up32(NN);
+                    } else {
+                        TRY(tc_gemm(c, curh, curl, WTh, WTl, nxth, R, K, NN, ldk, NN, c->derr, st));
+                    }
+                }
+                launch_t_project(c, a, ell, lx_parts ? lxpart : nxth, 0, R, lx_parts, st);
+            }
+        }
+        if (ell < L) {
+            k_w_relax<<<dc, 256, 0, st>>>(a, ell, t);
+            c->launches++;
+        }
+    }
+    k_w_dyn<<<dc, 128, dyn_smem, st>>>(a, t);
+    c->launches++;
+    CUDA_TRY(c, cudaGetLastError());
+    return DR_OK;
 }
 
 static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
     NetDesc N = c->net;
     N.H = c->H;
-    const int n = N.n, L = N.L, H = N.H;
+    const int n = N.n, H = N.H;
     WideArgs a;
     memset(&a, 0, sizeof(a));
     a.net = N;
@@ -1092,116 +1217,47 @@ static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
     a.V = c->dV;
     a.status = c->dstatus;
     a.alpha_used = alpha_used;
-    const int Dc = wide_chunk(c, N);
-    float *lamA = nullptr, *lamB = nullptr, *lamC = nullptr, *lamD = nullptr, *part = nullptr, *lxpart = nullptr;
-    TRY(wide_bind(c, a, Dc, &lamA, &lamB, &lamC, &lamD, &part, &lxpart));
+    // Domains are independent: two lanes of chunks advance on two streams, so that one lane's
+    // memory-bound kernels overlap the other lane's tensor-core GEMMs.
+    const int lanes = c->D >= 256 ? 2 : 1;
+    const int Dc = (int)std::min<int64_t>(wide_chunk(c, N, lanes), (c->D + lanes - 1) / lanes);
+    WideLane w[2];
+    for (int l = 0; l < lanes; ++l) {
+        w[l].a = a;
+        TRY(wide_bind(c, w[l].a, Dc, lanes, l, &w[l].lamA, &w[l].lamB, &w[l].lamC, &w[l].lamD, &w[l].part, &w[l].lxpart));
+        w[l].st = c->stream;
+    }
     const bool tcore = c->opt.precision != DR_PREC_SIMT;
     if (tcore) CUDA_TRY(c, cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream));
-    const size_t dyn_smem = sizeof(double) * (n * n + 3 * n + 128);
-    for (int64_t d0 = 0; d0 < c->D; d0 += Dc) {
-        a.d0 = d0;
-        a.Dc = (int)std::min<int64_t>(Dc, c->D - d0);
-        const int dc = a.Dc;
-        k_w_seed<<<blocks_for((int64_t)dc * n, 256), 256, 0, c->stream>>>(a);
-        c->launches++;
-        for (int t = 0; t < H; ++t) {
-            k_w_view<<<dc, 128, 0, c->stream>>>(a);
-            c->launches++;
-            for (int ell = 1; ell <= L; ++ell) {
-                const int rows = N.w[ell];
-                const int64_t warps = (int64_t)dc * rows;
-                if (tcore && ell == 1) {
-                    // layer 1: Lambda_x = W_1, shared by every domain
-                    launch_t_project(c, a, 1, c->dW + N.Woff[0], 1, (int64_t)dc * rows, 0);
-                } else if (!tcore || ell == 1) {
-                    k_w_chain_init<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, ell, lamA);
-                    c->launches++;
-                    float* cur = lamA;
-                    float* nxt = lamB;
-                    for (int mm = ell - 1; mm >= 1; --mm) {
-                        const int K = N.w[mm], NN = N.w[mm - 1];
-                        const float* Wm = c->dW + N.Woff[mm - 1];
-                        dim3 grid((NN + 63) / 64, (rows + 63) / 64, dc);
-                        k_w_gemm_simt<<<grid, 256, 0, c->stream>>>(cur, Wm, nxt, rows, K, NN, a.lam_stride);
-                        c->launches++;
-                        if (mm - 1 >= 1) {
-                            k_w_level_epi<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, ell, mm - 1, nxt);
-                            c->launches++;
-                        }
-                        std::swap(cur, nxt);
-                    }
-                    if (ell == 1) k_w_project<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, 1, c->dW + N.Woff[0], 1);
-                    else k_w_project<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, ell, cur, 0);
-                    c->launches++;
-                } else {
-                    // tensor-core chain: rows of all domains stacked, A as TF32 parts, shared W^T parts;
-                    // levels that feed another level form the next operand in the GEMM epilogue, and
-                    // the last level (x W_1, n columns) is folded into the epilogue of the level before
-                    const int R = dc * rows;
-                    const bool fuse_final = N.n <= tc::kFinalCols && tc_bn(N.w[1]) >= 32;
-                    const size_t chain2_smem = sizeof(float) * (size_t)N.w[1] * (16 + 2);
-                    if (ell == 2 && N.n <= 16 && chain2_smem <= 48 * 1024) {
-                        // target 2: the whole chain W_2 diag(s_1) W_1 in one SIMT pass
-                        dim3 g2((unsigned)dc, (unsigned)((rows + 127) / 128));
-                        k_t_chain2<16><<<g2, 128, chain2_smem, c->stream>>>(a, c->dW2T, lamC);
-                        c->launches++;
-                        launch_t_project(c, a, ell, lamC, 0, R, 0);
-                    } else {
-                        int ldk = round_up32(N.w[ell - 1]);
-                        k_t_chain_init<<<blocks_for(warps * 32, 256), 256, 0, c->stream>>>(a, ell, lamA, lamB, ldk);
-                        c->launches++;
-                        float *curh = lamA, *curl = lamB, *nxth = lamC, *nxtl = lamD;
-                        int lx_parts = 0;
-                        for (int mm = ell - 1; mm >= 1; --mm) {
-                            const int K = N.w[mm], NN = N.w[mm - 1];
-                            const float* WTh = c->dWTh + c->WToff[mm - 1];
-                            const float* WTl = c->dWTl + c->WToff[mm - 1];
-                            if (mm - 1 >= 1) {
-                                const bool fin = mm == 2 && fuse_final;
-                                tc::ChainEpi epi{};
-                                epi.hs = a.hs;
-                                epi.hd = a.hd;
-                                epi.bias = c->db + N.boff[mm - 2];
-                                epi.hidden = N.hidden;
-                                epi.hoff = N.hoff[mm - 1];
-                                epi.rows_per_dom = rows;
-                                epi.Ah = nxth;
-                                epi.Al = nxtl;
-                                epi.ldk = round_up32(NN);
-                                epi.part = part;
-                                if (fin) {
-                                    epi.W1 = c->dW + N.Woff[0];
-                                    epi.n0 = N.n;
-                                    epi.lxpart = lxpart;
-                                }
-                                TRY(tc_gemm(c, curh, curl, WTh, WTl, nullptr, R, K, NN, ldk, 0, c->derr, c->stream, &epi));
-                                const int ntiles = (NN + tc_bn(NN) - 1) / tc_bn(NN) * tc::epi_groups(tc_bn(NN));
-                                k_t_partials<<<blocks_for(R, 256), 256, 0, c->stream>>>(a, ell, part, ntiles);
-                                c->launches++;
-                                if (fin) {
-                                    lx_parts = ntiles;
-                                    break;
-                                }
-                                std::swap(curh, nxth);
-                                std::swap(curl, nxtl);
-                                ldk = round_up32(NN);
-                            } else {
-                                TRY(tc_gemm(c, curh, curl, WTh, WTl, nxth, R, K, NN, ldk, NN, c->derr, c->stream));
-                            }
-                        }
-                        launch_t_project(c, a, ell, lx_parts ? lxpart : nxth, 0, R, lx_parts);
-                    }
-                }
-                if (ell < L) {
-                    k_w_relax<<<dc, 256, 0, c->stream>>>(a, ell, t);
-                    c->launches++;
-                }
-            }
-            k_w_dyn<<<dc, 128, dyn_smem, c->stream>>>(a, t);
+    if (lanes == 2) {
+        if (!c->aux) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+        if (!c->ev_fork) CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+        if (!c->ev_join) CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+        CUDA_TRY(c, cudaEventRecord(c->ev_fork, c->stream));
+        CUDA_TRY(c, cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+        w[1].st = c->aux;
+    }
+    int rc = DR_OK;
+    for (int64_t d0 = 0; d0 < c->D && rc == DR_OK; d0 += (int64_t)lanes * Dc) {
+        for (int l = 0; l < lanes; ++l) {
+            const int64_t s0 = d0 + (int64_t)l * Dc;
+            w[l].active = s0 < c->D;
+            if (!w[l].active) continue;
+            w[l].a.d0 = s0;
+            w[l].a.Dc = (int)std::min<int64_t>(Dc, c->D - s0);
+            k_w_seed<<<blocks_for((int64_t)w[l].a.Dc * n, 256), 256, 0, w[l].st>>>(w[l].a);
             c->launches++;
         }
-        CUDA_TRY(c, cudaGetLastError());
+        for (int t = 0; t < H && rc == DR_OK; ++t)
+            for (int l = 0; l < lanes && rc == DR_OK; ++l)
+                if (w[l].active) rc = wide_step(c, w[l], t, tcore);
     }
+    if (lanes == 2) {
+        // join the second lane back into the context's stream (also on the error path)
+        cudaEventRecord(c->ev_join, c->aux);
+        cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    }
+    if (rc != DR_OK) return rc;
     if (tcore) {
         int herr = 0;
         CUDA_TRY(c, cudaMemcpyAsync(&herr, c->derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
