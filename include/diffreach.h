@@ -91,7 +91,10 @@ typedef struct dr_options {
                               into the Taylor model)                                        */
     int32_t tuning;        /* 0 = pick the fused kernel's launch shape by timing the candidates on
                               first use (cached per architecture and widths; file DR_TUNE_CACHE
-                              if set), 1 = no search                                          */
+                              if set), 1 = no search (first candidate that fits), 2 + v = use
+                              candidate v (0..9; DR_ERR_SHAPE if it does not fit the controller):
+                              0..2 one warp per domain (16/8/4 warps per CTA; two hidden layers,
+                              n, m <= 8, hidden widths <= 128), 3..9 several domains per CTA   */
     int32_t reserved[5];
 } dr_options;
 

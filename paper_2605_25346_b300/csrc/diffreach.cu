@@ -17,6 +17,7 @@
 #include "fused_core.cuh"
 #include "fused_bwd.cuh"
 #include "fused_multi.cuh"
+#include "fused_warp.cuh"
 #include "tc_gemm.cuh"
 #include "wide.cuh"
 
@@ -337,6 +338,81 @@ static MultiLayout multi_layout(const NetDesc& N, int G) {
 
 static const int kMaxSmem = 227 * 1024;
 
+// Shared-memory layout of the warp-per-domain kernel (two hidden layers), WPC warps per CTA.
+static bool warp_applicable(const NetDesc& N) {
+    return N.L == 3 && N.n <= kWarpNX && N.m <= kWarpNX && N.w[1] <= kWarpHMAX && N.w[2] <= kWarpHMAX;
+}
+
+static WarpLayout warp_layout(const NetDesc& N, int WPC, bool splits) {
+    WarpLayout Y;
+    memset(&Y, 0, sizeof(Y));
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = (off + 15) & ~size_t(15);
+        const size_t r = off;
+        off += bytes;
+        return (int)r;
+    };
+    const int n = N.n, m = N.m, H1 = N.w[1], H2 = N.w[2];
+    Y.ld1 = odd_ld(n);
+    Y.ld2 = odd_ld(H1);
+    Y.W1 = take(sizeof(float) * H1 * Y.ld1);
+    Y.W2 = take(sizeof(float) * H2 * Y.ld2);
+    Y.W3 = take(sizeof(float) * m * H2);
+    Y.bs = take(sizeof(float) * (H1 + H2 + m));
+    Y.A = take(sizeof(double) * n * n);
+    Y.B = take(sizeof(double) * n * m);
+    Y.e = take(sizeof(double) * n);
+    Y.dom0 = (int)((off + 15) & ~size_t(15));
+    size_t d = 0;
+    auto dtake = [&](size_t bytes) {
+        d = (d + 15) & ~size_t(15);
+        const size_t r = d;
+        d += bytes;
+        return (int)r;
+    };
+    Y.c = dtake(sizeof(double) * n);
+    Y.P = dtake(sizeof(double) * n * n);
+    Y.Ilo = dtake(sizeof(double) * n);
+    Y.Ihi = dtake(sizeof(double) * n);
+    Y.v = dtake(sizeof(double) * n);
+    Y.w = dtake(sizeof(double) * 1);
+    Y.cn = dtake(sizeof(double) * n);
+    Y.Pn = dtake(sizeof(double) * n * n);
+    Y.Ilon = dtake(sizeof(double) * n);
+    Y.Ihin = dtake(sizeof(double) * n);
+    Y.cf = dtake(sizeof(float) * n);
+    Y.Pf = dtake(sizeof(float) * n * n);
+    Y.Ilof = dtake(sizeof(float) * n);
+    Y.Ihif = dtake(sizeof(float) * n);
+    Y.vf = dtake(sizeof(float) * (n + 1));
+    Y.hl = dtake(sizeof(float) * (H1 + H2));
+    Y.hu = dtake(sizeof(float) * (H1 + H2));
+    Y.hs = dtake(sizeof(float) * (H1 + H2));
+    Y.hd = dtake(sizeof(float) * (H1 + H2));
+    Y.sb1 = dtake(sizeof(float) * H1);
+    Y.B1 = dtake(sizeof(float) * H1 * ((n + 3) & ~3));
+    Y.W3s = dtake(sizeof(float) * m * H2);
+    Y.L31 = dtake(sizeof(float) * m * H1);
+    Y.Lx3 = dtake(sizeof(float) * m * n);
+    Y.Pu = dtake(sizeof(float) * m * kWarpNX);
+    Y.cu = dtake(sizeof(float) * m);
+    Y.Iulo = dtake(sizeof(float) * m);
+    Y.Iuhi = dtake(sizeof(float) * m);
+    const int hm = splits ? std::max(H1, H2) : 1;
+    Y.sa = dtake(sizeof(float) * hm);
+    Y.klo = dtake(sizeof(float) * hm);
+    Y.khi = dtake(sizeof(float) * hm);
+    Y.sRlo = dtake(sizeof(float) * hm);
+    Y.sRhi = dtake(sizeof(float) * hm);
+    Y.sS = dtake(sizeof(float) * hm);
+    Y.Gs = dtake(sizeof(float) * hm * kWarpNX);
+    Y.misc = dtake(sizeof(int) * 2);
+    Y.stride = (int)((d + 15) & ~size_t(15));
+    Y.total = Y.dom0 + WPC * Y.stride;
+    return Y;
+}
+
 
 static bool fused_fits(const NetDesc& N) { return fused_layout(N).total <= kMaxSmem; }
 
@@ -447,11 +523,33 @@ static inline int round_up32(int x) { return (x + 31) & ~31; }
 // grouped fused kernel: launch variants and the autotuner
 // ------------------------------------------------------------------------------------------------
 
+// Launch variants of the bounds-only forward pass: warp-per-domain kernels (group < 0: -group
+// warps per CTA; controllers with two hidden layers) and grouped kernels (threads, domains per CTA).
 struct MultiVariant {
     int threads, group;
 };
-static const MultiVariant kMultiVariants[] = {{256, 8}, {512, 8}, {256, 4}, {512, 4}, {128, 2}, {256, 2}, {128, 1}};
+static const MultiVariant kMultiVariants[] = {{512, -16}, {256, -8}, {128, -4}, {256, 8}, {512, 8}, {256, 4},
+                                              {512, 4},   {128, 2},  {256, 2},  {128, 1}};
 static const int kNumMultiVariants = (int)(sizeof(kMultiVariants) / sizeof(kMultiVariants[0]));
+
+static bool variant_fits(const MultiArgs& a, int v) {
+    const MultiVariant mv = kMultiVariants[v];
+    if (mv.group < 0)
+        return warp_applicable(a.net) && warp_layout(a.net, -mv.group, a.sp_row != nullptr).total <= kMaxSmem;
+    return multi_layout(a.net, mv.group).total <= kMaxSmem;
+}
+
+template <int WPC>
+static int launch_warp_t(dr_ctx* c, const MultiArgs& a) {
+    const bool splits = a.sp_row != nullptr;
+    const WarpLayout Y = warp_layout(a.net, WPC, splits);
+    if (!warp_applicable(a.net) || Y.total > kMaxSmem) return fail(c, DR_ERR_SHAPE, "warp variant does not fit");
+    CUDA_TRY(c, cudaFuncSetAttribute(k_fused_warp<WPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, Y.total));
+    k_fused_warp<WPC><<<(unsigned)((a.D + WPC - 1) / WPC), 32 * WPC, Y.total, c->stream>>>(a, Y, splits ? 1 : 0);
+    CUDA_TRY(c, cudaGetLastError());
+    c->launches++;
+    return DR_OK;
+}
 
 template <int NT, int G>
 static int launch_multi_t(dr_ctx* c, MultiArgs a) {
@@ -467,12 +565,15 @@ static int launch_multi_t(dr_ctx* c, MultiArgs a) {
 
 static int launch_multi(dr_ctx* c, const MultiArgs& a, int v) {
     switch (v) {
-        case 0: return launch_multi_t<256, 8>(c, a);
-        case 1: return launch_multi_t<512, 8>(c, a);
-        case 2: return launch_multi_t<256, 4>(c, a);
-        case 3: return launch_multi_t<512, 4>(c, a);
-        case 4: return launch_multi_t<128, 2>(c, a);
-        case 5: return launch_multi_t<256, 2>(c, a);
+        case 0: return launch_warp_t<16>(c, a);
+        case 1: return launch_warp_t<8>(c, a);
+        case 2: return launch_warp_t<4>(c, a);
+        case 3: return launch_multi_t<256, 8>(c, a);
+        case 4: return launch_multi_t<512, 8>(c, a);
+        case 5: return launch_multi_t<256, 4>(c, a);
+        case 6: return launch_multi_t<512, 4>(c, a);
+        case 7: return launch_multi_t<128, 2>(c, a);
+        case 8: return launch_multi_t<256, 2>(c, a);
         default: return launch_multi_t<128, 1>(c, a);
     }
 }
@@ -518,9 +619,16 @@ static void tune_file_store() {
 // stream), the winner is cached per (architecture, widths).  dr_options.tuning = 1 disables the
 // search and takes the first fitting variant with the largest group.
 static int tuned_variant(dr_ctx* c, const MultiArgs& a, int* out) {
+    if (c->opt.tuning >= 2) {
+        const int v = c->opt.tuning - 2;
+        if (v >= kNumMultiVariants || !variant_fits(a, v))
+            return fail(c, DR_ERR_SHAPE, "launch variant %d does not fit this controller", v);
+        *out = v;
+        return DR_OK;
+    }
     std::lock_guard<std::mutex> lock(g_tune_mu);
     tune_file_load();
-    const std::string key = tune_key(a.net, c->device);
+    const std::string key = tune_key(a.net, c->device) + (a.sp_row ? ":splits" : "");
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
         *out = it->second;
@@ -528,7 +636,7 @@ static int tuned_variant(dr_ctx* c, const MultiArgs& a, int* out) {
     }
     int first_fit = -1;
     for (int v = 0; v < kNumMultiVariants; ++v)
-        if (multi_layout(a.net, kMultiVariants[v].group).total <= kMaxSmem) {
+        if (variant_fits(a, v)) {
             first_fit = v;
             break;
         }
@@ -549,7 +657,7 @@ static int tuned_variant(dr_ctx* c, const MultiArgs& a, int* out) {
     float best = 1e30f;
     int bestv = first_fit;
     for (int v = 0; v < kNumMultiVariants; ++v) {
-        if (multi_layout(a.net, kMultiVariants[v].group).total > kMaxSmem) continue;
+        if (!variant_fits(a, v)) continue;
         TRY(launch_multi(c, t, v));  // warm-up
         CUDA_TRY(c, cudaEventRecord(e0, c->stream));
         TRY(launch_multi(c, t, v));

@@ -24,12 +24,12 @@ def _api():
     return api
 
 
-def gpu_bounds(prob, mode=None, alpha=None, on_device=True, rho=None, precision=0, chunk=0):
+def gpu_bounds(prob, mode=None, alpha=None, on_device=True, rho=None, precision=0, chunk=0, tuning=0):
     api = _api()
     r = api.Reach(0)
     r.load(prob, mode=mode, rho=rho, precision=precision)
-    if chunk:
-        r.set_options(mode=prob.mode if mode is None else mode, precision=precision, rho=rho, chunk=chunk)
+    if chunk or tuning:
+        r.set_options(mode=prob.mode if mode is None else mode, precision=precision, rho=rho, chunk=chunk, tuning=tuning)
     if alpha is not None:
         r.set_alpha(alpha)
     out = r.bounds(on_device=on_device)
@@ -124,6 +124,47 @@ def test_split_domains(beta_scale):
     p = _with_splits(wl.random_problem(8, [6, 40, 40, 3], D=64, H=6, eps=0.2), 1, beta_scale)
     assert p.splits.nnz > 50
     compare(p, gpu_bounds(p), orc.reach(p))
+
+
+# Launch variants of the bounds-only pass, forced through dr_options.tuning = 2 + v: v = 0..2 one warp
+# per domain (16, 8, 4 warps per CTA; two hidden layers), v = 3 several domains per CTA.
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_launch_variants_on_workloads(variant):
+    for p in (wl.double_integrator_tiny(), wl.quad6_batched(), wl.cartpole_diff()):
+        compare(p, gpu_bounds(p, tuning=2 + variant), orc.reach(p))
+
+
+@pytest.mark.parametrize("variant,widths,mode", [(v, w, m) for v in (0, 2, 3) for w, m in (
+    ([5, 37, 23, 3], orc.MODE_CHORD), ([2, 128, 128, 1], orc.MODE_ZERO), ([4, 1, 1, 1], orc.MODE_ADAPTIVE))] +
+    [(2, [8, 100, 60, 8], orc.MODE_CHORD)])  # 16 warps of this width exceed shared memory; 4 fit
+def test_launch_variants_random_shapes(variant, widths, mode):
+    p = wl.random_problem(hash((tuple(widths), mode, 7)) % 1000, widths, D=45, H=5, eps=0.15, mode=mode)
+    compare(p, gpu_bounds(p, tuning=2 + variant), orc.reach(p))
+
+
+@pytest.mark.parametrize("variant", [0, 3])
+@pytest.mark.parametrize("beta_scale", [0.0, 0.5])
+def test_launch_variants_split_domains(variant, beta_scale):
+    p = _with_splits(wl.random_problem(8, [6, 40, 40, 3], D=64, H=6, eps=0.2), 1, beta_scale)
+    compare(p, gpu_bounds(p, tuning=2 + variant), orc.reach(p))
+
+
+def test_launch_variant_user_slopes():
+    p = wl.random_problem(3, [4, 33, 17, 2], D=40, H=6, eps=0.3)
+    g = torch.Generator().manual_seed(0)
+    alpha32 = torch.rand(p.D, p.H, p.hidden, generator=g, dtype=torch.float64).float().numpy()
+    o = orc.reach(p, alpha=torch.as_tensor(alpha32, dtype=torch.float64), mode=orc.MODE_USER)
+    compare(p, gpu_bounds(p, alpha=alpha32, tuning=2), o)
+
+
+def test_launch_variant_that_does_not_fit_is_an_error():
+    api = _api()
+    p = wl.random_problem(9, [3, 16, 16, 16, 2], D=4, H=2)  # three hidden layers: no warp variant
+    r = api.Reach(0).load(p)
+    with pytest.raises(RuntimeError, match="does not fit"):
+        r.set_options(mode=p.mode, tuning=2)
+        r.bounds()
+    r.close()
 
 
 def test_host_and_device_outputs_identical():
