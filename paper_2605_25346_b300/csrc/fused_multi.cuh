@@ -55,39 +55,45 @@ struct MultiArgs {
 
 __host__ __device__ __forceinline__ int ru4(int x) { return (x + 3) & ~3; }
 
-// C [M x N] (ld ldc) = A [M x K] (ld lda) * B [K x N] (ld ldb, ldb % 4 == 0, 16-byte aligned, padding
-// columns finite): 4 x 4 register tiles, one float4 of B and four A values per k.
+// Rows per register tile: 4 unless the 4 x 4 tiles would leave more than half of the CTA's threads
+// idle; then 1 (short, wide products such as an output layer's chain level).
 template <int NT>
-__device__ __forceinline__ void gemm_shared_a(const float* __restrict__ A, int lda, const float* __restrict__ B, int ldb,
-                                              float* __restrict__ C, int ldc, int M, int K, int N) {
-    const int tilesM = (M + 3) >> 2, tilesN = (N + 3) >> 2;
+__device__ __forceinline__ bool tile4(int M, int N) {
+    return ((M + 3) >> 2) * ((N + 3) >> 2) * 2 >= NT;
+}
+
+// C [M x N] (ld ldc) = A [M x K] (ld lda) * B [K x N] (ld ldb, ldb % 4 == 0, 16-byte aligned, padding
+// columns finite): TR x 4 register tiles, one float4 of B and TR A values per k.
+template <int NT, int TR>
+__device__ __forceinline__ void gemm_shared_a_t(const float* __restrict__ A, int lda, const float* __restrict__ B, int ldb,
+                                                float* __restrict__ C, int ldc, int M, int K, int N) {
+    const int tilesM = (M + TR - 1) / TR, tilesN = (N + 3) >> 2;
     for (int tt = threadIdx.x; tt < tilesM * tilesN; tt += NT) {
         const int tm = tt / tilesN, tn = tt - tm * tilesN;
-        const int i0 = tm << 2, c0 = tn << 2;
-        const float* a0 = A + min(i0, M - 1) * lda;
-        const float* a1 = A + min(i0 + 1, M - 1) * lda;
-        const float* a2 = A + min(i0 + 2, M - 1) * lda;
-        const float* a3 = A + min(i0 + 3, M - 1) * lda;
-        const float* bp = B + c0;
-        float acc[4][4];
+        const int i0 = tm * TR, c0 = tn << 2;
+        const float* ar[TR];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < TR; ++r) ar[r] = A + min(i0 + r, M - 1) * lda;
+        const float* bp = B + c0;
+        float acc[TR][4];
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
 #pragma unroll 4
         for (int j = 0; j < K; ++j) {
             const float4 b = *reinterpret_cast<const float4*>(bp + j * ldb);
-            const float x[4] = {a0[j], a1[j], a2[j], a3[j]};
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                acc[r][0] = fmaf(x[r], b.x, acc[r][0]);
-                acc[r][1] = fmaf(x[r], b.y, acc[r][1]);
-                acc[r][2] = fmaf(x[r], b.z, acc[r][2]);
-                acc[r][3] = fmaf(x[r], b.w, acc[r][3]);
+            for (int r = 0; r < TR; ++r) {
+                const float x = ar[r][j];
+                acc[r][0] = fmaf(x, b.x, acc[r][0]);
+                acc[r][1] = fmaf(x, b.y, acc[r][1]);
+                acc[r][2] = fmaf(x, b.z, acc[r][2]);
+                acc[r][3] = fmaf(x, b.w, acc[r][3]);
             }
         }
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < TR; ++r) {
             if (i0 + r >= M) break;
 #pragma unroll
             for (int q = 0; q < 4; ++q)
@@ -95,30 +101,36 @@ __device__ __forceinline__ void gemm_shared_a(const float* __restrict__ A, int l
         }
     }
 }
+template <int NT>
+__device__ __forceinline__ void gemm_shared_a(const float* __restrict__ A, int lda, const float* __restrict__ B, int ldb,
+                                              float* __restrict__ C, int ldc, int M, int K, int N) {
+    if (tile4<NT>(M, N)) gemm_shared_a_t<NT, 4>(A, lda, B, ldb, C, ldc, M, K, N);
+    else gemm_shared_a_t<NT, 1>(A, lda, B, ldb, C, ldc, M, K, N);
+}
 
 // Stacked rows of all domains: C[(g*rows + i)*ldc + k] = sum_j A_g[i][j] s_g[j] B[j][k] for g < gcount,
 // A_g = Ab + g*a_gs + i*lda (a_gs = 0: one shared A), s_g = sb + g*s_gs, B [K][N] (ld ldb).  4 x 4 tiles.
-template <int NT>
-__device__ __forceinline__ void gemm_stacked_scaled(const float* __restrict__ Ab, int a_gs, int lda, const float* __restrict__ sb,
-                                                    int s_gs, const float* __restrict__ B, int ldb, float* __restrict__ C,
-                                                    int ldc, int gcount, int rows, int K, int N) {
+template <int NT, int TR>
+__device__ __forceinline__ void gemm_stacked_scaled_t(const float* __restrict__ Ab, int a_gs, int lda, const float* __restrict__ sb,
+                                                      int s_gs, const float* __restrict__ B, int ldb, float* __restrict__ C,
+                                                      int ldc, int gcount, int rows, int K, int N) {
     const int M = gcount * rows;
-    const int tilesM = (M + 3) >> 2, tilesN = (N + 3) >> 2;
+    const int tilesM = (M + TR - 1) / TR, tilesN = (N + 3) >> 2;
     for (int tt = threadIdx.x; tt < tilesM * tilesN; tt += NT) {
         const int tm = tt / tilesN, tn = tt - tm * tilesN;
-        const int i0 = tm << 2, c0 = tn << 2;
-        const float* ap[4];
-        const float* sp[4];
+        const int i0 = tm * TR, c0 = tn << 2;
+        const float* ap[TR];
+        const float* sp[TR];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < TR; ++r) {
             const int R = min(i0 + r, M - 1), g = R / rows, i = R - g * rows;
             ap[r] = Ab + g * a_gs + i * lda;
             sp[r] = sb + g * s_gs;
         }
         const int cc[4] = {min(c0, N - 1), min(c0 + 1, N - 1), min(c0 + 2, N - 1), min(c0 + 3, N - 1)};
-        float acc[4][4];
+        float acc[TR][4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < TR; ++r)
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
 #pragma unroll 2
@@ -126,20 +138,42 @@ __device__ __forceinline__ void gemm_stacked_scaled(const float* __restrict__ Ab
             const float* brow = B + j * ldb;
             const float b[4] = {brow[cc[0]], brow[cc[1]], brow[cc[2]], brow[cc[3]]};
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
+            for (int r = 0; r < TR; ++r) {
                 const float x = ap[r][j] * sp[r][j];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(x, b[q], acc[r][q]);
             }
         }
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < TR; ++r) {
             if (i0 + r >= M) break;
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 if (c0 + q < N) C[(i0 + r) * ldc + c0 + q] = acc[r][q];
         }
     }
+}
+template <int NT>
+__device__ __forceinline__ void gemm_stacked_scaled(const float* __restrict__ Ab, int a_gs, int lda, const float* __restrict__ sb,
+                                                    int s_gs, const float* __restrict__ B, int ldb, float* __restrict__ C,
+                                                    int ldc, int gcount, int rows, int K, int N) {
+    if (tile4<NT>(gcount * rows, N))
+        gemm_stacked_scaled_t<NT, 4>(Ab, a_gs, lda, sb, s_gs, B, ldb, C, ldc, gcount, rows, K, N);
+    else
+        gemm_stacked_scaled_t<NT, 1>(Ab, a_gs, lda, sb, s_gs, B, ldb, C, ldc, gcount, rows, K, N);
+}
+
+// Lanes per (row, domain) in the intercept sums: the columns are split over JS consecutive lanes
+// (a power of two <= 32) when there are fewer rows x domains than threads, then tree-reduced.
+template <int NT>
+__device__ __forceinline__ int intercept_lanes(int items) {
+    int js = 1;
+    while (js < 32 && items * js * 2 <= NT) js <<= 1;
+    return js;
+}
+__device__ __forceinline__ float lanes_sum(float x, int js) {
+    for (int o = js >> 1; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
 }
 
 template <int NT, int G>
@@ -278,7 +312,34 @@ __global__ void __launch_bounds__(NT) k_fused_forward_multi(const MultiArgs a) {
                     }
                 }
                 if (first) __syncthreads();
-                if (first) {
+                if (first && rows * G < NT) {
+                    // intercepts of a short target: (row i, domain g) with the columns split over JS lanes
+                    const int items = rows * G, JS = intercept_lanes<NT>(items);
+                    for (int base = 0; base < items * JS; base += NT) {
+                        const int idx = base + tid;
+                        const bool act = idx < items * JS;
+                        const int it = idx / JS, jp = idx - it * JS;
+                        const int i = act ? it / G : 0, g = act ? it - (it / G) * G : 0;
+                        float sp = 0.f, sn = 0.f, sbv = 0.f;
+                        if (act && g < gcount) {
+                            const float* row = curb + i * cur_ld;
+                            for (int j = jp; j < cur_cols; j += JS) {
+                                const float x = row[j];
+                                const float2 ev = E[j * G + g];
+                                sp = fmaf(posf(x), ev.x, sp);
+                                sn = fmaf(negf(x), ev.x, sn);
+                                sbv = fmaf(x, ev.y, sbv);
+                            }
+                        }
+                        sp = lanes_sum(sp, JS);
+                        sn = lanes_sum(sn, JS);
+                        sbv = lanes_sum(sbv, JS);
+                        if (act && jp == 0 && g < gcount) {
+                            MF(g, Y.khi)[i] += sp + sbv;
+                            MF(g, Y.klo)[i] += sn + sbv;
+                        }
+                    }
+                } else if (first) {
                     // intercepts: thread = (row i, GQ domains); the W_ell row is loaded once for them
                     constexpr int GQ = G < 4 ? G : 4;
                     const int gq = G / GQ;
@@ -307,20 +368,32 @@ __global__ void __launch_bounds__(NT) k_fused_forward_multi(const MultiArgs a) {
                         }
                     }
                 } else {
-                    for (int idx = tid; idx < gcount * rows; idx += NT) {
-                        const int g = idx / rows, i = idx - g * rows;
-                        const float* row = curb + g * cur_gs + i * cur_ld;
-                        const float* sl = MF(g, Y.hs) + N.hoff[mm];
-                        const float* dl = MF(g, Y.hd) + N.hoff[mm];
+                    // (domain g, row i) with the columns split over JS lanes
+                    const int items = gcount * rows, JS = intercept_lanes<NT>(items);
+                    for (int base = 0; base < items * JS; base += NT) {
+                        const int idx = base + tid;
+                        const bool act = idx < items * JS;
+                        const int it = idx / JS, jp = idx - it * JS;
+                        const int g = act ? it / rows : 0, i = act ? it - (it / rows) * rows : 0;
                         float spos = 0.f, sneg = 0.f, sb = 0.f;
-                        for (int j = 0; j < cur_cols; ++j) {
-                            const float x = row[j];
-                            spos = fmaf(posf(x), dl[j], spos);
-                            sneg = fmaf(negf(x), dl[j], sneg);
-                            sb = fmaf(x * sl[j], bm[j], sb);
+                        if (act) {
+                            const float* row = curb + g * cur_gs + i * cur_ld;
+                            const float* sl = MF(g, Y.hs) + N.hoff[mm];
+                            const float* dl = MF(g, Y.hd) + N.hoff[mm];
+                            for (int j = jp; j < cur_cols; j += JS) {
+                                const float x = row[j];
+                                spos = fmaf(posf(x), dl[j], spos);
+                                sneg = fmaf(negf(x), dl[j], sneg);
+                                sb = fmaf(x * sl[j], bm[j], sb);
+                            }
                         }
-                        MF(g, Y.khi)[i] += spos + sb;
-                        MF(g, Y.klo)[i] += sneg + sb;
+                        spos = lanes_sum(spos, JS);
+                        sneg = lanes_sum(sneg, JS);
+                        sb = lanes_sum(sb, JS);
+                        if (act && jp == 0) {
+                            MF(g, Y.khi)[i] += spos + sb;
+                            MF(g, Y.klo)[i] += sneg + sb;
+                        }
                     }
                 }
                 if (shared_a) {
