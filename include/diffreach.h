@@ -160,7 +160,9 @@ int dr_optimize_slopes(dr_ctx* ctx, int steps, double lr_alpha, double lr_beta, 
  *   the tube-volume proxy V, i.e. g_lo = -1 and g_hi = +1 on steps 1..H; one NULL = zeros);
  *   dalpha [D x H x hidden] FP32; dbeta [nnz] FP32.  Step 0 (the input box) carries no gradient.
  * Pointers are host memory unless on_device != 0.  Recomputes the forward pass with a per-step tape
- * (library-owned, D*H*(n^2+4n+2) doubles) and runs the fused reverse sweep. */
+ * (library-owned, D*H*(n^2+4n+2) doubles) and runs the fused reverse sweep, which recomputes each
+ * step's back-substitution levels from the tape.  Controllers whose per-domain working set exceeds
+ * shared memory run the same kernels out of library-owned per-CTA global-memory slabs (up to 2 GiB). */
 int dr_backward(dr_ctx* ctx, const double* dV_dlo, const double* dV_dhi, float* dalpha, float* dbeta,
                 int on_device);
 
