@@ -76,7 +76,9 @@ struct dr_ctx {
     float* dWTh = nullptr;
     float* dWTl = nullptr;
     int64_t WToff[DR_MAXL] = {};
-    float* dW2T = nullptr;  // W_2 transposed [n_1][n_2], FP32 (null for a one-layer controller)
+    // W_2 and [W_2^+; W_2^-] as blocked TF32 parts (left operands of the target-2 GEMMs), rows
+    // padded to 128, K = ru32(n_1); null for a one-layer controller
+    float *dA2h = nullptr, *dA2l = nullptr, *dA2ph = nullptr, *dA2pl = nullptr;
     int* derr = nullptr;
     // per-CTA global slabs for the fused kernels on wide controllers (tape runs)
     unsigned char* gslab = nullptr;
@@ -746,7 +748,10 @@ void dr_destroy(dr_ctx* c) {
     cudaFree(c->dalpha);
     cudaFree(c->dWTh);
     cudaFree(c->dWTl);
-    cudaFree(c->dW2T);
+    cudaFree(c->dA2h);
+    cudaFree(c->dA2l);
+    cudaFree(c->dA2ph);
+    cudaFree(c->dA2pl);
     cudaFree(c->derr);
     if (c->aux) cudaStreamDestroy(c->aux);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -857,15 +862,41 @@ int dr_load_controller(dr_ctx* c, int L, const int32_t* widths, const void* cons
         }
         dev_free(c, (void*&)c->dWTh, 0);
         dev_free(c, (void*&)c->dWTl, 0);
-        dev_free(c, (void*&)c->dW2T, 0);
+        dev_free(c, (void*&)c->dA2h, 0);
+        dev_free(c, (void*&)c->dA2l, 0);
+        dev_free(c, (void*&)c->dA2ph, 0);
+        dev_free(c, (void*&)c->dA2pl, 0);
         TRY(dev_alloc(c, c->dWTh, tot));
         TRY(dev_alloc(c, c->dWTl, tot));
+        std::vector<float> a2h, a2l, a2ph, a2pl;
         if (L >= 2) {
-            std::vector<float> w2t((size_t)widths[1] * widths[2]);
-            for (int ii = 0; ii < widths[2]; ++ii)
-                for (int kk = 0; kk < widths[1]; ++kk) w2t[(size_t)kk * widths[2] + ii] = hw[N.Woff[1] + (int64_t)ii * widths[1] + kk];
-            TRY(dev_alloc(c, c->dW2T, w2t.size()));
-            CUDA_TRY(c, cudaMemcpyAsync(c->dW2T, w2t.data(), w2t.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+            const int K = widths[1], R2 = widths[2], ldk = (K + 31) & ~31, nk = ldk / 32;
+            const size_t m1 = (size_t)((R2 + 127) / 128) * 128, m2 = (size_t)((2 * R2 + 127) / 128) * 128;
+            a2h.assign(m1 * ldk, 0.f);
+            a2l.assign(m1 * ldk, 0.f);
+            a2ph.assign(m2 * ldk, 0.f);
+            a2pl.assign(m2 * ldk, 0.f);
+            for (int ii = 0; ii < R2; ++ii)
+                for (int kk = 0; kk < K; ++kk) {
+                    const float x = hw[N.Woff[1] + (int64_t)ii * K + kk];
+                    const float xp = x > 0.f ? x : 0.f, xn = x < 0.f ? x : 0.f;
+                    const int64_t o = tc::blk_index(ii, kk, nk), op = tc::blk_index(ii, kk, nk),
+                                  on = tc::blk_index(R2 + ii, kk, nk);
+                    a2h[o] = tf32(x);
+                    a2l[o] = tf32(x - a2h[o]);
+                    a2ph[op] = tf32(xp);
+                    a2pl[op] = tf32(xp - a2ph[op]);
+                    a2ph[on] = tf32(xn);
+                    a2pl[on] = tf32(xn - a2ph[on]);
+                }
+            TRY(dev_alloc(c, c->dA2h, a2h.size()));
+            TRY(dev_alloc(c, c->dA2l, a2l.size()));
+            TRY(dev_alloc(c, c->dA2ph, a2ph.size()));
+            TRY(dev_alloc(c, c->dA2pl, a2pl.size()));
+            CUDA_TRY(c, cudaMemcpyAsync(c->dA2h, a2h.data(), a2h.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+            CUDA_TRY(c, cudaMemcpyAsync(c->dA2l, a2l.data(), a2l.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+            CUDA_TRY(c, cudaMemcpyAsync(c->dA2ph, a2ph.data(), a2ph.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+            CUDA_TRY(c, cudaMemcpyAsync(c->dA2pl, a2pl.data(), a2pl.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
         }
         if (!c->derr) TRY(dev_alloc(c, c->derr, 1));
         CUDA_TRY(c, cudaMemcpyAsync(c->dWTh, th.data(), tot * sizeof(float), cudaMemcpyHostToDevice, c->stream));
@@ -1090,6 +1121,10 @@ static size_t wide_bytes_per_domain(const NetDesc& N) {
     b += sizeof(float) * 4 * wide_lam_stride(N);                  // Lambda buffers (two TF32 pairs)
     b += sizeof(float) * 3 * wide_part_per_domain(N);             // intercept partials of fused levels
     b += sizeof(float) * (size_t)N.maxw * wide_lx_parts(N) * n;   // partial Lambda_x rows of a fused final level
+    if (N.L >= 2) {                                                // target-2 GEMM operands and results
+        const size_t ldk1 = (N.w[1] + 31) & ~31;
+        b += sizeof(float) * (2 * (n + 1) * ldk1 + 2 * ldk1 + (size_t)N.w[2] * (n + 1) + 2 * (size_t)N.w[2]);
+    }
     return b + 16 * 24;
 }
 
@@ -1102,8 +1137,12 @@ static int64_t wide_lam_pad(const NetDesc& N) {
     return (int64_t)tc::BM * ldk;
 }
 
+struct T2Scratch {
+    float *Bh, *Bl, *Dh, *Dl, *C1, *C2;
+};
+
 static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, int lanes, int lane, float** lamA, float** lamB, float** lamC,
-                     float** lamD, float** part, float** lxpart) {
+                     float** lamD, float** part, float** lxpart, T2Scratch* t2) {
     const NetDesc& N = a.net;
     const size_t need = (wide_bytes_per_domain(N) * (size_t)Dc + 4 * (sizeof(float) * wide_lam_pad(N) + 256) + 4096 + 255) & ~size_t(255);
     if (!c->wscratch || c->wscratch_bytes < need * lanes || c->wDc != Dc || c->wLanes != lanes) {
@@ -1163,6 +1202,16 @@ static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, int lanes, int lane, float*
     *lamD = (float*)take(sizeof(float) * (D * a.lam_stride + lam_pad));
     *part = (float*)take(sizeof(float) * D * 3 * wide_part_per_domain(N));
     *lxpart = (float*)take(sizeof(float) * D * N.maxw * wide_lx_parts(N) * n);
+    memset(t2, 0, sizeof(*t2));
+    if (N.L >= 2) {
+        const size_t ldk1 = (N.w[1] + 31) & ~31, NB = n + 1;
+        t2->Bh = (float*)take(sizeof(float) * D * NB * ldk1);
+        t2->Bl = (float*)take(sizeof(float) * D * NB * ldk1);
+        t2->Dh = (float*)take(sizeof(float) * D * ldk1);
+        t2->Dl = (float*)take(sizeof(float) * D * ldk1);
+        t2->C1 = (float*)take(sizeof(float) * (size_t)N.w[2] * D * NB);
+        t2->C2 = (float*)take(sizeof(float) * 2 * (size_t)N.w[2] * D);
+    }
     if (off > need) return fail(c, DR_ERR_OOM, "staged scratch layout overflow");
     return DR_OK;
 }
@@ -1188,6 +1237,7 @@ static void launch_t_project(dr_ctx* c, const WideArgs& a, int ell, const float*
 struct WideLane {
     WideArgs a;
     float *lamA, *lamB, *lamC, *lamD, *part, *lxpart;
+    T2Scratch t2;
     cudaStream_t st;
     bool active;
 };
@@ -1235,11 +1285,14 @@ static int wide_step(dr_ctx* c, WideLane& w, int t, bool tcore) {
             // the last level (x W_1, n columns) is folded into the epilogue of the level before
             const int R = dc * rows;
             const bool fuse_final = N.n <= tc::kFinalCols && tc_bn(N.w[1]) >= 32;
-            const size_t chain2_smem = sizeof(float) * (size_t)N.w[1] * (16 + 2);
-            if (ell == 2 && N.n <= 16 && chain2_smem <= 48 * 1024) {
-                // target 2: the whole chain W_2 diag(s_1) W_1 in one SIMT pass
-                dim3 g2((unsigned)dc, (unsigned)((rows + 127) / 128));
-                k_t_chain2<16><<<g2, 128, chain2_smem, st>>>(a, c->dW2T, lamC);
+            if (ell == 2) {
+                // target 2: two GEMMs with the shared W_2 (and its sign parts) as the left operand
+                const int ldk1 = round_up32(N.w[1]), NB = N.n + 1;
+                k_t2_prep<<<blocks_for((int64_t)dc * ldk1, 256), 256, 0, st>>>(a, ldk1, w.t2.Bh, w.t2.Bl, w.t2.Dh, w.t2.Dl);
+                c->launches++;
+                TRY(tc_gemm(c, c->dA2h, c->dA2l, w.t2.Bh, w.t2.Bl, w.t2.C1, rows, N.w[1], dc * NB, ldk1, dc * NB, c->derr, st));
+                TRY(tc_gemm(c, c->dA2ph, c->dA2pl, w.t2.Dh, w.t2.Dl, w.t2.C2, 2 * rows, N.w[1], dc, ldk1, dc, c->derr, st));
+                k_t2_finish<<<blocks_for((int64_t)R, 256), 256, 0, st>>>(a, w.t2.C1, w.t2.C2, lamC);
                 c->launches++;
                 launch_t_project(c, a, ell, lamC, 0, R, 0, st);
             } else {
@@ -1332,7 +1385,8 @@ static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
     WideLane w[2];
     for (int l = 0; l < lanes; ++l) {
         w[l].a = a;
-        TRY(wide_bind(c, w[l].a, Dc, lanes, l, &w[l].lamA, &w[l].lamB, &w[l].lamC, &w[l].lamD, &w[l].part, &w[l].lxpart));
+        TRY(wide_bind(c, w[l].a, Dc, lanes, l, &w[l].lamA, &w[l].lamB, &w[l].lamC, &w[l].lamD, &w[l].part, &w[l].lxpart,
+                      &w[l].t2));
         w[l].st = c->stream;
     }
     const bool tcore = c->opt.precision != DR_PREC_SIMT;

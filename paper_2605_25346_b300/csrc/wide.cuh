@@ -482,60 +482,51 @@ __global__ void k_t_chain_init(const WideArgs a, int ell, float* __restrict__ Ah
     }
 }
 
-// Whole chain of target 2 (n <= NX) in FP32: kappa as k_t_chain_init and Lambda_x = W_2 diag(s_1) W_1.
-// Block (domain d, 128 rows of W_2), one thread per row i.  The domain's right factor
-// B[k][:] = s_1[k] W_1[k][:], d_1 and s_1*b_1 are staged in shared memory (broadcast reads), and
-// W2T = W_2 transposed [n_1][n_2] gives coalesced row loads.  Rows Lx [Dc*n_2][n].
-template <int NX>
-__global__ void __launch_bounds__(128) k_t_chain2(const WideArgs a, const float* __restrict__ W2T, float* __restrict__ Lx) {
-    extern __shared__ __align__(16) float sm2[];
+// Target 2 on the tensor cores.  Its chain is one level, Lambda_x = W_2 diag(s_1) W_1, with the
+// intercepts W_2^+ d_1, W_2^- d_1 and W_2 (s_1 b_1): all are products of the shared W_2 (or its
+// positive and negative parts) with per-domain columns.  k_t2_prep writes those columns as TF32 parts,
+// B^T [(d*NB + c)][ldk] with NB = n + 1 (c < n: s_1 W_1[:, c]; c = n: s_1 b_1) and D^T [d][ldk] (d_1);
+// two GEMMs give C1 = W_2 B [n_2][Dc*NB] and C2 = [W_2^+; W_2^-] D [2 n_2][Dc]; k_t2_finish
+// scatters them into Lambda_x rows and kappa.
+__global__ void k_t2_prep(const WideArgs a, int ldk, float* __restrict__ Bh, float* __restrict__ Bl, float* __restrict__ Dh,
+                          float* __restrict__ Dl) {
     const NetDesc& N = a.net;
-    const int rows = N.w[2], n = N.n, K = N.w[1];
-    const int d = blockIdx.x;
-    float* Bk = sm2;                  // [K][NX]
-    float* dk = Bk + (size_t)K * NX;  // [K]
-    float* sbk = dk + K;              // [K]
-    const float* s = a.hs + (int64_t)d * N.hidden + N.hoff[1];
-    const float* dd = a.hd + (int64_t)d * N.hidden + N.hoff[1];
-    const float* bm = a.b + N.boff[0];
+    const int n = N.n, K = N.w[1], NB = n + 1;
     const float* W1 = a.W + N.Woff[0];
-    for (int idx = threadIdx.x; idx < K * NX; idx += blockDim.x) {
-        const int k = idx / NX, c = idx - k * NX;
-        Bk[idx] = c < n ? s[k] * W1[(int64_t)k * n + c] : 0.f;
-    }
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        dk[k] = dd[k];
-        sbk[k] = s[k] * bm[k];
-    }
-    __syncthreads();
-    const int i = blockIdx.y * blockDim.x + threadIdx.x;
-    if (i >= rows) return;
-    float spos = 0.f, sneg = 0.f, sb = 0.f;
-    float px[NX];
-#pragma unroll
-    for (int c = 0; c < NX; ++c) px[c] = 0.f;
-    for (int k = 0; k < K; ++k) {
-        const float w = W2T[(int64_t)k * rows + i];
-        spos = fmaf(posf(w), dk[k], spos);
-        sneg = fmaf(negf(w), dk[k], sneg);
-        sb = fmaf(w, sbk[k], sb);
-        const float4* b4 = reinterpret_cast<const float4*>(Bk + (size_t)k * NX);
-#pragma unroll
-        for (int q = 0; q < NX / 4; ++q) {
-            const float4 bv = b4[q];
-            px[4 * q] = fmaf(w, bv.x, px[4 * q]);
-            px[4 * q + 1] = fmaf(w, bv.y, px[4 * q + 1]);
-            px[4 * q + 2] = fmaf(w, bv.z, px[4 * q + 2]);
-            px[4 * q + 3] = fmaf(w, bv.w, px[4 * q + 3]);
+    const float* b1 = a.b + N.boff[0];
+    const int64_t total = (int64_t)a.Dc * ldk;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int d = (int)(idx / ldk), k = (int)(idx - (int64_t)d * ldk);
+        const bool in = k < K;
+        const float sk = in ? a.hs[(int64_t)d * N.hidden + N.hoff[1] + k] : 0.f;
+        for (int c = 0; c <= n; ++c) {
+            const float x = !in ? 0.f : (c < n ? sk * W1[(int64_t)k * n + c] : sk * b1[k]);
+            const float h = tf32_part(x);
+            const int64_t o = ((int64_t)d * NB + c) * ldk + k;
+            Bh[o] = h;
+            Bl[o] = tf32_part(x - h);
         }
+        const float dk = in ? a.hd[(int64_t)d * N.hidden + N.hoff[1] + k] : 0.f;
+        const float h = tf32_part(dk);
+        Dh[idx] = h;
+        Dl[idx] = tf32_part(dk - h);
     }
-    const int64_t r = (int64_t)d * rows + i;
-#pragma unroll
-    for (int c = 0; c < NX; ++c)
-        if (c < n) Lx[r * n + c] = px[c];
-    const float bi = a.b[N.boff[1] + i];
-    a.khi[(int64_t)d * N.maxw + i] = bi + spos + sb;
-    a.klo[(int64_t)d * N.maxw + i] = bi + sneg + sb;
+}
+
+__global__ void k_t2_finish(const WideArgs a, const float* __restrict__ C1, const float* __restrict__ C2,
+                            float* __restrict__ Lx) {
+    const NetDesc& N = a.net;
+    const int n = N.n, rows = N.w[2], NB = n + 1;
+    const int64_t ld1 = (int64_t)a.Dc * NB, ld2 = a.Dc;
+    const int64_t total = (int64_t)a.Dc * rows;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < total; r += (int64_t)gridDim.x * blockDim.x) {
+        const int d = (int)(r / rows), i = (int)(r - (int64_t)d * rows);
+        const float* c1 = C1 + i * ld1 + (int64_t)d * NB;
+        for (int c = 0; c < n; ++c) Lx[r * n + c] = c1[c];
+        const float bi = a.b[N.boff[1] + i], sb = c1[n];
+        a.khi[(int64_t)d * N.maxw + i] = bi + C2[i * ld2 + d] + sb;
+        a.klo[(int64_t)d * N.maxw + i] = bi + C2[(rows + i) * ld2 + d] + sb;
+    }
 }
 
 // Adds the per-column-tile intercept partials of a fused chain level into kappa (fixed order).
