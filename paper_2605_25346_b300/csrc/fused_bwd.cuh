@@ -12,6 +12,19 @@
 #pragma once
 #include "fused_core.cuh"
 
+// Sums over a target's rows for few outputs (TM adjoints, dual adjoints): each output gets JS
+// consecutive lanes (a power of two <= 32) that stride over the rows, then a shuffle tree.
+template <int NT>
+__device__ __forceinline__ int row_lanes(int items) {
+    int js = 1;
+    while (js < 32 && items * js * 2 <= NT) js <<= 1;
+    return js;
+}
+__device__ __forceinline__ double lanes_sumd(double x, int js) {
+    for (int o = js >> 1; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT) k_fused_backward(const FusedArgs a) {
     extern __shared__ __align__(16) unsigned char sm_dyn[];
@@ -255,39 +268,66 @@ __global__ void __launch_bounds__(NT) k_fused_backward(const FusedArgs a) {
                         gG[i * gld + k] += -g_l * sgnf(x - vb[k]) + g_u * sgnf(x + vb[k]);
                     }
                 }
-                for (int k = tid; k < n; k += NT) {
-                    double acc = 0.0;
-                    for (int i = 0; i < rows; ++i) {
-                        const float x = s.G[i * gld + k];
-                        acc += (double)(gl[ho + i] * sgnf(x - vb[k]) + gu[ho + i] * sgnf(x + vb[k]));
+                {
+                    // adjoint of the dual (v: n entries, w: entry n), rows split over JS lanes
+                    const int items = n + 1, JS = row_lanes<NT>(items);
+                    for (int base = 0; base < items * JS; base += NT) {
+                        const int idx = base + tid;
+                        const bool act = idx < items * JS;
+                        const int k = idx / JS, jp = idx - k * JS;
+                        double acc = 0.0;
+                        if (act && k < n) {
+                            for (int i = jp; i < rows; i += JS) {
+                                const float x = s.G[i * gld + k];
+                                acc += (double)(gl[ho + i] * sgnf(x - vb[k]) + gu[ho + i] * sgnf(x + vb[k]));
+                            }
+                        } else if (act) {
+                            for (int i = jp; i < rows; i += JS) acc += (double)(gu[ho + i] - gl[ho + i]);
+                        }
+                        acc = lanes_sumd(acc, JS);
+                        if (act && jp == 0) {
+                            if (k < n) gv[k] += acc;
+                            else gw[0] += acc;
+                        }
                     }
-                    gv[k] += acc;
-                }
-                if (tid == 0) {
-                    double acc = 0.0;
-                    for (int i = 0; i < rows; ++i) acc += (double)(gu[ho + i] - gl[ho + i]);
-                    gw[0] += acc;
                 }
                 __syncthreads();
             }
             // ---- input projection reverse: TM adjoints and Lambda_x adjoint
-            for (int idx = tid; idx < n * n; idx += NT) {
-                const int j = idx / n, k = idx - j * n;
-                double acc = 0.0;
-                for (int i = 0; i < rows; ++i) acc += (double)(cur[i * ld + j] * gG[i * gld + k]);
-                gP[idx] += acc;
-            }
-            for (int j = tid; j < n; j += NT) {
-                double c_ = 0.0, lo_ = 0.0, hi_ = 0.0;
-                for (int i = 0; i < rows; ++i) {
-                    const float x = cur[i * ld + j];
-                    c_ += (double)(x * ga[i]);
-                    lo_ += (double)(gRlo[i] * posf(x) + gRhi[i] * negf(x));
-                    hi_ += (double)(gRlo[i] * negf(x) + gRhi[i] * posf(x));
+            {
+                // gP[j][k] += sum_i Lx[i][j] gG[i][k]; gc, gIlo, gIhi likewise; rows split over JS lanes
+                const int items = n * n + n, JS = row_lanes<NT>(items);
+                for (int base = 0; base < items * JS; base += NT) {
+                    const int idx = base + tid;
+                    const bool act = idx < items * JS;
+                    const int it = idx / JS, jp = idx - it * JS;
+                    double acc = 0.0, lo_ = 0.0, hi_ = 0.0;
+                    if (act && it < n * n) {
+                        const int j = it / n, k = it - j * n;
+                        for (int i = jp; i < rows; i += JS) acc += (double)(cur[i * ld + j] * gG[i * gld + k]);
+                    } else if (act) {
+                        const int j = it - n * n;
+                        for (int i = jp; i < rows; i += JS) {
+                            const float x = cur[i * ld + j];
+                            acc += (double)(x * ga[i]);
+                            lo_ += (double)(gRlo[i] * posf(x) + gRhi[i] * negf(x));
+                            hi_ += (double)(gRlo[i] * negf(x) + gRhi[i] * posf(x));
+                        }
+                    }
+                    acc = lanes_sumd(acc, JS);
+                    lo_ = lanes_sumd(lo_, JS);
+                    hi_ = lanes_sumd(hi_, JS);
+                    if (act && jp == 0) {
+                        if (it < n * n) {
+                            gP[it] += acc;
+                        } else {
+                            const int j = it - n * n;
+                            gc[j] += acc;
+                            gIlo[j] += lo_;
+                            gIhi[j] += hi_;
+                        }
+                    }
                 }
-                gc[j] += c_;
-                gIlo[j] += lo_;
-                gIhi[j] += hi_;
             }
             float* gLprev = SMF(Y.gL0);  // adjoint of Lambda^(0) = Lambda_x
             const int xld = odd_ld(n);

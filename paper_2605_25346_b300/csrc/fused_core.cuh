@@ -208,17 +208,33 @@ __device__ const float* chain(const Dom& s, const NetDesc& N, int ell, float* le
         const float* sl = s.hs + N.hoff[mm];
         const float* dl = s.hd + N.hoff[mm];
         const float* bm = s.bs + N.boff[mm - 1];
-        for (int i = tid; i < rows; i += NT) {
+        // intercept sums: a short target (fewer rows than threads) splits each row's columns over JS
+        // consecutive lanes (a power of two <= 32) and reduces them with shuffles
+        int JS = 1;
+        while (JS < 32 && rows * JS * 2 <= NT) JS <<= 1;
+        for (int base = 0; base < rows * JS; base += NT) {
+            const int idx = base + tid;
+            const bool act = idx < rows * JS;
+            const int i = idx / JS, jp = idx - i * JS;
             float spos = 0.f, sneg = 0.f, sb = 0.f;
-            const float* row = cur + i * cur_ld;
-            for (int j = 0; j < cur_cols; ++j) {
-                const float x = row[j];
-                spos = fmaf(posf(x), dl[j], spos);
-                sneg = fmaf(negf(x), dl[j], sneg);
-                sb = fmaf(x * sl[j], bm[j], sb);
+            if (act) {
+                const float* row = cur + i * cur_ld;
+                for (int j = jp; j < cur_cols; j += JS) {
+                    const float x = row[j];
+                    spos = fmaf(posf(x), dl[j], spos);
+                    sneg = fmaf(negf(x), dl[j], sneg);
+                    sb = fmaf(x * sl[j], bm[j], sb);
+                }
             }
-            s.khi[i] += spos + sb;
-            s.klo[i] += sneg + sb;
+            for (int o = JS >> 1; o > 0; o >>= 1) {
+                spos += __shfl_xor_sync(0xffffffffu, spos, o);
+                sneg += __shfl_xor_sync(0xffffffffu, sneg, o);
+                sb += __shfl_xor_sync(0xffffffffu, sb, o);
+            }
+            if (act && jp == 0) {
+                s.khi[i] += spos + sb;
+                s.klo[i] += sneg + sb;
+            }
         }
         const int K = N.w[mm], NN = N.w[mm - 1];
         const float* Wm = s.W(mm - 1);
