@@ -98,12 +98,14 @@ def measure_refinement(local):
 def measure_wide_refinement(local):
     """Slope (and split multiplier) refinement on samples of the two wide workloads, whose fused
     forward/reverse kernels keep their working set in per-CTA global slabs."""
+    import dataclasses
     from paper_2605_25346_b300 import api
     out = {}
     for name, prob, steps, lrb in (
             ("branch12 12-256x3-4, 256 of 65536 branch domains, H=30, alpha+beta", wl.quadrotor_branch(only=np.arange(256)),
              2, 0.005),
-            ("large16 16-512x4-8, 8 of 262144 sub-boxes, H=50, alpha", wl.large16().subset(np.arange(8)), 2, 0.0)):
+            ("large16 16-512x4-8, 148 of 262144 sub-boxes, H=10 (one domain per SM), alpha",
+             dataclasses.replace(wl.large16().subset(np.arange(148)), H=10), 2, 0.0)):
         r = api.Reach(local).load(prob)
         r.optimize(1, 0.1, lrb)  # warm-up: slabs, tape and gradient buffers
         r.close()

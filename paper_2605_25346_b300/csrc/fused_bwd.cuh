@@ -26,7 +26,8 @@ __device__ __forceinline__ double lanes_sumd(double x, int js) {
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT) k_fused_backward(const FusedArgs a) {
+// Two CTAs per SM: narrow controllers fit twice in shared memory, and the register cap keeps that occupancy.
+__global__ void __launch_bounds__(NT, 2) k_fused_backward(const FusedArgs a) {
     extern __shared__ __align__(16) unsigned char sm_dyn[];
     unsigned char* sm = a.gslab ? a.gslab + (int64_t)blockIdx.x * a.slab_stride : sm_dyn;
     const NetDesc& N = a.net;

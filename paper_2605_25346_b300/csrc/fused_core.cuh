@@ -9,6 +9,7 @@
 //   EvalInt.
 #pragma once
 #include "common.cuh"
+#include "tiles.cuh"
 
 struct FusedLayout {  // byte offsets into dynamic shared memory
     int Ws[DR_MAXL];
@@ -241,13 +242,14 @@ __device__ const float* chain(const Dom& s, const NetDesc& N, int ell, float* le
         const int wld = odd_ld(NN);
         float* nxt = lev ? (lev + lev_offset(N, ell, mm - 1)) : reinterpret_cast<float*>(s.sm + (buf ? s.Y->lam1 : s.Y->lam0));
         const int nld = odd_ld(NN);
-        for (int idx = tid; idx < rows * NN; idx += NT) {
-            const int i = idx / NN, k = idx - i * NN;
-            const float* row = cur + i * cur_ld;
-            float acc = 0.f;
-            for (int j = 0; j < K; ++j) acc = fmaf(row[j] * sl[j], Wm[j * wld + k], acc);
-            nxt[i * nld + k] = acc;
-        }
+        // nxt[i][k] = sum_j (row_i[j] s_j) W_m[j][k]: register tiles when they still give every
+        // thread of the CTA work (wide levels), one element per thread otherwise
+        if (((rows + 3) >> 2) * ((NN + 3) >> 2) >= NT)
+            gemm_stacked_scaled_t<NT, 4>(cur, 0, cur_ld, sl, 0, Wm, wld, nxt, nld, 1, rows, K, NN);
+        else if (rows * ((NN + 3) >> 2) >= NT)
+            gemm_stacked_scaled_t<NT, 1>(cur, 0, cur_ld, sl, 0, Wm, wld, nxt, nld, 1, rows, K, NN);
+        else
+            gemm_stacked_scaled_1<NT>(cur, 0, cur_ld, sl, 0, Wm, wld, nxt, nld, 1, rows, K, NN);
         __syncthreads();
         cur = nxt;
         cur_ld = nld;
@@ -471,7 +473,7 @@ __device__ void controller_pass(const Dom& s, const NetDesc& N, const FusedArgs&
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT) k_fused_forward(const FusedArgs a) {
+__global__ void __launch_bounds__(NT, 2) k_fused_forward(const FusedArgs a) {
     extern __shared__ __align__(16) unsigned char sm_dyn[];
     unsigned char* sm = a.gslab ? a.gslab + (int64_t)blockIdx.x * a.slab_stride : sm_dyn;
     const NetDesc& N = a.net;
