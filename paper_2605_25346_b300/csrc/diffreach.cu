@@ -80,9 +80,11 @@ struct dr_ctx {
     // padded to 128, K = ru32(n_1); null for a one-layer controller
     float *dA2h = nullptr, *dA2l = nullptr, *dA2ph = nullptr, *dA2pl = nullptr;
     int* derr = nullptr;
-    // per-CTA global slabs for the fused kernels on wide controllers (tape runs)
+    // per-CTA global slabs for the fused kernels on wide controllers (tape runs), and the one padded
+    // weight copy they share
     unsigned char* gslab = nullptr;
     size_t gslab_bytes = 0;
+    float* dWpad = nullptr;
     // staged (wide) path chunk scratch
     void* wscratch = nullptr;
     size_t wscratch_bytes = 0;
@@ -724,6 +726,7 @@ static void free_outputs(dr_ctx* c) {
     c->wscratch_bytes = 0;
     dev_free(c, (void*&)c->gslab, c->gslab_bytes);
     c->gslab_bytes = 0;
+    dev_free(c, (void*&)c->dWpad, 0);
     c->wDc = 0;
     c->out_bytes = 0;
     c->tape_bytes = 0;
@@ -825,6 +828,7 @@ int dr_load_controller(dr_ctx* c, int L, const int32_t* widths, const void* cons
     CUDA_TRY(c, cudaSetDevice(c->device));
     dev_free(c, (void*&)c->dW, 0);
     dev_free(c, (void*&)c->db, 0);
+    dev_free(c, (void*&)c->dWpad, 0);
     TRY(dev_alloc(c, c->dW, nw));
     TRY(dev_alloc(c, c->db, nb));
     CUDA_TRY(c, cudaMemcpyAsync(c->dW, hw.data(), nw * sizeof(float), cudaMemcpyHostToDevice, c->stream));
@@ -1429,6 +1433,16 @@ static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
     return DR_OK;
 }
 
+// The shared padded weights of slab mode (same offsets as the shared-memory layout's weight region).
+static int ensure_wpad(dr_ctx* c, const NetDesc& N, const FusedLayout& Y) {
+    if (c->dWpad) return DR_OK;
+    TRY(dev_alloc(c, c->dWpad, (size_t)(Y.bs - Y.Ws[0]) / sizeof(float)));
+    k_pad_weights<<<296, 256, 0, c->stream>>>(N, Y, c->dW, c->dWpad);
+    CUDA_TRY(c, cudaGetLastError());
+    c->launches++;
+    return DR_OK;
+}
+
 // Domains per launch and the slab buffer for running the fused kernels out of global memory.
 static int slab_chunk(dr_ctx* c, size_t per_cta, int64_t* chunk) {
     const size_t budget = size_t(2) << 30;
@@ -1524,7 +1538,9 @@ static int run_forward(dr_ctx* c, int mode, float* alpha_used, bool tape) {
     if (slab) {
         a.slab_stride = ((int64_t)a.lay.total + 255) & ~int64_t(255);
         TRY(slab_chunk(c, (size_t)a.slab_stride, &chunk));
+        TRY(ensure_wpad(c, N, a.lay));
         a.gslab = c->gslab;
+        a.gwpad = c->dWpad;
         smem = 0;
     }
     for (int64_t d0 = 0; d0 < c->D; d0 += chunk) {
@@ -1677,7 +1693,9 @@ static int launch_backward(dr_ctx* c, int mode, const double* wlo, const double*
     if (slab) {
         a.slab_stride = ((int64_t)a.lay.total + 255) & ~int64_t(255);
         TRY(slab_chunk(c, (size_t)a.slab_stride, &chunk));
+        TRY(ensure_wpad(c, N, a.lay));
         a.gslab = c->gslab;
+        a.gwpad = c->dWpad;
         smem = 0;
     }
     for (int64_t d0 = 0; d0 < c->D; d0 += chunk) {

@@ -32,7 +32,8 @@ __global__ void __launch_bounds__(NT, 2) k_fused_backward(const FusedArgs a) {
     unsigned char* sm = a.gslab ? a.gslab + (int64_t)blockIdx.x * a.slab_stride : sm_dyn;
     const NetDesc& N = a.net;
     const FusedLayout& Y = a.lay;
-    const Dom s = make_dom(sm, Y);
+    Dom s = make_dom(sm, Y);
+    s.gw = a.gwpad;
     const int tid = threadIdx.x;
     const int64_t dom = a.d0 + blockIdx.x;
     const int n = N.n, m = N.m, L = N.L, H = N.H, gld = odd_ld(n);
@@ -358,6 +359,62 @@ __global__ void __launch_bounds__(NT, 2) k_fused_backward(const FusedArgs a) {
                 const float* bm = s.bs + N.boff[mm - 1];
                 float* gLnext = SMF(buf ? Y.gL1 : Y.gL0);
                 // column j of Lambda_s adjoint: sum_k gLprev[i][k] W_m[j][k] + (gklo_i + gkhi_i) b_m[j]
+                const int ncg = (K + 3) >> 2;
+                if (ncg * 2 >= NT && rows >= 4) {
+                    // wide level: a thread owns 4 columns and walks the rows in blocks of 4 (4 x 4
+                    // register tile per block); per element the same operation order as below
+                    for (int cg = tid; cg < ncg; cg += NT) {
+                        const int j0 = cg << 2;
+                        int jj[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) jj[q] = min(j0 + q, K - 1);
+                        float acc_s[4] = {0.f, 0.f, 0.f, 0.f}, acc_d[4] = {0.f, 0.f, 0.f, 0.f};
+                        for (int i0 = 0; i0 < rows; i0 += 4) {
+                            int ii[4];
+                            float g[4][4];
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) {
+                                ii[r] = min(i0 + r, rows - 1);
+                                const float gk = gklo[ii[r]] + gkhi[ii[r]];
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) g[r][q] = gk * bm[jj[q]];
+                            }
+                            for (int k = 0; k < NN; ++k) {
+                                float pv[4], wv[4];
+#pragma unroll
+                                for (int r = 0; r < 4; ++r) pv[r] = gLprev[ii[r] * prev_ld + k];
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) wv[q] = Wm[jj[q] * wld + k];
+#pragma unroll
+                                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                                    for (int q = 0; q < 4; ++q) g[r][q] = fmaf(pv[r], wv[q], g[r][q]);
+                            }
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) {
+                                if (i0 + r >= rows) break;
+                                const int i = i0 + r;
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) {
+                                    const int j = j0 + q;
+                                    if (j >= K) break;
+                                    const float x = Lm[i * lmld + j];
+                                    acc_s[q] = fmaf(g[r][q], x, acc_s[q]);
+                                    acc_d[q] += gkhi[i] * posf(x) + gklo[i] * negf(x);
+                                    if (mm < ell - 1)
+                                        gLnext[i * lmld + j] = g[r][q] * sl[j] + gkhi[i] * (x > 0.f ? dl[j] : 0.f) +
+                                                               gklo[i] * (x < 0.f ? dl[j] : 0.f);
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            if (j0 + q >= K) break;
+                            gs[N.hoff[mm] + j0 + q] += acc_s[q];
+                            gd[N.hoff[mm] + j0 + q] += acc_d[q];
+                        }
+                    }
+                } else
                 for (int j = tid; j < K; j += NT) {
                     float acc_s = 0.f, acc_d = 0.f;
                     for (int i = 0; i < rows; ++i) {

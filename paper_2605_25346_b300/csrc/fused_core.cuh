@@ -68,6 +68,7 @@ struct FusedArgs {
     // dynamic shared memory (slab of CTA b at gslab + b * slab_stride)
     unsigned char* gslab;
     int64_t slab_stride;
+    const float* gwpad;  // slab mode: one padded weight copy shared by all CTAs (offsets Ws[l] - Ws[0])
     // reverse kernel
     const double* wlo;  // [D][H+1][n] upstream gradient of lo (null: -1 on steps 1..H)
     const double* whi;  // [D][H+1][n] upstream gradient of hi (null: +1 on steps 1..H)
@@ -83,17 +84,21 @@ struct FusedArgs {
 struct Dom {
     unsigned char* sm;
     const FusedLayout* Y;
+    const float* gw;  // shared padded weights in global memory (slab mode), else null
     double *c, *P, *Ilo, *Ihi, *v, *wv, *cn, *Pn, *Ilon, *Ihin, *A, *B, *e;
     float *cf, *Pf, *Ilof, *Ihif, *vf, *hl, *hu, *hs, *hd, *hl0, *hu0, *klo, *khi, *G, *sa, *sRlo, *sRhi, *sS, *cu,
         *Iulo, *Iuhi, *bs;
     int* misc;
-    __device__ float* W(int l) const { return reinterpret_cast<float*>(sm + Y->Ws[l]); }
+    __device__ float* W(int l) const {
+        return gw ? const_cast<float*>(gw) + (Y->Ws[l] - Y->Ws[0]) / 4 : reinterpret_cast<float*>(sm + Y->Ws[l]);
+    }
 };
 
 __device__ __forceinline__ Dom make_dom(unsigned char* sm, const FusedLayout& Y) {
     Dom s;
     s.sm = sm;
     s.Y = &Y;
+    s.gw = nullptr;
     s.c = SMD(Y.c);
     s.P = SMD(Y.P);
     s.Ilo = SMD(Y.Ilo);
@@ -137,7 +142,7 @@ template <int NT>
 __device__ void load_params(const Dom& s, const FusedArgs& a) {
     const NetDesc& N = a.net;
     const int tid = threadIdx.x, n = N.n, m = N.m;
-    for (int l = 0; l < N.L; ++l) {
+    for (int l = 0; l < N.L && !s.gw; ++l) {
         const int rows = N.w[l + 1], cols = N.w[l], ld = odd_ld(cols);
         float* dst = s.W(l);
         const float* src = a.W + N.Woff[l];
@@ -452,6 +457,19 @@ __device__ double eval_box(const Dom& s, const NetDesc& N, const FusedArgs& a, i
     return vsum;
 }
 
+// Slab mode: the padded weight layout of the shared-memory region Ws, written once for all CTAs.
+__global__ void k_pad_weights(const NetDesc N, FusedLayout Y, const float* __restrict__ W, float* __restrict__ out) {
+    for (int l = 0; l < N.L; ++l) {
+        const int rows = N.w[l + 1], cols = N.w[l], ld = odd_ld(cols);
+        float* dst = out + (Y.Ws[l] - Y.Ws[0]) / 4;
+        for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)rows * ld;
+             idx += (int64_t)gridDim.x * blockDim.x) {
+            const int r = (int)(idx / ld), q = (int)(idx - (int64_t)r * ld);
+            dst[idx] = q < cols ? W[N.Woff[l] + (int64_t)r * cols + q] : 0.f;
+        }
+    }
+}
+
 // One controller pass of step t (all targets) on the current FP32 view.  With `vsnap`
 // non-null the dual vector seen by each hidden layer's concretisation is kept.
 template <int NT>
@@ -477,7 +495,8 @@ __global__ void __launch_bounds__(NT, 2) k_fused_forward(const FusedArgs a) {
     extern __shared__ __align__(16) unsigned char sm_dyn[];
     unsigned char* sm = a.gslab ? a.gslab + (int64_t)blockIdx.x * a.slab_stride : sm_dyn;
     const NetDesc& N = a.net;
-    const Dom s = make_dom(sm, a.lay);
+    Dom s = make_dom(sm, a.lay);
+    s.gw = a.gwpad;
     const int tid = threadIdx.x;
     const int64_t dom = a.d0 + blockIdx.x;
     const int n = N.n, H = N.H;
