@@ -459,19 +459,46 @@ __global__ void k_t_chain_init(const WideArgs a, int ell, float* __restrict__ Ah
     const float* bm = a.b + N.boff[ell - 2];
     const int nk = ldk >> 5;
     float spos = 0.f, sneg = 0.f, sb = 0.f;
-    for (int j = lane; j < ldk; j += 32) {
-        float xs = 0.f;
-        if (j < K) {
-            const float x = Wrow[j];
-            spos = fmaf(posf(x), dd[j], spos);
-            sneg = fmaf(negf(x), dd[j], sneg);
-            xs = x * s[j];
-            sb = fmaf(xs, bm[j], sb);
+    const bool vec = K == ldk && ((reinterpret_cast<uintptr_t>(Wrow) | reinterpret_cast<uintptr_t>(s) |
+                                   reinterpret_cast<uintptr_t>(dd) | reinterpret_cast<uintptr_t>(bm)) & 15) == 0;
+    if (vec) {
+        // four consecutive columns per lane (16-byte loads and stores; K is a multiple of 32)
+        for (int j = 4 * lane; j < K; j += 128) {
+            const float4 x = *reinterpret_cast<const float4*>(Wrow + j);
+            const float4 dv = *reinterpret_cast<const float4*>(dd + j);
+            const float4 sv = *reinterpret_cast<const float4*>(s + j);
+            const float4 bv = *reinterpret_cast<const float4*>(bm + j);
+            const float xa[4] = {x.x, x.y, x.z, x.w}, da[4] = {dv.x, dv.y, dv.z, dv.w};
+            const float sa[4] = {sv.x, sv.y, sv.z, sv.w}, ba[4] = {bv.x, bv.y, bv.z, bv.w};
+            float h[4], l[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                spos = fmaf(posf(xa[q]), da[q], spos);
+                sneg = fmaf(negf(xa[q]), da[q], sneg);
+                const float xs = xa[q] * sa[q];
+                sb = fmaf(xs, ba[q], sb);
+                h[q] = tf32_part(xs);
+                l[q] = tf32_part(xs - h[q]);
+            }
+            const int64_t o = tc::blk_index(wid, j, nk);
+            *reinterpret_cast<float4*>(Ah + o) = make_float4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<float4*>(Al + o) = make_float4(l[0], l[1], l[2], l[3]);
         }
-        const float h = tf32_part(xs);
-        const int64_t o = tc::blk_index(wid, j, nk);
-        Ah[o] = h;
-        Al[o] = tf32_part(xs - h);
+    } else {
+        for (int j = lane; j < ldk; j += 32) {
+            float xs = 0.f;
+            if (j < K) {
+                const float x = Wrow[j];
+                spos = fmaf(posf(x), dd[j], spos);
+                sneg = fmaf(negf(x), dd[j], sneg);
+                xs = x * s[j];
+                sb = fmaf(xs, bm[j], sb);
+            }
+            const float h = tf32_part(xs);
+            const int64_t o = tc::blk_index(wid, j, nk);
+            Ah[o] = h;
+            Al[o] = tf32_part(xs - h);
+        }
     }
     spos = warp_sum(spos);
     sneg = warp_sum(sneg);
