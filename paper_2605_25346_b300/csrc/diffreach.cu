@@ -90,9 +90,10 @@ struct dr_ctx {
     size_t wscratch_bytes = 0;
     int wDc = 0;
     int wLanes = 0;
-    // second stream (and fork/join events) for the staged path's independent domain lanes
-    cudaStream_t aux = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // extra streams (and fork/join events) for the staged path's independent domain lanes
+    static constexpr int kMaxLanes = 4;
+    cudaStream_t aux[kMaxLanes] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kMaxLanes] = {};
 };
 
 static thread_local std::string g_create_err;
@@ -756,9 +757,11 @@ void dr_destroy(dr_ctx* c) {
     cudaFree(c->dA2ph);
     cudaFree(c->dA2pl);
     cudaFree(c->derr);
-    if (c->aux) cudaStreamDestroy(c->aux);
+    for (int l = 0; l < dr_ctx::kMaxLanes; ++l) {
+        if (c->aux[l]) cudaStreamDestroy(c->aux[l]);
+        if (c->ev_join[l]) cudaEventDestroy(c->ev_join[l]);
+    }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
 }
 
@@ -1386,7 +1389,7 @@ static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
     // memory-bound kernels overlap the other lane's tensor-core GEMMs.
     const int lanes = c->D >= 256 ? 2 : 1;
     const int Dc = (int)std::min<int64_t>(wide_chunk(c, N, lanes), (c->D + lanes - 1) / lanes);
-    WideLane w[2];
+    WideLane w[dr_ctx::kMaxLanes];
     for (int l = 0; l < lanes; ++l) {
         w[l].a = a;
         TRY(wide_bind(c, w[l].a, Dc, lanes, l, &w[l].lamA, &w[l].lamB, &w[l].lamC, &w[l].lamD, &w[l].part, &w[l].lxpart,
@@ -1395,13 +1398,15 @@ static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
     }
     const bool tcore = c->opt.precision != DR_PREC_SIMT;
     if (tcore) CUDA_TRY(c, cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream));
-    if (lanes == 2) {
-        if (!c->aux) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+    if (lanes > 1) {
         if (!c->ev_fork) CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
-        if (!c->ev_join) CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
         CUDA_TRY(c, cudaEventRecord(c->ev_fork, c->stream));
-        CUDA_TRY(c, cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
-        w[1].st = c->aux;
+        for (int l = 1; l < lanes; ++l) {
+            if (!c->aux[l]) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->aux[l], cudaStreamNonBlocking));
+            if (!c->ev_join[l]) CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_join[l], cudaEventDisableTiming));
+            CUDA_TRY(c, cudaStreamWaitEvent(c->aux[l], c->ev_fork, 0));
+            w[l].st = c->aux[l];
+        }
     }
     int rc = DR_OK;
     for (int64_t d0 = 0; d0 < c->D && rc == DR_OK; d0 += (int64_t)lanes * Dc) {
@@ -1418,10 +1423,10 @@ static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
             for (int l = 0; l < lanes && rc == DR_OK; ++l)
                 if (w[l].active) rc = wide_step(c, w[l], t, tcore);
     }
-    if (lanes == 2) {
-        // join the second lane back into the context's stream (also on the error path)
-        cudaEventRecord(c->ev_join, c->aux);
-        cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    for (int l = 1; l < lanes; ++l) {
+        // join the other lanes back into the context's stream (also on the error path)
+        cudaEventRecord(c->ev_join[l], c->aux[l]);
+        cudaStreamWaitEvent(c->stream, c->ev_join[l], 0);
     }
     if (rc != DR_OK) return rc;
     if (tcore) {
