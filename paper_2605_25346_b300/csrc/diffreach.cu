@@ -1331,11 +1331,12 @@ static int wide_step(dr_ctx* c, WideLane& w, int t, bool tcore) {
                             epi.lxpart = lxpart;
                         }
                         TRY(tc_gemm(c, curh, curl, WTh, WTl, nullptr, R, K, NN, ldk, 0, c->derr, st, &epi));
-                        const int ntiles = (NN + tc_bn(NN) - 1) / tc_bn(NN) * tc::epi_groups(tc_bn(NN));
+                        const int gx = (NN + tc_bn(NN) - 1) / tc_bn(NN);  // column tiles of the GEMM
+                        const int ntiles = gx * tc::epi_groups(tc_bn(NN));
                         k_t_partials<<<blocks_for(R, 256), 256, 0, st>>>(a, ell, part, ntiles);
                         c->launches++;
                         if (fin) {
-                            lx_parts = ntiles;
+                            lx_parts = gx;  // one Lambda_x partial per column tile
                             break;
                         }
                         std::swap(curh, nxth);

@@ -130,6 +130,18 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float* v) {
     for (int j = 0; j < 64; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
 // TMA tensor store of one box from shared memory (bulk-group completion).
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
     asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(reinterpret_cast<uint64_t>(map)),
@@ -155,14 +167,14 @@ struct ChainEpi {
     float* part;       // [column tiles * column groups][3][R] partial intercepts (rows contiguous)
     const float* W1;   // final level: W_1 [N][n0] (row-major), else null
     int n0;            // columns of W_1 (<= kFinalCols)
-    float* lxpart;     // final level: [column tiles * column groups][n0][R] partial Lambda_x entries
+    float* lxpart;     // final level: [column tiles][n0][R] partial Lambda_x entries
 };
 constexpr int kFinalCols = 16;  // widest input layer the fused final level handles
-// pipeline stages, 1 KB alignment slack, 256 B of barriers, the epilogue's per-column table and
-// the final level's W_1 rows
-__host__ __device__ constexpr int psmem_bytes(int bn) {
-    return pstages_for(bn) * stage_bytes(bn) + 1024 + 256 + 16 * bn + 4 * kFinalCols * bn;
-}
+// Shared memory: pipeline stages, 256 B of barriers, the epilogue's per-column table, then (1 KB
+// aligned) the final level's right operand W_1^T as TF32 parts in the 128-byte swizzle layout
+// ([part][32-column chunk][kFinalCols rows][128 B]), plus 1 KB of base alignment slack.
+__host__ __device__ constexpr int w1b_offset(int bn) { return (pstages_for(bn) * stage_bytes(bn) + 256 + 16 * bn + 1023) & ~1023; }
+__host__ __device__ constexpr int psmem_bytes(int bn) { return w1b_offset(bn) + 2 * bn * kFinalCols * 4 + 1024; }
 constexpr int kPartials = 3;  // TMEM partial buffers: the MMA issuer may run two chunks ahead of the epilogue
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -213,10 +225,11 @@ __global__ void __launch_bounds__(gemm_threads(BN), 1) k_tc_gemm_p(const __grid_
     uint64_t* empty = full + S;
     uint64_t* pfull = empty + S;   // [NP] partial ready (MMA commit)
     uint64_t* pfree = pfull + NP;  // [NP] partial consumed (4 epilogue warps)
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(pfree + NP);
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(pfree + NP + 1);
     int* abort_flag = reinterpret_cast<int*>(tmem_holder + 1);
     float4* coltab = reinterpret_cast<float4*>(base + S * SB + 256);  // [BN] (s, d, bias) of the tile's columns
-    float* w1tab = reinterpret_cast<float*>(coltab + BN);               // [BN][kFinalCols] W_1 rows (final level)
+    unsigned char* w1b = base + w1b_offset(BN);  // final level: W_1^T TF32 parts (see psmem_bytes)
+    uint64_t* fbar = pfree + NP;                 // final level: the W_1 product is in TMEM (after tmem_holder)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int nk = (K + BK - 1) / BK;
@@ -230,6 +243,7 @@ __global__ void __launch_bounds__(gemm_threads(BN), 1) k_tc_gemm_p(const __grid_
             mbar_init(&pfull[p], 1);
             mbar_init(&pfree[p], 4 * EG);
         }
+        mbar_init(pfree + NP, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -317,11 +331,19 @@ __global__ void __launch_bounds__(gemm_threads(BN), 1) k_tc_gemm_p(const __grid_
         bool uniform = false;
         if constexpr (EPI != 0) {
             if constexpr (EPI == 2) {
-                for (int idx = threadIdx.x - 64; idx < BN * kFinalCols; idx += 128 * EG) {
-                    const int j = idx / kFinalCols, c = idx - j * kFinalCols;
-                    const int col = n0 + j;
-                    w1tab[idx] = (col < N && c < epi.n0) ? epi.W1[(int64_t)col * epi.n0 + c] : 0.f;
+                // W_1 rows of this tile's columns as the K-major right operand (N = kFinalCols outputs)
+                constexpr int NCH = BN / 32;
+                for (int idx = threadIdx.x - 64; idx < NCH * kFinalCols * 32; idx += 128 * EG) {
+                    const int c = idx / (kFinalCols * 32), rem = idx - c * (kFinalCols * 32);
+                    const int r = rem >> 5, k = rem & 31;
+                    const int col = n0 + c * 32 + k;
+                    const float x = (col < N && r < epi.n0) ? epi.W1[(int64_t)col * epi.n0 + r] : 0.f;
+                    const float h = tf32_part_rna(x);
+                    const int off = c * (kFinalCols * 128) + r * 128 + ((((k >> 2) ^ (r & 7))) << 4) + ((k & 3) << 2);
+                    *reinterpret_cast<float*>(w1b + off) = h;
+                    *reinterpret_cast<float*>(w1b + NCH * kFinalCols * 128 + off) = tf32_part_rna(x - h);
                 }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             }
             const int dom0 = m0 / epi.rows_per_dom;
             uniform = R > 0 && dom0 == (min(m0 + BM, R) - 1) / epi.rows_per_dom;
@@ -411,29 +433,81 @@ __global__ void __launch_bounds__(gemm_threads(BN), 1) k_tc_gemm_p(const __grid_
             }
             const int cmax = min(BN, epi.ldk - n0);  // columns of this tile inside the operand (incl. zero padding)
             if constexpr (EPI == 2) {
-                // final level: this thread's share of Lambda_x row = sum over its columns of
-                // (x*s)_j W_1[j][:], in FP32 (W_1 rows broadcast from shared memory)
-                float px[kFinalCols];
+                // final level: Lambda_x partial = (x*s) W_1 over this tile's columns on the tensor
+                // cores.  x*s is staged as TF32 parts in the 128-byte swizzle layout (the MMA's K-major
+                // A operand), one thread issues M = 128, N = kFinalCols MMAs per 32-column chunk into
+                // its own TMEM accumulator, and the first column group sums the chunks in FP32.
+                constexpr int NCH = BN / 32;
+                const int rr = sub * 32 + lane;
+                const int nch = cmax >> 5;
 #pragma unroll
-                for (int c = 0; c < kFinalCols; ++c) px[c] = 0.f;
+                for (int cl = 0; cl < BNH / 32; ++cl) {
+                    const int c = cofs / 32 + cl;
+                    if (c < nch) {
 #pragma unroll
-                for (int j = 0; j < BNH; ++j) {
-                    const float xs = acc[j];
-                    const float4* w = reinterpret_cast<const float4*>(w1tab + (cofs + j) * kFinalCols);
-#pragma unroll
-                    for (int q = 0; q < kFinalCols / 4; ++q) {
-                        const float4 wv = w[q];
-                        px[4 * q] = fmaf(xs, wv.x, px[4 * q]);
-                        px[4 * q + 1] = fmaf(xs, wv.y, px[4 * q + 1]);
-                        px[4 * q + 2] = fmaf(xs, wv.z, px[4 * q + 2]);
-                        px[4 * q + 3] = fmaf(xs, wv.w, px[4 * q + 3]);
+                        for (int u = 0; u < 8; ++u) {
+                            const int j = cl * 32 + u * 4;
+                            const float h0 = tf32_part_rna(acc[j]), h1 = tf32_part_rna(acc[j + 1]);
+                            const float h2 = tf32_part_rna(acc[j + 2]), h3 = tf32_part_rna(acc[j + 3]);
+                            const float4 lv = make_float4(tf32_part_rna(acc[j] - h0), tf32_part_rna(acc[j + 1] - h1),
+                                                          tf32_part_rna(acc[j + 2] - h2), tf32_part_rna(acc[j + 3] - h3));
+                            const int off = c * 16384 + rr * 128 + ((u ^ (rr & 7)) << 4);
+                            *reinterpret_cast<float4*>(base + off) = make_float4(h0, h1, h2, h3);
+                            *reinterpret_cast<float4*>(base + NCH * 16384 + off) = lv;
+                        }
                     }
                 }
-                if (live) {
-                    float* o = epi.lxpart + ((int64_t)blockIdx.x * EG + grp) * epi.n0 * (int64_t)R + row;
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                epi_bar<EG>();
+                const uint32_t dcol = (uint32_t)(NP * PB);  // accumulators after the partial buffers
+                if (threadIdx.x == 64) {
+                    fence_after();
+                    if (ok) {
+                        constexpr uint32_t ID16 = idesc_tf32(BM, kFinalCols);
+                        const uint32_t sa = smem_u32(base), sb = smem_u32(w1b);
+                        for (int c = 0; c < nch; ++c) {
+                            const uint32_t d = tmem + dcol + (uint32_t)(c * kFinalCols);
+                            const uint64_t ah = sw128_desc(sa + c * 16384), al = sw128_desc(sa + NCH * 16384 + c * 16384);
+                            const uint64_t bh = sw128_desc(sb + c * (kFinalCols * 128));
+                            const uint64_t bl = sw128_desc(sb + NCH * kFinalCols * 128 + c * (kFinalCols * 128));
 #pragma unroll
-                    for (int c = 0; c < kFinalCols; ++c)
-                        if (c < epi.n0) o[(int64_t)c * R] = px[c];
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint64_t o = (uint64_t)(kk * 32) >> 4;
+                                mma_tf32(d, ah + o, bl + o, ID16, kk ? 1u : 0u);
+                                mma_tf32(d, al + o, bh + o, ID16, 1u);
+                            }
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint64_t o = (uint64_t)(kk * 32) >> 4;
+                                mma_tf32(d, ah + o, bh + o, ID16, 1u);
+                            }
+                        }
+                        mma_commit(fbar);
+                    } else {
+                        mbar_expect_tx(fbar, 0);  // complete the phase so the readers do not wait out their budget
+                    }
+                }
+                if (grp == 0) {
+                    const bool have = mbar_wait(fbar, 0);
+                    fence_after();
+                    if (!have) atomicExch(err, 1);
+                    float px[kFinalCols];
+#pragma unroll
+                    for (int q = 0; q < kFinalCols; ++q) px[q] = 0.f;
+                    if (have && ok) {
+                        for (int c = 0; c < nch; ++c) {
+                            float v[kFinalCols];
+                            tmem_ld16(tmem + lane_base + dcol + (uint32_t)(c * kFinalCols), v);
+#pragma unroll
+                            for (int q = 0; q < kFinalCols; ++q) px[q] += v[q];
+                        }
+                    }
+                    if (live) {
+                        float* o = epi.lxpart + (int64_t)blockIdx.x * epi.n0 * (int64_t)R + row;
+#pragma unroll
+                        for (int q = 0; q < kFinalCols; ++q)
+                            if (q < epi.n0) o[(int64_t)q * R] = px[q];
+                    }
                 }
             } else if constexpr (BN >= 32) {
                 // Both TF32 parts staged in the idle pipeline buffers as 128-row x 32-column boxes in
