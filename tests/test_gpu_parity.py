@@ -268,8 +268,11 @@ def test_tensor_core_path_narrow_configs(cfg):
     compare(sub, gpu_bounds(sub, precision=TCORE, chunk=257), orc.reach(sub))
 
 
+# [20, ...]: more than 16 states, so the last chain level is not folded into the GEMM epilogue;
+# [16, 48, 130, 90, 4]: exactly 16 states with a 48-wide first layer (32-column epilogue tiles).
 @pytest.mark.parametrize("widths,mode", [([5, 37, 23, 3], orc.MODE_CHORD), ([7, 96, 96, 96, 2], orc.MODE_ZERO),
-                                         ([3, 70, 130, 65, 2], orc.MODE_CHORD), ([9, 300, 40, 5], orc.MODE_CHORD)])
+                                         ([3, 70, 130, 65, 2], orc.MODE_CHORD), ([9, 300, 40, 5], orc.MODE_CHORD),
+                                         ([20, 64, 48, 40, 3], orc.MODE_CHORD), ([16, 48, 130, 90, 4], orc.MODE_CHORD)])
 def test_tensor_core_path_random_shapes(widths, mode):
     p = wl.random_problem(hash(tuple(widths)) % 1000 + 1, widths, D=45, H=4, eps=0.15, mode=mode)
     compare(p, gpu_bounds(p, precision=TCORE, chunk=16), orc.reach(p))
