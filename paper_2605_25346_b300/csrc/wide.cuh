@@ -619,15 +619,47 @@ __global__ void __launch_bounds__(128) k_t_project(const WideArgs a, int ell, co
             }
         }
         float g1 = 0.f, gm = 0.f, gp = 0.f;
-        for (int k = 0; k < n; ++k) {
-            float acc = 0.f;
+        if ((n & 3) == 0) {
+            // G = x P with P's rows read as 16-byte vectors (same accumulation order over j)
+            float gr[NMAX];
 #pragma unroll
-            for (int j = 0; j < NMAX; ++j)
-                if (j < n) acc = fmaf(x[j], Pf[j * n + k], acc);
-            G[k] = acc;
-            g1 += fabsf(acc);
-            gm += fabsf(acc - vf[k]);
-            gp += fabsf(acc + vf[k]);
+            for (int k = 0; k < NMAX; ++k) gr[k] = 0.f;
+#pragma unroll
+            for (int j = 0; j < NMAX; ++j) {
+                if (j < n) {
+                    const float4* prow = reinterpret_cast<const float4*>(Pf + j * n);
+#pragma unroll
+                    for (int q = 0; q < NMAX / 4; ++q) {
+                        if (4 * q < n) {
+                            const float4 pv = prow[q];
+                            gr[4 * q] = fmaf(x[j], pv.x, gr[4 * q]);
+                            gr[4 * q + 1] = fmaf(x[j], pv.y, gr[4 * q + 1]);
+                            gr[4 * q + 2] = fmaf(x[j], pv.z, gr[4 * q + 2]);
+                            gr[4 * q + 3] = fmaf(x[j], pv.w, gr[4 * q + 3]);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NMAX; ++k) {
+                if (k < n) {
+                    G[k] = gr[k];
+                    g1 += fabsf(gr[k]);
+                    gm += fabsf(gr[k] - vf[k]);
+                    gp += fabsf(gr[k] + vf[k]);
+                }
+            }
+        } else {
+            for (int k = 0; k < n; ++k) {
+                float acc = 0.f;
+#pragma unroll
+                for (int j = 0; j < NMAX; ++j)
+                    if (j < n) acc = fmaf(x[j], Pf[j * n + k], acc);
+                G[k] = acc;
+                g1 += fabsf(acc);
+                gm += fabsf(acc - vf[k]);
+                gp += fabsf(acc + vf[k]);
+            }
         }
         // layer 1 has no chain: its intercepts are the bias (and kappa is recorded for the splits)
         float klo, khi;
