@@ -95,7 +95,11 @@ typedef struct dr_options {
                               candidate v (0..9; DR_ERR_SHAPE if it does not fit the controller):
                               0..2 one warp per domain (16/8/4 warps per CTA; two hidden layers,
                               n, m <= 8, hidden widths <= 128), 3..9 several domains per CTA   */
-    int32_t reserved[5];
+    int32_t graphs;        /* 0 = dr_compute_bounds captures its launch sequence in a CUDA graph on
+                              the second call with unchanged buffers, options and slope mode, and
+                              replays it afterwards (needs a stream other than the legacy default
+                              stream; any capture failure falls back to plain launches); 1 = never */
+    int32_t reserved[4];
 } dr_options;
 
 /* Create a context on `device` whose work is ordered on `cuda_stream` (a cudaStream_t;
@@ -226,8 +230,12 @@ int dr_slope_gradient_static(const dr_static_args* args);
  * device memory; synchronises `stream`.  DR_ERR_TIMEOUT if a bounded pipeline wait expired. */
 int dr_tf32x3_gemm(int M, int N, int K, const float* A, const float* BT, float* C, void* stream);
 
-/* Number of kernels this context has launched (monotone counter, for accounting). */
+/* Number of kernels this context has launched (monotone counter, for accounting; a graph replay
+ * counts the kernels of the captured pass). */
 int64_t dr_kernel_launches(const dr_ctx* ctx);
+
+/* Number of dr_compute_bounds calls served by replaying a captured CUDA graph (dr_options.graphs). */
+int64_t dr_graph_replays(const dr_ctx* ctx);
 
 /* Message of the last failing call on ctx (or of the last failing dr_create when ctx is
  * NULL).  The pointer stays valid until the next call on the same context. */

@@ -20,7 +20,7 @@ DR_STATUS_NONFINITE, DR_STATUS_INFEASIBLE = 1, 2
 EXPORTS = [
     "dr_create", "dr_destroy", "dr_load_controller", "dr_load_dynamics", "dr_set_boxes", "dr_set_splits",
     "dr_set_horizon", "dr_set_options", "dr_compute_bounds", "dr_get_objective", "dr_optimize_slopes",
-    "dr_backward", "dr_get_alpha", "dr_set_alpha", "dr_get_beta", "dr_set_beta", "dr_kernel_launches", "dr_last_error",
+    "dr_backward", "dr_get_alpha", "dr_set_alpha", "dr_get_beta", "dr_set_beta", "dr_kernel_launches", "dr_graph_replays", "dr_last_error",
     "dr_slope_gradient_static", "dr_tf32x3_gemm",
 ]
 
@@ -41,7 +41,7 @@ class dr_options(ctypes.Structure):
     _fields_ = [("slope_mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("margin_rho", ctypes.c_double),
                 ("chunk_domains", ctypes.c_int64), ("mem_cap_bytes", ctypes.c_int64),
                 ("box_margin", ctypes.c_double), ("tuning", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("graphs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 _lib = None
@@ -74,6 +74,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dr_get_beta": (i32, [vp, fp, i32]),
         "dr_set_beta": (i32, [vp, fp, i32]),
         "dr_kernel_launches": (i64, [vp]),
+        "dr_graph_replays": (i64, [vp]),
         "dr_last_error": (ctypes.c_char_p, [vp]),
         "dr_slope_gradient_static": (i32, [ctypes.POINTER(dr_static_args)]),
         "dr_tf32x3_gemm": (i32, [i32, i32, i32, vp, vp, vp, vp]),

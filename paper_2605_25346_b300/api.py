@@ -54,9 +54,11 @@ class Reach:
 
     # ---- problem upload -------------------------------------------------------------------
     def set_options(self, mode: Optional[int] = None, precision: int = _lib.DR_PREC_AUTO, rho: Optional[float] = None,
-                    chunk: int = 0, mem_cap: int = 0, box_margin: Optional[float] = None, tuning: int = 0):
+                    chunk: int = 0, mem_cap: int = 0, box_margin: Optional[float] = None, tuning: int = 0,
+                    graphs: int = 0):
         o = _lib.dr_options()
         o.tuning = tuning
+        o.graphs = graphs
         o.slope_mode = _MODE[mode] if mode is not None else _lib.DR_SLOPE_CHORD
         o.precision = precision
         o.margin_rho = 0.0 if rho is None else rho
@@ -179,6 +181,9 @@ class Reach:
 
     def launches(self) -> int:
         return int(self.lib.dr_kernel_launches(self.ctx))
+
+    def graph_replays(self) -> int:
+        return int(self.lib.dr_graph_replays(self.ctx))
 
 
 class BoundsFunction(torch.autograd.Function):

@@ -90,6 +90,14 @@ struct dr_ctx {
     size_t wscratch_bytes = 0;
     int wDc = 0;
     int wLanes = 0;
+    // CUDA-graph replay of dr_compute_bounds: any device allocation or free bumps `epoch`; a graph is
+    // captured on the second call with the same (epoch, slope mode, hull) and replayed while they hold
+    uint64_t epoch = 1;
+    cudaGraphExec_t gexec = nullptr;
+    uint64_t g_epoch = 0, seen_epoch = 0;
+    int g_mode = -1, g_hull = -1, seen_mode = -1, seen_hull = -1;
+    int64_t graph_launches = 0, graph_replays = 0;
+    bool capturing = false, graphs_broken = false, g_check_tc = false, last_tc = false;
     // extra streams (and fork/join events) for the staged path's independent domain lanes
     static constexpr int kMaxLanes = 4;
     cudaStream_t aux[kMaxLanes] = {};
@@ -117,6 +125,7 @@ static int fail(dr_ctx* c, int code, const char* fmt, ...) {
 
 static void dev_free(dr_ctx* c, void*& p, size_t bytes) {
     if (p) {
+        c->epoch++;
         cudaFree(p);
         c->owned -= std::min(c->owned, bytes);
         p = nullptr;
@@ -135,6 +144,7 @@ static int dev_alloc(dr_ctx* c, T*& p, size_t count) {
         cudaGetLastError();
         return fail(c, DR_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
     }
+    c->epoch++;
     c->owned += bytes;
     p = reinterpret_cast<T*>(q);
     return DR_OK;
@@ -757,6 +767,7 @@ void dr_destroy(dr_ctx* c) {
     cudaFree(c->dA2ph);
     cudaFree(c->dA2pl);
     cudaFree(c->derr);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
     for (int l = 0; l < dr_ctx::kMaxLanes; ++l) {
         if (c->aux[l]) cudaStreamDestroy(c->aux[l]);
         if (c->ev_join[l]) cudaEventDestroy(c->ev_join[l]);
@@ -769,6 +780,8 @@ const char* dr_last_error(const dr_ctx* c) { return c ? c->err.c_str() : g_creat
 
 int64_t dr_kernel_launches(const dr_ctx* c) { return c ? c->launches : 0; }
 
+int64_t dr_graph_replays(const dr_ctx* c) { return c ? c->graph_replays : 0; }
+
 int dr_set_options(dr_ctx* c, const dr_options* o) {
     if (!c) return DR_ERR_ARG;
     dr_options n = o ? *o : default_options();
@@ -780,6 +793,7 @@ int dr_set_options(dr_ctx* c, const dr_options* o) {
     if (n.slope_mode == DR_SLOPE_USER && !c->alpha_set && c->D > 0)
         return fail(c, DR_ERR_STATE, "DR_SLOPE_USER requires dr_set_alpha first");
     c->opt = n;
+    c->epoch++;  // kernel arguments may change
     return DR_OK;
 }
 
@@ -979,12 +993,24 @@ int dr_set_boxes(dr_ctx* c, int64_t D, const double* lo, const double* hi, int o
             if (lo[i] > hi[i]) return fail(c, DR_ERR_ARG, "box %lld has lo > hi", (long long)(i / n));
         }
     CUDA_TRY(c, cudaSetDevice(c->device));
-    clear_domain_state(c);
-    dev_free(c, (void*&)c->dlo0, 0);
-    dev_free(c, (void*&)c->dhi0, 0);
-    c->D = D;
-    TRY(dev_alloc(c, c->dlo0, (size_t)D * n));
-    TRY(dev_alloc(c, c->dhi0, (size_t)D * n));
+    if (D > 0 && D == c->D && c->dlo0 && c->dhi0) {
+        // same domain count: keep the box and output buffers (and any captured graph); the
+        // per-domain splits and slopes are reset as for new boxes
+        dev_free(c, (void*&)c->dsp_row, 0);
+        dev_free(c, (void*&)c->dsp, 0);
+        dev_free(c, (void*&)c->dbeta, 0);
+        dev_free(c, (void*&)c->dalpha, 0);
+        c->nnz = 0;
+        c->alpha_set = false;
+        if (c->opt.slope_mode == DR_SLOPE_USER) c->opt.slope_mode = DR_SLOPE_CHORD;
+    } else {
+        clear_domain_state(c);
+        dev_free(c, (void*&)c->dlo0, 0);
+        dev_free(c, (void*&)c->dhi0, 0);
+        c->D = D;
+        TRY(dev_alloc(c, c->dlo0, (size_t)D * n));
+        TRY(dev_alloc(c, c->dhi0, (size_t)D * n));
+    }
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (D > 0) {
         CUDA_TRY(c, cudaMemcpyAsync(c->dlo0, lo, sizeof(double) * D * n, k, c->stream));
@@ -1240,6 +1266,15 @@ static void launch_t_project(dr_ctx* c, const WideArgs& a, int ell, const float*
     c->launches++;
 }
 
+// The tensor-core pipeline's error flag (a bounded wait that expired) after the work on the stream.
+static int check_tc_error(dr_ctx* c) {
+    int herr = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&herr, c->derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (herr) return fail(c, DR_ERR_TIMEOUT, "a tensor-core pipeline wait timed out");
+    return DR_OK;
+}
+
 // One lane of the staged path: a chunk of domains with its own scratch, advanced on its own stream.
 struct WideLane {
     WideArgs a;
@@ -1430,12 +1465,8 @@ static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
         cudaStreamWaitEvent(c->stream, c->ev_join[l], 0);
     }
     if (rc != DR_OK) return rc;
-    if (tcore) {
-        int herr = 0;
-        CUDA_TRY(c, cudaMemcpyAsync(&herr, c->derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-        if (herr) return fail(c, DR_ERR_TIMEOUT, "a tensor-core pipeline wait timed out");
-    }
+    c->last_tc = tcore;
+    if (tcore && !c->capturing) TRY(check_tc_error(c));  // a captured pass is checked after each replay
     return DR_OK;
 }
 
@@ -1572,13 +1603,64 @@ int dr_compute_bounds(dr_ctx* c, double* lo, double* hi, double* hull_lo, double
     CUDA_TRY(c, cudaSetDevice(c->device));
     TRY(ensure_outputs(c));
     if (c->opt.slope_mode == DR_SLOPE_USER && !c->alpha_set) return fail(c, DR_ERR_STATE, "DR_SLOPE_USER without slopes");
-    TRY(run_forward(c, c->opt.slope_mode, nullptr, false));
     const int n = c->net.n, H = c->H;
     const int TN = (H + 1) * n;
-    if (c->D > 0 && (hull_lo || hull_hi)) {
-        k_hull<<<TN, 256, 0, c->stream>>>(c->dout_lo, c->dout_hi, c->dstatus, c->D, TN, c->dhull, c->dhull + TN);
-        CUDA_TRY(c, cudaGetLastError());
-        c->launches++;
+    const int mode = c->opt.slope_mode, hull = (hull_lo || hull_hi) ? 1 : 0;
+    auto pass = [&]() -> int {
+        TRY(run_forward(c, mode, nullptr, false));
+        if (c->D > 0 && hull) {
+            k_hull<<<TN, 256, 0, c->stream>>>(c->dout_lo, c->dout_hi, c->dstatus, c->D, TN, c->dhull, c->dhull + TN);
+            CUDA_TRY(c, cudaGetLastError());
+            c->launches++;
+        }
+        return DR_OK;
+    };
+    const bool graphs = c->opt.graphs == 0 && !c->graphs_broken && c->stream != nullptr && c->D > 0;
+    if (graphs && c->gexec && c->g_epoch == c->epoch && c->g_mode == mode && c->g_hull == hull) {
+        CUDA_TRY(c, cudaGraphLaunch(c->gexec, c->stream));
+        c->launches += c->graph_launches;
+        c->graph_replays++;
+        if (c->g_check_tc) TRY(check_tc_error(c));
+    } else if (graphs && c->seen_epoch == c->epoch && c->seen_mode == mode && c->seen_hull == hull) {
+        // second call with unchanged state: capture the pass (its first run already tuned and allocated)
+        if (c->gexec) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        const int64_t l0 = c->launches;
+        int rc = DR_OK;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            c->capturing = true;
+            rc = pass();
+            c->capturing = false;
+            const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+            if (rc == DR_OK && e == cudaSuccess && g && cudaGraphInstantiate(&c->gexec, g, 0) == cudaSuccess) {
+                c->g_epoch = c->epoch;
+                c->g_mode = mode;
+                c->g_hull = hull;
+                c->g_check_tc = c->last_tc;
+                c->graph_launches = c->launches - l0;
+            } else {
+                c->gexec = nullptr;
+            }
+            if (g) cudaGraphDestroy(g);
+        }
+        if (!c->gexec) {
+            // capture is not possible here: plain launches from now on
+            cudaGetLastError();
+            c->graphs_broken = true;
+            c->launches = l0;
+            TRY(pass());
+        } else {
+            CUDA_TRY(c, cudaGraphLaunch(c->gexec, c->stream));
+            if (c->g_check_tc) TRY(check_tc_error(c));
+        }
+    } else {
+        TRY(pass());
+        c->seen_epoch = c->epoch;
+        c->seen_mode = mode;
+        c->seen_hull = hull;
     }
     const size_t ob = sizeof(double) * (size_t)c->D * TN;
     const cudaMemcpyKind k = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
