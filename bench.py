@@ -35,9 +35,9 @@ FP32_LANES_PER_SM = 128
 SMS = 148
 
 
-# DRAM bytes (read + write) of one fused forward launch on the 4096-box workload, from the ncu capture
-# summarised in profiles/k_fused_forward_multi_quad6.md; the working set lives in shared memory, so
-# this is the boxes and weights read once.
+# DRAM bytes (read + write) of one fused forward launch on the 4096-box workload, measured with ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum of one steady-state launch); the working set lives in
+# shared memory, so this is the boxes and weights read once.
 FUSED_TRAFFIC_BYTES = 548864
 
 
@@ -402,7 +402,7 @@ def main():
     peak = SMS * FP32_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12
     achieved = flops / (k_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            # dram read + write bytes of one launch, ncu capture of the <256, 4> launch shape of this kernel (profiles/)
+            # dram read + write bytes of one launch (ncu capture of the <256, 4> launch shape)
             "traffic": FUSED_TRAFFIC_BYTES, "traffic_unit": "B per launch",
             "kernel": "k_fused_forward_multi (grouped fused forward, autotuned launch shape)",
             "kernel_ms": k_ms,
