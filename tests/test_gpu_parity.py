@@ -1,7 +1,7 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
 Tolerance (floating point): |gpu - oracle| <= 1e-5 * max(|o_lo|, |o_hi|, o_hi - o_lo) for every
-domain, step and coordinate.  Soundness against the oracle: the GPU machine is never tighter than the
+domain, step and coordinate.  Soundness against the oracle: the box computed on the GPU is never tighter than the
 oracle's, i.e. g_lo <= o_lo and g_hi >= o_hi (the reported boxes carry the outward margin 2^-18 of
 their L1 magnitude, sized to cover the FP32 pass's deviation from FP64).  Status words are compared
 exactly.
@@ -16,7 +16,7 @@ from paper_2605_25346_b300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 RTOL = 1e-5
-RHO = 0.0  # no slack: the GPU machine must enclose the oracle's box
+RHO = 0.0  # no slack: the box computed on the GPU must enclose the oracle's box
 
 
 def _api():
