@@ -19,6 +19,7 @@
 #include "fused_multi.cuh"
 #include "fused_warp.cuh"
 #include "tc_gemm.cuh"
+#include "tc_gemm_persistent.cuh"
 #include "wide.cuh"
 
 
@@ -493,6 +494,35 @@ static int launch_tc_gemm_bn(dr_ctx* c, const CUtensorMap* m, float* C, int R, i
     return DR_OK;
 }
 
+static int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            n = 0;
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+// 128-column GEMMs with at least two tiles per SM run persistently (one CTA per SM, the epilogue of
+// one tile overlapped with the main loop of the next).
+template <int EPI>
+static int launch_tc_gemm_persistent(dr_ctx* c, const CUtensorMap* m, float* C, int R, int K, int N, int ldc, int* err,
+                                     cudaStream_t st, const tc::ChainEpi& epi, int64_t tiles, int nsm) {
+    const int smem = tc::pp_smem_bytes();
+    CUDA_TRY(c, cudaFuncSetAttribute(tc::k_tc_gemm_pp<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    cudaFuncAttributes fa;
+    CUDA_TRY(c, cudaFuncGetAttributes(&fa, tc::k_tc_gemm_pp<EPI>));
+    // the warpgroup register split needs exactly the registers it was designed for at entry
+    if (fa.numRegs != tc::kRegsLaunch) return fail(c, DR_ERR_STATE, "persistent GEMM compiled with %d registers", fa.numRegs);
+    const int grid = (int)std::min<int64_t>(tiles, nsm);
+    tc::k_tc_gemm_pp<EPI><<<grid, tc::kPersistThreads, smem, st>>>(m[0], m[1], m[2], m[3], C, R, K, N, ldc, err, epi);
+    CUDA_TRY(c, cudaGetLastError());
+    if (c) c->launches++;
+    return DR_OK;
+}
+
 // C [R x N] (ld ldc) = A B with A given as TF32 parts Ah/Al (blocked layout, tc::blk_index, ldk
 // columns) and B as BTh/BTl [N][ldk]; with `epi` the chain epilogue replaces the store of C.
 static int tc_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* BTh, const float* BTl, float* C, int R, int K,
@@ -516,6 +546,15 @@ static int tc_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* BTh
     if (epi) e = *epi;
     if (epi && epi->W1 && (BN < 32 || epi->n0 > tc::kFinalCols))
         return fail(c, DR_ERR_SHAPE, "fused final chain level needs >= 32 columns and n <= %d", tc::kFinalCols);
+    if (BN == 128) {
+        const int nsm = sm_count();
+        const int64_t tiles = ((int64_t)(R + tc::BM - 1) / tc::BM) * ((N + 127) / 128);
+        if (tiles >= 2 * (int64_t)nsm && tiles <= 0x7fffffffll) {
+            if (!epi) return launch_tc_gemm_persistent<0>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm);
+            return epi->W1 ? launch_tc_gemm_persistent<2>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm)
+                           : launch_tc_gemm_persistent<1>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm);
+        }
+    }
 #define DR_TC_CASE(bn)                                                                                        \
     case bn:                                                                                                  \
         return !epi ? launch_tc_gemm_bn<bn, 0>(c, m, C, R, K, N, ldc, err, st, e)                             \

@@ -361,7 +361,8 @@ __global__ void __launch_bounds__(gemm_threads(BN), 1) k_tc_gemm_p(const __grid_
         }
         for (int kc = 0; kc < nk; ++kc) {
             const int p = kc % NP;
-            if (*(volatile int*)abort_flag || !mbar_wait(&pfull[p], (kc / NP) & 1)) {
+            const bool good = !*(volatile int*)abort_flag && mbar_wait(&pfull[p], (kc / NP) & 1);
+            if (!__all_sync(0xffffffffu, good)) {  // TMEM loads are warp-collective: decide per warp
                 ok = false;
                 break;
             }

@@ -276,3 +276,13 @@ def test_tensor_core_path_narrow_configs(cfg):
 def test_tensor_core_path_random_shapes(widths, mode):
     p = wl.random_problem(hash(tuple(widths)) % 1000 + 1, widths, D=45, H=4, eps=0.15, mode=mode)
     compare(p, gpu_bounds(p, precision=TCORE, chunk=16), orc.reach(p))
+
+
+# 128 domains of 160-row chain levels: R = 20,480 stacked rows in 128-row tiles, at least two
+# 128 x 128 tiles per SM, so the chain levels run in the persistent GEMM (epilogues overlapped with
+# the next tile).  160 rows per domain leave most row tiles spanning two domains (per-row slopes).
+# n = 4 folds the last level into the epilogue (W_1 product); n = 20 ends on a plain GEMM.
+@pytest.mark.parametrize("widths", [[4, 160, 160, 160, 160, 2], [20, 160, 160, 160, 2]])
+def test_tensor_core_path_persistent_gemm(widths):
+    p = wl.random_problem(hash(tuple(widths)) % 1000 + 2, widths, D=128, H=2, eps=0.15, mode=orc.MODE_CHORD)
+    compare(p, gpu_bounds(p, precision=TCORE, chunk=128), orc.reach(p))
