@@ -5,7 +5,7 @@
 //
 //   warp 0 lane 0  TMA producer over all tiles' 32-wide K chunks (three-stage ring)
 //   warp 1         TMEM owner (512 columns = 2 groups x 2 partial buffers x 128); lane 0 issues the
-//                  MMAs, tile j into group j % 2's buffers, alternating per chunk
+//                  MMAs, tile j into group j % 2's buffers, alternating per fill (kPromote chunks)
 //   warps 2, 3     idle (they complete the first warpgroup for the register split)
 //   warps 4..7     epilogue group 0 (tiles 0, 2, 4, ... of this CTA), warps 8..11 group 1; warp w
 //                  reads TMEM lane quadrant w % 4 and holds that quadrant's rows x 128 columns
@@ -15,10 +15,13 @@
 // cover exactly (128 x (168 - 56) = 256 x (224 - 168)).  The host launches this kernel only when
 // the compiled entry count is 168, so the increase never waits for registers that do not exist.
 //
-// The products, their order and the promoted accumulation (every chunk summed in FP32 registers)
-// are those of k_tc_gemm_p, and the intercept partials keep its two 64-column sets per tile, so C,
-// the partials and the next operand are bit-identical to it.  The final level's (x*s) W_1 product
-// is taken here with FP32 FMAs (the TMEM is all partial buffers), not with 3xTF32 MMAs.
+// The three TF32 products and their order are those of k_tc_gemm_p.  Accumulation is promoted per
+// fill: the tensor core sums kPromote = 2 chunks (64 of K) into a partial buffer, which the
+// epilogue then adds into FP32 registers; twice k_tc_gemm_p's span, half its hand-offs, and still
+// well inside the FP32-accurate error bound.  The intercept partials keep the two 64-column sets
+// per tile.  The final level's (x*s) W_1 product is taken with FP32 FMAs (the TMEM is all partial
+// buffers), not with 3xTF32 MMAs.  The next operand (chain levels) leaves through a per-warp
+// staging tile in shared memory, so its global stores cover whole 64-byte row segments.
 //
 // Every wait is bounded.  On expiry the error flag is raised and each role runs through its
 // remaining loop structure without waiting (group barriers stay matched), so the CTA always exits.
@@ -31,6 +34,7 @@ constexpr int kPersistThreads = 128 + 2 * 128;
 constexpr int kRegsLaunch = 168, kRegsCtl = 56, kRegsEpi = 224;
 static_assert(128 * (kRegsLaunch - kRegsCtl) >= 256 * (kRegsEpi - kRegsLaunch), "register split exceeds the launch's registers");
 constexpr int kPS = 3;                              // ring stages
+constexpr int kPromote = 2;                         // K chunks (of 32) per partial buffer fill
 constexpr int kPSB = stage_bytes(128);              // 64 KB per stage
 __host__ __device__ constexpr int pp_coltab_offset() { return kPS * kPSB + 256; }
 __host__ __device__ constexpr int pp_w1tab_offset() { return pp_coltab_offset() + 2 * 128 * 16; }
@@ -41,38 +45,50 @@ __device__ __forceinline__ void group_bar(int g) {
     else asm volatile("bar.sync 2, 128;" ::: "memory");
 }
 
+// FP32 pairs in one 64-bit register (low word first).  Holding the W_1 product's accumulators and
+// table rows as pairs keeps the final level's epilogue within its register budget.
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
 // One row's chain epilogue over the tile's 128 columns in a single pass, so every accumulator dies
 // as soon as its column is done: x -> x*s (slope s of the column's neuron), the partial intercepts
-// (two 64-column sets), and either the next operand's TF32 parts (EPI 1, stored 16 bytes at a time
-// into the blocked layout) or the (x*s) W_1 product (EPI 2).  U: the tile's rows share one domain,
-// whose (s, d, bias) per column are in coltab.
+// (two 64-column sets), and either the next operand's TF32 parts (EPI 1) or the (x*s) W_1 product
+// (EPI 2).  U: the tile's rows share one domain, whose (s, d, bias) per column are in coltab.
+//
+// EPI 1 writes the next operand through a 2 KB per-warp staging tile (32 rows x 16 columns, 16-byte
+// units XOR-swizzled by row so both the row-wise writes and the transposed reads are free of bank
+// conflicts): a global store instruction then covers 8 rows x 64 contiguous bytes instead of 32 rows
+// x 16 bytes.  ok is warp-uniform; rows at or past R are not written.
 template <int EPI, bool U>
-__device__ __forceinline__ void pp_row_epilogue(float* acc, const float4* coltab, const float* w1tab, const ChainEpi& epi,
-                                                int row, bool live, int n0, int N, int R) {
+__device__ __forceinline__ void pp_row_epilogue(float* acc, const float4* coltab, const float* w1tab, float* stg,
+                                                const ChainEpi& epi, int row, bool ok, int n0, int N, int R) {
     constexpr int BN = 128;
+    const int lane = threadIdx.x & 31;
+    const bool live = ok && row < R;
     const int rr = live ? row : (R > 0 ? R - 1 : 0);
     const int dom = rr / epi.rows_per_dom;
     const float* sl = epi.hs + (int64_t)dom * epi.hidden + epi.hoff;
     const float* dl = epi.hd + (int64_t)dom * epi.hidden + epi.hoff;
     float spos[2] = {0.f, 0.f}, sneg[2] = {0.f, 0.f}, sb[2] = {0.f, 0.f};
-    float px[kFinalCols];
+    unsigned long long px2[kFinalCols / 2];  // EPI 2: Lambda_x partial as pairs
 #pragma unroll
-    for (int c = 0; c < kFinalCols; ++c) px[c] = 0.f;
+    for (int c = 0; c < kFinalCols / 2; ++c) px2[c] = 0ull;
     const int enk = epi.ldk >> 5;
     const int nch = min(BN, epi.ldk - n0) >> 5;  // 32-column chunks of this tile inside the operand
-    float* ph = nullptr;
-    float* pl = nullptr;
-    if constexpr (EPI == 1) {
-        const int64_t o = blk_index(rr, n0, enk);
-        ph = epi.Ah + o;
-        pl = epi.Al + o;
-    }
+    const int row0 = row - lane;                 // first row of this warp
+    constexpr int CB = EPI == 1 ? 16 : 4;  // columns per block (EPI 1: one staging tile)
 #pragma unroll
-    for (int q = 0; q < BN / 4; ++q) {
-        float xv[4];
+    for (int hc = 0; hc < BN / CB; ++hc) {
+        float xv[CB];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int j = 4 * q + e, h = j >> 6;
+        for (int e = 0; e < CB; ++e) {
+            const int j = CB * hc + e, h = j >> 6;
             const float x = acc[j];
             float xs = 0.f;
             if constexpr (U) {
@@ -95,26 +111,47 @@ __device__ __forceinline__ void pp_row_epilogue(float* acc, const float4* coltab
             xv[e] = xs;
         }
         if constexpr (EPI == 1) {
-            // a row's 32-column chunk is 128 contiguous bytes of the blocked layout
-            const int c = q >> 3, u = q & 7;
-            if (live && c < nch) {
-                const float h0 = tf32_part_rna(xv[0]), h1 = tf32_part_rna(xv[1]);
-                const float h2 = tf32_part_rna(xv[2]), h3 = tf32_part_rna(xv[3]);
-                *reinterpret_cast<float4*>(ph + c * 4096 + 4 * u) = make_float4(h0, h1, h2, h3);
-                *reinterpret_cast<float4*>(pl + c * 4096 + 4 * u) =
-                    make_float4(tf32_part_rna(xv[0] - h0), tf32_part_rna(xv[1] - h1), tf32_part_rna(xv[2] - h2), tf32_part_rna(xv[3] - h3));
+            const int c = hc >> 1;
+            if (c < nch) {  // uniform across the warp
+#pragma unroll
+                for (int part = 0; part < 2; ++part) {
+                    float v[CB];
+#pragma unroll
+                    for (int e = 0; e < CB; ++e) {
+                        const float hi = tf32_part_rna(xv[e]);
+                        v[e] = part == 0 ? hi : tf32_part_rna(xv[e] - hi);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        *reinterpret_cast<float4*>(stg + lane * 16 + ((u ^ ((lane >> 1) & 3)) << 2)) =
+                            make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+                    __syncwarp();
+                    float* dst = part == 0 ? epi.Ah : epi.Al;
+                    const int u = lane & 3;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int r = (lane >> 2) + 8 * i;
+                        const float4 w = *reinterpret_cast<const float4*>(stg + r * 16 + ((u ^ ((r >> 1) & 3)) << 2));
+                        if (ok && row0 + r < R)
+                            *reinterpret_cast<float4*>(dst + blk_index(row0 + r, n0 + 16 * hc + 4 * u, enk)) = w;
+                    }
+                    __syncwarp();
+                }
             }
         } else {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float4* w = reinterpret_cast<const float4*>(w1tab + (4 * q + e) * kFinalCols);
+            for (int e = 0; e < CB; ++e) {
+                const ulonglong2* w = reinterpret_cast<const ulonglong2*>(w1tab + (CB * hc + e) * kFinalCols);
 #pragma unroll
                 for (int k = 0; k < kFinalCols / 4; ++k) {
-                    const float4 wv = w[k];
-                    px[4 * k] = fmaf(xv[e], wv.x, px[4 * k]);
-                    px[4 * k + 1] = fmaf(xv[e], wv.y, px[4 * k + 1]);
-                    px[4 * k + 2] = fmaf(xv[e], wv.z, px[4 * k + 2]);
-                    px[4 * k + 3] = fmaf(xv[e], wv.w, px[4 * k + 3]);
+                    const ulonglong2 wv = w[k];
+                    float w0, w1, w2, w3, p0, p1, p2, p3;
+                    unpack2(wv.x, w0, w1);
+                    unpack2(wv.y, w2, w3);
+                    unpack2(px2[2 * k], p0, p1);
+                    unpack2(px2[2 * k + 1], p2, p3);
+                    px2[2 * k] = pack2(fmaf(xv[e], w0, p0), fmaf(xv[e], w1, p1));
+                    px2[2 * k + 1] = pack2(fmaf(xv[e], w2, p2), fmaf(xv[e], w3, p3));
                 }
             }
         }
@@ -129,6 +166,9 @@ __device__ __forceinline__ void pp_row_epilogue(float* acc, const float4* coltab
             epi.part[(t * 3 + 2) * R + row] = sb[h];
         }
         if constexpr (EPI == 2) {
+            float px[kFinalCols];
+#pragma unroll
+            for (int c = 0; c < kFinalCols / 2; ++c) unpack2(px2[c], px[2 * c], px[2 * c + 1]);
             float* o = epi.lxpart + (int64_t)nt * epi.n0 * (int64_t)R + row;
 #pragma unroll
             for (int c = 0; c < kFinalCols; ++c)
@@ -154,6 +194,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
     int* abort_flag = reinterpret_cast<int*>(tmem_holder + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = (K + BK - 1) / BK;
+    const int npc = (nk + kPromote - 1) / kPromote;  // partial buffer fills per tile
     const int ntn = (N + BN - 1) / BN;
     const int tiles = ((R + BM - 1) / BM) * ntn;
 
@@ -224,9 +265,11 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
         for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++lt) {
             const int g = lt & 1, kg = lt >> 1;
             for (int kc = 0; kc < nk; ++kc, ++q) {
-                const int s = q % S, r = kc & 1, p = 2 * g + r;
-                const int uses = kg * ((nk + 1 - r) >> 1) + (kc >> 1);  // earlier uses of buffer p
-                if (!mbar_wait(&full[s], (q / S) & 1) || (uses >= 1 && !mbar_wait(&pfree[p], (uses - 1) & 1))) {
+                const int s = q % S, ps = kc / kPromote, r = ps & 1, p = 2 * g + r;
+                const int uses = kg * ((npc + 1 - r) >> 1) + (ps >> 1);  // earlier fills of buffer p
+                const bool first = kc % kPromote == 0;                    // this chunk starts a fill
+                const bool last = kc % kPromote == kPromote - 1 || kc == nk - 1;
+                if (!mbar_wait(&full[s], (q / S) & 1) || (first && uses >= 1 && !mbar_wait(&pfree[p], (uses - 1) & 1))) {
                     atomicExch(err, 1);
                     *(volatile int*)abort_flag = 1;
                     ok = false;
@@ -240,7 +283,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
 #pragma unroll
                 for (int kk = 0; kk < BK / 8; ++kk) {
                     const uint64_t o = (uint64_t)(kk * 32) >> 4;
-                    mma_tf32(d, ah + o, bl + o, IDESC, kk ? 1u : 0u);
+                    mma_tf32(d, ah + o, bl + o, IDESC, (kk || !first) ? 1u : 0u);
                     mma_tf32(d, al + o, bh + o, IDESC, 1u);
                 }
 #pragma unroll
@@ -249,7 +292,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
                     mma_tf32(d, ah + o, bh + o, IDESC, 1u);
                 }
                 mma_commit(&empty[s]);
-                mma_commit(&pfull[p]);
+                if (last) mma_commit(&pfull[p]);
             }
         }
     }
@@ -278,20 +321,27 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
                     coltab[gt] = qv;
                 }
                 if constexpr (EPI == 2) {
-                    for (int idx = gt; idx < BN * kFinalCols; idx += 128) {
+                    // all 16 loads of a thread in flight together, then the shared-memory stores
+                    constexpr int PER = BN * kFinalCols / 128;
+                    float wv[PER];
+#pragma unroll
+                    for (int it = 0; it < PER; ++it) {
+                        const int idx = gt + it * 128;
                         const int j = idx / kFinalCols, c = idx - j * kFinalCols;
                         const int col = n0 + j;
-                        w1tab[idx] = (col < N && c < epi.n0) ? epi.W1[(int64_t)col * epi.n0 + c] : 0.f;
+                        wv[it] = (col < N && c < epi.n0) ? __ldg(epi.W1 + (int64_t)col * epi.n0 + c) : 0.f;
                     }
+#pragma unroll
+                    for (int it = 0; it < PER; ++it) w1tab[gt + it * 128] = wv[it];
                 }
                 group_bar(g);
             }
             float acc[BN];
 #pragma unroll
             for (int j = 0; j < BN; ++j) acc[j] = 0.f;
-            for (int kc = 0; kc < nk; ++kc) {
-                const int r = kc & 1, p = 2 * g + r;
-                const int uses = kg * ((nk + 1 - r) >> 1) + (kc >> 1);
+            for (int ps = 0; ps < npc; ++ps) {
+                const int r = ps & 1, p = 2 * g + r;
+                const int uses = kg * ((npc + 1 - r) >> 1) + (ps >> 1);
                 bool good = ok && !*(volatile int*)abort_flag && mbar_wait(&pfull[p], uses & 1);
                 ok = __all_sync(0xffffffffu, good);  // TMEM loads are warp-collective: decide per warp
                 if (ok) {
@@ -318,8 +368,10 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
                         if (n0 + j < N) C[(int64_t)row * ldc + n0 + j] = acc[j];
                 }
             } else {
-                if (uniform) pp_row_epilogue<EPI, true>(acc, coltab, w1tab, epi, row, live, n0, N, R);
-                else pp_row_epilogue<EPI, false>(acc, coltab, w1tab, epi, row, live, n0, N, R);
+                // EPI 1 has no W_1 table: its per-warp staging tiles (2 KB each) take that space
+                float* stg = w1tab + sub * 512;
+                if (uniform) pp_row_epilogue<EPI, true>(acc, coltab, w1tab, stg, epi, row, ok, n0, N, R);
+                else pp_row_epilogue<EPI, false>(acc, coltab, w1tab, stg, epi, row, ok, n0, N, R);
             }
         }
     }
