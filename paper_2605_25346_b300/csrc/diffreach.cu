@@ -1297,11 +1297,19 @@ static int wide_chunk(dr_ctx* c, const NetDesc& N, int lanes) {
 
 static inline unsigned blocks_for(int64_t threads, int bs) { return (unsigned)((threads + bs - 1) / bs); }
 
+// Concretisation launch: one thread per row for large row counts (whole-line loads of the
+// entry-major Lambda_x partials), four per row for small ones (a shorter dependent chain per row).
 static void launch_t_project(dr_ctx* c, const WideArgs& a, int ell, const float* Lx, int shared_lx, int64_t R, int lx_parts,
-                             cudaStream_t st) {
-    const unsigned blocks = (unsigned)std::min<int64_t>((R + 127) / 128, (int64_t)148 * 16);
-    if (a.net.n <= 16) k_t_project<16><<<blocks, 128, 0, st>>>(a, ell, Lx, shared_lx, lx_parts);
-    else k_t_project<64><<<blocks, 128, 0, st>>>(a, ell, Lx, shared_lx, lx_parts);
+                             cudaStream_t st, const float* part = nullptr, int ntiles = 0) {
+    if (a.net.n <= 16 && R < (int64_t)148 * 128) {
+        const unsigned blocks = (unsigned)((R + 63) / 64);
+        if (a.net.n % 4 == 0) k_t_project4<true><<<blocks, 256, 0, st>>>(a, ell, Lx, shared_lx, lx_parts, part, ntiles);
+        else k_t_project4<false><<<blocks, 256, 0, st>>>(a, ell, Lx, shared_lx, lx_parts, part, ntiles);
+    } else {
+        const unsigned blocks = (unsigned)std::min<int64_t>((R + 127) / 128, (int64_t)148 * 16);
+        if (a.net.n <= 16) k_t_project<16><<<blocks, 128, 0, st>>>(a, ell, Lx, shared_lx, lx_parts, part, ntiles);
+        else k_t_project<64><<<blocks, 128, 0, st>>>(a, ell, Lx, shared_lx, lx_parts, part, ntiles);
+    }
     c->launches++;
 }
 
@@ -1381,7 +1389,7 @@ static int wide_step(dr_ctx* c, WideLane& w, int t, bool tcore) {
                 k_t_chain_init<<<blocks_for(warps * 32, 256), 256, 0, st>>>(a, ell, lamA, lamB, ldk);
                 c->launches++;
                 float *curh = lamA, *curl = lamB, *nxth = lamC, *nxtl = lamD;
-                int lx_parts = 0;
+                int lx_parts = 0, fin_tiles = 0;
                 for (int mm = ell - 1; mm >= 1; --mm) {
                     const int K = N.w[mm], NN = N.w[mm - 1];
                     const float* WTh = c->dWTh + c->WToff[mm - 1];
@@ -1407,12 +1415,13 @@ static int wide_step(dr_ctx* c, WideLane& w, int t, bool tcore) {
                         TRY(tc_gemm(c, curh, curl, WTh, WTl, nullptr, R, K, NN, ldk, 0, c->derr, st, &epi));
                         const int gx = (NN + tc_bn(NN) - 1) / tc_bn(NN);  // column tiles of the GEMM
                         const int ntiles = gx * tc::epi_groups(tc_bn(NN));
-                        k_t_partials<<<blocks_for(R, 256), 256, 0, st>>>(a, ell, part, ntiles);
-                        c->launches++;
                         if (fin) {
-                            lx_parts = gx;  // one Lambda_x partial per column tile
+                            lx_parts = gx;        // one Lambda_x partial per column tile
+                            fin_tiles = ntiles;   // its intercept partials are added by the projection
                             break;
                         }
+                        k_t_partials<<<blocks_for(R, 256), 256, 0, st>>>(a, ell, part, ntiles);
+                        c->launches++;
                         std::swap(curh, nxth);
                         std::swap(curl, nxtl);
                         ldk = round_up32(NN);
@@ -1420,7 +1429,7 @@ static int wide_step(dr_ctx* c, WideLane& w, int t, bool tcore) {
                         TRY(tc_gemm(c, curh, curl, WTh, WTl, nxth, R, K, NN, ldk, NN, c->derr, st));
                     }
                 }
-                launch_t_project(c, a, ell, lx_parts ? lxpart : nxth, 0, R, lx_parts, st);
+                launch_t_project(c, a, ell, lx_parts ? lxpart : nxth, 0, R, lx_parts, st, part, fin_tiles);
             }
         }
         if (ell < L) {

@@ -574,6 +574,152 @@ __global__ void k_t_partials(const WideArgs a, int ell, const float* __restrict_
     }
 }
 
+// Concretisation of target ell (n <= 16) with four threads per (domain, row): thread q of a quad
+// owns Lambda_x entries j = 4q..4q+3 (summing the partial rows in order) and G's columns
+// k = 4q..4q+3.  The quad exchanges the row by shuffles for G = Lambda_x P; the sums over j (the
+// centre and remainder terms) and over k (|G|, |G -+ v|) are split by quad and reduced by
+// shuffles, so their rounding order differs from k_t_project's; G itself is summed in the same
+// order.  With ntiles > 0 the final chain level's intercept partials (k_t_partials' sums) are
+// added to kappa here, the tiles split over the quad in the same way.
+template <bool VEC>
+__global__ void __launch_bounds__(256, 3) k_t_project4(const WideArgs a, int ell, const float* __restrict__ Lxb, int shared_lx,
+                                                    int lx_parts, const float* __restrict__ part, int ntiles) {
+    const NetDesc& N = a.net;
+    const int n = N.n, L = N.L, rows = N.w[ell];
+    const int64_t R = (int64_t)a.Dc * rows;
+    const int lane = threadIdx.x & 31, q = lane & 3, qb = lane & ~3;
+    const int rows_per_block = blockDim.x >> 2;
+    const int k0 = 4 * q;
+    for (int64_t base = (int64_t)blockIdx.x * rows_per_block; base < R; base += (int64_t)gridDim.x * rows_per_block) {
+        // every thread of a block takes the same number of trips, so the quad shuffles stay full-warp
+        const int64_t r = base + (threadIdx.x >> 2);
+        const bool live = r < R;
+        const int64_t rc = live ? r : R - 1;
+        const int d = (int)(rc / rows), i = (int)(rc - (int64_t)d * rows);
+        const float* Pf = a.Pf + (int64_t)d * n * n;
+        const float* vf = a.vf + (int64_t)d * (n + 1);
+        // all stores come after the last load, so the loads need not wait for them
+        float xl[4], cj[4], lj[4], hj[4], vk[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int j = k0 + e;
+            float v = 0.f;
+            cj[e] = lj[e] = hj[e] = vk[e] = 0.f;
+            if (j < n) {
+                if (lx_parts > 0) {
+                    for (int t = 0; t < lx_parts; ++t) v += Lxb[((int64_t)t * n + j) * R + rc];
+                } else {
+                    v = shared_lx ? Lxb[(int64_t)i * n + j] : Lxb[rc * n + j];
+                }
+                cj[e] = a.cf[(int64_t)d * n + j];
+                lj[e] = a.Ilof[(int64_t)d * n + j];
+                hj[e] = a.Ihif[(int64_t)d * n + j];
+                vk[e] = vf[j];
+            }
+            xl[e] = v;
+        }
+        const float wf = vf[n];
+        float klo = 0.f, khi = 0.f;
+        if (shared_lx) klo = khi = a.b[N.boff[0] + i];
+        else {
+            klo = a.klo[(int64_t)d * N.maxw + i];
+            khi = a.khi[(int64_t)d * N.maxw + i];
+        }
+        float sp = 0.f, sn = 0.f, sb = 0.f;
+        if (!shared_lx && ntiles > 0) {
+            for (int t = q; t < ntiles; t += 4) {
+                sp += part[((int64_t)t * 3 + 0) * R + rc];
+                sn += part[((int64_t)t * 3 + 1) * R + rc];
+                sb += part[((int64_t)t * 3 + 2) * R + rc];
+            }
+        }
+        float av = 0.f, rlo = 0.f, rhi = 0.f;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float v = xl[e];
+            av = fmaf(v, cj[e], av);
+            rlo = fmaf(posf(v), lj[e], fmaf(negf(v), hj[e], rlo));
+            rhi = fmaf(posf(v), hj[e], fmaf(negf(v), lj[e], rhi));
+        }
+        float gr[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const float xj = __shfl_sync(0xffffffffu, xl[j & 3], qb | (j >> 2));
+            if (j < n && k0 < n) {
+                float4 pv;
+                if constexpr (VEC) {
+                    pv = *reinterpret_cast<const float4*>(Pf + j * n + k0);
+                } else {
+                    pv = make_float4(Pf[j * n + k0], 0.f, 0.f, 0.f);
+                    if (k0 + 1 < n) pv.y = Pf[j * n + k0 + 1];
+                    if (k0 + 2 < n) pv.z = Pf[j * n + k0 + 2];
+                    if (k0 + 3 < n) pv.w = Pf[j * n + k0 + 3];
+                }
+                gr[0] = fmaf(xj, pv.x, gr[0]);
+                gr[1] = fmaf(xj, pv.y, gr[1]);
+                gr[2] = fmaf(xj, pv.z, gr[2]);
+                gr[3] = fmaf(xj, pv.w, gr[3]);
+            }
+        }
+        float g1 = 0.f, gm = 0.f, gp = 0.f;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (k0 + e < n) {
+                g1 += fabsf(gr[e]);
+                gm += fabsf(gr[e] - vk[e]);
+                gp += fabsf(gr[e] + vk[e]);
+            }
+        }
+        // quad sums (xor 1, then xor 2): every thread of the quad ends with the same totals
+#pragma unroll
+        for (int o = 1; o <= 2; o <<= 1) {
+            av += __shfl_xor_sync(0xffffffffu, av, o);
+            rlo += __shfl_xor_sync(0xffffffffu, rlo, o);
+            rhi += __shfl_xor_sync(0xffffffffu, rhi, o);
+            g1 += __shfl_xor_sync(0xffffffffu, g1, o);
+            gm += __shfl_xor_sync(0xffffffffu, gm, o);
+            gp += __shfl_xor_sync(0xffffffffu, gp, o);
+            sp += __shfl_xor_sync(0xffffffffu, sp, o);
+            sn += __shfl_xor_sync(0xffffffffu, sn, o);
+            sb += __shfl_xor_sync(0xffffffffu, sb, o);
+        }
+        if (!live) continue;
+        if (k0 < n) {
+            float* G = a.G + ((int64_t)d * N.maxw + i) * n + k0;
+            if constexpr (VEC) {
+                *reinterpret_cast<float4*>(G) = make_float4(gr[0], gr[1], gr[2], gr[3]);
+            } else {
+                G[0] = gr[0];
+                if (k0 + 1 < n) G[1] = gr[1];
+                if (k0 + 2 < n) G[2] = gr[2];
+                if (k0 + 3 < n) G[3] = gr[3];
+            }
+        }
+        if (q != 0) continue;
+        if (!shared_lx && ntiles > 0) {
+            khi += sp + sb;
+            klo += sn + sb;
+        }
+        if (shared_lx || ntiles > 0) {
+            a.klo[(int64_t)d * N.maxw + i] = klo;
+            a.khi[(int64_t)d * N.maxw + i] = khi;
+        }
+        const float S = fabsf(av) + g1 + fabsf(klo) + fabsf(khi) + fabsf(rlo) + fabsf(rhi) + fabsf(wf);
+        if (ell < L) {
+            a.hl[(int64_t)d * N.hidden + N.hoff[ell] + i] = av + klo + rlo - gm - wf - a.rho * S;
+            a.hu[(int64_t)d * N.hidden + N.hoff[ell] + i] = av + khi + rhi + gp + wf + a.rho * S;
+            a.sa[(int64_t)d * N.maxw + i] = av;
+            a.sRlo[(int64_t)d * N.maxw + i] = rlo;
+            a.sRhi[(int64_t)d * N.maxw + i] = rhi;
+            a.sS[(int64_t)d * N.maxw + i] = S;
+        } else {
+            a.cu[(int64_t)d * N.m + i] = av + 0.5f * (klo + khi);
+            a.Iulo[(int64_t)d * N.m + i] = 0.5f * (klo - khi) + rlo - a.rho * S;
+            a.Iuhi[(int64_t)d * N.m + i] = 0.5f * (khi - klo) + rhi + a.rho * S;
+        }
+    }
+}
+
 // Concretisation of target ell with one thread per (domain, row); Lambda_x rows of domain d start at
 // Lxb + d * rows * n (ld n), or, with shared_lx, every domain uses the same rows Lxb + i * n (the
 // first layer: Lambda_x = W_1 and kappa = b_1).  Same arithmetic as k_w_project.  NMAX >= n is a compile-time bound
@@ -582,12 +728,31 @@ __global__ void k_t_partials(const WideArgs a, int ell, const float* __restrict_
 // entry j of part t at Lxb[(t*n + j)*R + r].
 template <int NMAX>
 __global__ void __launch_bounds__(128) k_t_project(const WideArgs a, int ell, const float* __restrict__ Lxb, int shared_lx,
-                                                   int lx_parts) {
+                                                   int lx_parts, const float* __restrict__ part, int ntiles) {
     const NetDesc& N = a.net;
     const int n = N.n, L = N.L, rows = N.w[ell];
     const int64_t R = (int64_t)a.Dc * rows;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
         const int d = (int)(r / rows), i = (int)(r - (int64_t)d * rows);
+        // kappa (and the final chain level's intercept partials, summed as k_t_partials does) is read
+        // before anything is stored
+        float klo, khi;
+        if (shared_lx) {
+            klo = khi = a.b[N.boff[0] + i];
+        } else {
+            klo = a.klo[(int64_t)d * N.maxw + i];
+            khi = a.khi[(int64_t)d * N.maxw + i];
+            if (ntiles > 0) {
+                float sp = 0.f, sn = 0.f, sb = 0.f;
+                for (int t = 0; t < ntiles; ++t) {
+                    sp += part[((int64_t)t * 3 + 0) * R + r];
+                    sn += part[((int64_t)t * 3 + 1) * R + r];
+                    sb += part[((int64_t)t * 3 + 2) * R + r];
+                }
+                khi += sp + sb;
+                klo += sn + sb;
+            }
+        }
         const float* Lx = shared_lx ? Lxb + (int64_t)i * n : Lxb + r * n;
         const float* Pf = a.Pf + (int64_t)d * n * n;
         const float* cf = a.cf + (int64_t)d * n;
@@ -662,14 +827,9 @@ __global__ void __launch_bounds__(128) k_t_project(const WideArgs a, int ell, co
             }
         }
         // layer 1 has no chain: its intercepts are the bias (and kappa is recorded for the splits)
-        float klo, khi;
-        if (shared_lx) {
-            klo = khi = a.b[N.boff[0] + i];
+        if (shared_lx || ntiles > 0) {
             a.klo[(int64_t)d * N.maxw + i] = klo;
             a.khi[(int64_t)d * N.maxw + i] = khi;
-        } else {
-            klo = a.klo[(int64_t)d * N.maxw + i];
-            khi = a.khi[(int64_t)d * N.maxw + i];
         }
         const float wf = vf[n];
         const float S = fabsf(av) + g1 + fabsf(klo) + fabsf(khi) + fabsf(rlo) + fabsf(rhi) + fabsf(wf);
