@@ -120,6 +120,43 @@ def measure_wide_refinement(local):
     return out
 
 
+def measure_tf32_peak(local, n=8192, sustain_s=4.0):
+    """Dense TF32 tensor throughput of this GPU: cuBLAS FP32 matmul with TF32 allowed, n^3, best of 10
+    (burst) and back to back for `sustain_s` seconds (sustained).  The denominator of the 3xTF32 path."""
+    dev = torch.device("cuda", local)
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        g = torch.Generator(device=dev).manual_seed(7)
+        a = torch.randn(n, n, device=dev, generator=g)
+        b = torch.randn(n, n, device=dev, generator=g)
+        c = torch.empty(n, n, device=dev)
+        for _ in range(3):
+            torch.matmul(a, b, out=c)
+        torch.cuda.synchronize(dev)
+        best = float("inf")
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) * 1e-3)
+        reps = max(1, int(sustain_s / best))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            torch.matmul(a, b, out=c)
+        e1.record()
+        e1.synchronize()
+        sus = e0.elapsed_time(e1) * 1e-3 / reps
+        fl = 2.0 * n ** 3
+        return {"tf32_tflops_burst": fl / best / 1e12, "tf32_tflops_sustained": fl / sus / 1e12,
+                "how": f"torch.matmul FP32 with TF32 allowed (cuBLAS), {n}^3, best of 10 and {reps} back to back"}
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
 def measure_wide(local, reps=2):
     """Throughput of the staged tcgen05 path on domain samples of the two wide workloads."""
     from paper_2605_25346_b300 import api
@@ -132,6 +169,8 @@ def measure_wide(local, reps=2):
         bf16_burst, bf16_sus, basis = 1800.0, 1400.0, "of fallback"
     peak_tf32 = bf16_burst * 1.1 / 2.25  # nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)
     peak_tf32_sus = bf16_sus * 1.1 / 2.25
+    tf32 = measure_tf32_peak(local)
+    out["tf32_peak_measured"] = tf32
     for name, prob in (("branch12 12-256x3-4, 4096 of 65536 branch domains, H=30",
                         wl.quadrotor_branch(only=np.arange(4096))),
                        ("large16 16-512x4-8, 2048 of 262144 sub-boxes, H=50", wl.large16().subset(np.arange(2048)))):
@@ -150,6 +189,8 @@ def measure_wide(local, reps=2):
                      "fp32eq_peak_tflops_sustained": peak_tf32_sus / 3.0,
                      "frac_of_fp32eq_tensor_peak_burst": fl / t / 1e12 / (peak_tf32 / 3.0),
                      "frac_of_fp32eq_tensor_peak_sustained": fl / t / 1e12 / (peak_tf32_sus / 3.0),
+                     "frac_of_measured_tf32_over_3_burst": fl / t / 1e12 / (tf32["tf32_tflops_burst"] / 3.0),
+                     "frac_of_measured_tf32_over_3_sustained": fl / t / 1e12 / (tf32["tf32_tflops_sustained"] / 3.0),
                      "peak_basis": f"3xTF32: one FP32-equivalent FLOP = 3 TF32 tensor FLOPs; TF32 peak = bf16 "
                                    f"{basis} x 1.1/2.25 (nominal ratio); a pass of H={prob.H} steps is a "
                                    f"long, power-capped run, so the sustained figure is the relevant one"}

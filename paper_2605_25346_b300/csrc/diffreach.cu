@@ -1288,9 +1288,19 @@ static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, int lanes, int lane, float*
     return DR_OK;
 }
 
+// Domains per lane chunk: the option if set, else as many as a scratch budget allows.  The budget is
+// 16 GiB (larger chunks mean longer GEMM launches with fewer partial waves), at most a quarter of the
+// free device memory and at most the memory cap left, and never below 1 GiB.
 static int wide_chunk(dr_ctx* c, const NetDesc& N, int lanes) {
     if (c->opt.chunk_domains > 0) return (int)std::min<int64_t>(std::min<int64_t>(c->opt.chunk_domains, c->D), 65535);
-    const size_t budget = (size_t(4) << 30) / lanes;
+    size_t total = size_t(16) << 30;
+    size_t free_b = 0, all_b = 0;
+    // the scratch this context already holds counts as free, so the choice is stable across calls
+    if (cudaMemGetInfo(&free_b, &all_b) == cudaSuccess) total = std::min(total, (free_b + c->wscratch_bytes) / 4);
+    if (c->opt.mem_cap_bytes > 0)
+        total = std::min(total, (size_t)c->opt.mem_cap_bytes > c->owned ? (size_t)c->opt.mem_cap_bytes - c->owned : size_t(0));
+    total = std::max(total, size_t(1) << 30);
+    const size_t budget = total / lanes;
     const int64_t dc = std::max<int64_t>(1, (int64_t)(budget / wide_bytes_per_domain(N)));
     return (int)std::min<int64_t>(std::min<int64_t>(dc, c->D), 65535);
 }
