@@ -684,7 +684,7 @@ __global__ void __launch_bounds__(256, 3) k_t_project4(const WideArgs a, int ell
             sb += __shfl_xor_sync(0xffffffffu, sb, o);
         }
         if (!live) continue;
-        if (k0 < n) {
+        if (k0 < n && (ell == L || a.sp_row != nullptr)) {  // G rows nobody reads are not stored
             float* G = a.G + ((int64_t)d * N.maxw + i) * n + k0;
             if constexpr (VEC) {
                 *reinterpret_cast<float4*>(G) = make_float4(gr[0], gr[1], gr[2], gr[3]);
@@ -760,6 +760,9 @@ __global__ void __launch_bounds__(128) k_t_project(const WideArgs a, int ell, co
         const float* Ihif = a.Ihif + (int64_t)d * n;
         const float* vf = a.vf + (int64_t)d * (n + 1);
         float* G = a.G + ((int64_t)d * N.maxw + i) * n;
+        // G = Lambda_x P is read back only as a split's constraint row (hidden layers) or as the
+        // controller TM's linear part (output layer)
+        const bool keepG = ell == L || a.sp_row != nullptr;
         float x[NMAX];
         if (lx_parts > 0) {
 #pragma unroll
@@ -808,11 +811,15 @@ __global__ void __launch_bounds__(128) k_t_project(const WideArgs a, int ell, co
 #pragma unroll
             for (int k = 0; k < NMAX; ++k) {
                 if (k < n) {
-                    G[k] = gr[k];
                     g1 += fabsf(gr[k]);
                     gm += fabsf(gr[k] - vf[k]);
                     gp += fabsf(gr[k] + vf[k]);
                 }
+            }
+            if (keepG) {
+#pragma unroll
+                for (int q = 0; q < NMAX / 4; ++q)
+                    if (4 * q < n) reinterpret_cast<float4*>(G)[q] = make_float4(gr[4 * q], gr[4 * q + 1], gr[4 * q + 2], gr[4 * q + 3]);
             }
         } else {
             for (int k = 0; k < n; ++k) {
@@ -820,7 +827,7 @@ __global__ void __launch_bounds__(128) k_t_project(const WideArgs a, int ell, co
 #pragma unroll
                 for (int j = 0; j < NMAX; ++j)
                     if (j < n) acc = fmaf(x[j], Pf[j * n + k], acc);
-                G[k] = acc;
+                if (keepG) G[k] = acc;
                 g1 += fabsf(acc);
                 gm += fabsf(acc - vf[k]);
                 gp += fabsf(acc + vf[k]);
