@@ -286,3 +286,26 @@ def test_tensor_core_path_random_shapes(widths, mode):
 def test_tensor_core_path_persistent_gemm(widths):
     p = wl.random_problem(hash(tuple(widths)) % 1000 + 2, widths, D=128, H=2, eps=0.15, mode=orc.MODE_CHORD)
     compare(p, gpu_bounds(p, precision=TCORE, chunk=128), orc.reach(p))
+
+
+# The staged tensor-core path in the launch configuration bench.py times for the two wide workloads
+# (16-512x4-8: the first 2048 of 262,144 sub-boxes, H = 50, two lanes of 1024 domains, persistent
+# chain GEMMs; 12-256x3-4: 4096 of the 65,536 branch domains, H = 30), checked on sampled domains
+# that span both lanes and the chunk edges, each against the oracle run on that domain alone
+# (domains are independent through every step).
+def _sampled(prob, g, idx):
+    return {"lo": g["lo"][idx], "hi": g["hi"][idx], "status": g["status"][idx], "V": g["V"][idx]}
+
+
+def test_large16_bench_configuration_sampled():
+    p = wl.large16().subset(np.arange(2048))
+    g = gpu_bounds(p)
+    idx = np.array([0, 1, 511, 1023, 1024, 1535, 2047])
+    compare(p.subset(idx), _sampled(p, g, idx), orc.reach(p.subset(idx)), check_hull=False)
+
+
+def test_branch12_bench_configuration_sampled():
+    p = wl.quadrotor_branch(only=np.arange(4096))
+    g = gpu_bounds(p)
+    idx = np.array([0, 5, 1023, 2047, 2048, 3071, 4090, 4095])
+    compare(p.subset(idx), _sampled(p, g, idx), orc.reach(p.subset(idx)), check_hull=False)
