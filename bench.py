@@ -415,14 +415,17 @@ def main():
     ms = float(ms_t.item())
     value = world * D * H / (ms * 1e-3)
 
-    # end to end through the C ABI with host buffers (copies inside the timed region)
-    hlo = np.empty((D, H + 1, n))
-    hhi = np.empty_like(hlo)
-    hhl = np.empty((H + 1, n))
-    hhh = np.empty_like(hhl)
-    hst = np.empty(D, dtype=np.uint32)
-    lo0 = np.ascontiguousarray(prob.lo)
-    hi0 = np.ascontiguousarray(prob.hi)
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    def pinned(shape, dtype):
+        return torch.empty(shape, dtype=dtype, pin_memory=True)
+
+    hlo = pinned((D, H + 1, n), torch.float64)
+    hhi = pinned((D, H + 1, n), torch.float64)
+    hhl = pinned((H + 1, n), torch.float64)
+    hhh = pinned((H + 1, n), torch.float64)
+    hst = pinned((D,), torch.int32)
+    lo0 = torch.from_numpy(np.ascontiguousarray(prob.lo, dtype=np.float64)).pin_memory()
+    hi0 = torch.from_numpy(np.ascontiguousarray(prob.hi, dtype=np.float64)).pin_memory()
 
     def e2e_step():
         r._c(r.lib.dr_set_boxes(r.ctx, D, P(lo0), P(hi0), 0))
