@@ -339,11 +339,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the refinement and wide-controller measurements")
+    ap.add_argument("--tf32-probe", action="store_true",
+                    help="only the cuBLAS TF32 8192^3 throughput probe (the denominator of the 3xTF32 path)")
     ap.add_argument("--wide-pass", nargs=2, type=int, metavar=("DOMAINS", "H"), default=None,
                     help="profiling aid: run two staged tensor-core passes on a 16-512x4-8 sample and exit")
     args = ap.parse_args()
     if args.wide_pass:
         return wide_pass(*args.wide_pass)
+    if args.tf32_probe:
+        print(json.dumps({"tf32_probe": measure_tf32_peak(0, sustain_s=0.0)}), flush=True)
+        return
     args.warmup = max(args.warmup, 3)
 
     rank = int(os.environ.get("RANK", "0"))
