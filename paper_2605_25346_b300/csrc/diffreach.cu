@@ -1216,7 +1216,8 @@ struct T2Scratch {
 static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, int lanes, int lane, float** lamA, float** lamB, float** lamC,
                      float** lamD, float** part, float** lxpart, T2Scratch* t2) {
     const NetDesc& N = a.net;
-    const size_t need = (wide_bytes_per_domain(N) * (size_t)Dc + 4 * (sizeof(float) * wide_lam_pad(N) + 256) + 4096 + 255) & ~size_t(255);
+    // + 256 B of alignment for each of the (fewer than 64) buffers carved below, whatever Dc is
+    const size_t need = (wide_bytes_per_domain(N) * (size_t)Dc + 4 * sizeof(float) * wide_lam_pad(N) + 64 * 256 + 255) & ~size_t(255);
     if (!c->wscratch || c->wscratch_bytes < need * lanes || c->wDc != Dc || c->wLanes != lanes) {
         dev_free(c, c->wscratch, c->wscratch_bytes);
         c->wscratch_bytes = 0;
