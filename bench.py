@@ -198,6 +198,28 @@ def measure_wide(local, reps=2):
     return out
 
 
+def full_large16():
+    """One pass of the staged tensor-core path over all 262,144 sub-boxes of the 16-512x4-8 workload
+    with H = 50 (about 1.1e16 FP32-equivalent FLOP), after one warm-up pass on 2048 of them."""
+    from paper_2605_25346_b300 import api
+    prob = wl.large16()
+    warm = api.Reach(0).load(prob.subset(np.arange(2048)))
+    warm.bounds(on_device=True)
+    warm.close()
+    r = api.Reach(0).load(prob)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = r.bounds(on_device=True)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    fl = fused_flops_per_domain_step(prob.widths) * prob.D * prob.H
+    finite = bool(torch.isfinite(out["lo"]).all() and torch.isfinite(out["hi"]).all())
+    print(json.dumps({"full_large16": {"domains": prob.D, "horizon": prob.H, "seconds": t,
+                                       "domain_steps_per_s": prob.D * prob.H / t, "fp32eq_tflops": fl / t / 1e12,
+                                       "all_finite": finite, "launches": r.launches()}}), flush=True)
+    r.close()
+
+
 def wide_pass(domains, horizon):
     """Two bounds passes of the staged path on the first `domains` sub-boxes of the 16-512x4-8
     workload with horizon `horizon` (a small case for kernel profiling)."""
@@ -339,6 +361,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the refinement and wide-controller measurements")
+    ap.add_argument("--full-large16", action="store_true",
+                    help="one staged pass over all 262,144 sub-boxes of the 16-512x4-8 workload (H = 50)")
     ap.add_argument("--tf32-probe", action="store_true",
                     help="only the cuBLAS TF32 8192^3 throughput probe (the denominator of the 3xTF32 path)")
     ap.add_argument("--wide-pass", nargs=2, type=int, metavar=("DOMAINS", "H"), default=None,
@@ -346,6 +370,8 @@ def main():
     args = ap.parse_args()
     if args.wide_pass:
         return wide_pass(*args.wide_pass)
+    if args.full_large16:
+        return full_large16()
     if args.tf32_probe:
         print(json.dumps({"tf32_probe": measure_tf32_peak(0, sustain_s=0.0)}), flush=True)
         return
