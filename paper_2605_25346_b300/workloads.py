@@ -420,10 +420,10 @@ def random_problem(seed: int, widths, D: int, H: int, eps: float = 0.1, mode: in
                    mode=mode)
 
 
-CONFIGS = {
-    1: double_integrator_tiny,
-    2: quad6_batched,
-    3: cartpole_diff,
-    4: quadrotor_branch,
-    5: large16,
+WORKLOADS = {
+    "double_integrator_tiny": double_integrator_tiny,
+    "quad6_batched": quad6_batched,
+    "cartpole_diff": cartpole_diff,
+    "quadrotor_branch": quadrotor_branch,
+    "large16": large16,
 }

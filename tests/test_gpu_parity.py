@@ -228,9 +228,9 @@ def test_invalid_arguments_are_errors():
 STAGED = 1  # DR_PREC_SIMT: staged path with the CUDA-core chain GEMM
 
 
-@pytest.mark.parametrize("cfg", [2, 3])
-def test_staged_path_narrow_configs(cfg):
-    p = wl.CONFIGS[cfg]()
+@pytest.mark.parametrize("name", ["quad6_batched", "cartpole_diff"])
+def test_staged_path_narrow_workloads(name):
+    p = wl.WORKLOADS[name]()
     sub = p.subset(np.arange(0, p.D, 4))
     compare(sub, gpu_bounds(sub, precision=STAGED, chunk=97), orc.reach(sub))
 
@@ -264,9 +264,9 @@ def test_large16_subset():
 TCORE = 2  # DR_PREC_TF32X3
 
 
-@pytest.mark.parametrize("cfg", [2, 3])
-def test_tensor_core_path_narrow_configs(cfg):
-    p = wl.CONFIGS[cfg]()
+@pytest.mark.parametrize("name", ["quad6_batched", "cartpole_diff"])
+def test_tensor_core_path_narrow_workloads(name):
+    p = wl.WORKLOADS[name]()
     sub = p.subset(np.arange(0, p.D, 4))
     compare(sub, gpu_bounds(sub, precision=TCORE, chunk=257), orc.reach(sub))
 

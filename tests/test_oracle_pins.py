@@ -156,12 +156,12 @@ def test_containment_double_integrator_grid():
         assert (x >= r["lo"][0, t].numpy() - 1e-12).all() and (x <= r["hi"][0, t].numpy() + 1e-12).all()
 
 
-@pytest.mark.parametrize("cfg", [2, 3])
-def test_containment_configs(cfg):
-    p = wl.CONFIGS[cfg]()
+@pytest.mark.parametrize("name", ["quad6_batched", "cartpole_diff"])
+def test_containment_workloads(name):
+    p = wl.WORKLOADS[name]()
     sub = p.subset(np.arange(0, p.D, p.D // 32))
     r = orc.reach(sub)
-    ok, n = _contained(sub, r, 10000, cfg)
+    ok, n = _contained(sub, r, 10000, {"quad6_batched": 2, "cartpole_diff": 3}[name])
     assert ok
 
 
