@@ -285,10 +285,12 @@ def test_tensor_core_path_random_shapes(widths, mode):
 # 128 x 128 tiles per SM, so the chain levels run in the persistent GEMM (epilogues overlapped with
 # the next tile).  160 rows per domain leave most row tiles spanning two domains (per-row slopes).
 # n = 4 folds the last level into the epilogue (W_1 product); n = 20 ends on a plain GEMM.
-@pytest.mark.parametrize("widths", [[4, 160, 160, 160, 160, 2], [20, 160, 160, 160, 2]])
-def test_tensor_core_path_persistent_gemm(widths):
-    p = wl.random_problem(hash(tuple(widths)) % 1000 + 2, widths, D=128, H=2, eps=0.15, mode=orc.MODE_CHORD)
-    compare(p, gpu_bounds(p, precision=TCORE, chunk=128), orc.reach(p))
+# 256-wide levels on 80 domains: 160 row tiles x 2 column tiles, also persistent.
+@pytest.mark.parametrize("widths,D", [([4, 160, 160, 160, 160, 2], 128), ([20, 160, 160, 160, 2], 128),
+                                      ([4, 256, 256, 256, 256, 2], 80), ([20, 256, 256, 256, 2], 80)])
+def test_tensor_core_path_persistent_gemm(widths, D):
+    p = wl.random_problem(hash(tuple(widths)) % 1000 + 2, widths, D=D, H=2, eps=0.15, mode=orc.MODE_CHORD)
+    compare(p, gpu_bounds(p, precision=TCORE, chunk=D), orc.reach(p))
 
 
 # The staged tensor-core path in the launch configuration bench.py times for the two wide workloads

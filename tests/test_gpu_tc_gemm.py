@@ -2,7 +2,7 @@
 
 FP32-accurate means: |C - C64| <= 2^-18 * (|A| |B|) elementwise (a single TF32 pass is off by ~2^-11).
 Shapes cover every tile width (N = 12..512), ragged M, N and K, and K not a multiple of 32; the
-three tall shapes have at least two 128 x 128 tiles per SM, which the persistent kernel takes."""
+four tall shapes have at least two 128 x 128 tiles per SM, which the persistent kernel takes."""
 import ctypes
 
 import numpy as np
@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("M,N,K", [(128, 256, 512), (300, 200, 100), (1000, 12, 256), (4096, 512, 512), (5, 16, 40),
                                    (129, 129, 33), (257, 64, 64), (640, 32, 1000),
-                                   (19000, 130, 64), (40000, 257, 96), (38000, 512, 512)])
+                                   (19000, 130, 64), (40000, 257, 96), (38000, 512, 512), (20000, 256, 160)])
 def test_tf32x3_gemm_matches_fp64(M, N, K):
     from paper_2605_25346_b300 import _lib
     lib = _lib.load()
