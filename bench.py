@@ -220,6 +220,21 @@ def full_large16():
     r.close()
 
 
+def wide_refine(domains, horizon):
+    """One projected-gradient slope step (forward with tape, reverse sweep, update) on the first
+    `domains` sub-boxes of the 16-512x4-8 workload with horizon `horizon` (a profiling case)."""
+    import dataclasses
+    from paper_2605_25346_b300 import api
+    prob = dataclasses.replace(wl.large16().subset(np.arange(domains)), H=horizon)
+    r = api.Reach(0).load(prob)
+    t0 = time.perf_counter()
+    hist = r.optimize(1, 0.1, 0.0)
+    torch.cuda.synchronize()
+    print(json.dumps({"wide_refine": {"domains": domains, "horizon": horizon, "seconds": time.perf_counter() - t0,
+                                      "V": [float(v) for v in hist], "launches": r.launches()}}), flush=True)
+    r.close()
+
+
 def wide_pass(domains, horizon):
     """Two bounds passes of the staged path on the first `domains` sub-boxes of the 16-512x4-8
     workload with horizon `horizon` (a small case for kernel profiling)."""
@@ -361,6 +376,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the refinement and wide-controller measurements")
+    ap.add_argument("--wide-refine", nargs=2, type=int, metavar=("DOMAINS", "H"), default=None,
+                    help="profiling aid: one slope-refinement step on a 16-512x4-8 sample and exit")
     ap.add_argument("--full-large16", action="store_true",
                     help="one staged pass over all 262,144 sub-boxes of the 16-512x4-8 workload (H = 50)")
     ap.add_argument("--tf32-probe", action="store_true",
@@ -370,6 +387,8 @@ def main():
     args = ap.parse_args()
     if args.wide_pass:
         return wide_pass(*args.wide_pass)
+    if args.wide_refine:
+        return wide_refine(*args.wide_refine)
     if args.full_large16:
         return full_large16()
     if args.tf32_probe:

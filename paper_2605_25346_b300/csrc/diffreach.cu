@@ -1637,7 +1637,7 @@ static int run_forward(dr_ctx* c, int mode, float* alpha_used, bool tape) {
         TRY(ensure_wpad(c, N, a.lay));
         a.gslab = c->gslab;
         a.gwpad = c->dWpad;
-        smem = 0;
+        smem = nt == 256 ? (int)(sizeof(float) * kSlabTileFloats) : 0;  // the chain products' tiles
     }
     for (int64_t d0 = 0; d0 < c->D; d0 += chunk) {
         a.d0 = d0;
@@ -1843,7 +1843,7 @@ static int launch_backward(dr_ctx* c, int mode, const double* wlo, const double*
         TRY(ensure_wpad(c, N, a.lay));
         a.gslab = c->gslab;
         a.gwpad = c->dWpad;
-        smem = 0;
+        smem = nt == 256 ? (int)(sizeof(float) * kSlabTileFloats) : 0;  // the chain products' tiles
     }
     for (int64_t d0 = 0; d0 < c->D; d0 += chunk) {
         a.d0 = d0;

@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused_backward(const FusedArgs a) {
     const FusedLayout& Y = a.lay;
     Dom s = make_dom(sm, Y);
     s.gw = a.gwpad;
+    s.tiles = (NT == 256 && a.gslab) ? reinterpret_cast<float*>(sm_dyn) : nullptr;  // slab mode: GEMM tiles
     const int tid = threadIdx.x;
     const int64_t dom = a.d0 + blockIdx.x;
     const int n = N.n, m = N.m, L = N.L, H = N.H, gld = odd_ld(n);
@@ -360,7 +361,24 @@ __global__ void __launch_bounds__(NT, 2) k_fused_backward(const FusedArgs a) {
                 float* gLnext = SMF(buf ? Y.gL1 : Y.gL0);
                 // column j of Lambda_s adjoint: sum_k gLprev[i][k] W_m[j][k] + (gklo_i + gkhi_i) b_m[j]
                 const int ncg = (K + 3) >> 2;
-                if (ncg * 2 >= NT && rows >= 4) {
+                if (NT == 256 && s.tiles && rows >= 32 && K >= 32 && NN >= 32) {
+                    // slab mode: the products through shared-memory tiles into gLnext (used as scratch
+                    // also on the last level), then per column the same epilogue as below
+                    gemm_nt_tiled256(gLprev, prev_ld, Wm, wld, gLnext, lmld, rows, K, NN, gklo, gkhi, bm, s.tiles);
+                    for (int j = tid; j < K; j += NT) {
+                        float acc_s = 0.f, acc_d = 0.f;
+                        for (int i = 0; i < rows; ++i) {
+                            const float gls = gLnext[i * lmld + j];
+                            const float x = Lm[i * lmld + j];
+                            acc_s = fmaf(gls, x, acc_s);
+                            acc_d += gkhi[i] * posf(x) + gklo[i] * negf(x);
+                            if (mm < ell - 1)
+                                gLnext[i * lmld + j] = gls * sl[j] + gkhi[i] * (x > 0.f ? dl[j] : 0.f) + gklo[i] * (x < 0.f ? dl[j] : 0.f);
+                        }
+                        gs[N.hoff[mm] + j] += acc_s;
+                        gd[N.hoff[mm] + j] += acc_d;
+                    }
+                } else if (ncg * 2 >= NT && rows >= 4) {
                     // wide level: a thread owns 4 columns and walks the rows in blocks of 4 (4 x 4
                     // register tile per block); per element the same operation order as below
                     for (int cg = tid; cg < ncg; cg += NT) {

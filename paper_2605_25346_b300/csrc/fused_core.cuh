@@ -85,6 +85,7 @@ struct Dom {
     unsigned char* sm;
     const FusedLayout* Y;
     const float* gw;  // shared padded weights in global memory (slab mode), else null
+    float* tiles;     // slab mode with 256 threads: shared-memory GEMM tiles (kSlabTileFloats), else null
     double *c, *P, *Ilo, *Ihi, *v, *wv, *cn, *Pn, *Ilon, *Ihin, *A, *B, *e;
     float *cf, *Pf, *Ilof, *Ihif, *vf, *hl, *hu, *hs, *hd, *hl0, *hu0, *klo, *khi, *G, *sa, *sRlo, *sRhi, *sS, *cu,
         *Iulo, *Iuhi, *bs;
@@ -99,6 +100,7 @@ __device__ __forceinline__ Dom make_dom(unsigned char* sm, const FusedLayout& Y)
     s.sm = sm;
     s.Y = &Y;
     s.gw = nullptr;
+    s.tiles = nullptr;
     s.c = SMD(Y.c);
     s.P = SMD(Y.P);
     s.Ilo = SMD(Y.Ilo);
@@ -249,7 +251,9 @@ __device__ const float* chain(const Dom& s, const NetDesc& N, int ell, float* le
         const int nld = odd_ld(NN);
         // nxt[i][k] = sum_j (row_i[j] s_j) W_m[j][k]: register tiles when they still give every
         // thread of the CTA work (wide levels), one element per thread otherwise
-        if (((rows + 3) >> 2) * ((NN + 3) >> 2) >= NT)
+        if (NT == 256 && s.tiles && rows >= 32 && K >= 32 && NN >= 32)
+            gemm_nn_scaled_tiled256(cur, cur_ld, sl, Wm, wld, nxt, nld, rows, K, NN, s.tiles);
+        else if (((rows + 3) >> 2) * ((NN + 3) >> 2) >= NT)
             gemm_stacked_scaled_t<NT, 4>(cur, 0, cur_ld, sl, 0, Wm, wld, nxt, nld, 1, rows, K, NN);
         else if (rows * ((NN + 3) >> 2) >= NT)
             gemm_stacked_scaled_t<NT, 1>(cur, 0, cur_ld, sl, 0, Wm, wld, nxt, nld, 1, rows, K, NN);
@@ -497,6 +501,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused_forward(const FusedArgs a) {
     const NetDesc& N = a.net;
     Dom s = make_dom(sm, a.lay);
     s.gw = a.gwpad;
+    s.tiles = (NT == 256 && a.gslab) ? reinterpret_cast<float*>(sm_dyn) : nullptr;  // slab mode: GEMM tiles
     const int tid = threadIdx.x;
     const int64_t dom = a.d0 + blockIdx.x;
     const int n = N.n, H = N.H;
