@@ -132,59 +132,66 @@ __device__ __forceinline__ void gemm_stacked_scaled(const float* __restrict__ Ab
 
 
 // ---- slab mode (fused kernels whose working set lives in global memory, 256 threads): the wide
-// products are staged through shared-memory tiles (kSlabTileFloats floats of dynamic shared memory)
-constexpr int kSlabTileFloats = 2 * 32 * 68;
+// products are staged through shared-memory tiles (kSlabTileFloats floats of dynamic shared memory):
+// 128 x 128 outputs per pass, an 8 x 8 register tile per thread (rows 4ty..4ty+3 and 64+4ty..,
+// columns likewise), K in slices of 32 held transposed ([k][row], rows padded to 132 floats).
+constexpr int kSlabLd = 132;
+constexpr int kSlabTileFloats = 2 * 32 * kSlabLd;
 
-// Slab mode (the working set in global memory): C[i][j] = (glo_i + ghi_i) b_j + sum_k A[i][k] B[j][k]
-// for i < M, j < N, through shared-memory tiles: 64 x 64 outputs per pass, a 4 x 4 register tile per
-// thread, K in slices of 32 staged transposed in `tiles` (2 x 32 x 68 floats).  Per element the
-// same operations in the same order as the register-tiled loop of the wide levels (the intercept
-// term first, then k ascending), so the results are identical; only the loads change.
+__device__ __forceinline__ void slab_tile_fma(const float* At, const float* Bt, int kn, float (&acc)[8][8], int ty, int tx) {
+    for (int kk = 0; kk < kn; ++kk) {
+        const float4 a0 = *reinterpret_cast<const float4*>(At + kk * kSlabLd + 4 * ty);
+        const float4 a1 = *reinterpret_cast<const float4*>(At + kk * kSlabLd + 64 + 4 * ty);
+        const float4 b0 = *reinterpret_cast<const float4*>(Bt + kk * kSlabLd + 4 * tx);
+        const float4 b1 = *reinterpret_cast<const float4*>(Bt + kk * kSlabLd + 64 + 4 * tx);
+        const float ar[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float br[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[r][q] = fmaf(ar[r], br[q], acc[r][q]);
+    }
+}
+__device__ __forceinline__ int slab_row(int base, int ty, int r) { return base + (r < 4 ? 4 * ty + r : 64 + 4 * ty + r - 4); }
 
+// C[i][j] = (glo_i + ghi_i) b_j + sum_k A[i][k] B[j][k] for i < M, j < N (A [M][Kd], B [N][Kd]).  Per
+// element the same operations in the same order as the register-tiled loop of the reverse sweep's
+// wide levels (the intercept term first, then k ascending), so the results are identical.
 __device__ __forceinline__ void gemm_nt_tiled256(const float* A, int lda, const float* B, int ldb, float* C, int ldc, int M,
                                                  int N, int Kd, const float* glo, const float* ghi, const float* bvec,
                                                  float* tiles) {
-    float* At = tiles;            // [32][68]: At[kk][ii] = A[mt + ii][k0 + kk]
-    float* Bt = tiles + 32 * 68;  // [32][68]: Bt[kk][jj] = B[nt + jj][k0 + kk]
+    float* At = tiles;                // At[kk][ii] = A[mt + ii][k0 + kk]
+    float* Bt = tiles + 32 * kSlabLd;  // Bt[kk][jj] = B[nt + jj][k0 + kk]
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    for (int mt = 0; mt < M; mt += 64) {
-        for (int nt = 0; nt < N; nt += 64) {
-            float acc[4][4];
+    for (int mt = 0; mt < M; mt += 128) {
+        for (int nt = 0; nt < N; nt += 128) {
+            float acc[8][8];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int i = min(mt + 4 * ty + r, M - 1);
+            for (int r = 0; r < 8; ++r) {
+                const int i = min(slab_row(mt, ty, r), M - 1);
                 const float gk = glo[i] + ghi[i];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[r][q] = gk * bvec[min(nt + 4 * tx + q, N - 1)];
+                for (int q = 0; q < 8; ++q) acc[r][q] = gk * bvec[min(slab_row(nt, tx, q), N - 1)];
             }
             for (int k0 = 0; k0 < Kd; k0 += 32) {
                 __syncthreads();  // the previous slice (or tile) is no longer read
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
+#pragma unroll 4
+                for (int u = 0; u < 16; ++u) {
                     const int idx = tid + 256 * u, ii = idx >> 5, kk = idx & 31;
                     const bool kin = k0 + kk < Kd;
-                    At[kk * 68 + ii] = (kin && mt + ii < M) ? A[(int64_t)(mt + ii) * lda + k0 + kk] : 0.f;
-                    Bt[kk * 68 + ii] = (kin && nt + ii < N) ? B[(int64_t)(nt + ii) * ldb + k0 + kk] : 0.f;
+                    At[kk * kSlabLd + ii] = (kin && mt + ii < M) ? A[(int64_t)(mt + ii) * lda + k0 + kk] : 0.f;
+                    Bt[kk * kSlabLd + ii] = (kin && nt + ii < N) ? B[(int64_t)(nt + ii) * ldb + k0 + kk] : 0.f;
                 }
                 __syncthreads();
-                const int kn = min(32, Kd - k0);
-                for (int kk = 0; kk < kn; ++kk) {
-                    const float4 av = *reinterpret_cast<const float4*>(At + kk * 68 + 4 * ty);
-                    const float4 bv = *reinterpret_cast<const float4*>(Bt + kk * 68 + 4 * tx);
-                    const float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-                    for (int r = 0; r < 4; ++r)
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(ar[r], br[q], acc[r][q]);
-                }
+                slab_tile_fma(At, Bt, min(32, Kd - k0), acc, ty, tx);
             }
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int i = mt + 4 * ty + r;
-                if (i >= M) break;
+            for (int r = 0; r < 8; ++r) {
+                const int i = slab_row(mt, ty, r);
+                if (i >= M) continue;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int j = nt + 4 * tx + q;
+                for (int q = 0; q < 8; ++q) {
+                    const int j = slab_row(nt, tx, q);
                     if (j < N) C[(int64_t)i * ldc + j] = acc[r][q];
                 }
             }
@@ -193,50 +200,40 @@ __device__ __forceinline__ void gemm_nt_tiled256(const float* A, int lda, const 
     __syncthreads();
 }
 
-// Slab mode: C[i][k] = sum_j (A[i][j] s_j) B[j][k] for i < M, k < N, j < Kd (B row-major [Kd][N]) through
-// the same shared-memory tiles; per element the same operations and order as gemm_stacked_scaled_t
-// (the scaled A value formed first, k ascending from 0).
+// C[i][k] = sum_j (A[i][j] s_j) B[j][k] for i < M, k < N, j < Kd (B row-major [Kd][N]); per element the
+// same operations and order as gemm_stacked_scaled_t (the scaled A value formed first, j ascending).
 __device__ __forceinline__ void gemm_nn_scaled_tiled256(const float* A, int lda, const float* sv, const float* B, int ldb,
                                                         float* C, int ldc, int M, int Kd, int N, float* tiles) {
-    float* At = tiles;            // [32][68]: At[kk][ii] = A[mt + ii][k0 + kk] s[k0 + kk]
-    float* Bt = tiles + 32 * 68;  // [32][68]: Bt[kk][jj] = B[k0 + kk][nt + jj]
+    float* At = tiles;                // At[kk][ii] = A[mt + ii][k0 + kk] s[k0 + kk]
+    float* Bt = tiles + 32 * kSlabLd;  // Bt[kk][jj] = B[k0 + kk][nt + jj]
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    for (int mt = 0; mt < M; mt += 64) {
-        for (int nt = 0; nt < N; nt += 64) {
-            float acc[4][4];
+    for (int mt = 0; mt < M; mt += 128) {
+        for (int nt = 0; nt < N; nt += 128) {
+            float acc[8][8];
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+            for (int r = 0; r < 8; ++r)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
+                for (int q = 0; q < 8; ++q) acc[r][q] = 0.f;
             for (int k0 = 0; k0 < Kd; k0 += 32) {
                 __syncthreads();  // the previous slice (or tile) is no longer read
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
+#pragma unroll 4
+                for (int u = 0; u < 16; ++u) {
                     const int idx = tid + 256 * u;
                     const int ii = idx >> 5, ka = idx & 31;
-                    At[ka * 68 + ii] = (k0 + ka < Kd && mt + ii < M) ? A[(int64_t)(mt + ii) * lda + k0 + ka] * sv[k0 + ka] : 0.f;
-                    const int kb = idx >> 6, jj = idx & 63;
-                    Bt[kb * 68 + jj] = (k0 + kb < Kd && nt + jj < N) ? B[(int64_t)(k0 + kb) * ldb + nt + jj] : 0.f;
+                    At[ka * kSlabLd + ii] = (k0 + ka < Kd && mt + ii < M) ? A[(int64_t)(mt + ii) * lda + k0 + ka] * sv[k0 + ka] : 0.f;
+                    const int kb = idx >> 7, jj = idx & 127;
+                    Bt[kb * kSlabLd + jj] = (k0 + kb < Kd && nt + jj < N) ? B[(int64_t)(k0 + kb) * ldb + nt + jj] : 0.f;
                 }
                 __syncthreads();
-                const int kn = min(32, Kd - k0);
-                for (int kk = 0; kk < kn; ++kk) {
-                    const float4 av = *reinterpret_cast<const float4*>(At + kk * 68 + 4 * ty);
-                    const float4 bv = *reinterpret_cast<const float4*>(Bt + kk * 68 + 4 * tx);
-                    const float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-                    for (int r = 0; r < 4; ++r)
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(ar[r], br[q], acc[r][q]);
-                }
+                slab_tile_fma(At, Bt, min(32, Kd - k0), acc, ty, tx);
             }
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int i = mt + 4 * ty + r;
-                if (i >= M) break;
+            for (int r = 0; r < 8; ++r) {
+                const int i = slab_row(mt, ty, r);
+                if (i >= M) continue;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int k = nt + 4 * tx + q;
+                for (int q = 0; q < 8; ++q) {
+                    const int k = slab_row(nt, tx, q);
                     if (k < N) C[(int64_t)i * ldc + k] = acc[r][q];
                 }
             }
