@@ -116,6 +116,23 @@ def measure_wide_refinement(local):
         t = time.perf_counter() - t0
         out[name] = {"alpha_opt_steps_per_s": steps / t, "domain_steps_per_s": prob.D * prob.H * steps / t,
                      "V_first": float(hist[0]), "V_best": float(hist[-1])}
+        if name.startswith("branch12"):
+            # batched vs plain (one domain per call, same steps and rates) on a sample of the domains
+            Vb = r.objective()
+            sample = 4
+            tp, Vp = 0.0, []
+            for d in range(sample):
+                rr = api.Reach(local).load(prob.subset([d]))
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                rr.optimize(steps, 0.1, lrb)
+                tp += time.perf_counter() - t1
+                Vp.append(rr.objective()[0])
+                rr.close()
+            out[name].update({"batched_domains_per_s": prob.D / t, "plain_domains_per_s": sample / tp,
+                              "plain_sample_domains": sample, "batched_over_plain": (prob.D / t) / (sample / tp),
+                              "max_rel_V_gap_batched_vs_plain": float(np.max(np.abs(np.array(Vp) - Vb[:sample]) /
+                                                                              np.abs(Vb[:sample])))})
         r.close()
     return out
 
