@@ -82,7 +82,9 @@ typedef struct dr_options {
                               (pre-activation bounds, controller remainder, split constraint)
                               is widened by rho * S, S the L1 magnitude of its summed terms.
                               Default 0: such margins compound through the closed loop.      */
-    int64_t chunk_domains; /* domains per device pass (bounds scratch memory); 0 = automatic    */
+    int64_t chunk_domains; /* domains per device pass of the staged path (bounds its scratch);
+                              0 = automatic: as many as 16 GiB of scratch holds, at most a quarter
+                              of the free device memory and within mem_cap_bytes              */
     int64_t mem_cap_bytes; /* cap on library-owned device memory; 0 = no cap                    */
     double box_margin;     /* outward margin of every reported box: lo -= b*S_box, hi += b*S_box,
                               S_box = |c| + sum|P| + |I| + |w| + sum|v| of the FP64 Taylor model;
