@@ -212,6 +212,10 @@ def measure_wide(local, reps=2):
                                    f"{basis} x 1.1/2.25 (nominal ratio); a pass of H={prob.H} steps is a "
                                    f"long, power-capped run, so the sustained figure is the relevant one"}
         r.close()
+        # the FP64 oracle on the host cores, on the first domains of the same sample (bounded time)
+        cpu = oracle_baseline(prob, target_s=5.0, max_domains=4 if prob.widths[1] >= 512 else 32)
+        out[name]["cpu_baseline"] = cpu
+        out[name]["gpu_over_cpu"] = out[name]["domain_steps_per_s"] / cpu["value"]
     return out
 
 
