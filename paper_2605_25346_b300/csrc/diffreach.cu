@@ -505,6 +505,19 @@ static int sm_count() {
     return n;
 }
 
+// The persistent kernel's warpgroup register split needs exactly the registers it was designed for
+// at entry; a build that compiled it otherwise keeps the one-tile-per-CTA kernel.
+template <int EPI>
+static bool persistent_gemm_usable() {
+    static int ok = -1;
+    if (ok < 0) {
+        cudaFuncAttributes fa;
+        ok = cudaFuncGetAttributes(&fa, tc::k_tc_gemm_pp<EPI>) == cudaSuccess && fa.numRegs == tc::kRegsLaunch;
+        cudaGetLastError();
+    }
+    return ok == 1;
+}
+
 // 128-column GEMMs with at least two tiles per SM run persistently (one CTA per SM, the epilogue of
 // one tile overlapped with the main loop of the next).
 template <int EPI>
@@ -512,10 +525,6 @@ static int launch_tc_gemm_persistent(dr_ctx* c, const CUtensorMap* m, float* C, 
                                      cudaStream_t st, const tc::ChainEpi& epi, int64_t tiles, int nsm) {
     const int smem = tc::pp_smem_bytes();
     CUDA_TRY(c, cudaFuncSetAttribute(tc::k_tc_gemm_pp<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    cudaFuncAttributes fa;
-    CUDA_TRY(c, cudaFuncGetAttributes(&fa, tc::k_tc_gemm_pp<EPI>));
-    // the warpgroup register split needs exactly the registers it was designed for at entry
-    if (fa.numRegs != tc::kRegsLaunch) return fail(c, DR_ERR_STATE, "persistent GEMM compiled with %d registers", fa.numRegs);
     const int grid = (int)std::min<int64_t>(tiles, nsm);
     tc::k_tc_gemm_pp<EPI><<<grid, tc::kPersistThreads, smem, st>>>(m[0], m[1], m[2], m[3], C, R, K, N, ldc, err, epi);
     CUDA_TRY(c, cudaGetLastError());
@@ -550,9 +559,12 @@ static int tc_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* BTh
         const int nsm = sm_count();
         const int64_t tiles = ((int64_t)(R + tc::BM - 1) / tc::BM) * ((N + 127) / 128);
         if (tiles >= 2 * (int64_t)nsm && tiles <= 0x7fffffffll) {
-            if (!epi) return launch_tc_gemm_persistent<0>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm);
-            return epi->W1 ? launch_tc_gemm_persistent<2>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm)
-                           : launch_tc_gemm_persistent<1>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm);
+            if (!epi && persistent_gemm_usable<0>())
+                return launch_tc_gemm_persistent<0>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm);
+            if (epi && epi->W1 && persistent_gemm_usable<2>())
+                return launch_tc_gemm_persistent<2>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm);
+            if (epi && !epi->W1 && persistent_gemm_usable<1>())
+                return launch_tc_gemm_persistent<1>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm);
         }
     }
 #define DR_TC_CASE(bn)                                                                                        \
