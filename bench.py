@@ -105,7 +105,9 @@ def measure_wide_refinement(local):
             ("branch12 12-256x3-4, 256 of 65536 branch domains, H=30, alpha+beta", wl.quadrotor_branch(only=np.arange(256)),
              2, 0.005),
             ("large16 16-512x4-8, 148 of 262144 sub-boxes, H=10 (one domain per SM), alpha",
-             dataclasses.replace(wl.large16().subset(np.arange(148)), H=10), 2, 0.0)):
+             dataclasses.replace(wl.large16().subset(np.arange(148)), H=10), 2, 0.0),
+            ("large16 16-512x4-8, 296 of 262144 sub-boxes, H=10 (two domains per SM), alpha",
+             dataclasses.replace(wl.large16().subset(np.arange(296)), H=10), 2, 0.0)):
         r = api.Reach(local).load(prob)
         r.optimize(1, 0.1, lrb)  # warm-up: slabs, tape and gradient buffers
         r.close()

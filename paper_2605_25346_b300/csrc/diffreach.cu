@@ -1552,8 +1552,13 @@ static int ensure_wpad(dr_ctx* c, const NetDesc& N, const FusedLayout& Y) {
 }
 
 // Domains per launch and the slab buffer for running the fused kernels out of global memory.
+// Slab budget: 8 GiB (enough for two CTAs per SM of the widest controllers), at most a quarter of the
+// free device memory (the context's own slabs counted as free), never below 1 GiB.
 static int slab_chunk(dr_ctx* c, size_t per_cta, int64_t* chunk) {
-    const size_t budget = size_t(2) << 30;
+    size_t budget = size_t(8) << 30;
+    size_t free_b = 0, all_b = 0;
+    if (cudaMemGetInfo(&free_b, &all_b) == cudaSuccess) budget = std::min(budget, (free_b + c->gslab_bytes) / 4);
+    budget = std::max(budget, size_t(1) << 30);
     int64_t ch = std::max<int64_t>(1, std::min<int64_t>(c->D, (int64_t)(budget / std::max<size_t>(per_cta, 1))));
     ch = std::min<int64_t>(ch, 4 * 148);
     const size_t need = (size_t)ch * per_cta;
