@@ -134,25 +134,94 @@ __device__ __forceinline__ void gemm_stacked_scaled(const float* __restrict__ Ab
 // ---- slab mode (fused kernels whose working set lives in global memory, 256 threads): the wide
 // products are staged through shared-memory tiles (kSlabTileFloats floats of dynamic shared memory):
 // 128 x 128 outputs per pass, an 8 x 8 register tile per thread (rows 4ty..4ty+3 and 64+4ty..,
-// columns likewise), K in slices of 32 held transposed ([k][row], rows padded to 132 floats).
+// columns likewise), K in slices of 32 held transposed ([k][row], rows padded to 132 floats), two
+// slices in flight: the next slice is copied element by element with cp.async (the slab rows are
+// odd-padded, so 4-byte copies) while the current one is multiplied.
 constexpr int kSlabLd = 132;
-constexpr int kSlabTileFloats = 2 * 32 * kSlabLd;
+constexpr int kSlabStage = 2 * 32 * kSlabLd + 32;  // A slice, B slice, 32 slopes
+constexpr int kSlabTileFloats = 2 * kSlabStage;
 
-__device__ __forceinline__ void slab_tile_fma(const float* At, const float* Bt, int kn, float (&acc)[8][8], int ty, int tx) {
-    for (int kk = 0; kk < kn; ++kk) {
-        const float4 a0 = *reinterpret_cast<const float4*>(At + kk * kSlabLd + 4 * ty);
-        const float4 a1 = *reinterpret_cast<const float4*>(At + kk * kSlabLd + 64 + 4 * ty);
-        const float4 b0 = *reinterpret_cast<const float4*>(Bt + kk * kSlabLd + 4 * tx);
-        const float4 b1 = *reinterpret_cast<const float4*>(Bt + kk * kSlabLd + 64 + 4 * tx);
-        const float ar[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        const float br[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-        for (int r = 0; r < 8; ++r)
-#pragma unroll
-            for (int q = 0; q < 8; ++q) acc[r][q] = fmaf(ar[r], br[q], acc[r][q]);
-    }
+__device__ __forceinline__ void slab_cp4(float* dst, const float* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
 }
+__device__ __forceinline__ void slab_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void slab_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void slab_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ int slab_row(int base, int ty, int r) { return base + (r < 4 ? 4 * ty + r : 64 + 4 * ty + r - 4); }
+
+// One 128 x 128 output tile, K streamed in slices of 32 through two stages.  NN: C = (A diag(s)) B with
+// B [Kd][N] row-major, the scaled value a * s formed before its multiply-add; NT: C = A B^T with B
+// [N][Kd].  acc is initialised by the caller; per element the multiply-adds run over k ascending.
+template <bool NN>
+__device__ __forceinline__ void slab_tile(const float* A, int lda, const float* sv, const float* B, int ldb, int M, int N,
+                                          int Kd, int mt, int nt, float* tiles, float (&acc)[8][8]) {
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    auto stage = [&](int buf, int k0) {
+        float* At = tiles + buf * kSlabStage;
+        float* Bt = At + 32 * kSlabLd;
+        float* St = Bt + 32 * kSlabLd;
+#pragma unroll 4
+        for (int u = 0; u < 16; ++u) {
+            const int idx = tid + 256 * u;
+            const int ii = idx >> 5, ka = idx & 31;
+            float* da = At + ka * kSlabLd + ii;
+            if (k0 + ka < Kd && mt + ii < M) slab_cp4(da, A + (int64_t)(mt + ii) * lda + k0 + ka);
+            else *da = 0.f;
+            if constexpr (NN) {
+                const int kb = idx >> 7, jj = idx & 127;
+                float* db = Bt + kb * kSlabLd + jj;
+                if (k0 + kb < Kd && nt + jj < N) slab_cp4(db, B + (int64_t)(k0 + kb) * ldb + nt + jj);
+                else *db = 0.f;
+            } else {
+                float* db = Bt + ka * kSlabLd + ii;
+                if (k0 + ka < Kd && nt + ii < N) slab_cp4(db, B + (int64_t)(nt + ii) * ldb + k0 + ka);
+                else *db = 0.f;
+            }
+        }
+        if constexpr (NN) {
+            if (tid < 32) {
+                if (k0 + tid < Kd) slab_cp4(St + tid, sv + k0 + tid);
+                else St[tid] = 0.f;
+            }
+        }
+        slab_commit();
+    };
+    const int ns = (Kd + 31) >> 5;
+    __syncthreads();  // both stages free (previous tile or caller)
+    stage(0, 0);
+    for (int sidx = 0; sidx < ns; ++sidx) {
+        if (sidx + 1 < ns) {
+            stage((sidx + 1) & 1, (sidx + 1) * 32);
+            slab_wait_all_but_one();
+        } else {
+            slab_wait_all();
+        }
+        __syncthreads();  // slice sidx visible to every thread
+        const float* At = tiles + (sidx & 1) * kSlabStage;
+        const float* Bt = At + 32 * kSlabLd;
+        const float* St = Bt + 32 * kSlabLd;
+        const int kn = min(32, Kd - sidx * 32);
+        for (int kk = 0; kk < kn; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(At + kk * kSlabLd + 4 * ty);
+            const float4 a1 = *reinterpret_cast<const float4*>(At + kk * kSlabLd + 64 + 4 * ty);
+            const float4 b0 = *reinterpret_cast<const float4*>(Bt + kk * kSlabLd + 4 * tx);
+            const float4 b1 = *reinterpret_cast<const float4*>(Bt + kk * kSlabLd + 64 + 4 * tx);
+            float ar[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            if constexpr (NN) {
+                const float s = St[kk];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) ar[r] = ar[r] * s;
+            }
+            const float br[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc[r][q] = fmaf(ar[r], br[q], acc[r][q]);
+        }
+        __syncthreads();  // slice sidx no longer read: its stage may be refilled
+    }
+    slab_wait_all();  // nothing left in flight (also when Kd == 0)
+}
 
 // C[i][j] = (glo_i + ghi_i) b_j + sum_k A[i][k] B[j][k] for i < M, j < N (A [M][Kd], B [N][Kd]).  Per
 // element the same operations in the same order as the register-tiled loop of the reverse sweep's
@@ -160,8 +229,6 @@ __device__ __forceinline__ int slab_row(int base, int ty, int r) { return base +
 __device__ __forceinline__ void gemm_nt_tiled256(const float* A, int lda, const float* B, int ldb, float* C, int ldc, int M,
                                                  int N, int Kd, const float* glo, const float* ghi, const float* bvec,
                                                  float* tiles) {
-    float* At = tiles;                // At[kk][ii] = A[mt + ii][k0 + kk]
-    float* Bt = tiles + 32 * kSlabLd;  // Bt[kk][jj] = B[nt + jj][k0 + kk]
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
     for (int mt = 0; mt < M; mt += 128) {
         for (int nt = 0; nt < N; nt += 128) {
@@ -173,18 +240,7 @@ __device__ __forceinline__ void gemm_nt_tiled256(const float* A, int lda, const 
 #pragma unroll
                 for (int q = 0; q < 8; ++q) acc[r][q] = gk * bvec[min(slab_row(nt, tx, q), N - 1)];
             }
-            for (int k0 = 0; k0 < Kd; k0 += 32) {
-                __syncthreads();  // the previous slice (or tile) is no longer read
-#pragma unroll 4
-                for (int u = 0; u < 16; ++u) {
-                    const int idx = tid + 256 * u, ii = idx >> 5, kk = idx & 31;
-                    const bool kin = k0 + kk < Kd;
-                    At[kk * kSlabLd + ii] = (kin && mt + ii < M) ? A[(int64_t)(mt + ii) * lda + k0 + kk] : 0.f;
-                    Bt[kk * kSlabLd + ii] = (kin && nt + ii < N) ? B[(int64_t)(nt + ii) * ldb + k0 + kk] : 0.f;
-                }
-                __syncthreads();
-                slab_tile_fma(At, Bt, min(32, Kd - k0), acc, ty, tx);
-            }
+            slab_tile<false>(A, lda, nullptr, B, ldb, M, N, Kd, mt, nt, tiles, acc);
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
                 const int i = slab_row(mt, ty, r);
@@ -204,8 +260,6 @@ __device__ __forceinline__ void gemm_nt_tiled256(const float* A, int lda, const 
 // same operations and order as gemm_stacked_scaled_t (the scaled A value formed first, j ascending).
 __device__ __forceinline__ void gemm_nn_scaled_tiled256(const float* A, int lda, const float* sv, const float* B, int ldb,
                                                         float* C, int ldc, int M, int Kd, int N, float* tiles) {
-    float* At = tiles;                // At[kk][ii] = A[mt + ii][k0 + kk] s[k0 + kk]
-    float* Bt = tiles + 32 * kSlabLd;  // Bt[kk][jj] = B[k0 + kk][nt + jj]
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
     for (int mt = 0; mt < M; mt += 128) {
         for (int nt = 0; nt < N; nt += 128) {
@@ -214,19 +268,7 @@ __device__ __forceinline__ void gemm_nn_scaled_tiled256(const float* A, int lda,
             for (int r = 0; r < 8; ++r)
 #pragma unroll
                 for (int q = 0; q < 8; ++q) acc[r][q] = 0.f;
-            for (int k0 = 0; k0 < Kd; k0 += 32) {
-                __syncthreads();  // the previous slice (or tile) is no longer read
-#pragma unroll 4
-                for (int u = 0; u < 16; ++u) {
-                    const int idx = tid + 256 * u;
-                    const int ii = idx >> 5, ka = idx & 31;
-                    At[ka * kSlabLd + ii] = (k0 + ka < Kd && mt + ii < M) ? A[(int64_t)(mt + ii) * lda + k0 + ka] * sv[k0 + ka] : 0.f;
-                    const int kb = idx >> 7, jj = idx & 127;
-                    Bt[kb * kSlabLd + jj] = (k0 + kb < Kd && nt + jj < N) ? B[(int64_t)(k0 + kb) * ldb + nt + jj] : 0.f;
-                }
-                __syncthreads();
-                slab_tile_fma(At, Bt, min(32, Kd - k0), acc, ty, tx);
-            }
+            slab_tile<true>(A, lda, sv, B, ldb, M, N, Kd, mt, nt, tiles, acc);
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
                 const int i = slab_row(mt, ty, r);
