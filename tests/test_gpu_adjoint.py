@@ -122,6 +122,18 @@ def test_dalpha_wide_controller():
     _grad_close(ga, ga_o.numpy())
 
 
+def test_dalpha_wide_controller_three_hidden_ragged():
+    # three hidden layers of widths that are no multiple of the 128 x 128 tiles or the 32-wide K
+    # slices of the slab kernels' shared-memory products
+    p = wl.random_problem(66, [3, 200, 150, 130, 2], D=4, H=3, eps=0.2)
+    alpha = _interior_alpha(p, 6)
+    _, ga_o, _ = orc.value_and_grad(p, alpha)
+    r = _api().Reach(0).load(p)
+    r.set_alpha(alpha.float().numpy())
+    ga, _ = r.backward()
+    _grad_close(ga, ga_o.numpy())
+
+
 def test_branch12_gradients_subset():
     import dataclasses
     p = dataclasses.replace(wl.quadrotor_branch(only=np.arange(4)), H=4)
