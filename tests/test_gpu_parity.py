@@ -354,3 +354,13 @@ def test_dead_and_saturated_layers(precision):
 def test_single_domain_single_step(precision):
     p = wl.random_problem(24, [3, 33, 2], D=1, H=1, eps=0.3)
     compare(p, gpu_bounds(p, precision=precision), orc.reach(p))
+
+
+def test_large16_all_sub_boxes_one_step_sampled():
+    # every one of the 262,144 sub-boxes in one call (the largest domain count of the workloads; many
+    # lane chunks of the staged path), one step, checked on domains spread over the whole range
+    import dataclasses
+    p = dataclasses.replace(wl.large16(), H=1)
+    g = gpu_bounds(p)
+    idx = np.array([0, 1, 65535, 131072, 199999, 262142, 262143])
+    compare(p.subset(idx), _sampled(p, g, idx), orc.reach(p.subset(idx)), check_hull=False)
