@@ -173,6 +173,8 @@ static dr_options default_options() {
 // fused-path layout
 // ------------------------------------------------------------------------------------------------
 
+static const int kMaxSmem = 227 * 1024;
+
 static FusedLayout fused_layout(const NetDesc& N, bool backward = false) {
     FusedLayout Y;
     memset(&Y, 0, sizeof(Y));
@@ -269,6 +271,11 @@ static FusedLayout fused_layout(const NetDesc& N, bool backward = false) {
         Y.gRhi = take(sizeof(float) * N.maxw);
         Y.gL0 = take(sizeof(float) * gl);
         Y.gL1 = take(sizeof(float) * gl);
+        if (((off + 15) & ~size_t(15)) > (size_t)kMaxSmem) {
+            // slab mode anyway: keep every target's levels and kappa of the replayed step
+            Y.levall = take(sizeof(float) * std::max(levall_offset(N, N.L + 1), 1));
+            Y.kall = take(sizeof(float) * 2 * kall_total(N));
+        }
     }
     Y.total = (int)((off + 15) & ~size_t(15));
     return Y;
@@ -352,7 +359,6 @@ static MultiLayout multi_layout(const NetDesc& N, int G) {
     return Y;
 }
 
-static const int kMaxSmem = 227 * 1024;
 
 // Shared-memory layout of the warp-per-domain kernel (two hidden layers), WPC warps per CTA.
 static bool warp_applicable(const NetDesc& N) {

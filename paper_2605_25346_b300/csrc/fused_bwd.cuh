@@ -64,6 +64,8 @@ __global__ void __launch_bounds__(NT, 2) k_fused_backward(const FusedArgs a) {
     float* gRhi = SMF(Y.gRhi);
     float* vsnap = SMF(Y.vsnap);
     float* lev = SMF(Y.lev);
+    float* levall = Y.levall ? SMF(Y.levall) : nullptr;  // slab mode: every target's levels of the step
+    float* kall = Y.kall ? SMF(Y.kall) : nullptr;
 
     load_params<NT>(s, a);
     for (int idx = tid; idx < n * n; idx += NT) gPn[idx] = 0.0;
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused_backward(const FusedArgs a) {
         __syncthreads();
         const int cursor0 = s.misc[0];
         tm_view<NT>(s, n);
-        controller_pass<NT>(s, N, a, dom, sp_end, t, vsnap);
+        controller_pass<NT>(s, N, a, dom, sp_end, t, vsnap, levall, kall);
         dynamics<NT>(s, N);
 
         // ---- EvalInt of box t+1 (uses the dual state after step t)
@@ -179,7 +181,22 @@ __global__ void __launch_bounds__(NT, 2) k_fused_backward(const FusedArgs a) {
         for (int ell = L; ell >= 1; --ell) {
             const int rows = N.w[ell];
             int ld;
-            const float* cur = chain<NT>(s, N, ell, lev, &ld);
+            const float* cur;
+            float* levp = lev;  // this target's chain levels
+            if (levall) {
+                // kept by the replayed controller pass: no second evaluation of the chain
+                if (ell >= 2) levp = levall + levall_offset(N, ell);
+                cur = ell >= 2 ? levp + lev_offset(N, ell, 0) : s.W(0);
+                ld = odd_ld(N.w[0]);
+                const int ko = kall_offset(N, ell), kt = kall_total(N);
+                for (int i = tid; i < rows; i += NT) {
+                    s.klo[i] = kall[ko + i];
+                    s.khi[i] = kall[kt + ko + i];
+                }
+                __syncthreads();
+            } else {
+                cur = chain<NT>(s, N, ell, lev, &ld);
+            }
             if (ell < L) {
                 for (int k = tid; k <= n; k += NT) s.vf[k] = vsnap[ell * (n + 1) + k];
                 __syncthreads();
@@ -353,7 +370,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused_backward(const FusedArgs a) {
                 const int K = N.w[mm], NN = N.w[mm - 1];
                 const float* Wm = s.W(mm - 1);
                 const int wld = odd_ld(NN);
-                const float* Lm = (mm == ell - 1) ? s.W(ell - 1) : (lev + lev_offset(N, ell, mm));
+                const float* Lm = (mm == ell - 1) ? s.W(ell - 1) : (levp + lev_offset(N, ell, mm));
                 const int lmld = odd_ld(K);
                 const float* sl = s.hs + N.hoff[mm];
                 const float* dl = s.hd + N.hoff[mm];

@@ -29,6 +29,7 @@ struct FusedLayout {  // byte offsets into dynamic shared memory
     // reverse kernel only
     int vsnap;                   // [L][n+1] floats: dual vector seen by each hidden layer
     int lev;                     // chain levels of one target (offsets from lev_offset)
+    int levall, kall;            // slab mode: every target's levels and kappa of one step (0: not kept)
     int gc, gP, gIlo, gIhi;      // adjoint of TM_t (double)
     int gcn, gPn, gIlon, gIhin;  // adjoint of TM_{t+1} (double)
     int gPu, gcu, gIulo, gIuhi;  // adjoint of the controller TM (double)
@@ -194,6 +195,21 @@ __host__ __device__ __forceinline__ int lev_offset(const NetDesc& N, int ell, in
     for (int q = 0; q < k; ++q) off += N.w[ell] * odd_ld(N.w[q]);
     return off;
 }
+
+// Slab mode keeps one step's chain levels of every target (levall) and their kappa (kall), so the
+// reverse sweep need not evaluate each chain a second time: target ell's levels start at
+// levall_offset(N, ell) floats; its kappa_lo at kall_offset(N, ell), kappa_hi kall_total(N) later.
+__host__ __device__ __forceinline__ int levall_offset(const NetDesc& N, int ell) {
+    int off = 0;
+    for (int l = 2; l < ell; ++l) off += lev_offset(N, l, l - 1);
+    return off;
+}
+__host__ __device__ __forceinline__ int kall_offset(const NetDesc& N, int ell) {
+    int off = 0;
+    for (int l = 1; l < ell; ++l) off += N.w[l];
+    return off;
+}
+__host__ __device__ __forceinline__ int kall_total(const NetDesc& N) { return kall_offset(N, N.L + 1); }
 
 // a4: back-substitution chain of target layer ell.  Initialises kappa to b_ell, walks the
 // levels m = ell-1..1 and returns Lambda_x (rows n_ell, ld *ld) in shared memory.  With
@@ -478,11 +494,19 @@ __global__ void k_pad_weights(const NetDesc N, FusedLayout Y, const float* __res
 // non-null the dual vector seen by each hidden layer's concretisation is kept.
 template <int NT>
 __device__ void controller_pass(const Dom& s, const NetDesc& N, const FusedArgs& a, int64_t dom, int64_t sp_end, int t,
-                                float* vsnap) {
+                                float* vsnap, float* levall = nullptr, float* kall = nullptr) {
     const int n = N.n, L = N.L;
     for (int ell = 1; ell <= L; ++ell) {
         int ld;
-        const float* cur = chain<NT>(s, N, ell, nullptr, &ld);
+        const float* cur = chain<NT>(s, N, ell, (levall && ell >= 2) ? levall + levall_offset(N, ell) : nullptr, &ld);
+        if (kall) {
+            const int ko = kall_offset(N, ell), kt = kall_total(N);
+            for (int i = threadIdx.x; i < N.w[ell]; i += NT) {
+                kall[ko + i] = s.klo[i];
+                kall[kt + ko + i] = s.khi[i];
+            }
+            __syncthreads();
+        }
         if (vsnap && ell < L) {
             for (int k = threadIdx.x; k <= n; k += NT) vsnap[ell * (n + 1) + k] = s.vf[k];
         }
