@@ -1312,6 +1312,9 @@ static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, int lanes, int lane, float*
 // free device memory and at most the memory cap left, and never below 1 GiB.
 static int wide_chunk(dr_ctx* c, const NetDesc& N, int lanes) {
     if (c->opt.chunk_domains > 0) return (int)std::min<int64_t>(std::min<int64_t>(c->opt.chunk_domains, c->D), 65535);
+    // a captured pass repeats the plain pass before it: keep its chunk, and query no device state
+    // while the stream is being captured
+    if (c->capturing && c->wDc > 0 && c->wLanes == lanes) return c->wDc;
     size_t total = size_t(16) << 30;
     size_t free_b = 0, all_b = 0;
     // the scratch this context already holds counts as free, so the choice is stable across calls

@@ -29,12 +29,14 @@ def _same(a, b):
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
 
 
-@pytest.mark.parametrize("case", ["fused", "staged"])
+@pytest.mark.parametrize("case", ["fused", "staged", "staged_auto_chunk"])
 def test_replay_matches_plain_launches(case):
     if case == "fused":
         p, prec, chunk = wl.random_problem(71, [5, 40, 30, 3], D=300, H=6, eps=0.2), 0, 0
-    else:
+    elif case == "staged":
         p, prec, chunk = wl.random_problem(72, [6, 96, 80, 64, 2], D=300, H=4, eps=0.15), TCORE, 64
+    else:  # the chunk chosen from the device's free memory on the plain call is kept while capturing
+        p, prec, chunk = wl.random_problem(75, [6, 96, 80, 64, 2], D=300, H=4, eps=0.15), TCORE, 0
     ref = _reach(p, graphs=1, precision=prec, chunk=chunk)
     want = ref.bounds(on_device=False)
     ref.close()
