@@ -364,3 +364,13 @@ def test_large16_all_sub_boxes_one_step_sampled():
     g = gpu_bounds(p)
     idx = np.array([0, 1, 65535, 131072, 199999, 262142, 262143])
     compare(p.subset(idx), _sampled(p, g, idx), orc.reach(p.subset(idx)), check_hull=False)
+
+
+def test_tensor_core_bounds_contain_trajectories():
+    # soundness of the staged 3xTF32 path itself (not only agreement with the oracle): simulated
+    # trajectories from sub-boxes of the 16-512x4-8 workload stay inside the GPU machines
+    import dataclasses
+    p = dataclasses.replace(wl.large16().subset(np.arange(0, 262144, 32768)), H=10)
+    g = gpu_bounds(p)
+    dom, xs, _ = wl.sample_trajectories(p, 4000, 11)
+    assert ((xs >= g["lo"][dom]) & (xs <= g["hi"][dom])).all()
