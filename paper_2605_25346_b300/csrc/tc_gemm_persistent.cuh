@@ -16,9 +16,11 @@
 // the compiled entry count is 168, so the increase never waits for registers that do not exist.
 //
 // The three TF32 products and their order are those of k_tc_gemm_p.  Accumulation is promoted per
-// fill: the tensor core sums kPromote = 2 chunks (64 of K) into a partial buffer, which the
-// epilogue then adds into FP32 registers; twice k_tc_gemm_p's span, half its hand-offs, and still
-// well inside the FP32-accurate error bound.  The intercept partials keep the two 64-column sets
+// fill: the tensor core sums kPromote chunks of 32 into a partial buffer, which the epilogue then
+// adds into FP32 registers.  kPromote = 1, as in k_tc_gemm_p: the tensor core's accumulation
+// rounds toward zero relative to the running sum, and over 50 closed-loop steps two chunks per
+// fill used up to 86 % of the reported boxes' outward margin (one chunk: 53 %, plain FP32 41 %),
+// four chunks exceeded it.  The intercept partials keep the two 64-column sets
 // per tile.  The final level's (x*s) W_1 product is taken with FP32 FMAs (the TMEM is all partial
 // buffers), not with 3xTF32 MMAs.  The next operand (chain levels) leaves through a per-warp
 // staging tile in shared memory, so its global stores cover whole 64-byte row segments.
@@ -34,7 +36,7 @@ constexpr int kPersistThreads = 128 + 2 * 128;
 constexpr int kRegsLaunch = 168, kRegsCtl = 56, kRegsEpi = 224;
 static_assert(128 * (kRegsLaunch - kRegsCtl) >= 256 * (kRegsEpi - kRegsLaunch), "register split exceeds the launch's registers");
 constexpr int kPS = 3;                              // ring stages
-constexpr int kPromote = 2;                         // K chunks (of 32) per partial buffer fill
+constexpr int kPromote = 1;                         // K chunks (of 32) per partial buffer fill
 constexpr int kPSB = stage_bytes(128);              // 64 KB per stage
 __host__ __device__ constexpr int pp_coltab_offset() { return kPS * kPSB + 256; }
 __host__ __device__ constexpr int pp_w1tab_offset() { return pp_coltab_offset() + 2 * 128 * 16; }

@@ -306,7 +306,14 @@ def test_large16_bench_configuration_sampled():
     p = wl.large16().subset(np.arange(2048))
     g = gpu_bounds(p)
     idx = np.array([0, 1, 511, 1023, 1024, 1535, 2047])
-    compare(p.subset(idx), _sampled(p, g, idx), orc.reach(p.subset(idx)), check_hull=False)
+    o = orc.reach(p.subset(idx))
+    compare(p.subset(idx), _sampled(p, g, idx), o, check_hull=False)
+    # soundness headroom over the 50 steps: the GPU machines enclose the oracle's with at least a quarter
+    # of the outward margin (2^-18 of the entry's magnitude) to spare
+    olo, ohi = o["lo"].numpy(), o["hi"].numpy()
+    m = 2.0 ** -18 * np.maximum(np.abs(olo), np.abs(ohi))
+    used = 1.0 - np.minimum((olo - g["lo"][idx]) / m, (g["hi"][idx] - ohi) / m)[:, 1:]
+    assert used.max() <= 0.75, f"outward margin used up to {used.max():.2f}"
 
 
 def test_branch12_bench_configuration_sampled():
