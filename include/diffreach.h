@@ -232,6 +232,14 @@ int dr_slope_gradient_static(const dr_static_args* args);
  * device memory; synchronises `stream`.  DR_ERR_TIMEOUT if a bounded pipeline wait expired. */
 int dr_tf32x3_gemm(int M, int N, int K, const float* A, const float* BT, float* C, void* stream);
 
+/* Check of the bounded device-side waits behind DR_ERR_TIMEOUT: one thread on the current device
+ * waits, through the same bounded mbarrier wait the tensor-core pipelines use, on a barrier phase
+ * that nothing completes, with a budget of `seconds` (0 < seconds <= 2) of SM clock cycles at the
+ * device's rated clock.  Returns DR_ERR_TIMEOUT when the wait gave up and reported it (the designed
+ * outcome; the device stays usable), DR_OK if the phase completed (it cannot), DR_ERR_ARG for a
+ * budget outside the range, DR_ERR_CUDA / DR_ERR_OOM on a device error.  Synchronises the device. */
+int dr_check_wait_expiry(double seconds);
+
 /* Number of kernels this context has launched (monotone counter, for accounting; a graph replay
  * counts the kernels of the captured pass). */
 int64_t dr_kernel_launches(const dr_ctx* ctx);

@@ -21,7 +21,7 @@ EXPORTS = [
     "dr_create", "dr_destroy", "dr_load_controller", "dr_load_dynamics", "dr_set_boxes", "dr_set_splits",
     "dr_set_horizon", "dr_set_options", "dr_compute_bounds", "dr_get_objective", "dr_optimize_slopes",
     "dr_backward", "dr_get_alpha", "dr_set_alpha", "dr_get_beta", "dr_set_beta", "dr_kernel_launches", "dr_graph_replays", "dr_last_error",
-    "dr_slope_gradient_static", "dr_tf32x3_gemm",
+    "dr_slope_gradient_static", "dr_tf32x3_gemm", "dr_check_wait_expiry",
 ]
 
 
@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dr_last_error": (ctypes.c_char_p, [vp]),
         "dr_slope_gradient_static": (i32, [ctypes.POINTER(dr_static_args)]),
         "dr_tf32x3_gemm": (i32, [i32, i32, i32, vp, vp, vp, vp]),
+        "dr_check_wait_expiry": (i32, [ctypes.c_double]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

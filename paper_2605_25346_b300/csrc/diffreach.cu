@@ -2020,6 +2020,41 @@ extern "C" int dr_tf32x3_gemm(int M, int N, int K, const float* A, const float* 
     return rc;
 }
 
+// One thread waits on the first phase of a fresh mbarrier that nothing arrives on: the bounded wait
+// every pipeline stage uses must give up after its budget and raise the error flag.
+__global__ void k_wait_expiry(int* err, long long budget) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (!tc::mbar_wait_for(&bar, 0, budget)) atomicExch(err, 1);
+    }
+}
+
+extern "C" int dr_check_wait_expiry(double seconds) {
+    if (!(seconds > 0.0) || seconds > 2.0) return fail(nullptr, DR_ERR_ARG, "dr_check_wait_expiry: seconds must be in (0, 2]");
+    int dev = 0, khz = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess || khz <= 0) {
+        cudaGetLastError();
+        return fail(nullptr, DR_ERR_CUDA, "dr_check_wait_expiry: no device");
+    }
+    int* err = nullptr;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, DR_ERR_OOM, "dr_check_wait_expiry: allocation failed");
+    }
+    int rc = DR_OK, herr = 0;
+    cudaMemset(err, 0, sizeof(int));
+    k_wait_expiry<<<1, 32>>>(err, (long long)(seconds * 1e3 * khz));
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) rc = fail(nullptr, DR_ERR_CUDA, "dr_check_wait_expiry: %s", cudaGetErrorString(e));
+    else if (herr) rc = fail(nullptr, DR_ERR_TIMEOUT, "dr_check_wait_expiry: the wait gave up as designed");
+    cudaFree(err);
+    return rc;
+}
+
 // ------------------------------------------------------------------------------------------------
 // Allocation-free slope gradient (dr_slope_gradient_static): the reverse sweep with its tape in a
 // statically reserved device array instead of context-owned memory.

@@ -56,14 +56,15 @@ __device__ __forceinline__ bool mbar_try_sleep(uint64_t* bar, uint32_t parity, u
     return ok != 0;
 }
 // Bounded wait on an mbarrier phase, suspended between tests (a spinning test loop takes issue
-// slots from the warps doing the work); false when the clock budget ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// slots from the warps doing the work); false when `budget` SM clock cycles ran out.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, long long budget) {
     const long long t0 = clock64();
     while (!mbar_try_sleep(bar, parity, 100000u)) {
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > budget) return false;
     }
     return true;
 }
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) { return mbar_wait_for(bar, parity, kWaitCycles); }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
     asm volatile(
