@@ -12,8 +12,13 @@
 * refinement: keep-best projected gradient never increases V; zero slopes are inclusion-monotone
   under input splitting at the first step;
 * derivatives: reverse-mode dV/dalpha and dV/dbeta agree with central finite differences;
-* planted mistakes in the oracle (dropped intercept, swapped Lambda+/-, wrong chord slope) are
-  caught by these pins.
+* the split dual and empty domains (a reading: the paper only cites beta-CROWN): a hand-derived
+  two-step example with one split and beta in {0, 3}, where beta = 3 reaches the exact lower bound;
+  a split that contradicts its box sets the INFEASIBLE bit and leaves the domain out of the hull;
+* the adaptive slope's tie u = -l takes slope 1 (hand-derived box);
+* planted mistakes in the oracle are caught by these pins: dropped intercept, swapped
+  Lambda+/-, wrong chord slope, the split dual's linear term dropped from EvalInt or from the
+  intermediate bounds, no infeasibility check, the adaptive tie taking slope 0.
 """
 import json
 import os
@@ -316,3 +321,130 @@ def test_planted_wrong_chord(monkeypatch):
     monkeypatch.setattr(orc, "relax", bad)
     lo, hi = _hand_box(orc.MODE_CHORD)
     assert (lo, hi) != pytest.approx((-2.75, 3.0))
+
+
+# ---------------------------------------------------------------------------------------------
+# split dual, infeasible domains, hull and the adaptive tie: hand-derived goldens
+# ---------------------------------------------------------------------------------------------
+
+def _golden(name):
+    return json.load(open(os.path.join(GOLDEN, name)))
+
+
+def _scalar_net(g):
+    return [np.array(g["W1"]), np.array(g["W2"])], [np.array(g["b1"]), np.array(g["b2"])]
+
+
+def _split_dual_problem(g, beta):
+    W, b = _scalar_net(g)
+    s = g["split"]
+    sp = wl.Splits(np.array([0, 1], np.int64), np.array([s["t"]], np.int32), np.array([s["layer"]], np.int32),
+                   np.array([s["neuron"]], np.int32), np.array([s["sign"]], np.int32))
+    return wl.Problem("split-dual", [1, 1, 1], W, b, np.array(g["A"]), np.array(g["B"]), np.zeros(1),
+                      np.array([g["lo"]]), np.array([g["hi"]]), g["H"], mode=orc.MODE_CHORD, splits=sp,
+                      beta=np.array([beta]))
+
+
+def _split_dual_matches(case):
+    """True iff the oracle reproduces every hand-derived value of one split-dual case."""
+    g = _golden("split_dual_example.json")
+    c = g["cases"][case]
+    r = orc.reach(_split_dual_problem(g, c["beta"]), keep_intermediate=True)
+    ok = True
+    for t, (l, u) in enumerate(c["layer1_bounds"]):
+        ok &= abs(r["l"][0, t, 0].item() - l) <= 1e-13 and abs(r["u"][0, t, 0].item() - u) <= 1e-13
+    for t, (lo, hi) in enumerate(c["box"]):
+        ok &= abs(r["lo"][0, t, 0].item() - lo) <= 1e-13 and abs(r["hi"][0, t, 0].item() - hi) <= 1e-13
+    return bool(ok), r
+
+
+@pytest.mark.parametrize("case", ["beta3", "beta0"])
+def test_split_dual_hand_example(case):
+    ok, r = _split_dual_matches(case)
+    assert ok
+    g = _golden("split_dual_example.json")
+    assert int(r["status"][0]) == 0
+    for t, (lo, hi) in enumerate(g["true_range"]):
+        assert r["lo"][0, t, 0].item() <= lo and r["hi"][0, t, 0].item() >= hi
+
+
+def test_split_dual_tightens_the_lower_bound():
+    # beta = 3 reaches the exact minimum of x_1 over the split domain; beta = 0 does not
+    g = _golden("split_dual_example.json")
+    r3 = orc.reach(_split_dual_problem(g, 3.0))
+    r0 = orc.reach(_split_dual_problem(g, 0.0))
+    assert r3["lo"][0, 1, 0].item() == pytest.approx(g["true_range"][1][0], abs=1e-14)
+    assert r3["lo"][0, 1, 0].item() > r0["lo"][0, 1, 0].item() + 1.0
+
+
+def _infeasible_problem():
+    g = _golden("infeasible_split_example.json")
+    W, b = _scalar_net(g)
+    s = g["splits"]
+    sp = wl.Splits(np.array(s["row_ptr"], np.int64), np.array(s["t"], np.int32), np.array(s["layer"], np.int32),
+                   np.array(s["neuron"], np.int32), np.array(s["sign"], np.int32))
+    p = wl.Problem("infeasible", [1, 1, 1], W, b, np.array(g["A"]), np.array(g["B"]), np.zeros(1),
+                   np.array(g["lo"]), np.array(g["hi"]), g["H"], mode=orc.MODE_CHORD, splits=sp)
+    return g, p
+
+
+def _infeasible_matches():
+    g, p = _infeasible_problem()
+    r = orc.reach(p)
+    ok = [int(x) for x in r["status"]] == g["status"]
+    for t, (lo, hi) in enumerate(g["hull"]):
+        ok &= abs(r["hull_lo"][t, 0].item() - lo) <= 1e-14 and abs(r["hull_hi"][t, 0].item() - hi) <= 1e-14
+    return bool(ok)
+
+
+def test_infeasible_split_flagged_and_excluded_from_hull():
+    assert _infeasible_matches()
+
+
+def _adaptive_tie_box():
+    g = _golden("adaptive_tie_example.json")
+    W, b = _scalar_net(g)
+    p = wl.Problem("tie", [1, 1, 1], W, b, np.array(g["A"]), np.array(g["B"]), np.zeros(1),
+                   np.array([g["lo"]]), np.array([g["hi"]]), g["H"], mode=orc.MODE_ADAPTIVE)
+    r = orc.reach(p, keep_intermediate=True)
+    return g, r
+
+
+def test_adaptive_tie_takes_slope_one():
+    g, r = _adaptive_tie_box()
+    assert (r["l"][0, 0, 0].item(), r["u"][0, 0, 0].item()) == tuple(g["layer1_bounds"])
+    assert r["lo"][0, 1, 0].item() == pytest.approx(g["box1"][0], abs=1e-14)
+    assert r["hi"][0, 1, 0].item() == pytest.approx(g["box1"][1], abs=1e-14)
+
+
+def _mutate(monkeypatch, fn_name, edits):
+    """Install a copy of oracle function `fn_name` with textual edits (old -> new) applied."""
+    import inspect
+    src = inspect.getsource(getattr(orc, fn_name))
+    for old, new in edits:
+        assert old in src, f"mutation target not found: {old!r}"
+        src = src.replace(old, new)
+    ns = dict(vars(orc))
+    exec(compile(src, orc.__file__, "exec"), ns)
+    monkeypatch.setattr(orc, fn_name, ns[fn_name])
+
+
+def test_planted_dual_dropped_in_evalint(monkeypatch):
+    _mutate(monkeypatch, "reach", [("pm = P - v[:, None, :]", "pm = P"), ("pp = P + v[:, None, :]", "pp = P")])
+    assert not _split_dual_matches("beta3")[0]
+
+
+def test_planted_dual_dropped_in_intermediate_bounds(monkeypatch):
+    _mutate(monkeypatch, "reach", [("gm = G - v[:, None, :]", "gm = G"), ("gp = G + v[:, None, :]", "gp = G")])
+    assert not _split_dual_matches("beta3")[0]
+
+
+def test_planted_no_infeasibility_check(monkeypatch):
+    _mutate(monkeypatch, "reach", [("bad = (l > u).any(-1)", "bad = torch.zeros_like((l > u).any(-1))")])
+    assert not _infeasible_matches()
+
+
+def test_planted_adaptive_tie_takes_zero(monkeypatch):
+    _mutate(monkeypatch, "relax", [("a = torch.where(u >= -l, one, zero)", "a = torch.where(u > -l, one, zero)")])
+    g, r = _adaptive_tie_box()
+    assert (r["lo"][0, 1, 0].item(), r["hi"][0, 1, 0].item()) == pytest.approx(tuple(g["box1_if_tie_took_zero"]))
