@@ -104,43 +104,61 @@ typedef struct dr_options {
     int32_t reserved[4];
 } dr_options;
 
-/* Create a context on `device` whose work is ordered on `cuda_stream` (a cudaStream_t;
+/* Paper: no passage; the engine of Sec. IV runs batched on a single GPU (Sec. VI), and a context
+ * is this library's handle for that device and its stream.
+ * Create a context on `device` whose work is ordered on `cuda_stream` (a cudaStream_t;
  * NULL = the legacy default stream).  Fails with DR_ERR_CUDA if the device is missing
  * or is not compute capability 10.3.  *out receives the context. */
 int dr_create(dr_ctx** out, int device, void* cuda_stream);
 
-/* Release the context and all device memory it owns (after draining its stream). */
+/* Paper: no passage (resource management).
+ * Release the context and all device memory it owns (after draining its stream). */
 void dr_destroy(dr_ctx* ctx);
 
-/* Controller pi: L affine layers; widths[0..L] = (n, n_1, ..., n_{L-1}, m).
+/* Paper: the neural component that CROWN certifies (Thm. 2, Sec. IV-C), here the ReLU feedback
+ * controller of the discrete-time loop (closing remark of Sec. IV-E).
+ * Controller pi: L affine layers; widths[0..L] = (n, n_1, ..., n_{L-1}, m).
  * W[l] points to n_{l+1} x n_l row-major values (layer l+1), b[l] to n_{l+1} values,
  * both host memory of element type `dtype` (DR_F32 or DR_F64).  The device computes in
  * FP32 (values are rounded once).  ReLU follows every layer but the last. */
 int dr_load_controller(dr_ctx* ctx, int L, const int32_t* widths, const void* const* W,
                        const void* const* b, int dtype);
 
-/* Dynamics x' = A x + B u + e: A [n x n], B [n x m], e [n] (NULL = 0), host FP64.
+/* Paper: the one-step map x_{k+1} = f(x_k, u_k) of Sec. IV-E and Alg. 2, read here as linear
+ * dynamics driven by the controller output u_k = pi(x_k).
+ * Dynamics x' = A x + B u + e: A [n x n], B [n x m], e [n] (NULL = 0), host FP64.
  * n and m must match the controller's input and output widths. */
 int dr_load_dynamics(dr_ctx* ctx, int n, int m, const double* A, const double* B, const double* e);
 
-/* D initial boxes [lo, hi] (each [D x n], FP64, lo <= hi), host (on_device = 0) or device.
+/* Paper: the initial box X_0 = [x_lo, x_hi] of Alg. 2 (B_eps(x_hat) of Sec. III-A), one per domain;
+ * many sub-boxes of one initial set are the input splitting of Sec. VI-A (Table I).  Each box is
+ * turned into a linear TM by BuildLinearTM (Alg. 2) inside dr_compute_bounds.
+ * D initial boxes [lo, hi] (each [D x n], FP64, lo <= hi), host (on_device = 0) or device.
  * Resets the slopes (alpha), the split list and the multipliers (beta). */
 int dr_set_boxes(dr_ctx* ctx, int64_t D, const double* lo, const double* hi, int on_device);
 
-/* Branch-domain splits in CSR form: domain d owns s[row_ptr[d] .. row_ptr[d+1]), sorted
+/* Paper: no passage.  Split constraints and their multipliers beta come from beta-CROWN, which the
+ * paper only cites; the Lagrangian dual used here is this library's reading of how a split enters
+ * a shared-slope TM bound.
+ * Branch-domain splits in CSR form: domain d owns s[row_ptr[d] .. row_ptr[d+1]), sorted
  * by (t, layer).  row_ptr [D+1] (row_ptr[0] = 0, non-decreasing), s [nnz], beta [nnz]
  * multipliers >= 0 (NULL = all 0); host memory.  Every concretisation after a split's own
  * layer uses the Lagrangian dual min_zeta p^T zeta >= -|p - sum beta_k g_k|_1 - sum beta_k h_k
  * of the split constraints g_k^T zeta + h_k >= 0. */
 int dr_set_splits(dr_ctx* ctx, const int64_t* row_ptr, const dr_split* s, const float* beta);
 
-/* Horizon H >= 1 (number of controller/dynamics steps). */
+/* Paper: the horizon H of Alg. 2.
+ * Horizon H >= 1 (number of controller/dynamics steps). */
 int dr_set_horizon(dr_ctx* ctx, int H);
 
-/* Options (copied).  NULL restores the defaults. */
+/* Paper: slope_mode selects the relaxation under the shared-slope constraint of Sec. IV-C (the
+ * paper fixes no rule); the other fields are numerics and resource limits with no passage.
+ * Options (copied).  NULL restores the defaults. */
 int dr_set_options(dr_ctx* ctx, const dr_options* opt);
 
-/* Bounds for all domains and steps (Alg. 2):
+/* Paper: Alg. 2 (BuildLinearTM, then per step the CROWN certification of Thm. 3 and EvalInt),
+ * with the closed loop of Sec. IV-E; the hull is the union over input splits of Sec. VI-A.
+ * Bounds for all domains and steps (Alg. 2):
  *   lo, hi          [D x (H+1) x n]  box of every domain and step (step 0 = the input box)
  *   hull_lo/hull_hi [(H+1) x n]      min/max over domains without DR_STATUS_INFEASIBLE
  *   status          [D]              DR_STATUS_* bits
@@ -153,14 +171,18 @@ int dr_compute_bounds(dr_ctx* ctx, double* lo, double* hi, double* hull_lo, doub
  * (Sec. V-A), [D] FP64. */
 int dr_get_objective(dr_ctx* ctx, double* V, int on_device);
 
-/* Projected-gradient refinement: alpha <- clip(alpha - lr_alpha dV/dalpha, 0, 1),
+/* Paper: "gradient-based refinement" of Sec. VI-A (Table I, 20 iterations), minimising the
+ * tube-volume proxy of Sec. V-A; the update rule and keep-best are this library's reading.
+ * Projected-gradient refinement: alpha <- clip(alpha - lr_alpha dV/dalpha, 0, 1),
  * beta <- max(beta - lr_beta dV/dbeta, 0), keeping per domain the best (alpha, beta, V).
  * If no slopes were set, they start at the CHORD slopes.  V_out [steps+1] (host, may be
  * NULL) receives sum_d best V_d after each evaluation.  Afterwards the context holds the
  * best slopes and multipliers and slope mode DR_SLOPE_USER. */
 int dr_optimize_slopes(dr_ctx* ctx, int steps, double lr_alpha, double lr_beta, double* V_out);
 
-/* Reverse-mode gradient of the scalar sum_{d,t,i} (g_lo[d,t,i] * lo[d,t,i] + g_hi[d,t,i] * hi[d,t,i])
+/* Paper: the gradient of a reachable-set objective that Sec. V-A (L_reach) and the refinement of
+ * Sec. VI-A differentiate, taken here with respect to the relaxation slopes and split multipliers.
+ * Reverse-mode gradient of the scalar sum_{d,t,i} (g_lo[d,t,i] * lo[d,t,i] + g_hi[d,t,i] * hi[d,t,i])
  * at the current slopes (DR_SLOPE_USER; the slopes of the current mode otherwise, with dalpha 0):
  *   dV_dlo, dV_dhi [D x (H+1) x n] FP64 upstream gradients g_lo, g_hi of the boxes (NULL for both =
  *   the tube-volume proxy V, i.e. g_lo = -1 and g_hi = +1 on steps 1..H; one NULL = zeros);
@@ -172,12 +194,14 @@ int dr_optimize_slopes(dr_ctx* ctx, int steps, double lr_alpha, double lr_beta, 
 int dr_backward(dr_ctx* ctx, const double* dV_dlo, const double* dV_dhi, float* dalpha, float* dbeta,
                 int on_device);
 
-/* Slopes alpha [D x H x hidden] FP32 (hidden = n_1 + ... + n_{L-1}, layers concatenated);
+/* Paper: the shared slope of each unstable ReLU under the shared-slope constraint (Sec. IV-C).
+ * Slopes alpha [D x H x hidden] FP32 (hidden = n_1 + ... + n_{L-1}, layers concatenated);
  * only unstable neurons read them.  dr_set_alpha switches the slope mode to DR_SLOPE_USER. */
 int dr_get_alpha(dr_ctx* ctx, float* alpha, int on_device);
 int dr_set_alpha(dr_ctx* ctx, const float* alpha, int on_device);
 
-/* Split multipliers beta [nnz] FP32 (>= 0). */
+/* Paper: no passage (beta-CROWN multipliers, only cited by the paper; see dr_set_splits).
+ * Split multipliers beta [nnz] FP32 (>= 0). */
 int dr_get_beta(dr_ctx* ctx, float* beta, int on_device);
 int dr_set_beta(dr_ctx* ctx, const float* beta, int on_device);
 
@@ -198,8 +222,10 @@ int dr_set_beta(dr_ctx* ctx, const float* beta, int on_device);
  * Limits: D*H*(n^2 + 4n + 2) doubles of scratch must fit DR_STATIC_SCRATCH_BYTES (8 MiB), and
  * the controller must fit the fused kernels (widths up to a few hundred); larger problems are
  * rejected with DR_ERR_SHAPE and a message, before any device work.
- * The first call on a device looks up the scratch address (cudaGetSymbolAddress); make that
- * first call before capturing a stream into a graph.  Every call shares the same scratch array:
+ * Every call made outside stream capture looks up the scratch address (cudaGetSymbolAddress,
+ * which loads the library's device code on first use); a call made while `stream` is being
+ * captured reuses the address of the last call on that device, so make a first call before
+ * capturing a stream into a graph.  Every call shares the same scratch array:
  * calls that overlap on the GPU (other streams, other threads) race and must be serialised by
  * the caller.  Each call overwrites the scratch before reading it, so no clearing is needed. */
 #define DR_STATIC_SCRATCH_BYTES (8u << 20)
@@ -232,7 +258,8 @@ int dr_slope_gradient_static(const dr_static_args* args);
  * device memory; synchronises `stream`.  DR_ERR_TIMEOUT if a bounded pipeline wait expired. */
 int dr_tf32x3_gemm(int M, int N, int K, const float* A, const float* BT, float* C, void* stream);
 
-/* Check of the bounded device-side waits behind DR_ERR_TIMEOUT: one thread on the current device
+/* Paper: no passage (device-side safety of this library's tensor-core pipelines).
+ * Check of the bounded device-side waits behind DR_ERR_TIMEOUT: one thread on the current device
  * waits, through the same bounded mbarrier wait the tensor-core pipelines use, on a barrier phase
  * that nothing completes, with a budget of `seconds` (0 < seconds <= 2) of SM clock cycles at the
  * device's rated clock.  Returns DR_ERR_TIMEOUT when the wait gave up and reported it (the designed
@@ -240,14 +267,17 @@ int dr_tf32x3_gemm(int M, int N, int K, const float* A, const float* BT, float* 
  * budget outside the range, DR_ERR_CUDA / DR_ERR_OOM on a device error.  Synchronises the device. */
 int dr_check_wait_expiry(double seconds);
 
-/* Number of kernels this context has launched (monotone counter, for accounting; a graph replay
+/* Paper: no passage (accounting).
+ * Number of kernels this context has launched (monotone counter, for accounting; a graph replay
  * counts the kernels of the captured pass). */
 int64_t dr_kernel_launches(const dr_ctx* ctx);
 
-/* Number of dr_compute_bounds calls served by replaying a captured CUDA graph (dr_options.graphs). */
+/* Paper: no passage (accounting).
+ * Number of dr_compute_bounds calls served by replaying a captured CUDA graph (dr_options.graphs). */
 int64_t dr_graph_replays(const dr_ctx* ctx);
 
-/* Message of the last failing call on ctx (or of the last failing dr_create when ctx is
+/* Paper: no passage (error reporting).
+ * Message of the last failing call on ctx (or of the last failing dr_create when ctx is
  * NULL).  The pointer stays valid until the next call on the same context. */
 const char* dr_last_error(const dr_ctx* ctx);
 

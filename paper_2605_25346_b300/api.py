@@ -190,34 +190,43 @@ class BoundsFunction(torch.autograd.Function):
     """Differentiable bounds: (alpha, beta) -> (lo, hi), backward through the library's adjoint.
 
     alpha [D, H, hidden] float32 and beta [nnz] float32 are CUDA tensors; lo/hi [D, H+1, n]
-    float64.  The backward pass hands torch's upstream gradients of lo and hi to dr_backward.
+    float64.  The backward pass hands torch's upstream gradients of lo and hi to dr_backward at the
+    slopes and multipliers this forward call was given (saved with the graph), so several forward
+    calls on one Reach before a backward each get their own gradient.
     """
+
+    @staticmethod
+    def _install(reach: "Reach", a: torch.Tensor, b: torch.Tensor):
+        reach._c(reach.lib.dr_set_alpha(reach.ctx, _ptr(a), 1))
+        if b.numel():
+            reach._c(reach.lib.dr_set_beta(reach.ctx, _ptr(b), 1))
 
     @staticmethod
     def forward(ctx, reach: "Reach", alpha: torch.Tensor, beta: torch.Tensor):
         a = alpha.detach().to(torch.float32).contiguous()
-        reach._c(reach.lib.dr_set_alpha(reach.ctx, _ptr(a), 1))
-        if beta.numel():
-            b = beta.detach().to(torch.float32).contiguous()
-            reach._c(reach.lib.dr_set_beta(reach.ctx, _ptr(b), 1))
+        b = beta.detach().to(torch.float32).contiguous()
+        BoundsFunction._install(reach, a, b)
         out = reach.bounds(on_device=True, hull=False)
         ctx.reach = reach
-        ctx.shapes = (alpha.shape, beta.shape)
+        ctx.dtypes = (alpha.dtype, beta.dtype)
+        ctx.save_for_backward(a, b)
         return out["lo"], out["hi"]
 
     @staticmethod
     def backward(ctx, glo, ghi):
         r = ctx.reach
         p = r.prob
+        a, b = ctx.saved_tensors
         dev = f"cuda:{r.device}"
         zeros = torch.zeros(p.D, p.H + 1, p.n, dtype=torch.float64, device=dev)
         wlo = (glo if glo is not None else zeros).to(torch.float64).contiguous()
         whi = (ghi if ghi is not None else zeros).to(torch.float64).contiguous()
-        ga = torch.empty(ctx.shapes[0], dtype=torch.float32, device=dev)
-        gb = torch.empty(max(1, ctx.shapes[1].numel()), dtype=torch.float32, device=dev)
+        ga = torch.empty(a.shape, dtype=torch.float32, device=dev)
+        gb = torch.empty(max(1, b.numel()), dtype=torch.float32, device=dev)
         torch.cuda.synchronize()
+        BoundsFunction._install(r, a, b)
         r._c(r.lib.dr_backward(r.ctx, _ptr(wlo), _ptr(whi), _ptr(ga), _ptr(gb), 1))
-        return None, ga, gb[: ctx.shapes[1].numel()].reshape(ctx.shapes[1])
+        return None, ga.to(ctx.dtypes[0]), gb[: b.numel()].reshape(b.shape).to(ctx.dtypes[1])
 
 
 def bounds(reach: "Reach", alpha: torch.Tensor, beta: torch.Tensor):

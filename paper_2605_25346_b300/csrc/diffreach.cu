@@ -2068,14 +2068,20 @@ static std::mutex g_static_mu;
 static double* g_static_tape_ptr[64];  // device address of g_static_tape, per device ordinal
 static bool g_static_ready[64];
 
-// Host code cannot use g_static_tape directly (it names a host-side shadow); look up the device
-// address once per device, with that device current.
-static int static_tape_ptr(int dev, double** out) {
+// Host code cannot use g_static_tape directly (it names a host-side shadow); it needs the device
+// address, looked up with the device current.  Outside stream capture the address is looked up
+// on every call (the module may have been loaded again, e.g. after cudaDeviceReset, at another
+// address); inside a capture, where the lookup could load the module and break the capture, the
+// address from the last call outside capture on this device is used.
+static int static_tape_ptr(int dev, cudaStream_t st, double** out) {
     if (dev < 0 || dev >= 64) return fail(nullptr, DR_ERR_CUDA, "device ordinal %d out of range", dev);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return fail(nullptr, DR_ERR_CUDA, "cudaStreamIsCapturing: %s", cudaGetErrorString(e));
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_ready[dev]) {
+    if (cs == cudaStreamCaptureStatusNone || !g_static_ready[dev]) {
         void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_tape);
+        e = cudaGetSymbolAddress(&p, g_static_tape);
         if (e != cudaSuccess) return fail(nullptr, DR_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
         g_static_tape_ptr[dev] = reinterpret_cast<double*>(p);
         g_static_ready[dev] = true;
@@ -2126,9 +2132,9 @@ extern "C" int dr_slope_gradient_static(const dr_static_args* s) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(nullptr, DR_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-    double* tape = nullptr;
-    TRY(static_tape_ptr(dev, &tape));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(s->stream);
+    double* tape = nullptr;
+    TRY(static_tape_ptr(dev, st, &tape));
 
     FusedArgs a;
     memset(&a, 0, sizeof(a));

@@ -44,11 +44,18 @@ def test_null_context_arguments_are_rejected():
     assert lib.dr_kernel_launches(None) == 0
 
 
-def test_wait_expiry_check_argument_errors_without_device():
+def test_wait_expiry_check_refuses_bad_budgets():
+    # the budget is checked before any device query, with or without a GPU
+    lib = _lib.load()
+    assert lib.dr_check_wait_expiry(0.0) == _lib.DR_ERR_ARG
+    assert lib.dr_check_wait_expiry(-1.0) == _lib.DR_ERR_ARG
+    assert lib.dr_check_wait_expiry(3.0) == _lib.DR_ERR_ARG
+    assert lib.dr_check_wait_expiry(float("nan")) == _lib.DR_ERR_ARG
+
+
+def test_wait_expiry_check_without_device():
     import torch
     if torch.cuda.is_available():
         pytest.skip("a device is present")
     lib = _lib.load()
-    assert lib.dr_check_wait_expiry(0.0) == _lib.DR_ERR_ARG
-    assert lib.dr_check_wait_expiry(3.0) == _lib.DR_ERR_ARG
     assert lib.dr_check_wait_expiry(0.1) == _lib.DR_ERR_CUDA  # no device to wait on

@@ -92,6 +92,29 @@ def test_autograd_function_matches_backward():
     _grad_close(a.grad.cpu().numpy(), ga_o.numpy())
 
 
+def test_autograd_two_forwards_then_backward_of_the_first():
+    # each output's gradient is taken at the slopes its own forward call was given
+    api = _api()
+    p = wl.random_problem(66, [3, 16, 16, 2], D=8, H=3, eps=0.3)
+    a1 = _interior_alpha(p, 5).float()
+    a2 = _interior_alpha(p, 6).float()
+    r = api.Reach(0).load(p)
+    x1 = a1.cuda().requires_grad_(True)
+    x2 = a2.cuda().requires_grad_(True)
+    b = torch.zeros(0, device="cuda", requires_grad=True)
+    lo1, hi1 = api.bounds(r, x1, b)
+    lo2, hi2 = api.bounds(r, x2, b)
+    (hi1[:, 1:] - lo1[:, 1:]).sum().backward()
+    r.set_alpha(a1.numpy())
+    g1, _ = r.backward()
+    np.testing.assert_allclose(x1.grad.cpu().numpy(), g1, rtol=1e-6, atol=1e-6 * np.abs(g1).max())
+    (hi2[:, 1:] - lo2[:, 1:]).sum().backward()
+    r.set_alpha(a2.numpy())
+    g2, _ = r.backward()
+    np.testing.assert_allclose(x2.grad.cpu().numpy(), g2, rtol=1e-6, atol=1e-6 * np.abs(g2).max())
+    assert np.abs(g1 - g2).max() > 1e-3 * np.abs(g1).max()
+
+
 def test_refinement_cartpole_subset():
     p = wl.cartpole_diff()
     sub = p.subset(np.arange(0, p.D, 16))  # 64 of the 1024 sub-boxes

@@ -40,6 +40,8 @@ def test_static_gradient_matches_backward_on_two_calls():
     alpha = np.clip(chord + 0.1 * (np.random.default_rng(0).random(chord.shape) - 0.5), 0.05, 0.95).astype(np.float32)
     r.set_alpha(alpha)
     ref, _ = r.backward()
+    r.bounds(on_device=False)
+    V_ref = r.objective()
     r.close()
 
     dev = "cuda:0"
@@ -62,6 +64,7 @@ def test_static_gradient_matches_backward_on_two_calls():
     scale = np.abs(ref).max()
     for _call in range(2):
         bufs["dalpha"].fill_(float("nan"))
+        bufs["V"].fill_(float("nan"))
         torch.cuda.synchronize()
         rc = lib.dr_slope_gradient_static(ctypes.byref(args))
         assert rc == _lib.DR_OK, lib.dr_last_error(None)
@@ -69,6 +72,9 @@ def test_static_gradient_matches_backward_on_two_calls():
         got = bufs["dalpha"].cpu().numpy()
         assert np.isfinite(got).all()
         assert np.abs(got - ref).max() <= 1e-4 * scale
+        # the objective at these slopes, as the context-based bound pass reports it
+        V = bufs["V"].cpu().numpy()
+        np.testing.assert_allclose(V, V_ref, rtol=1e-5)
 
 
 def test_static_gradient_rejects_oversized_problem():
