@@ -1,15 +1,16 @@
 #!/usr/bin/env python
 """Throughput of sound reachable-set bounds: domain-steps per second on one B300.
 
-A step is one pass of the whole bound computation over the batched workload: every domain's
-Taylor-model seed, the per-layer back-substitution chains and concretisations, the controller
-Taylor model, the dynamics, the FP64 boxes of every horizon step and the hull over domains.
+A step is one pass of the whole bound computation over one batch of domains: every domain's
+Taylor-model seed, the per-layer back-substitution chains (3xTF32 on the tcgen05 tensor cores) and
+concretisations, the controller Taylor model, the dynamics, the FP64 boxes of every horizon step and
+the hull over domains.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Workload (default): 6-state stable linear dynamics, ReLU controller 6-64-64-3 (FP32 weights),
-the initial box split into a uniform 4^6 = 4096 sub-box grid, horizon 10, chord slopes.
-Prints one JSON line on rank 0.
+Workload (default): the large workload, 16-state stable linear dynamics with the ReLU controller
+16-512-512-512-512-8 (FP32 weights), horizon 50, chord slopes; a step bounds a chunk of 16,384 of its
+262,144 sub-boxes (rank r of N takes the r-th chunk).  Prints one JSON line on rank 0.
 """
 import argparse
 import json
@@ -39,6 +40,14 @@ SMS = 148
 # (dram__bytes_read.sum + dram__bytes_write.sum of one steady-state launch); the working set lives in
 # shared memory, so this is the boxes and weights read once.
 FUSED_TRAFFIC_BYTES = 548864
+
+# DRAM bytes (read + write) per stacked row of one persistent chain-level GEMM launch (K = N = 512):
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch over R = 65,536 rows (ncu, small case),
+# divided by R.  The traffic grows with R (the left operand is read once and the next one written
+# once), so a full launch's traffic is this times its rows.
+CHAIN_GEMM_TRAFFIC_PER_ROW = (271.4e6 + 227.1e6) / 65536
+
+HEADLINE_CHUNK = 16384
 
 
 def fused_flops_per_domain_step(widths):
@@ -176,20 +185,16 @@ def measure_tf32_peak(local, n=8192, sustain_s=4.0):
         torch.backends.cuda.matmul.allow_tf32 = prev
 
 
-def measure_wide(local, reps=2):
+def measure_wide(local, reps=2, tf32=None):
     """Throughput of the staged tcgen05 path on domain samples of the two wide workloads."""
     from paper_2605_25346_b300 import api
     out = {}
-    try:
-        import json as _json
-        mp = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        bf16_burst, bf16_sus, basis = mp["bf16_tflops"], mp["bf16_tflops_sustained"], "of measured"
-    except Exception:
-        bf16_burst, bf16_sus, basis = 1800.0, 1400.0, "of fallback"
+    bf16_burst, bf16_sus, _hbm, basis = peaks()
     peak_tf32 = bf16_burst * 1.1 / 2.25  # nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)
     peak_tf32_sus = bf16_sus * 1.1 / 2.25
-    tf32 = measure_tf32_peak(local)
-    out["tf32_peak_measured"] = tf32
+    if tf32 is None:
+        tf32 = measure_tf32_peak(local)
+        out["tf32_peak_measured"] = tf32
     for name, prob in (("branch12 12-256x3-4, 4096 of 65536 branch domains, H=30",
                         wl.quadrotor_branch(only=np.arange(4096))),
                        ("large16 16-512x4-8, 2048 of 262144 sub-boxes, H=50", wl.large16().subset(np.arange(2048)))):
@@ -274,12 +279,99 @@ def wide_pass(domains, horizon):
 
 
 def workload(rank=0):
-    p = wl.quad6_batched()
-    if rank:
-        # weak scaling: every rank bounds its own 4096 sub-boxes (a shifted copy of the grid)
-        p.lo = p.lo + 0.01 * rank
-        p.hi = p.hi + 0.01 * rank
-    return p
+    """The rank's chunk of 16,384 consecutive sub-boxes of the large workload (weak scaling: every
+    rank bounds its own chunk; chunks wrap around after the 16 chunks of the grid)."""
+    p = wl.large16()
+    c0 = (rank * HEADLINE_CHUNK) % p.D
+    return p.subset(np.arange(c0, c0 + HEADLINE_CHUNK))
+
+
+def peaks():
+    """(bf16 burst, bf16 sustained, hbm GB/s, basis) from the measured peaks file, else the fallback."""
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(mp["bf16_tflops"]), float(mp["bf16_tflops_sustained"]), float(mp.get("hbm_gbs", 6400.0)), "of measured"
+    except Exception:
+        return 1800.0, 1400.0, 6400.0, "of fallback"
+
+
+def measure_quad6(local, steps=10, warmup=3):
+    """The 4096-sub-box workload (6-64-64-3, H = 10) on the grouped fused kernel: one launch per
+    pass plus the hull, replayed from a CUDA graph; roofline of the fused kernel against FP32 issue."""
+    from paper_2605_25346_b300 import api
+    prob = wl.quad6_batched()
+    D, H, n = prob.D, prob.H, prob.n
+    stream = torch.cuda.Stream()
+    r = api.Reach(local, stream=stream).load(prob)
+    dev = f"cuda:{local}"
+    lo = torch.empty(D, H + 1, n, dtype=torch.float64, device=dev)
+    hi = torch.empty_like(lo)
+    hl = torch.empty(H + 1, n, dtype=torch.float64, device=dev)
+    hh = torch.empty_like(hl)
+    st = torch.empty(D, dtype=torch.int32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    P = api._ptr
+
+    def step(hull=True):
+        r._c(r.lib.dr_compute_bounds(r.ctx, P(lo), P(hi), P(hl) if hull else None, P(hh) if hull else None, P(st), 1))
+
+    out = {}
+    with torch.cuda.stream(stream):
+        for hull in (True, False):
+            for _ in range(warmup):
+                step(hull)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for i in range(steps):
+                flush.zero_()
+                ev[i][0].record(stream)
+                step(hull)
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            out[hull] = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    r.close()
+    flops = fused_flops_per_domain_step(prob.widths) * D * H
+    peak = SMS * FP32_LANES_PER_SM * 2 * 2032.0 * 1e6 / 1e12
+    achieved = flops / (out[False] * 1e-3) / 1e12
+    return {"workload": "quad6 6-64-64-3, 4^6 = 4096 sub-boxes, H=10, chord slopes (grouped fused kernel)",
+            "domain_steps_per_s": D * H / (out[True] * 1e-3), "ms_per_step": out[True],
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": FUSED_TRAFFIC_BYTES, "kernel": "k_fused_forward_multi", "kernel_ms": out[False],
+                         "peak_basis": "148 SMs x 128 FP32 lanes x 2 FLOP x 2032 MHz (FMA issue rate at max SM clock)"}}
+
+
+def measure_branch12_full(local, reps=3):
+    """All 65,536 branch domains (0..32 ReLU splits each) of the 12-256x3-4 workload, H = 30, on the
+    staged tensor-core path: one dr_compute_bounds per pass, replayed from a CUDA graph."""
+    from paper_2605_25346_b300 import api
+    bf_b, bf_s, _, basis = peaks()
+    t0 = time.perf_counter()
+    prob = wl.quadrotor_branch()
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    r = api.Reach(local, stream=stream).load(prob)
+    with torch.cuda.stream(stream):
+        for _ in range(2):  # the plain first call, then the call that captures the CUDA graph
+            r.bounds(on_device=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            out = r.bounds(on_device=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3 / reps
+    counts = np.diff(prob.splits.row_ptr)
+    fl = fused_flops_per_domain_step(prob.widths) * prob.D * prob.H
+    fp32eq_sus = bf_s * 1.1 / 2.25 / 3.0
+    res = {"workload": "branch12 12-256x3-4, all 65,536 branch domains with 0..32 splits (uniform count), H=30",
+           "splits_total": int(prob.splits.nnz), "splits_min": int(counts.min()), "splits_max": int(counts.max()),
+           "domain_steps_per_s": prob.D * prob.H / t, "ms_per_pass": 1e3 * t, "fp32eq_tflops_whole_pass": fl / t / 1e12,
+           "frac_of_fp32eq_tensor_peak_sustained": fl / t / 1e12 / fp32eq_sus,
+           "peak_basis": f"bf16 sustained {basis} x 1.1/2.25 / 3", "split_generation_s_host": gen_s,
+           "infeasible_domains": int(((out["status"] & 2) != 0).sum().item()),
+           "cuda_graph_replays": int(r.graph_replays())}
+    r.close()
+    return res
 
 
 class ClockSampler:
@@ -365,12 +457,13 @@ def oracle_baseline(prob, target_s=10.0, max_domains=None):
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the FP64 oracle on the host cores (rank 0 only)."""
+    """Reference arm: the FP64 oracle on the host cores (rank 0 only), each step a bounded sample of
+    the headline workload (its first domains, full horizon)."""
     if rank != 0:
         return
     from oracle import reach as orc
     prob = workload()
-    sample = 512
+    sample = 4
     sub = prob.subset(np.arange(sample))
     for _ in range(args.warmup):
         orc.reach(sub)
@@ -384,8 +477,8 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "quad6 6-64-64-3, 4^6 sub-boxes, H=10 (oracle step: 512-domain sample)",
-                       "domains": sample, "horizon": prob.H},
+            "config": {"workload": f"large16 16-512x4-8, chunk of {HEADLINE_CHUNK} of 262,144 sub-boxes, H=50 "
+                                   f"(oracle step: {sample}-domain sample)", "domains": sample, "horizon": prob.H},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
                              "sample": f"{sample} of {prob.D} domains x H={prob.H} per step"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -395,11 +488,11 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the refinement and wide-controller measurements")
+    ap.add_argument("--no-extras", action="store_true", help="skip the refinement and other-workload measurements")
     ap.add_argument("--wide-refine", nargs=2, type=int, metavar=("DOMAINS", "H"), default=None,
                     help="profiling aid: one slope-refinement step on a 16-512x4-8 sample and exit")
     ap.add_argument("--full-large16", action="store_true",
@@ -430,7 +523,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    from paper_2605_25346_b300 import api
+    from paper_2605_25346_b300 import _lib, api
 
     prob = workload(rank)
     D, H, n = prob.D, prob.H, prob.n
@@ -445,8 +538,8 @@ def main():
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     P = api._ptr
 
-    def step(hull=True):
-        r._c(r.lib.dr_compute_bounds(r.ctx, P(lo), P(hi), P(hl) if hull else None, P(hh) if hull else None, P(st), 1))
+    def step():
+        r._c(r.lib.dr_compute_bounds(r.ctx, P(lo), P(hi), P(hl), P(hh), P(st), 1))
 
     with torch.cuda.stream(stream), ClockSampler(local) as clk:
         for _ in range(args.warmup):
@@ -465,22 +558,13 @@ def main():
             step()
             ev[i][1].record(stream)
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
         t_wall = time.perf_counter() - t_wall
         clk.mark(h0, time.time())
         launches = r.launches() - l0
+        replays = r.graph_replays()
         step_ms = [a.elapsed_time(b) for a, b in ev]
-        # the dominant kernel alone (no hull launch), for the roofline; this call sequence is captured
-        # and replayed as its own CUDA graph, so it gets its own untimed warm-up
-        for _ in range(args.warmup):
-            step(hull=False)
-        kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        for i in range(args.steps):
-            flush.zero_()
-            kev[i][0].record(stream)
-            step(hull=False)
-            kev[i][1].record(stream)
-        torch.cuda.synchronize()
-        k_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
 
     ms = statistics.mean(step_ms)
     ms_t = torch.tensor([ms], device=dev)
@@ -488,6 +572,20 @@ def main():
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
     ms = float(ms_t.item())
     value = world * D * H / (ms * 1e-3)
+
+    # roofline of the dominant kernel: one more pass with every tensor-core GEMM launch bracketed by
+    # CUDA events on the stream it is launched on (plain launches, no graph)
+    r.set_options(mode=prob.mode, timing=1)
+    with torch.cuda.stream(stream):
+        flush.zero_()
+        step()
+        torch.cuda.synchronize()
+    kt = {}
+    for name, cls in (("all", _lib.DR_KT_GEMM_ALL), ("chain", _lib.DR_KT_GEMM_CHAIN), ("final", _lib.DR_KT_GEMM_FINAL),
+                      ("other", _lib.DR_KT_GEMM_OTHER)):
+        nl, tms, fl = r.kernel_timing(cls)
+        kt[name] = {"launches": nl, "ms": tms, "flop": fl}
+    r.set_options(mode=prob.mode, timing=0)
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     def pinned(shape, dtype):
@@ -505,51 +603,71 @@ def main():
         r._c(r.lib.dr_set_boxes(r.ctx, D, P(lo0), P(hi0), 0))
         r._c(r.lib.dr_compute_bounds(r.ctx, P(hlo), P(hhi), P(hhl), P(hhh), P(hst), 0))
 
-    for _ in range(2):
-        e2e_step()
+    e2e_steps = min(args.steps, 3)
+    e2e_step()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         e2e_step()
-    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
     h2d = 2 * D * n * 8
     d2h = 2 * D * (H + 1) * n * 8 + 2 * (H + 1) * n * 8 + 4 * D
+    r.close()
 
-    flops = fused_flops_per_domain_step(prob.widths) * D * H
-    clock = clk.summary()
-    peak_mhz = 2032.0
-    peak = SMS * FP32_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12
-    achieved = flops / (k_ms * 1e-3) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            # dram read + write bytes of one launch (ncu capture of the <256, 4> launch shape)
-            "traffic": FUSED_TRAFFIC_BYTES, "traffic_unit": "B per launch",
-            "kernel": "k_fused_forward_multi (grouped fused forward, autotuned launch shape)",
-            "kernel_ms": k_ms,
-            "peak_basis": "148 SMs x 128 FP32 lanes x 2 FLOP x 2032 MHz (FMA issue rate at max SM clock)",
-            "algorithmic_flops_per_launch": flops}
+    bf_b, bf_s, _hbm, basis = peaks()
+    # 3xTF32: one FP32-equivalent FLOP is three TF32 tensor FLOPs; TF32 = bf16 x 1.1/2.25 (nominal ratio).
+    # The GEMMs run inside a long, power-capped step, so the sustained figure is the denominator.
+    peak_sus = bf_s * 1.1 / 2.25 / 3.0
+    peak_burst = bf_b * 1.1 / 2.25 / 3.0
+    ch = kt["chain"]
+    achieved = ch["flop"] / (ch["ms"] * 1e-3) / 1e12 if ch["ms"] > 0 else None
+    rows_per_launch = ch["flop"] / max(1, ch["launches"]) / (2.0 * 512 * 512)
+    pass_flops = fused_flops_per_domain_step(prob.widths) * D * H
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak_sus, "unit": "TFLOP/s",
+            "frac": (achieved / peak_sus) if achieved else None,
+            "traffic": CHAIN_GEMM_TRAFFIC_PER_ROW * rows_per_launch, "traffic_unit": "B per launch",
+            "kernel": "tc::k_tc_gemm_pp<1> (persistent 3xTF32 chain-level GEMM, K = N = 512)",
+            "kernel_launches_timed": ch["launches"], "kernel_ms_avg": ch["ms"] / max(1, ch["launches"]),
+            "algorithmic_flops_per_launch": ch["flop"] / max(1, ch["launches"]),
+            "unit_of_work": "one stacked Lambda row: 2 x 512 x 512 FP32-equivalent FLOP; a launch processes "
+                            f"{rows_per_launch:.0f} rows (its lane's domains x 512)",
+            "peak_basis": f"bf16 sustained {basis} ({bf_s} TFLOP/s) x 1.1/2.25 (nominal TF32/BF16) / 3 MMAs per "
+                          "FP32-equivalent product",
+            "frac_burst_peak": (achieved / peak_burst) if achieved else None,
+            "all_gemms": {k: v for k, v in kt.items()},
+            "pass_fp32eq_tflops": pass_flops / (ms * 1e-3) / 1e12,
+            "pass_frac_of_peak": pass_flops / (ms * 1e-3) / 1e12 / peak_sus}
 
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline and world == 1:
-            cpu = oracle_baseline(prob, target_s=10.0)
+            cpu = oracle_baseline(prob, target_s=12.0, max_domains=8)
         extras = {}
         if not args.no_extras and world == 1:
+            tf32 = measure_tf32_peak(local)
+            extras["tf32_peak_measured"] = tf32
+            if achieved:
+                roof["frac_of_measured_tf32_over_3_sustained"] = achieved / (tf32["tf32_tflops_sustained"] / 3.0)
+                roof["frac_of_measured_tf32_over_3_burst"] = achieved / (tf32["tf32_tflops_burst"] / 3.0)
+            roof["pass_frac_of_measured_tf32_over_3_sustained"] = roof["pass_fp32eq_tflops"] / (tf32["tf32_tflops_sustained"] / 3.0)
+            extras["quad6"] = measure_quad6(local)
+            extras["branch12_full"] = measure_branch12_full(local)
             extras["refinement"] = measure_refinement(local)
-            extras["wide"] = measure_wide(local)
+            extras["wide"] = measure_wide(local, tf32=tf32)
             extras["wide_refinement"] = measure_wide_refinement(local)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": "quad6 6-64-64-3, 4^6 = 4096 sub-boxes, H=10, chord slopes",
-                           "domains_per_gpu": D, "horizon": H, "l2": "flushed between timed steps",
+                "vs_baseline": None, "dtype": "f32(3xtf32)+f64", "data": "synthetic",
+                "config": {"workload": f"large16 16-512x4-8, chunk of {D} of 262,144 sub-boxes per GPU, H={H}, "
+                                       "chord slopes", "domains_per_gpu": D, "horizon": H,
+                           "l2": "flushed between timed steps (working set 16 GiB, also above L2)",
                            "parallelism": f"domains sharded, {world} independent shard(s)"},
                 "e2e": {"value": world * D * H / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                        "d2h_bytes_per_step": d2h},
+                        "d2h_bytes_per_step": d2h, "steps": e2e_steps},
                 "gpu_launches": int(launches),
-                "cuda_graph_replays": int(r.graph_replays()),
+                "cuda_graph_replays": int(replays),
                 "wall_ms_per_step_incl_flush": 1e3 * t_wall / args.steps,
-                "roofline": roof, "cpu_baseline": cpu, "clocks": clock, "extras": extras}
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(), "extras": extras}
         print(json.dumps(line), flush=True)
-    r.close()
     if world > 1:
         dist.destroy_process_group()
 

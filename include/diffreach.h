@@ -101,7 +101,10 @@ typedef struct dr_options {
                               the second call with unchanged buffers, options and slope mode, and
                               replays it afterwards (needs a stream other than the legacy default
                               stream; any capture failure falls back to plain launches); 1 = never */
-    int32_t reserved[4];
+    int32_t timing;        /* 1 = time every tensor-core GEMM launch with a pair of CUDA events on the
+                              stream it is launched on (read with dr_kernel_timing); passes then run
+                              as plain launches, not graph replays.  0 (default) = off            */
+    int32_t reserved[3];
 } dr_options;
 
 /* Paper: no passage; the engine of Sec. IV runs batched on a single GPU (Sec. VI), and a context
@@ -271,6 +274,19 @@ int dr_check_wait_expiry(double seconds);
  * Number of kernels this context has launched (monotone counter, for accounting; a graph replay
  * counts the kernels of the captured pass). */
 int64_t dr_kernel_launches(const dr_ctx* ctx);
+
+/* Paper: no passage (measurement).
+ * Launch classes of dr_kernel_timing: */
+#define DR_KT_GEMM_ALL 0   /* every tcgen05 3xTF32 GEMM launch of the staged path                      */
+#define DR_KT_GEMM_CHAIN 1 /* persistent chain-level GEMM, next left operand formed in the epilogue     */
+#define DR_KT_GEMM_FINAL 2 /* persistent GEMM whose epilogue also multiplies by W_1 (last chain level) */
+#define DR_KT_GEMM_OTHER 3 /* the remaining GEMMs (one tile per CTA; target-2 products)                */
+/* Totals over the launches of class `which` timed since timing was switched on by dr_set_options
+ * (options.timing = 1): *launches, *ms (sum of the per-launch CUDA-event durations, each measured on
+ * the stream the launch went to) and *flop (algorithmic FP32-equivalent FLOP: 2 R K N per product
+ * of an R x K by K x N operand pair, plus 2 R N n for the fused x W_1 of the last level).  Waits for
+ * the recorded events.  Any output pointer may be NULL. */
+int dr_kernel_timing(dr_ctx* ctx, int which, int64_t* launches, double* ms, double* flop);
 
 /* Paper: no passage (accounting).
  * Number of dr_compute_bounds calls served by replaying a captured CUDA graph (dr_options.graphs). */

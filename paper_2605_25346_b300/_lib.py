@@ -15,12 +15,13 @@ DR_F32, DR_F64 = 0, 1
 DR_SLOPE_ADAPTIVE, DR_SLOPE_CHORD, DR_SLOPE_ZERO, DR_SLOPE_USER = 0, 1, 2, 3
 DR_PREC_AUTO, DR_PREC_SIMT, DR_PREC_TF32X3 = 0, 1, 2
 DR_STATUS_NONFINITE, DR_STATUS_INFEASIBLE = 1, 2
+DR_KT_GEMM_ALL, DR_KT_GEMM_CHAIN, DR_KT_GEMM_FINAL, DR_KT_GEMM_OTHER = 0, 1, 2, 3
 
 # every symbol the header declares
 EXPORTS = [
     "dr_create", "dr_destroy", "dr_load_controller", "dr_load_dynamics", "dr_set_boxes", "dr_set_splits",
     "dr_set_horizon", "dr_set_options", "dr_compute_bounds", "dr_get_objective", "dr_optimize_slopes",
-    "dr_backward", "dr_get_alpha", "dr_set_alpha", "dr_get_beta", "dr_set_beta", "dr_kernel_launches", "dr_graph_replays", "dr_last_error",
+    "dr_backward", "dr_get_alpha", "dr_set_alpha", "dr_get_beta", "dr_set_beta", "dr_kernel_launches", "dr_graph_replays", "dr_kernel_timing", "dr_last_error",
     "dr_slope_gradient_static", "dr_tf32x3_gemm", "dr_check_wait_expiry",
 ]
 
@@ -41,7 +42,7 @@ class dr_options(ctypes.Structure):
     _fields_ = [("slope_mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("margin_rho", ctypes.c_double),
                 ("chunk_domains", ctypes.c_int64), ("mem_cap_bytes", ctypes.c_int64),
                 ("box_margin", ctypes.c_double), ("tuning", ctypes.c_int32),
-                ("graphs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("graphs", ctypes.c_int32), ("timing", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 _lib = None
@@ -75,6 +76,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dr_set_beta": (i32, [vp, fp, i32]),
         "dr_kernel_launches": (i64, [vp]),
         "dr_graph_replays": (i64, [vp]),
+        "dr_kernel_timing": (i32, [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double)]),
         "dr_last_error": (ctypes.c_char_p, [vp]),
         "dr_slope_gradient_static": (i32, [ctypes.POINTER(dr_static_args)]),
         "dr_tf32x3_gemm": (i32, [i32, i32, i32, vp, vp, vp, vp]),

@@ -55,10 +55,11 @@ class Reach:
     # ---- problem upload -------------------------------------------------------------------
     def set_options(self, mode: Optional[int] = None, precision: int = _lib.DR_PREC_AUTO, rho: Optional[float] = None,
                     chunk: int = 0, mem_cap: int = 0, box_margin: Optional[float] = None, tuning: int = 0,
-                    graphs: int = 0):
+                    graphs: int = 0, timing: int = 0):
         o = _lib.dr_options()
         o.tuning = tuning
         o.graphs = graphs
+        o.timing = timing
         o.slope_mode = _MODE[mode] if mode is not None else _lib.DR_SLOPE_CHORD
         o.precision = precision
         o.margin_rho = 0.0 if rho is None else rho
@@ -184,6 +185,13 @@ class Reach:
 
     def graph_replays(self) -> int:
         return int(self.lib.dr_graph_replays(self.ctx))
+
+    def kernel_timing(self, which: int = _lib.DR_KT_GEMM_ALL):
+        """(launches, total ms, algorithmic FLOP) of the timed tensor-core GEMM launches of a class
+        (timing is switched on with set_options(timing=1))."""
+        nl, ms, fl = ctypes.c_int64(0), ctypes.c_double(0.0), ctypes.c_double(0.0)
+        self._c(self.lib.dr_kernel_timing(self.ctx, which, ctypes.byref(nl), ctypes.byref(ms), ctypes.byref(fl)))
+        return int(nl.value), float(ms.value), float(fl.value)
 
 
 class BoundsFunction(torch.autograd.Function):

@@ -103,6 +103,17 @@ struct dr_ctx {
     static constexpr int kMaxLanes = 4;
     cudaStream_t aux[kMaxLanes] = {};
     cudaEvent_t ev_fork = nullptr, ev_join[kMaxLanes] = {};
+    // per-launch timing of the tensor-core GEMMs (dr_options.timing): event pairs not yet read, a
+    // pool of reusable events and the per-class totals
+    struct KtPending {
+        int cls;
+        cudaEvent_t e0, e1;
+        double flop;
+    };
+    std::vector<KtPending> kt_pending;
+    std::vector<cudaEvent_t> kt_pool;
+    int64_t kt_launches[4] = {};
+    double kt_ms[4] = {}, kt_flop[4] = {};
 };
 
 static thread_local std::string g_create_err;
@@ -538,10 +549,47 @@ static int launch_tc_gemm_persistent(dr_ctx* c, const CUtensorMap* m, float* C, 
     return DR_OK;
 }
 
+static int tc_gemm_launch(dr_ctx* c, const float* Ah, const float* Al, const float* BTh, const float* BTl, float* C, int R,
+                          int K, int N, int ldk, int ldc, int* err, cudaStream_t st, const tc::ChainEpi* epi, int* cls);
+
+static cudaEvent_t kt_event(dr_ctx* c) {
+    cudaEvent_t e = nullptr;
+    if (!c->kt_pool.empty()) {
+        e = c->kt_pool.back();
+        c->kt_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        e = nullptr;
+    }
+    return e;
+}
+
 // C [R x N] (ld ldc) = A B with A given as TF32 parts Ah/Al (blocked layout, tc::blk_index, ldk
-// columns) and B as BTh/BTl [N][ldk]; with `epi` the chain epilogue replaces the store of C.
+// columns) and B as BTh/BTl [N][ldk]; with `epi` the chain epilogue replaces the store of C.  With
+// dr_options.timing set (and not capturing a graph) the launch is bracketed by two CUDA events on `st`.
 static int tc_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* BTh, const float* BTl, float* C, int R, int K,
                    int N, int ldk, int ldc, int* err, cudaStream_t st, const tc::ChainEpi* epi = nullptr) {
+    const bool timed = c && c->opt.timing && !c->capturing;
+    cudaEvent_t e0 = timed ? kt_event(c) : nullptr, e1 = timed ? kt_event(c) : nullptr;
+    if (e0 && e1) CUDA_TRY(c, cudaEventRecord(e0, st));
+    int cls = DR_KT_GEMM_OTHER;
+    const int rc = tc_gemm_launch(c, Ah, Al, BTh, BTl, C, R, K, N, ldk, ldc, err, st, epi, &cls);
+    if (timed) {
+        if (rc == DR_OK && e0 && e1) {
+            CUDA_TRY(c, cudaEventRecord(e1, st));
+            double flop = 2.0 * R * K * N;
+            if (epi && epi->W1) flop += 2.0 * R * N * epi->n0;
+            c->kt_pending.push_back({cls, e0, e1, flop});
+        } else {
+            if (e0) c->kt_pool.push_back(e0);
+            if (e1) c->kt_pool.push_back(e1);
+        }
+    }
+    return rc;
+}
+
+static int tc_gemm_launch(dr_ctx* c, const float* Ah, const float* Al, const float* BTh, const float* BTl, float* C, int R,
+                          int K, int N, int ldk, int ldc, int* err, cudaStream_t st, const tc::ChainEpi* epi, int* cls) {
     TRY(get_encoder(c));
     const int BN = tc_bn(N);
     CUtensorMap m[6];
@@ -567,10 +615,14 @@ static int tc_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* BTh
         if (tiles >= 2 * (int64_t)nsm && tiles <= 0x7fffffffll) {
             if (!epi && persistent_gemm_usable<0>())
                 return launch_tc_gemm_persistent<0>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm);
-            if (epi && epi->W1 && persistent_gemm_usable<2>())
+            if (epi && epi->W1 && persistent_gemm_usable<2>()) {
+                *cls = DR_KT_GEMM_FINAL;
                 return launch_tc_gemm_persistent<2>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm);
-            if (epi && !epi->W1 && persistent_gemm_usable<1>())
+            }
+            if (epi && !epi->W1 && persistent_gemm_usable<1>()) {
+                *cls = DR_KT_GEMM_CHAIN;
                 return launch_tc_gemm_persistent<1>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm);
+            }
         }
     }
 #define DR_TC_CASE(bn)                                                                                        \
@@ -830,6 +882,11 @@ void dr_destroy(dr_ctx* c) {
         if (c->ev_join[l]) cudaEventDestroy(c->ev_join[l]);
     }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    for (auto& p : c->kt_pending) {
+        cudaEventDestroy(p.e0);
+        cudaEventDestroy(p.e1);
+    }
+    for (cudaEvent_t e : c->kt_pool) cudaEventDestroy(e);
     delete c;
 }
 
@@ -849,8 +906,57 @@ int dr_set_options(dr_ctx* c, const dr_options* o) {
     if (n.chunk_domains < 0 || n.mem_cap_bytes < 0) return fail(c, DR_ERR_ARG, "negative chunk or memory cap");
     if (n.slope_mode == DR_SLOPE_USER && !c->alpha_set && c->D > 0)
         return fail(c, DR_ERR_STATE, "DR_SLOPE_USER requires dr_set_alpha first");
+    if (n.timing < 0 || n.timing > 1) return fail(c, DR_ERR_ARG, "timing %d out of range", n.timing);
+    if (n.timing && !c->opt.timing) {
+        // timing switched on: the totals start from zero
+        for (int k = 0; k < 4; ++k) {
+            c->kt_launches[k] = 0;
+            c->kt_ms[k] = c->kt_flop[k] = 0.0;
+        }
+    }
     c->opt = n;
     c->epoch++;  // kernel arguments may change
+    return DR_OK;
+}
+
+// Read the recorded event pairs into the per-class totals (waits for them) and recycle the events.
+static int kt_drain(dr_ctx* c) {
+    int rc = DR_OK;
+    for (auto& p : c->kt_pending) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(p.e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p.e0, p.e1);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(c, DR_ERR_CUDA, "dr_kernel_timing: %s", cudaGetErrorString(e));
+        } else {
+            c->kt_launches[p.cls]++;
+            c->kt_ms[p.cls] += ms;
+            c->kt_flop[p.cls] += p.flop;
+        }
+        c->kt_pool.push_back(p.e0);
+        c->kt_pool.push_back(p.e1);
+    }
+    c->kt_pending.clear();
+    return rc;
+}
+
+int dr_kernel_timing(dr_ctx* c, int which, int64_t* launches, double* ms, double* flop) {
+    if (!c) return DR_ERR_ARG;
+    if (which < DR_KT_GEMM_ALL || which > DR_KT_GEMM_OTHER) return fail(c, DR_ERR_ARG, "timing class %d", which);
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    TRY(kt_drain(c));
+    int64_t n = 0;
+    double t = 0.0, f = 0.0;
+    for (int k = 1; k <= 3; ++k) {
+        if (which != DR_KT_GEMM_ALL && which != k) continue;
+        n += c->kt_launches[k];
+        t += c->kt_ms[k];
+        f += c->kt_flop[k];
+    }
+    if (launches) *launches = n;
+    if (ms) *ms = t;
+    if (flop) *flop = f;
     return DR_OK;
 }
 
@@ -1700,7 +1806,7 @@ int dr_compute_bounds(dr_ctx* c, double* lo, double* hi, double* hull_lo, double
         }
         return DR_OK;
     };
-    const bool graphs = c->opt.graphs == 0 && !c->graphs_broken && c->stream != nullptr && c->D > 0;
+    const bool graphs = c->opt.graphs == 0 && !c->opt.timing && !c->graphs_broken && c->stream != nullptr && c->D > 0;
     if (graphs && c->gexec && c->g_epoch == c->epoch && c->g_mode == mode && c->g_hull == hull) {
         CUDA_TRY(c, cudaGraphLaunch(c->gexec, c->stream));
         c->launches += c->graph_launches;
