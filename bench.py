@@ -41,11 +41,14 @@ SMS = 148
 # shared memory, so this is the boxes and weights read once.
 FUSED_TRAFFIC_BYTES = 548864
 
-# DRAM bytes (read + write) per stacked row of one persistent chain-level GEMM launch (K = N = 512):
+# DRAM bytes (read + write) per stacked row of one persistent GEMM launch (K = N = 512):
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch over R = 65,536 rows (ncu, small case),
-# divided by R.  The traffic grows with R (the left operand is read once and the next one written
-# once), so a full launch's traffic is this times its rows.
-CHAIN_GEMM_TRAFFIC_PER_ROW = (271.4e6 + 227.1e6) / 65536
+# divided by R.  The traffic grows with R (the left operand is read once; the chain level also writes
+# the next one once), so a full launch's traffic is this times its rows.
+GEMM_TRAFFIC_PER_ROW = {"final": (271.5e6 + 18.6e6) / 65536, "chain": (271.4e6 + 227.1e6) / 65536}
+# launches of at least this many stacked rows are the full-size ones (hidden-layer targets:
+# domains x 512 rows); the controller-output target's launches have domains x 8 rows
+BIG_GEMM_ROWS = 65536
 
 HEADLINE_CHUNK = 16384
 
@@ -339,14 +342,10 @@ def measure_quad6(local, steps=10, warmup=3):
                          "peak_basis": "148 SMs x 128 FP32 lanes x 2 FLOP x 2032 MHz (FMA issue rate at max SM clock)"}}
 
 
-def measure_branch12_full(local, reps=3):
-    """All 65,536 branch domains (0..32 ReLU splits each) of the 12-256x3-4 workload, H = 30, on the
-    staged tensor-core path: one dr_compute_bounds per pass, replayed from a CUDA graph."""
+def _time_passes(local, prob, reps):
+    """Seconds per dr_compute_bounds pass (CUDA events; graph replays after two warm calls), the
+    last output and the replay count."""
     from paper_2605_25346_b300 import api
-    bf_b, bf_s, _, basis = peaks()
-    t0 = time.perf_counter()
-    prob = wl.quadrotor_branch()
-    gen_s = time.perf_counter() - t0
     stream = torch.cuda.Stream()
     r = api.Reach(local, stream=stream).load(prob)
     with torch.cuda.stream(stream):
@@ -359,7 +358,21 @@ def measure_branch12_full(local, reps=3):
             out = r.bounds(on_device=True)
         e1.record(stream)
         torch.cuda.synchronize()
-    t = e0.elapsed_time(e1) * 1e-3 / reps
+    replays = r.graph_replays()
+    r.close()
+    return e0.elapsed_time(e1) * 1e-3 / reps, out, replays
+
+
+def measure_branch12_full(local, reps=3):
+    """All 65,536 branch domains (0..32 ReLU splits each) of the 12-256x3-4 workload, H = 30, on the
+    staged tensor-core path: one dr_compute_bounds per pass, replayed from a CUDA graph.  The same
+    domains without their splits, timed the same way, show what the ragged split lists cost."""
+    bf_b, bf_s, _, basis = peaks()
+    t0 = time.perf_counter()
+    prob = wl.quadrotor_branch()
+    gen_s = time.perf_counter() - t0
+    t, out, replays = _time_passes(local, prob, reps)
+    t_nosplit, _, _ = _time_passes(local, wl.quadrotor_branch(with_splits=False), reps)
     counts = np.diff(prob.splits.row_ptr)
     fl = fused_flops_per_domain_step(prob.widths) * prob.D * prob.H
     fp32eq_sus = bf_s * 1.1 / 2.25 / 3.0
@@ -369,8 +382,9 @@ def measure_branch12_full(local, reps=3):
            "frac_of_fp32eq_tensor_peak_sustained": fl / t / 1e12 / fp32eq_sus,
            "peak_basis": f"bf16 sustained {basis} x 1.1/2.25 / 3", "split_generation_s_host": gen_s,
            "infeasible_domains": int(((out["status"] & 2) != 0).sum().item()),
-           "cuda_graph_replays": int(r.graph_replays())}
-    r.close()
+           "cuda_graph_replays": int(replays),
+           "ms_per_pass_same_domains_without_splits": 1e3 * t_nosplit,
+           "split_overhead": t / t_nosplit - 1.0}
     return res
 
 
@@ -583,8 +597,9 @@ def main():
     kt = {}
     for name, cls in (("all", _lib.DR_KT_GEMM_ALL), ("chain", _lib.DR_KT_GEMM_CHAIN), ("final", _lib.DR_KT_GEMM_FINAL),
                       ("other", _lib.DR_KT_GEMM_OTHER)):
-        nl, tms, fl = r.kernel_timing(cls)
-        kt[name] = {"launches": nl, "ms": tms, "flop": fl}
+        for size, mr in (("", 0), ("_big", BIG_GEMM_ROWS)):
+            nl, tms, fl = r.kernel_timing(cls, mr)
+            kt[name + size] = {"launches": nl, "ms": tms, "flop": fl}
     r.set_options(mode=prob.mode, timing=0)
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
@@ -618,22 +633,35 @@ def main():
     # The GEMMs run inside a long, power-capped step, so the sustained figure is the denominator.
     peak_sus = bf_s * 1.1 / 2.25 / 3.0
     peak_burst = bf_b * 1.1 / 2.25 / 3.0
-    ch = kt["chain"]
-    achieved = ch["flop"] / (ch["ms"] * 1e-3) / 1e12 if ch["ms"] > 0 else None
-    rows_per_launch = ch["flop"] / max(1, ch["launches"]) / (2.0 * 512 * 512)
+    def rate(k):
+        return k["flop"] / (k["ms"] * 1e-3) / 1e12 if k["ms"] > 0 else None
+
+    # the dominant kernel: the final-level persistent GEMM (x W_1 fused in its epilogue), which takes
+    # the largest share of the GEMM time; its full-size launches (hidden-layer targets)
+    fin = kt["final_big"]
+    achieved = rate(fin)
+    rows_per_launch = fin["flop"] / max(1, fin["launches"]) / (2.0 * 512 * (512 + 16))
     pass_flops = fused_flops_per_domain_step(prob.widths) * D * H
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak_sus, "unit": "TFLOP/s",
             "frac": (achieved / peak_sus) if achieved else None,
-            "traffic": CHAIN_GEMM_TRAFFIC_PER_ROW * rows_per_launch, "traffic_unit": "B per launch",
-            "kernel": "tc::k_tc_gemm_pp<1> (persistent 3xTF32 chain-level GEMM, K = N = 512)",
-            "kernel_launches_timed": ch["launches"], "kernel_ms_avg": ch["ms"] / max(1, ch["launches"]),
-            "algorithmic_flops_per_launch": ch["flop"] / max(1, ch["launches"]),
-            "unit_of_work": "one stacked Lambda row: 2 x 512 x 512 FP32-equivalent FLOP; a launch processes "
-                            f"{rows_per_launch:.0f} rows (its lane's domains x 512)",
+            "traffic": GEMM_TRAFFIC_PER_ROW["final"] * rows_per_launch, "traffic_unit": "B per launch",
+            "kernel": "tc::k_tc_gemm_pp<2> (persistent 3xTF32 GEMM of the last chain level, x W_1 in the epilogue; "
+                      "launches of the hidden-layer targets)",
+            "kernel_launches_timed": fin["launches"], "kernel_ms_avg": fin["ms"] / max(1, fin["launches"]),
+            "algorithmic_flops_per_launch": fin["flop"] / max(1, fin["launches"]),
+            "unit_of_work": "one stacked Lambda row: 2 x 512 x 512 (tensor) + 2 x 512 x 16 (x W_1) FP32-equivalent "
+                            f"FLOP; a launch processes {rows_per_launch:.0f} rows (a lane chunk's domains x 512)",
             "peak_basis": f"bf16 sustained {basis} ({bf_s} TFLOP/s) x 1.1/2.25 (nominal TF32/BF16) / 3 MMAs per "
                           "FP32-equivalent product",
             "frac_burst_peak": (achieved / peak_burst) if achieved else None,
-            "all_gemms": {k: v for k, v in kt.items()},
+            "timing": "CUDA events around every GEMM launch on its own lane stream, one pass of the same step "
+                      "(plain launches); the two lanes run concurrently, so a launch's duration includes the "
+                      "other lane's kernels sharing the GPU",
+            "chain_level_gemm_big": {"tflops": rate(kt["chain_big"]), "frac": (rate(kt["chain_big"]) or 0) / peak_sus,
+                                     "traffic_per_launch": GEMM_TRAFFIC_PER_ROW["chain"] * kt["chain_big"]["flop"] /
+                                     max(1, kt["chain_big"]["launches"]) / (2.0 * 512 * 512)},
+            "gemm_classes": kt,
+            "gemm_share_of_gemm_time": {k: kt[k]["ms"] / max(1e-9, kt["all"]["ms"]) for k in ("chain", "final", "other")},
             "pass_fp32eq_tflops": pass_flops / (ms * 1e-3) / 1e12,
             "pass_frac_of_peak": pass_flops / (ms * 1e-3) / 1e12 / peak_sus}
 
@@ -648,6 +676,8 @@ def main():
             if achieved:
                 roof["frac_of_measured_tf32_over_3_sustained"] = achieved / (tf32["tf32_tflops_sustained"] / 3.0)
                 roof["frac_of_measured_tf32_over_3_burst"] = achieved / (tf32["tf32_tflops_burst"] / 3.0)
+                roof["frac_named"] = ("frac uses the bf16-derived sustained peak; frac_of_measured_tf32_over_3_* use "
+                                      "the cuBLAS TF32 probe of this run")
             roof["pass_frac_of_measured_tf32_over_3_sustained"] = roof["pass_fp32eq_tflops"] / (tf32["tf32_tflops_sustained"] / 3.0)
             extras["quad6"] = measure_quad6(local)
             extras["branch12_full"] = measure_branch12_full(local)

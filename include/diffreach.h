@@ -180,7 +180,9 @@ int dr_get_objective(dr_ctx* ctx, double* V, int on_device);
  * beta <- max(beta - lr_beta dV/dbeta, 0), keeping per domain the best (alpha, beta, V).
  * If no slopes were set, they start at the CHORD slopes.  V_out [steps+1] (host, may be
  * NULL) receives sum_d best V_d after each evaluation.  Afterwards the context holds the
- * best slopes and multipliers and slope mode DR_SLOPE_USER. */
+ * best slopes and multipliers and slope mode DR_SLOPE_USER.  The first step runs as plain launches;
+ * the others replay one captured CUDA graph of a step when dr_options.graphs is 0 and the context
+ * has a stream other than the legacy default stream. */
 int dr_optimize_slopes(dr_ctx* ctx, int steps, double lr_alpha, double lr_beta, double* V_out);
 
 /* Paper: the gradient of a reachable-set objective that Sec. V-A (L_reach) and the refinement of
@@ -281,15 +283,17 @@ int64_t dr_kernel_launches(const dr_ctx* ctx);
 #define DR_KT_GEMM_CHAIN 1 /* persistent chain-level GEMM, next left operand formed in the epilogue     */
 #define DR_KT_GEMM_FINAL 2 /* persistent GEMM whose epilogue also multiplies by W_1 (last chain level) */
 #define DR_KT_GEMM_OTHER 3 /* the remaining GEMMs (one tile per CTA; target-2 products)                */
-/* Totals over the launches of class `which` timed since timing was switched on by dr_set_options
- * (options.timing = 1): *launches, *ms (sum of the per-launch CUDA-event durations, each measured on
- * the stream the launch went to) and *flop (algorithmic FP32-equivalent FLOP: 2 R K N per product
- * of an R x K by K x N operand pair, plus 2 R N n for the fused x W_1 of the last level).  Waits for
- * the recorded events.  Any output pointer may be NULL. */
-int dr_kernel_timing(dr_ctx* ctx, int which, int64_t* launches, double* ms, double* flop);
+/* Totals over the launches of class `which` with at least `min_rows` rows R (stacked Lambda rows, the
+ * M dimension) timed since timing was switched on by dr_set_options (options.timing = 1):
+ * *launches, *ms (sum of the per-launch CUDA-event durations, each measured on the stream the launch
+ * went to) and *flop (algorithmic FP32-equivalent FLOP: 2 R K N per product of an R x K by K x N
+ * operand pair, plus 2 R N n for the fused x W_1 of the last level).  Waits for the recorded events.
+ * Any output pointer may be NULL. */
+int dr_kernel_timing(dr_ctx* ctx, int which, int64_t min_rows, int64_t* launches, double* ms, double* flop);
 
 /* Paper: no passage (accounting).
- * Number of dr_compute_bounds calls served by replaying a captured CUDA graph (dr_options.graphs). */
+ * Number of dr_compute_bounds calls and dr_optimize_slopes steps served by replaying a captured CUDA
+ * graph (dr_options.graphs). */
 int64_t dr_graph_replays(const dr_ctx* ctx);
 
 /* Paper: no passage (error reporting).

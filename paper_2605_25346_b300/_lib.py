@@ -76,7 +76,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dr_set_beta": (i32, [vp, fp, i32]),
         "dr_kernel_launches": (i64, [vp]),
         "dr_graph_replays": (i64, [vp]),
-        "dr_kernel_timing": (i32, [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
+        "dr_kernel_timing": (i32, [vp, i32, i64, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double)]),
         "dr_last_error": (ctypes.c_char_p, [vp]),
         "dr_slope_gradient_static": (i32, [ctypes.POINTER(dr_static_args)]),

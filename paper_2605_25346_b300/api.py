@@ -186,11 +186,12 @@ class Reach:
     def graph_replays(self) -> int:
         return int(self.lib.dr_graph_replays(self.ctx))
 
-    def kernel_timing(self, which: int = _lib.DR_KT_GEMM_ALL):
-        """(launches, total ms, algorithmic FLOP) of the timed tensor-core GEMM launches of a class
-        (timing is switched on with set_options(timing=1))."""
+    def kernel_timing(self, which: int = _lib.DR_KT_GEMM_ALL, min_rows: int = 0):
+        """(launches, total ms, algorithmic FLOP) of the timed tensor-core GEMM launches of a class with
+        at least `min_rows` rows (timing is switched on with set_options(timing=1))."""
         nl, ms, fl = ctypes.c_int64(0), ctypes.c_double(0.0), ctypes.c_double(0.0)
-        self._c(self.lib.dr_kernel_timing(self.ctx, which, ctypes.byref(nl), ctypes.byref(ms), ctypes.byref(fl)))
+        self._c(self.lib.dr_kernel_timing(self.ctx, which, min_rows, ctypes.byref(nl), ctypes.byref(ms),
+                                          ctypes.byref(fl)))
         return int(nl.value), float(ms.value), float(fl.value)
 
 

@@ -71,6 +71,7 @@ struct dr_ctx {
     float* dbest_beta = nullptr;
     double* dbestV = nullptr;
     double* dVhist = nullptr;
+    int* dhist_slot = nullptr;  // next V history entry of dr_optimize_slopes (device-side counter)
     double* dwlo = nullptr;
     double* dwhi = nullptr;
     // transposed TF32 parts of every layer for the tensor-core chain: layer l -> [n_{l-1}][ru32(n_l)]
@@ -107,13 +108,18 @@ struct dr_ctx {
     // pool of reusable events and the per-class totals
     struct KtPending {
         int cls;
+        int64_t rows;
         cudaEvent_t e0, e1;
         double flop;
     };
+    struct KtDone {
+        int cls;
+        int64_t rows;
+        double ms, flop;
+    };
     std::vector<KtPending> kt_pending;
+    std::vector<KtDone> kt_done;
     std::vector<cudaEvent_t> kt_pool;
-    int64_t kt_launches[4] = {};
-    double kt_ms[4] = {}, kt_flop[4] = {};
 };
 
 static thread_local std::string g_create_err;
@@ -579,7 +585,7 @@ static int tc_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* BTh
             CUDA_TRY(c, cudaEventRecord(e1, st));
             double flop = 2.0 * R * K * N;
             if (epi && epi->W1) flop += 2.0 * R * N * epi->n0;
-            c->kt_pending.push_back({cls, e0, e1, flop});
+            c->kt_pending.push_back({cls, (int64_t)R, e0, e1, flop});
         } else {
             if (e0) c->kt_pool.push_back(e0);
             if (e1) c->kt_pool.push_back(e1);
@@ -840,6 +846,7 @@ static void free_outputs(dr_ctx* c) {
     dev_free(c, (void*&)c->dbest_beta, 0);
     dev_free(c, (void*&)c->dbestV, 0);
     dev_free(c, (void*&)c->dVhist, 0);
+    dev_free(c, (void*&)c->dhist_slot, 0);
     dev_free(c, (void*&)c->dwlo, 0);
     dev_free(c, (void*&)c->dwhi, 0);
     dev_free(c, c->wscratch, c->wscratch_bytes);
@@ -907,13 +914,7 @@ int dr_set_options(dr_ctx* c, const dr_options* o) {
     if (n.slope_mode == DR_SLOPE_USER && !c->alpha_set && c->D > 0)
         return fail(c, DR_ERR_STATE, "DR_SLOPE_USER requires dr_set_alpha first");
     if (n.timing < 0 || n.timing > 1) return fail(c, DR_ERR_ARG, "timing %d out of range", n.timing);
-    if (n.timing && !c->opt.timing) {
-        // timing switched on: the totals start from zero
-        for (int k = 0; k < 4; ++k) {
-            c->kt_launches[k] = 0;
-            c->kt_ms[k] = c->kt_flop[k] = 0.0;
-        }
-    }
+    if (n.timing && !c->opt.timing) c->kt_done.clear();  // timing switched on: the totals start from zero
     c->opt = n;
     c->epoch++;  // kernel arguments may change
     return DR_OK;
@@ -930,9 +931,7 @@ static int kt_drain(dr_ctx* c) {
             cudaGetLastError();
             rc = fail(c, DR_ERR_CUDA, "dr_kernel_timing: %s", cudaGetErrorString(e));
         } else {
-            c->kt_launches[p.cls]++;
-            c->kt_ms[p.cls] += ms;
-            c->kt_flop[p.cls] += p.flop;
+            c->kt_done.push_back({p.cls, p.rows, (double)ms, p.flop});
         }
         c->kt_pool.push_back(p.e0);
         c->kt_pool.push_back(p.e1);
@@ -941,18 +940,18 @@ static int kt_drain(dr_ctx* c) {
     return rc;
 }
 
-int dr_kernel_timing(dr_ctx* c, int which, int64_t* launches, double* ms, double* flop) {
+int dr_kernel_timing(dr_ctx* c, int which, int64_t min_rows, int64_t* launches, double* ms, double* flop) {
     if (!c) return DR_ERR_ARG;
     if (which < DR_KT_GEMM_ALL || which > DR_KT_GEMM_OTHER) return fail(c, DR_ERR_ARG, "timing class %d", which);
     CUDA_TRY(c, cudaSetDevice(c->device));
     TRY(kt_drain(c));
     int64_t n = 0;
     double t = 0.0, f = 0.0;
-    for (int k = 1; k <= 3; ++k) {
-        if (which != DR_KT_GEMM_ALL && which != k) continue;
-        n += c->kt_launches[k];
-        t += c->kt_ms[k];
-        f += c->kt_flop[k];
+    for (const auto& d : c->kt_done) {
+        if ((which != DR_KT_GEMM_ALL && which != d.cls) || d.rows < min_rows) continue;
+        n++;
+        t += d.ms;
+        f += d.flop;
     }
     if (launches) *launches = n;
     if (ms) *ms = t;
@@ -1311,9 +1310,9 @@ static size_t wide_bytes_per_domain(const NetDesc& N) {
     b += sizeof(int) + sizeof(uint32_t);                          // cursor, status
     b += sizeof(float) * (n + n * n + n + n + n + 1);            // FP32 view
     b += sizeof(float) * 4 * std::max(N.hidden, 1);               // l, u, s, d
-    b += sizeof(float) * 2 * N.maxw;                              // kappa
+    b += sizeof(double) * 2 * N.maxw;                             // kappa (FP64)
     b += sizeof(float) * ((size_t)N.maxw * n + 4 * N.maxw);       // G, a, R, S
-    b += sizeof(float) * 3 * m;                                   // controller TM
+    b += sizeof(double) * 3 * m;                                  // controller TM (FP64)
     b += sizeof(float) * 4 * wide_lam_stride(N);                  // Lambda buffers (two TF32 pairs)
     b += sizeof(float) * 3 * wide_part_per_domain(N);             // intercept partials of fused levels
     b += sizeof(float) * (size_t)N.maxw * wide_lx_parts(N) * n;   // partial Lambda_x rows of a fused final level
@@ -1381,16 +1380,16 @@ static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, int lanes, int lane, float*
     a.hu = (float*)take(sizeof(float) * D * hid);
     a.hs = (float*)take(sizeof(float) * D * hid);
     a.hd = (float*)take(sizeof(float) * D * hid);
-    a.klo = (float*)take(sizeof(float) * D * N.maxw);
-    a.khi = (float*)take(sizeof(float) * D * N.maxw);
+    a.klo = (double*)take(sizeof(double) * D * N.maxw);
+    a.khi = (double*)take(sizeof(double) * D * N.maxw);
     a.G = (float*)take(sizeof(float) * D * N.maxw * n);
     a.sa = (float*)take(sizeof(float) * D * N.maxw);
     a.sRlo = (float*)take(sizeof(float) * D * N.maxw);
     a.sRhi = (float*)take(sizeof(float) * D * N.maxw);
     a.sS = (float*)take(sizeof(float) * D * N.maxw);
-    a.cu = (float*)take(sizeof(float) * D * m);
-    a.Iulo = (float*)take(sizeof(float) * D * m);
-    a.Iuhi = (float*)take(sizeof(float) * D * m);
+    a.cu = (double*)take(sizeof(double) * D * m);
+    a.Iulo = (double*)take(sizeof(double) * D * m);
+    a.Iuhi = (double*)take(sizeof(double) * D * m);
     a.lam_stride = wide_lam_stride(N);
     const int64_t lam_pad = wide_lam_pad(N);
     *lamA = (float*)take(sizeof(float) * (D * a.lam_stride + lam_pad));
@@ -1670,6 +1669,11 @@ static int ensure_wpad(dr_ctx* c, const NetDesc& N, const FusedLayout& Y) {
 // Slab budget: 8 GiB (enough for two CTAs per SM of the widest controllers), at most a quarter of the
 // free device memory (the context's own slabs counted as free), never below 1 GiB.
 static int slab_chunk(dr_ctx* c, size_t per_cta, int64_t* chunk) {
+    if (c->capturing && c->gslab && c->gslab_bytes >= per_cta) {
+        // inside a graph capture: reuse the slab of the plain run before it (no device query, no allocation)
+        *chunk = std::min<int64_t>(std::min<int64_t>(c->D, (int64_t)(c->gslab_bytes / std::max<size_t>(per_cta, 1))), 4 * 148);
+        return DR_OK;
+    }
     size_t budget = size_t(8) << 30;
     size_t free_b = 0, all_b = 0;
     if (cudaMemGetInfo(&free_b, &all_b) == cudaSuccess) budget = std::min(budget, (free_b + c->gslab_bytes) / 4);
@@ -2056,15 +2060,23 @@ int dr_optimize_slopes(dr_ctx* c, int steps, double lr_alpha, double lr_beta, do
         CUDA_TRY(c, cudaMemcpyAsync(c->dbestV, inf.data(), sizeof(double) * c->D, cudaMemcpyHostToDevice, c->stream));
         CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     }
+    if (!c->dhist_slot) TRY(dev_alloc(c, c->dhist_slot, 1));
+    CUDA_TRY(c, cudaMemsetAsync(c->dhist_slot, 0, sizeof(int), c->stream));
     const int64_t* sp_row = c->nnz ? c->dsp_row : nullptr;
-    for (int it = 0; it <= steps; ++it) {
-        TRY(run_forward(c, DR_SLOPE_USER, nullptr, it < steps));
+    // evaluation at the current slopes (forward pass, with the tape when a gradient follows), keep-best
+    // per domain, and the next V history entry
+    auto evaluate = [&](bool tape) -> int {
+        TRY(run_forward(c, DR_SLOPE_USER, nullptr, tape));
         k_keep_best<<<(unsigned)c->D, 128, 0, c->stream>>>(c->dV, c->dbestV, c->dalpha, c->dbest_alpha, c->dbeta,
                                                           c->dbest_beta, sp_row, per_dom);
-        k_sum<<<1, 256, 0, c->stream>>>(c->dbestV, c->D, c->dVhist + it);
+        k_sum_hist<<<1, 256, 0, c->stream>>>(c->dbestV, c->D, c->dVhist, c->dhist_slot);
         CUDA_TRY(c, cudaGetLastError());
         c->launches += 2;
-        if (it == steps) break;
+        return DR_OK;
+    };
+    // one projected-gradient step: evaluate with the tape, reverse sweep, projected updates
+    auto step = [&]() -> int {
+        TRY(evaluate(true));
         TRY(launch_backward(c, DR_SLOPE_USER, nullptr, nullptr, c->dgalpha, c->dgbeta));
         if (na) {
             k_pgd<<<1184, 256, 0, c->stream>>>(c->dalpha, c->dgalpha, (int64_t)na, (float)lr_alpha, 0.f, 1.f);
@@ -2075,7 +2087,46 @@ int dr_optimize_slopes(dr_ctx* c, int steps, double lr_alpha, double lr_beta, do
             c->launches++;
         }
         CUDA_TRY(c, cudaGetLastError());
+        return DR_OK;
+    };
+    int it = 0;
+    if (steps > 0) {
+        TRY(step());  // the first step runs plain: it allocates the tape, slabs and padded weights
+        it = 1;
     }
+    // The remaining steps issue the same launches on the same buffers: capture one step in a CUDA
+    // graph and replay it (needs a stream other than the legacy default stream; if the capture
+    // fails, the steps run as plain launches).
+    if (steps - it >= 1 && c->opt.graphs == 0 && !c->opt.timing && !c->graphs_broken && c->stream != nullptr) {
+        const int64_t l0 = c->launches;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t gx = nullptr;
+        if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            c->capturing = true;
+            const int rc = step();
+            c->capturing = false;
+            const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+            if (rc != DR_OK || e != cudaSuccess || !g || cudaGraphInstantiate(&gx, g, 0) != cudaSuccess) gx = nullptr;
+            if (g) cudaGraphDestroy(g);
+        }
+        const int64_t per_step = c->launches - l0;
+        c->launches = l0;
+        if (!gx) {
+            cudaGetLastError();
+        } else {
+            int rc = DR_OK;
+            for (; it < steps && rc == DR_OK; ++it) {
+                const cudaError_t e = cudaGraphLaunch(gx, c->stream);
+                if (e != cudaSuccess) rc = fail(c, DR_ERR_CUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+                c->launches += per_step;
+                c->graph_replays++;
+            }
+            cudaGraphExecDestroy(gx);
+            if (rc != DR_OK) return rc;
+        }
+    }
+    for (; it < steps; ++it) TRY(step());
+    TRY(evaluate(false));
     // install the best slopes and multipliers and leave their bounds in the output buffers
     if (na) CUDA_TRY(c, cudaMemcpyAsync(c->dalpha, c->dbest_alpha, sizeof(float) * na, cudaMemcpyDeviceToDevice, c->stream));
     if (c->nnz) CUDA_TRY(c, cudaMemcpyAsync(c->dbeta, c->dbest_beta, sizeof(float) * c->nnz, cudaMemcpyDeviceToDevice, c->stream));

@@ -507,6 +507,25 @@ __global__ void k_pgd(float* __restrict__ x, const float* __restrict__ g, int64_
 }
 
 // Sum of D values into out[0] (single block, deterministic order per thread then tree).
+// Sum of v[0..D) into hist[*slot], then *slot += 1: the slot index lives on the device, so one
+// captured refinement step (CUDA graph) writes the next history entry on every replay.
+__global__ void k_sum_hist(const double* __restrict__ v, int64_t D, double* __restrict__ hist, int* __restrict__ slot) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < D; i += blockDim.x) acc += v[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int k = *slot;
+        hist[k] = red[0];
+        *slot = k + 1;
+    }
+}
+
 __global__ void k_sum(const double* __restrict__ v, int64_t D, double* __restrict__ out) {
     __shared__ double red[256];
     double acc = 0.0;

@@ -10,6 +10,11 @@
 //            next level's intercepts and A = Lambda diag(s_{m-1}) (row reductions)      (Thm. 2)
 //     proj   G = Lambda_x P, a = Lambda_x c, R = Lambda_x (x) I, concretisation with the
 //            split dual and the outward margin (Thm. 3), or the controller TM
+//
+// The intercepts kappa are summed across chain levels in FP64 and the concretisation adds its terms
+// in FP64 (the per-level and per-row partial sums stay FP32); pre-activation bounds are rounded to
+// FP32 outward and the controller TM stays FP64.  Accumulating kappa in FP32 was the largest source
+// of deviation from FP64 arithmetic over long horizons.
 //     relax  split clipping / dual records, shared-slope relaxation              (Sec. IV-C)
 //   dyn      FP64 dynamics on the TM and EvalInt (Alg. 2)
 #pragma once
@@ -44,9 +49,9 @@ struct WideArgs {
     uint32_t* st;
     float *cf, *Pf, *Ilof, *Ihif, *vf;  // vf: [Dc][n+1] (last = wf)
     float *hl, *hu, *hs, *hd;           // [Dc][hidden]
-    float *klo, *khi;                   // [Dc][maxw]
+    double *klo, *khi;                  // [Dc][maxw] intercepts, accumulated in FP64
     float *G, *sa, *sRlo, *sRhi, *sS;   // [Dc][maxw][n], [Dc][maxw]
-    float *cu, *Iulo, *Iuhi;            // [Dc][m]
+    double *cu, *Iulo, *Iuhi;           // [Dc][m] controller TM, FP64
     int64_t lam_stride;                 // floats per domain in a Lambda buffer
 };
 
@@ -120,8 +125,8 @@ __global__ void k_w_chain_init(const WideArgs a, int ell, float* __restrict__ Ao
     const float bi = a.b[N.boff[ell - 1] + i];
     if (ell == 1) {
         if (lane == 0) {
-            a.klo[(int64_t)d * N.maxw + i] = bi;
-            a.khi[(int64_t)d * N.maxw + i] = bi;
+            a.klo[(int64_t)d * N.maxw + i] = (double)bi;
+            a.khi[(int64_t)d * N.maxw + i] = (double)bi;
         }
         return;
     }
@@ -144,8 +149,8 @@ __global__ void k_w_chain_init(const WideArgs a, int ell, float* __restrict__ Ao
     sneg = warp_sum(sneg);
     sb = warp_sum(sb);
     if (lane == 0) {
-        a.khi[(int64_t)d * N.maxw + i] = bi + spos + sb;
-        a.klo[(int64_t)d * N.maxw + i] = bi + sneg + sb;
+        a.khi[(int64_t)d * N.maxw + i] = (double)bi + (double)spos + (double)sb;
+        a.klo[(int64_t)d * N.maxw + i] = (double)bi + (double)sneg + (double)sb;
     }
 }
 
@@ -175,8 +180,8 @@ __global__ void k_w_level_epi(const WideArgs a, int ell, int mm, float* __restri
     sneg = warp_sum(sneg);
     sb = warp_sum(sb);
     if (lane == 0) {
-        a.khi[(int64_t)d * N.maxw + i] += spos + sb;
-        a.klo[(int64_t)d * N.maxw + i] += sneg + sb;
+        a.khi[(int64_t)d * N.maxw + i] += (double)spos + (double)sb;
+        a.klo[(int64_t)d * N.maxw + i] += (double)sneg + (double)sb;
     }
 }
 
@@ -227,6 +232,28 @@ __global__ void __launch_bounds__(256) k_w_gemm_simt(const float* __restrict__ A
     }
 }
 
+// The concretisation of one row from its FP32 partial sums (centre term av, remainder rlo/rhi, |G|,
+// |G -+ v|) and its FP64 intercepts: the terms are added in FP64; pre-activation bounds are rounded
+// to FP32 outward (they feed the FP32 relaxation), the controller TM stays FP64.
+__device__ __forceinline__ void concretise(const WideArgs& a, int ell, int d, int i, float av, float rlo, float rhi,
+                                           float g1, float gm, float gp, float wf, double klo, double khi) {
+    const NetDesc& N = a.net;
+    const float S = fabsf(av) + g1 + (float)fabs(klo) + (float)fabs(khi) + fabsf(rlo) + fabsf(rhi) + fabsf(wf);
+    const double mr = (double)a.rho * (double)S;
+    if (ell < N.L) {
+        a.hl[(int64_t)d * N.hidden + N.hoff[ell] + i] = __double2float_rd((double)av + klo + (double)rlo - (double)gm - (double)wf - mr);
+        a.hu[(int64_t)d * N.hidden + N.hoff[ell] + i] = __double2float_ru((double)av + khi + (double)rhi + (double)gp + (double)wf + mr);
+        a.sa[(int64_t)d * N.maxw + i] = av;
+        a.sRlo[(int64_t)d * N.maxw + i] = rlo;
+        a.sRhi[(int64_t)d * N.maxw + i] = rhi;
+        a.sS[(int64_t)d * N.maxw + i] = S;
+    } else {
+        a.cu[(int64_t)d * N.m + i] = (double)av + 0.5 * (klo + khi);
+        a.Iulo[(int64_t)d * N.m + i] = 0.5 * (klo - khi) + (double)rlo - mr;
+        a.Iuhi[(int64_t)d * N.m + i] = 0.5 * (khi - klo) + (double)rhi + mr;
+    }
+}
+
 // Concretisation of target ell over the TM input.  One warp per (domain, row); Lx is the
 // domain's Lambda_x (rows x n, ld n) or, for ell == 1, the shared W_1.
 __global__ void k_w_project(const WideArgs a, int ell, const float* __restrict__ Lxb, int shared_lx) {
@@ -266,21 +293,8 @@ __global__ void k_w_project(const WideArgs a, int ell, const float* __restrict__
     rlo = warp_sum(rlo);
     rhi = warp_sum(rhi);
     if (lane != 0) return;
-    const float klo = a.klo[(int64_t)d * N.maxw + i], khi = a.khi[(int64_t)d * N.maxw + i];
-    const float wf = vf[n];
-    const float S = fabsf(av) + g1 + fabsf(klo) + fabsf(khi) + fabsf(rlo) + fabsf(rhi) + fabsf(wf);
-    if (ell < L) {
-        a.hl[(int64_t)d * N.hidden + N.hoff[ell] + i] = av + klo + rlo - gm - wf - a.rho * S;
-        a.hu[(int64_t)d * N.hidden + N.hoff[ell] + i] = av + khi + rhi + gp + wf + a.rho * S;
-        a.sa[(int64_t)d * N.maxw + i] = av;
-        a.sRlo[(int64_t)d * N.maxw + i] = rlo;
-        a.sRhi[(int64_t)d * N.maxw + i] = rhi;
-        a.sS[(int64_t)d * N.maxw + i] = S;
-    } else {
-        a.cu[(int64_t)d * N.m + i] = av + 0.5f * (klo + khi);
-        a.Iulo[(int64_t)d * N.m + i] = 0.5f * (klo - khi) + rlo - a.rho * S;
-        a.Iuhi[(int64_t)d * N.m + i] = 0.5f * (khi - klo) + rhi + a.rho * S;
-    }
+    const double klo = a.klo[(int64_t)d * N.maxw + i], khi = a.khi[(int64_t)d * N.maxw + i];
+    concretise(a, ell, d, i, av, rlo, rhi, g1, gm, gp, vf[n], klo, khi);
 }
 
 // Splits of (t, ell) and the shared-slope relaxation of hidden layer ell; one block per domain.
@@ -301,8 +315,8 @@ __global__ void k_w_relax(const WideArgs a, int ell, int t) {
                 const int j = r.neuron;
                 const int64_t q = (int64_t)d * N.maxw + j;
                 const float bt = a.beta ? a.beta[cpos] : 0.f;
-                const float hh = r.sign > 0 ? (a.sa[q] + a.khi[q] + a.sRhi[q] + a.rho * a.sS[q])
-                                            : (-(a.sa[q] + a.klo[q] + a.sRlo[q]) + a.rho * a.sS[q]);
+                const double hh = r.sign > 0 ? ((double)a.sa[q] + a.khi[q] + (double)a.sRhi[q] + (double)a.rho * a.sS[q])
+                                             : (-((double)a.sa[q] + a.klo[q] + (double)a.sRlo[q]) + (double)a.rho * a.sS[q]);
                 if (r.sign > 0) {
                     if (lh[j] < 0.f) lh[j] = 0.f;
                 } else {
@@ -367,9 +381,9 @@ __global__ void k_w_dyn(const WideArgs a, int t) {
     const double* Ilo = a.Ilo + (int64_t)d * n;
     const double* Ihi = a.Ihi + (int64_t)d * n;
     const float* G = a.G + (int64_t)d * N.maxw * n;
-    const float* cu = a.cu + (int64_t)d * m;
-    const float* Iulo = a.Iulo + (int64_t)d * m;
-    const float* Iuhi = a.Iuhi + (int64_t)d * m;
+    const double* cu = a.cu + (int64_t)d * m;
+    const double* Iulo = a.Iulo + (int64_t)d * m;
+    const double* Iuhi = a.Iuhi + (int64_t)d * m;
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
         const int i = idx / n, k = idx - i * n;
         double acc = 0.0;
@@ -387,9 +401,9 @@ __global__ void k_w_dyn(const WideArgs a, int t) {
         }
         for (int j = 0; j < m; ++j) {
             const double x = a.B[i * m + j];
-            acc = fma(x, (double)cu[j], acc);
-            lo_ += posd(x) * (double)Iulo[j] + negd(x) * (double)Iuhi[j];
-            hi_ += posd(x) * (double)Iuhi[j] + negd(x) * (double)Iulo[j];
+            acc = fma(x, cu[j], acc);
+            lo_ += posd(x) * Iulo[j] + negd(x) * Iuhi[j];
+            hi_ += posd(x) * Iuhi[j] + negd(x) * Iulo[j];
         }
         cn[i] = acc;
         Ilon[i] = lo_;
@@ -504,8 +518,8 @@ __global__ void k_t_chain_init(const WideArgs a, int ell, float* __restrict__ Ah
     sneg = warp_sum(sneg);
     sb = warp_sum(sb);
     if (lane == 0) {
-        a.khi[(int64_t)d * N.maxw + i] = bi + spos + sb;
-        a.klo[(int64_t)d * N.maxw + i] = bi + sneg + sb;
+        a.khi[(int64_t)d * N.maxw + i] = (double)bi + (double)spos + (double)sb;
+        a.klo[(int64_t)d * N.maxw + i] = (double)bi + (double)sneg + (double)sb;
     }
 }
 
@@ -550,9 +564,9 @@ __global__ void k_t2_finish(const WideArgs a, const float* __restrict__ C1, cons
         const int d = (int)(r / rows), i = (int)(r - (int64_t)d * rows);
         const float* c1 = C1 + i * ld1 + (int64_t)d * NB;
         for (int c = 0; c < n; ++c) Lx[r * n + c] = c1[c];
-        const float bi = a.b[N.boff[1] + i], sb = c1[n];
-        a.khi[(int64_t)d * N.maxw + i] = bi + C2[i * ld2 + d] + sb;
-        a.klo[(int64_t)d * N.maxw + i] = bi + C2[(rows + i) * ld2 + d] + sb;
+        const double bi = a.b[N.boff[1] + i], sb = c1[n];
+        a.khi[(int64_t)d * N.maxw + i] = bi + (double)C2[i * ld2 + d] + sb;
+        a.klo[(int64_t)d * N.maxw + i] = bi + (double)C2[(rows + i) * ld2 + d] + sb;
     }
 }
 
@@ -563,7 +577,7 @@ __global__ void k_t_partials(const WideArgs a, int ell, const float* __restrict_
     const int64_t R = (int64_t)a.Dc * rows;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
         const int d = (int)(r / rows), i = (int)(r - (int64_t)d * rows);
-        float sp = 0.f, sn = 0.f, sb = 0.f;
+        double sp = 0.0, sn = 0.0, sb = 0.0;
         for (int t = 0; t < ntiles; ++t) {
             sp += part[((int64_t)t * 3 + 0) * R + r];
             sn += part[((int64_t)t * 3 + 1) * R + r];
@@ -619,13 +633,13 @@ __global__ void __launch_bounds__(256, 3) k_t_project4(const WideArgs a, int ell
             xl[e] = v;
         }
         const float wf = vf[n];
-        float klo = 0.f, khi = 0.f;
+        double klo = 0.0, khi = 0.0;
         if (shared_lx) klo = khi = a.b[N.boff[0] + i];
         else {
             klo = a.klo[(int64_t)d * N.maxw + i];
             khi = a.khi[(int64_t)d * N.maxw + i];
         }
-        float sp = 0.f, sn = 0.f, sb = 0.f;
+        double sp = 0.0, sn = 0.0, sb = 0.0;
         if (!shared_lx && ntiles > 0) {
             for (int t = q; t < ntiles; t += 4) {
                 sp += part[((int64_t)t * 3 + 0) * R + rc];
@@ -704,19 +718,7 @@ __global__ void __launch_bounds__(256, 3) k_t_project4(const WideArgs a, int ell
             a.klo[(int64_t)d * N.maxw + i] = klo;
             a.khi[(int64_t)d * N.maxw + i] = khi;
         }
-        const float S = fabsf(av) + g1 + fabsf(klo) + fabsf(khi) + fabsf(rlo) + fabsf(rhi) + fabsf(wf);
-        if (ell < L) {
-            a.hl[(int64_t)d * N.hidden + N.hoff[ell] + i] = av + klo + rlo - gm - wf - a.rho * S;
-            a.hu[(int64_t)d * N.hidden + N.hoff[ell] + i] = av + khi + rhi + gp + wf + a.rho * S;
-            a.sa[(int64_t)d * N.maxw + i] = av;
-            a.sRlo[(int64_t)d * N.maxw + i] = rlo;
-            a.sRhi[(int64_t)d * N.maxw + i] = rhi;
-            a.sS[(int64_t)d * N.maxw + i] = S;
-        } else {
-            a.cu[(int64_t)d * N.m + i] = av + 0.5f * (klo + khi);
-            a.Iulo[(int64_t)d * N.m + i] = 0.5f * (klo - khi) + rlo - a.rho * S;
-            a.Iuhi[(int64_t)d * N.m + i] = 0.5f * (khi - klo) + rhi + a.rho * S;
-        }
+        concretise(a, ell, d, i, av, rlo, rhi, g1, gm, gp, wf, klo, khi);
     }
 }
 
@@ -736,14 +738,14 @@ __global__ void __launch_bounds__(128) k_t_project(const WideArgs a, int ell, co
         const int d = (int)(r / rows), i = (int)(r - (int64_t)d * rows);
         // kappa (and the final chain level's intercept partials, summed as k_t_partials does) is read
         // before anything is stored
-        float klo, khi;
+        double klo, khi;
         if (shared_lx) {
             klo = khi = a.b[N.boff[0] + i];
         } else {
             klo = a.klo[(int64_t)d * N.maxw + i];
             khi = a.khi[(int64_t)d * N.maxw + i];
             if (ntiles > 0) {
-                float sp = 0.f, sn = 0.f, sb = 0.f;
+                double sp = 0.0, sn = 0.0, sb = 0.0;
                 for (int t = 0; t < ntiles; ++t) {
                     sp += part[((int64_t)t * 3 + 0) * R + r];
                     sn += part[((int64_t)t * 3 + 1) * R + r];
@@ -838,19 +840,6 @@ __global__ void __launch_bounds__(128) k_t_project(const WideArgs a, int ell, co
             a.klo[(int64_t)d * N.maxw + i] = klo;
             a.khi[(int64_t)d * N.maxw + i] = khi;
         }
-        const float wf = vf[n];
-        const float S = fabsf(av) + g1 + fabsf(klo) + fabsf(khi) + fabsf(rlo) + fabsf(rhi) + fabsf(wf);
-        if (ell < L) {
-            a.hl[(int64_t)d * N.hidden + N.hoff[ell] + i] = av + klo + rlo - gm - wf - a.rho * S;
-            a.hu[(int64_t)d * N.hidden + N.hoff[ell] + i] = av + khi + rhi + gp + wf + a.rho * S;
-            a.sa[(int64_t)d * N.maxw + i] = av;
-            a.sRlo[(int64_t)d * N.maxw + i] = rlo;
-            a.sRhi[(int64_t)d * N.maxw + i] = rhi;
-            a.sS[(int64_t)d * N.maxw + i] = S;
-        } else {
-            a.cu[(int64_t)d * N.m + i] = av + 0.5f * (klo + khi);
-            a.Iulo[(int64_t)d * N.m + i] = 0.5f * (klo - khi) + rlo - a.rho * S;
-            a.Iuhi[(int64_t)d * N.m + i] = 0.5f * (khi - klo) + rhi + a.rho * S;
-        }
+        concretise(a, ell, d, i, av, rlo, rhi, g1, gm, gp, vf[n], klo, khi);
     }
 }

@@ -74,3 +74,43 @@ def test_replay_reads_new_boxes_and_recaptures_on_new_options():
     assert r.graph_replays() == n0 + 1  # plain, capture, replay
     r.close()
     ref.close()
+
+
+# Refinement: the first projected-gradient step runs plain, the others replay one captured step.
+# The V history, the kept slopes and multipliers and the final bounds equal those of a context with
+# graphs disabled, bit for bit; the shared-memory and the global-slab (wide controller) reverse
+# kernels, with and without split multipliers.
+@pytest.mark.parametrize("case", ["fused", "slab", "splits"])
+def test_refinement_steps_replayed_from_a_graph(case):
+    if case == "fused":
+        p, lrb = wl.random_problem(81, [4, 24, 24, 2], D=40, H=4, eps=0.3), 0.0
+    elif case == "slab":
+        p, lrb = wl.random_problem(82, [4, 300, 300, 2], D=6, H=3, eps=0.2), 0.0
+    else:
+        p = wl.random_problem(83, [6, 40, 40, 3], D=24, H=5, eps=0.2)
+        rng = np.random.default_rng(3)
+        p.splits = wl.branch_splits(p, rng, max_k=6)
+        p.beta = rng.uniform(0.0, 0.05, size=p.splits.nnz).astype(np.float32).astype(np.float64)
+        lrb = 0.01
+    steps = 5
+    out = {}
+    for graphs in (1, 0):
+        r = _reach(p, graphs=graphs)
+        with torch.cuda.stream(r.stream):
+            a0 = r.get_alpha()
+            g = torch.Generator().manual_seed(1)
+            alpha = np.clip(a0 + 0.1 * (torch.rand(a0.shape, generator=g).numpy() - 0.5), 0.0, 1.0).astype(np.float32)
+            r.set_alpha(alpha)
+            replays0 = r.graph_replays()
+            hist = r.optimize(steps, 0.05, lrb)
+            replays = r.graph_replays() - replays0
+            out[graphs] = (hist, r.get_alpha(), r.get_beta(), r.bounds(on_device=False), replays)
+        r.close()
+    h1, a1, b1, o1, rep1 = out[1]
+    h0, a0, b0, o0, rep0 = out[0]
+    assert rep1 == 0 and rep0 == steps - 1
+    np.testing.assert_array_equal(h0, h1)
+    np.testing.assert_array_equal(a0, a1)
+    np.testing.assert_array_equal(b0, b1)
+    _same(o0, o1)
+    assert (np.diff(h0) <= 0).all()
