@@ -150,6 +150,24 @@ int dr_set_boxes(dr_ctx* ctx, int64_t D, const double* lo, const double* hi, int
  * of the split constraints g_k^T zeta + h_k >= 0. */
 int dr_set_splits(dr_ctx* ctx, const int64_t* row_ptr, const dr_split* s, const float* beta);
 
+/* Paper: the planned or exogenous inputs {u_k} of Alg. 2 and the sampled action sequences of
+ * reachability-aware MPC (Sec. V-B).  Per-domain, per-step offsets of the dynamics,
+ *     x_{t+1} = A x_t + B pi(x_t) + e + e_off[d, t],
+ * e_off [D x H x n] FP64, host (on_device = 0) or device memory; NULL removes them.  With the state
+ * augmented by the planned input, y = [x; u], A = [[0 (or I), 0], [0, 0]], B = [[I], [0]] and
+ * e_off[d, t] = [0; u_{d,t+1}], the loop is the neural dynamics y_{t+1} = f(x_t, u_t) of Alg. 2 (the
+ * initial box carries u_{d,0} as a point), each domain one action sequence.  Set after the boxes and
+ * horizon; dr_set_boxes and a new horizon remove them.  DR_ERR_NONFINITE for a non-finite host value. */
+int dr_set_step_offsets(dr_ctx* ctx, const double* e_off, int on_device);
+
+/* Paper: the gradient of the reachable-set objective with respect to the planned inputs, which the
+ * planner of Sec. V-B refines.  After dr_backward: g [D x (H+1) x n] FP64, the gradient of the
+ * objective dr_backward differentiated with respect to a shift of the Taylor-model centre at step t
+ * (t = 0: the initial box centre; t >= 1: an offset added after step t-1).  For the augmented
+ * neural-dynamics form above, g[d, t, n_x:] is dV/du_{d,t} for t = 0..H-1.  DR_ERR_STATE if no
+ * dr_backward ran since the problem changed. */
+int dr_get_shift_gradient(dr_ctx* ctx, double* g, int on_device);
+
 /* Paper: the horizon H of Alg. 2.
  * Horizon H >= 1 (number of controller/dynamics steps). */
 int dr_set_horizon(dr_ctx* ctx, int H);

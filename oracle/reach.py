@@ -25,7 +25,9 @@ proxy), for each domain d independently:
             neurons lower alpha z, upper alpha z + max(-alpha l, (1-alpha) u)  (Sec. IV-C)
       a6  output layer: controller TM  P_u = G, c_u = a + (k_lo+k_hi)/2,
             I_u = +-(k_hi-k_lo)/2 + [R_lo, R_hi]                           (Thm. 3, App. B)
-    a7  dynamics: P' = A P + B P_u, c' = A c + B c_u + e, I' = A (x) [I] + B (x) [I_u]
+    a7  dynamics: P' = A P + B P_u, c' = A c + B c_u + e + e_{d,t}, I' = A (x) [I] + B (x) [I_u]
+        (e_{d,t}: optional per-domain, per-step offsets; with the state augmented by the planned
+        input, y = [x; u], they carry the planned inputs u_k of Alg. 2 into a neural dynamics model)
     a8  EvalInt: box_{t+1} = c' +- |P'|_1 + [I']                          (Alg. 2)
   a9  hull over domains; V_d = sum_{t=1..H} sum_i width(box_{t,i})           (Sec. V-A)
 
@@ -135,10 +137,14 @@ class _SplitIndex:
 
 
 def reach(prob, alpha: Optional[torch.Tensor] = None, beta: Optional[torch.Tensor] = None,
-          mode: Optional[int] = None, record: Optional[list] = None, keep_intermediate: bool = False):
+          mode: Optional[int] = None, record: Optional[list] = None, keep_intermediate: bool = False,
+          shift: Optional[torch.Tensor] = None):
     """Bounds for every domain, step and coordinate (Alg. 2 with the closed loop of Sec. IV-E).
 
     alpha: [D, H, hidden] (MODE_USER only); beta: [nnz] split multipliers (>= 0) or None.
+    shift: optional [D, H+1, n] shift of the TM centre, added to c_0 (entry 0) and to c_{t+1} after
+    the dynamics of step t (entry t+1), on top of the problem's offsets; used to differentiate V
+    with respect to the initial centre and the per-step offsets.
     Returns a dict with lo/hi [D, H+1, n], V [D], status [D] (int64), hull_lo/hull_hi [H+1, n],
     alpha_used [D, H, hidden] (the slopes in effect; zeros at stable neurons),
     and optionally the intermediate pre-activation bounds l/u [D, H, hidden].
@@ -158,8 +164,12 @@ def reach(prob, alpha: Optional[torch.Tensor] = None, beta: Optional[torch.Tenso
         beta = torch.zeros(nnz, dtype=_F64) if prob.beta is None else _t(prob.beta)
 
     lo0, hi0 = _t(prob.lo), _t(prob.hi)
+    eoff = _t(prob.eoff) if getattr(prob, "eoff", None) is not None else None
     # a1: BuildLinearTM over the normalised box
     c = 0.5 * (lo0 + hi0)
+    if shift is not None:
+        c = c + shift[:, 0, :]
+        lo0, hi0 = lo0 + shift[:, 0, :], hi0 + shift[:, 0, :]
     P = torch.diag_embed(0.5 * (hi0 - lo0))
     Ilo = torch.zeros(D, n, dtype=_F64)
     Ihi = torch.zeros(D, n, dtype=_F64)
@@ -248,6 +258,10 @@ def reach(prob, alpha: Optional[torch.Tensor] = None, beta: Optional[torch.Tenso
         # a7: linear dynamics on the TM
         P_n = A @ P + B @ Pu
         c_n = c @ A.T + cu @ B.T + e
+        if eoff is not None:
+            c_n = c_n + eoff[:, t, :]
+        if shift is not None:
+            c_n = c_n + shift[:, t + 1, :]
         aLo, aHi = interval_matvec(A, Ilo, Ihi)
         bLo, bHi = interval_matvec(B, Iulo, Iuhi)
         P, c, Ilo, Ihi = P_n, c_n, aLo + bLo, aHi + bHi
@@ -316,6 +330,18 @@ def value_and_grad(prob, alpha: torch.Tensor, beta: Optional[torch.Tensor] = Non
     ga = a.grad if a.grad is not None else torch.zeros_like(a)
     gb = bt.grad if bt.grad is not None else torch.zeros_like(bt)
     return res, ga, gb
+
+
+def value_and_shift_grad(prob, alpha: Optional[torch.Tensor] = None, beta: Optional[torch.Tensor] = None):
+    """V per domain and dV/dshift [D, H+1, n]: the gradient of V with respect to a shift of the TM
+    centre at step t (t = 0: the initial box centre; t >= 1: the offset added after step t-1).  For a
+    neural dynamics model over the state augmented by the planned input (workloads.neural_dynamics)
+    its action rows are dV/du_t, t = 0..H-1 (reverse-mode AD of the FP64 forward pass)."""
+    sh = torch.zeros(prob.D, prob.H + 1, prob.n, dtype=_F64, requires_grad=True)
+    kw = dict(mode=MODE_USER, alpha=alpha) if alpha is not None else {}
+    res = reach(prob, beta=beta, shift=sh, **kw)
+    res["V"].sum().backward()
+    return res, sh.grad
 
 
 def chord_alpha(prob) -> torch.Tensor:
@@ -409,7 +435,8 @@ def ibp_reach(prob) -> Dict[str, torch.Tensor]:
                 ulo, uhi = zl, zh
         al, ah = interval_matvec(A, lo, hi)
         bl, bh = interval_matvec(B, ulo, uhi)
-        lo, hi = al + bl + e, ah + bh + e
+        off = _t(prob.eoff)[:, _t_, :] if getattr(prob, "eoff", None) is not None else 0.0
+        lo, hi = al + bl + e + off, ah + bh + e + off
         los.append(lo)
         his.append(hi)
     return dict(lo=torch.stack(los, 1), hi=torch.stack(his, 1))

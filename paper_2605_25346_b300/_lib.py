@@ -20,7 +20,7 @@ DR_KT_GEMM_ALL, DR_KT_GEMM_CHAIN, DR_KT_GEMM_FINAL, DR_KT_GEMM_OTHER = 0, 1, 2, 
 # every symbol the header declares
 EXPORTS = [
     "dr_create", "dr_destroy", "dr_load_controller", "dr_load_dynamics", "dr_set_boxes", "dr_set_splits",
-    "dr_set_horizon", "dr_set_options", "dr_compute_bounds", "dr_get_objective", "dr_optimize_slopes",
+    "dr_set_horizon", "dr_set_step_offsets", "dr_get_shift_gradient", "dr_set_options", "dr_compute_bounds", "dr_get_objective", "dr_optimize_slopes",
     "dr_backward", "dr_get_alpha", "dr_set_alpha", "dr_get_beta", "dr_set_beta", "dr_kernel_launches", "dr_graph_replays", "dr_kernel_timing", "dr_last_error",
     "dr_slope_gradient_static", "dr_tf32x3_gemm", "dr_check_wait_expiry",
 ]
@@ -65,6 +65,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dr_set_boxes": (i32, [vp, i64, dp, dp, i32]),
         "dr_set_splits": (i32, [vp, vp, vp, fp]),
         "dr_set_horizon": (i32, [vp, i32]),
+        "dr_set_step_offsets": (i32, [vp, dp, i32]),
+        "dr_get_shift_gradient": (i32, [vp, dp, i32]),
         "dr_set_options": (i32, [vp, ctypes.POINTER(dr_options)]),
         "dr_compute_bounds": (i32, [vp, dp, dp, dp, dp, vp, i32]),
         "dr_get_objective": (i32, [vp, dp, i32]),

@@ -97,6 +97,8 @@ class Reach:
             self._c(self.lib.dr_set_boxes(self.ctx, prob.D, _ptr(lo), _ptr(hi), 0))
         if prob.splits is not None:
             self.set_splits(prob.splits, prob.beta)
+        if getattr(prob, "eoff", None) is not None:
+            self.set_step_offsets(prob.eoff)
         # dr_set_boxes resets the slope mode to the default; restore the requested one
         self.set_options(m0, precision, rho)
         return self
@@ -111,6 +113,25 @@ class Reach:
         rp = np.ascontiguousarray(splits.row_ptr, dtype=np.int64)
         bt = None if beta is None else np.ascontiguousarray(beta, dtype=np.float32)
         self._c(self.lib.dr_set_splits(self.ctx, _ptr(rp), _ptr(rec), None if bt is None else _ptr(bt)))
+
+    def set_step_offsets(self, eoff):
+        """Per-step dynamics offsets [D, H, n] (numpy host array or CUDA tensor); None removes them."""
+        if eoff is None:
+            self._c(self.lib.dr_set_step_offsets(self.ctx, None, 0))
+        elif isinstance(eoff, torch.Tensor):
+            e = eoff.to(torch.float64).contiguous()
+            self._c(self.lib.dr_set_step_offsets(self.ctx, _ptr(e), 1))
+            torch.cuda.synchronize()
+        else:
+            e = np.ascontiguousarray(eoff, dtype=np.float64)
+            self._c(self.lib.dr_set_step_offsets(self.ctx, _ptr(e), 0))
+
+    def shift_gradient(self) -> np.ndarray:
+        """dV/d(shift of the TM centre at step t) [D, H+1, n] of the last backward() call."""
+        p = self.prob
+        g = np.empty((p.D, p.H + 1, p.n))
+        self._c(self.lib.dr_get_shift_gradient(self.ctx, _ptr(g), 0))
+        return g
 
     # ---- computation ---------------------------------------------------------------------
     def bounds(self, on_device: bool = True, hull: bool = True):

@@ -55,6 +55,10 @@ struct dr_ctx {
     float* dalpha = nullptr;  // [D][H][hidden]
     bool alpha_set = false;
 
+    double* deoff = nullptr;    // [D][H][n] per-step offsets of the dynamics (null: none)
+    double* dgshift = nullptr;  // [D][H+1][n] shift gradient written by the last dr_backward
+    bool gshift_valid = false;
+
     // library-owned outputs / scratch
     double* dout_lo = nullptr;
     double* dout_hi = nullptr;
@@ -849,6 +853,8 @@ static void free_outputs(dr_ctx* c) {
     dev_free(c, (void*&)c->dhist_slot, 0);
     dev_free(c, (void*&)c->dwlo, 0);
     dev_free(c, (void*&)c->dwhi, 0);
+    dev_free(c, (void*&)c->dgshift, 0);
+    c->gshift_valid = false;
     dev_free(c, c->wscratch, c->wscratch_bytes);
     c->wscratch_bytes = 0;
     dev_free(c, (void*&)c->gslab, c->gslab_bytes);
@@ -876,6 +882,7 @@ void dr_destroy(dr_ctx* c) {
     cudaFree(c->dsp);
     cudaFree(c->dbeta);
     cudaFree(c->dalpha);
+    cudaFree(c->deoff);
     cudaFree(c->dWTh);
     cudaFree(c->dWTl);
     cudaFree(c->dA2h);
@@ -1134,6 +1141,7 @@ int dr_load_dynamics(dr_ctx* c, int n, int m, const double* A, const double* B, 
 
 static void clear_domain_state(dr_ctx* c) {
     free_outputs(c);
+    dev_free(c, (void*&)c->deoff, 0);
     dev_free(c, (void*&)c->dsp_row, 0);
     dev_free(c, (void*&)c->dsp, 0);
     dev_free(c, (void*&)c->dbeta, 0);
@@ -1157,7 +1165,8 @@ int dr_set_boxes(dr_ctx* c, int64_t D, const double* lo, const double* hi, int o
     CUDA_TRY(c, cudaSetDevice(c->device));
     if (D > 0 && D == c->D && c->dlo0 && c->dhi0) {
         // same domain count: keep the box and output buffers (and any captured graph); the
-        // per-domain splits and slopes are reset as for new boxes
+        // per-domain splits, slopes and step offsets are reset as for new boxes
+        dev_free(c, (void*&)c->deoff, 0);
         dev_free(c, (void*&)c->dsp_row, 0);
         dev_free(c, (void*&)c->dsp, 0);
         dev_free(c, (void*&)c->dbeta, 0);
@@ -1234,6 +1243,7 @@ int dr_set_horizon(dr_ctx* c, int H) {
     if (H < 1 || H > 100000) return fail(c, DR_ERR_ARG, "H = %d", H);
     if (H != c->H) {
         free_outputs(c);
+        dev_free(c, (void*&)c->deoff, 0);
         dev_free(c, (void*&)c->dalpha, 0);
         c->alpha_set = false;
         if (c->opt.slope_mode == DR_SLOPE_USER) c->opt.slope_mode = DR_SLOPE_CHORD;
@@ -1592,6 +1602,7 @@ static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
     a.A = c->dA;
     a.B = c->dB;
     a.e = c->de;
+    a.eoff = c->deoff;
     a.lo0 = c->dlo0;
     a.hi0 = c->dhi0;
     a.sp_row = c->nnz ? c->dsp_row : nullptr;
@@ -1718,6 +1729,7 @@ static int run_forward(dr_ctx* c, int mode, float* alpha_used, bool tape) {
         a.A = c->dA;
         a.B = c->dB;
         a.e = c->de;
+        a.eoff = c->deoff;
         a.lo0 = c->dlo0;
         a.hi0 = c->dhi0;
         a.D = c->D;
@@ -1748,6 +1760,7 @@ static int run_forward(dr_ctx* c, int mode, float* alpha_used, bool tape) {
     a.A = c->dA;
     a.B = c->dB;
     a.e = c->de;
+    a.eoff = c->deoff;
     a.lo0 = c->dlo0;
     a.hi0 = c->dhi0;
     a.sp_row = c->nnz ? c->dsp_row : nullptr;
@@ -1942,7 +1955,8 @@ int dr_set_beta(dr_ctx* c, const float* beta, int on_device) {
     return DR_OK;
 }
 
-static int launch_backward(dr_ctx* c, int mode, const double* wlo, const double* whi, float* galpha, float* gbeta) {
+static int launch_backward(dr_ctx* c, int mode, const double* wlo, const double* whi, float* galpha, float* gbeta,
+                           double* gshift = nullptr) {
     NetDesc N = c->net;
     N.H = c->H;
     if (c->D == 0) return DR_OK;
@@ -1956,6 +1970,7 @@ static int launch_backward(dr_ctx* c, int mode, const double* wlo, const double*
     a.A = c->dA;
     a.B = c->dB;
     a.e = c->de;
+    a.eoff = c->deoff;
     a.lo0 = c->dlo0;
     a.hi0 = c->dhi0;
     a.sp_row = c->nnz ? c->dsp_row : nullptr;
@@ -1970,6 +1985,7 @@ static int launch_backward(dr_ctx* c, int mode, const double* wlo, const double*
     a.whi = whi;
     a.dalpha = galpha;
     a.dbeta = gbeta;
+    a.gshift = gshift;
     const int nt = fused_threads(N);
     int smem = a.lay.total;
     int64_t chunk = 1 << 20;
@@ -2025,13 +2041,47 @@ int dr_backward(dr_ctx* c, const double* dV_dlo, const double* dV_dhi, float* da
         wlo = c->dwlo;
         whi = c->dwhi;
     }
+    if (!c->dgshift) TRY(dev_alloc(c, c->dgshift, nw));
+    c->gshift_valid = false;
     TRY(run_forward(c, mode, nullptr, true));
-    TRY(launch_backward(c, mode, wlo, whi, c->dgalpha, c->dgbeta));
+    TRY(launch_backward(c, mode, wlo, whi, c->dgalpha, c->dgbeta, c->dgshift));
+    c->gshift_valid = true;
     const size_t na = (size_t)c->D * c->H * c->net.hidden;
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (dalpha && na) CUDA_TRY(c, cudaMemcpyAsync(dalpha, c->dgalpha, sizeof(float) * na, k, c->stream));
     if (dbeta && c->nnz) CUDA_TRY(c, cudaMemcpyAsync(dbeta, c->dgbeta, sizeof(float) * c->nnz, k, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return DR_OK;
+}
+
+int dr_set_step_offsets(dr_ctx* c, const double* eoff, int on_device) {
+    if (!c) return DR_ERR_ARG;
+    TRY(check_ready(c));
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    if (!eoff) {
+        dev_free(c, (void*&)c->deoff, 0);
+        return DR_OK;
+    }
+    const size_t cnt = (size_t)c->D * c->H * c->net.n;
+    if (!on_device)
+        for (size_t i = 0; i < cnt; ++i)
+            if (!std::isfinite(eoff[i])) return fail(c, DR_ERR_NONFINITE, "non-finite step offset at %zu", i);
+    if (c->D == 0) return DR_OK;
+    if (!c->deoff) TRY(dev_alloc(c, c->deoff, cnt));
+    CUDA_TRY(c, cudaMemcpyAsync(c->deoff, eoff, sizeof(double) * cnt, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                c->stream));
+    if (!on_device) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return DR_OK;
+}
+
+int dr_get_shift_gradient(dr_ctx* c, double* g, int on_device) {
+    if (!c || !g) return fail(c, DR_ERR_ARG, "dr_get_shift_gradient: NULL");
+    if (!c->gshift_valid || !c->dgshift) return fail(c, DR_ERR_STATE, "no dr_backward since the problem changed");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    const size_t cnt = (size_t)c->D * (c->H + 1) * c->net.n;
+    CUDA_TRY(c, cudaMemcpyAsync(g, c->dgshift, sizeof(double) * cnt, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                c->stream));
+    if (!on_device) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return DR_OK;
 }
 

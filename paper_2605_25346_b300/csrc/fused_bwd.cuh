@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused_backward(const FusedArgs a) {
         const int cursor0 = s.misc[0];
         tm_view<NT>(s, n);
         controller_pass<NT>(s, N, a, dom, sp_end, t, vsnap, levall, kall);
-        dynamics<NT>(s, N);
+        dynamics<NT>(s, N, a.eoff ? a.eoff + (dom * H + t) * (int64_t)n : nullptr);
 
         // ---- EvalInt of box t+1 (uses the dual state after step t)
         const int64_t wrow = (dom * (H + 1) + t + 1) * n;
@@ -133,6 +133,9 @@ __global__ void __launch_bounds__(NT, 2) k_fused_backward(const FusedArgs a) {
             gw[0] += acc;
         }
         __syncthreads();
+        // gcn is now the whole adjoint of c_{t+1}: the gradient of a shift added after step t
+        if (a.gshift)
+            for (int i = tid; i < n; i += NT) a.gshift[(dom * (H + 1) + t + 1) * n + i] = gcn[i];
 
         // ---- dynamics reverse: TM_t and controller-TM adjoints
         for (int idx = tid; idx < n * n; idx += NT) {
@@ -481,6 +484,9 @@ __global__ void __launch_bounds__(NT, 2) k_fused_backward(const FusedArgs a) {
         }
         __syncthreads();
     }
+    // after step 0: the adjoint of the initial centre c_0
+    if (a.gshift)
+        for (int i = tid; i < n; i += NT) a.gshift[(dom * (H + 1)) * n + i] = gcn[i];
 }
 
 // Keep-best per domain: if V improved, remember the slopes and multipliers.

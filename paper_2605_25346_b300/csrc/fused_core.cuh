@@ -48,6 +48,7 @@ struct FusedArgs {
     const double* A;
     const double* B;
     const double* e;
+    const double* eoff;  // [D][H][n] per-step offsets of the dynamics (added after step t) or null
     const double* lo0;  // [D][n]
     const double* hi0;
     int64_t d0;         // first domain of this launch
@@ -71,6 +72,7 @@ struct FusedArgs {
     int64_t slab_stride;
     const float* gwpad;  // slab mode: one padded weight copy shared by all CTAs (offsets Ws[l] - Ws[0])
     // reverse kernel
+    double* gshift;     // [D][H+1][n] dV/d(shift of the TM centre at step t) or null
     const double* wlo;  // [D][H+1][n] upstream gradient of lo (null: -1 on steps 1..H)
     const double* whi;  // [D][H+1][n] upstream gradient of hi (null: +1 on steps 1..H)
     float* dalpha;      // [D][H][hidden] or null
@@ -422,7 +424,7 @@ __device__ void relax(const Dom& s, const NetDesc& N, const FusedArgs& a, int64_
 
 // a7: dynamics on the TM in FP64 into cn/Pn/Ilon/Ihin.  Ends with a barrier.
 template <int NT>
-__device__ void dynamics(const Dom& s, const NetDesc& N) {
+__device__ void dynamics(const Dom& s, const NetDesc& N, const double* off) {
     const int tid = threadIdx.x, n = N.n, m = N.m, gld = odd_ld(n);
     for (int idx = tid; idx < n * n; idx += NT) {
         const int i = idx / n, k = idx - i * n;
@@ -432,7 +434,7 @@ __device__ void dynamics(const Dom& s, const NetDesc& N) {
         s.Pn[idx] = acc;
     }
     for (int i = tid; i < n; i += NT) {
-        double acc = s.e[i], lo_ = 0.0, hi_ = 0.0;
+        double acc = s.e[i] + (off ? off[i] : 0.0), lo_ = 0.0, hi_ = 0.0;
         for (int j = 0; j < n; ++j) {
             const double aij = s.A[i * n + j];
             acc = fma(aij, s.c[j], acc);
@@ -572,7 +574,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused_forward(const FusedArgs a) {
         }
         tm_view<NT>(s, n);
         controller_pass<NT>(s, N, a, dom, sp_end, t, nullptr);
-        dynamics<NT>(s, N);
+        dynamics<NT>(s, N, a.eoff ? a.eoff + (dom * H + t) * (int64_t)n : nullptr);
         vacc += eval_box<NT>(s, N, a, dom, t + 1);
         __syncthreads();
         for (int idx = tid; idx < n * n; idx += NT) s.P[idx] = s.Pn[idx];

@@ -30,6 +30,7 @@ struct MultiArgs {
     const double* A;
     const double* B;
     const double* e;
+    const double* eoff;  // [D][H][n] per-step offsets of the dynamics or null
     const double* lo0;
     const double* hi0;
     int64_t D;
@@ -440,7 +441,7 @@ __global__ void __launch_bounds__(NT) k_fused_forward_multi(const MultiArgs a) {
             const float* cu = MF(g, Y.cu);
             const float* Iulo = MF(g, Y.Iulo);
             const float* Iuhi = MF(g, Y.Iuhi);
-            double acc = e[i], lo_ = 0.0, hi_ = 0.0;
+            double acc = e[i] + (a.eoff ? a.eoff[((dbase + g) * H + t) * n + i] : 0.0), lo_ = 0.0, hi_ = 0.0;
             for (int j = 0; j < n; ++j) {
                 const double x = A[i * n + j];
                 acc = fma(x, c[j], acc);

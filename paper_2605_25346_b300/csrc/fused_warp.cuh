@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(32 * WPC, (24 + WPC - 1) / WPC) k_fused_warp(c
             Pn[idx] = acc;
         }
         for (int i = lane; i < n; i += 32) {
-            double acc = e[i], lo_ = 0.0, hi_ = 0.0;
+            double acc = e[i] + (a.eoff ? a.eoff[(dom * H + t) * n + i] : 0.0), lo_ = 0.0, hi_ = 0.0;
             for (int j = 0; j < n; ++j) {
                 const double x = A[i * n + j];
                 acc = fma(x, c[j], acc);

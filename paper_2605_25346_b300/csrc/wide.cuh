@@ -27,6 +27,7 @@ struct WideArgs {
     const double* A;
     const double* B;
     const double* e;
+    const double* eoff;  // [D][H][n] per-step offsets of the dynamics or null
     const double* lo0;
     const double* hi0;
     int64_t d0;  // first domain of the chunk
@@ -392,7 +393,7 @@ __global__ void k_w_dyn(const WideArgs a, int t) {
         Pn[idx] = acc;
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        double acc = a.e ? a.e[i] : 0.0, lo_ = 0.0, hi_ = 0.0;
+        double acc = (a.e ? a.e[i] : 0.0) + (a.eoff ? a.eoff[(dom * H + t) * n + i] : 0.0), lo_ = 0.0, hi_ = 0.0;
         for (int j = 0; j < n; ++j) {
             const double x = a.A[i * n + j];
             acc = fma(x, c[j], acc);

@@ -80,6 +80,7 @@ class Problem:
     lr_alpha: float = 0.1
     lr_beta: float = 0.1
     meta: dict = field(default_factory=dict)
+    eoff: Optional[np.ndarray] = None  # float64 [D, H, n] per-step offsets: x_{t+1} = A x + B pi(x) + e + eoff[d, t]
 
     @property
     def D(self) -> int:
@@ -111,7 +112,8 @@ class Problem:
             beta = self.beta[sel.astype(np.int64)].copy()
         return Problem(self.name + f"[{len(idx)}]", list(self.widths), self.W, self.b, self.A, self.B, self.e,
                        self.lo[idx].copy(), self.hi[idx].copy(), self.H, self.mode, sp, beta,
-                       self.alpha_steps, self.lr_alpha, self.lr_beta, dict(self.meta, subset=True))
+                       self.alpha_steps, self.lr_alpha, self.lr_beta, dict(self.meta, subset=True),
+                       None if self.eoff is None else self.eoff[idx].copy())
 
 
 # ---------------------------------------------------------------------------------------------
@@ -174,11 +176,12 @@ def box_grid(center: np.ndarray, eps: float, parts: List[int]):
     return np.ascontiguousarray(lo), np.ascontiguousarray(hi)
 
 
-def nominal_preactivations(prob: Problem, x0: np.ndarray) -> List[np.ndarray]:
+def nominal_preactivations(prob: Problem, x0: np.ndarray, dom: Optional[np.ndarray] = None) -> List[np.ndarray]:
     """Pre-activations of every hidden layer along the nominal closed-loop trajectories from x0.
 
     Plain point evaluation of the system (no bounds); returns a list over t of
-    arrays [D, hidden] (hidden layers concatenated).
+    arrays [D, hidden] (hidden layers concatenated).  ``dom`` names the domain of each row of x0
+    (for the per-step offsets; default: row i is domain i).
     """
     x = x0.copy()
     out = []
@@ -192,9 +195,16 @@ def nominal_preactivations(prob: Problem, x0: np.ndarray) -> List[np.ndarray]:
                 h = np.maximum(z, 0.0)
             else:
                 u = z
-        out.append(np.concatenate(zs, axis=1))
-        x = x @ prob.A.T + u @ prob.B.T + prob.e
+        out.append(np.concatenate(zs, axis=1) if zs else np.zeros((x.shape[0], 0)))
+        x = x @ prob.A.T + u @ prob.B.T + prob.e + _offset(prob, dom, _t)
     return out
+
+
+def _offset(prob: Problem, dom, t: int):
+    """The per-step dynamics offsets of the given domains at step t (0 when the problem has none)."""
+    if prob.eoff is None:
+        return 0.0
+    return prob.eoff[np.arange(prob.D) if dom is None else dom, t]
 
 
 def branch_splits(prob: Problem, rng: np.random.Generator, max_k: int = 32, pool: int = 4,
@@ -221,7 +231,7 @@ def branch_splits(prob: Problem, rng: np.random.Generator, max_k: int = 32, pool
     chunk = 4096
     for c0 in range(0, len(sel), chunk):
         c1 = min(len(sel), c0 + chunk)
-        z = nominal_preactivations(prob, centre[c0:c1])  # H x [c, hid]
+        z = nominal_preactivations(prob, centre[c0:c1], sel[c0:c1])  # H x [c, hid]
         za = np.abs(np.stack(z, axis=1)).reshape(c1 - c0, -1)  # [c, H*hid]
         kk = min(pool * max_k, za.shape[1] - 1)
         cand = np.argpartition(za, kk, axis=1)[:, : pool * max_k]
@@ -255,14 +265,14 @@ def sample_trajectories(prob: Problem, n_traj: int, seed: int):
     u01 = rng.random(size=(n_traj, prob.n))
     x0 = prob.lo[dom] + u01 * (prob.hi[dom] - prob.lo[dom])
     xs = [x0]
-    pre = nominal_preactivations(prob, x0)
+    pre = nominal_preactivations(prob, x0, dom)
     x = x0
     for _t in range(prob.H):
         h = x
         for l in range(prob.L):
             z = h @ prob.W[l].T + prob.b[l]
             h = np.maximum(z, 0.0) if l < prob.L - 1 else z
-        x = x @ prob.A.T + h @ prob.B.T + prob.e
+        x = x @ prob.A.T + h @ prob.B.T + prob.e + _offset(prob, dom, _t)
         xs.append(x)
     return dom, np.stack(xs, axis=1), np.stack(pre, axis=1)
 
@@ -406,6 +416,68 @@ def large16(D_grid=(4, 4) + (2,) * 14, alpha_steps: int = 10) -> Problem:
                    50, mode=MODE_CHORD, alpha_steps=alpha_steps)
 
 
+def neural_dynamics(name: str, W, b, n: int, k: int, lo: np.ndarray, hi: np.ndarray, actions: np.ndarray,
+                    mode: int = MODE_CHORD, residual: bool = False) -> Problem:
+    """Discrete-time neural dynamics x_{t+1} = f(x_t, u_t) (or x_t + f(x_t, u_t) with ``residual``) with
+    planned inputs u_t per domain (Alg. 2), written as a closed loop over the augmented state
+    y = [x; u] of size n + k:
+
+        y_{t+1} = A y_t + B f(y_t) + eoff[d, t],   A = [[I or 0, 0], [0, 0]],  B = [[I_n], [0]],
+        eoff[d, t] = [0; u_{d, t+1}] (u_{d, H} = 0),  initial box [lo_d; u_{d, 0}] x [hi_d; u_{d, 0}].
+
+    f is the MLP with input width n + k (widths[0]) and output width n; actions [D, H, k].  Each domain
+    is one action sequence (an MPC sample) with its own initial box.
+    """
+    D, H = actions.shape[0], actions.shape[1]
+    N = n + k
+    A = np.zeros((N, N))
+    if residual:
+        A[:n, :n] = np.eye(n)
+    B = np.zeros((N, n))
+    B[:n, :n] = np.eye(n)
+    eoff = np.zeros((D, H, N))
+    eoff[:, :H - 1, n:] = actions[:, 1:, :]
+    lo_a = np.concatenate([lo, actions[:, 0, :]], axis=1)
+    hi_a = np.concatenate([hi, actions[:, 0, :]], axis=1)
+    widths = [N] + [w.shape[0] for w in W]
+    return Problem(name, widths, W, b, A, B, np.zeros(N), lo_a, hi_a, H, mode=mode,
+                   meta=dict(state_dims=n, action_dims=k), eoff=eoff)
+
+
+def tpush_dt(D: int = 128, H: int = 10, eps: float = 0.05, seed_offset: int = 0) -> Problem:
+    """The paper's DT benchmark shape (Sec. VI-A with the T-pushing model of App. D): neural dynamics
+    with state (T pose: position, orientation; pusher position) n = 5, action (pusher velocity) k = 2,
+    residual MLP x_{t+1} = x_t + f(x_t, u_t), f 7-96-96-96-5 with random weights (FP32 values; hidden
+    gain 0.7, output gain 0.2), D random initial boxes B_eps(x_hat), x_hat ~ U[-1, 1]^5, eps = 0.05 (the
+    T-pushing planning perturbation of Sec. VI-D), action sequences u ~ U[-1, 1]^2, horizon 10.
+
+    An untrained direct-form model x_{t+1} = f(x_t, u_t) either blows the tube up (N(0, 1/fan_in)
+    gains: width 4e9 after 10 steps) or collapses it to a point (small output gain: width 1e-9); the
+    residual form with these gains keeps the tube near its initial size (width 0.11 -> 0.22 over 10
+    steps) with about 13 % of the neurons unstable."""
+    rng = np.random.default_rng(SEED_BASE + 6 + seed_offset)
+    n, k = 5, 2
+    W, b = mlp(rng, [n + k, 96, 96, 96, n], f32=True, hidden_gain=0.7, out_gain=0.2)
+    xhat = rng.uniform(-1, 1, size=(D, n))
+    actions = rng.uniform(-1, 1, size=(D, H, k))
+    return neural_dynamics(f"tpush-dt 7-96x3-5 (residual), {D} boxes x action sequences, H={H}", W, b, n, k,
+                           xhat - eps, xhat + eps, actions, residual=True)
+
+
+def tpush_mpc(samples: int = 1024, H: int = 10, eps: float = 0.05) -> Problem:
+    """Sampling-based MPC over the T-pushing DT dynamics (Sec. V-B): one nominal initial box
+    B_eps(x_hat) and `samples` candidate action sequences u ~ U[-1, 1]^{H x 2}, each a domain."""
+    base = tpush_dt(D=1, H=H, eps=eps)
+    rng = np.random.default_rng(SEED_BASE + 7)
+    n, k = 5, 2
+    xhat = 0.5 * (base.lo[0, :n] + base.hi[0, :n])
+    actions = rng.uniform(-1, 1, size=(samples, H, k))
+    lo = np.repeat((xhat - eps)[None], samples, axis=0)
+    hi = np.repeat((xhat + eps)[None], samples, axis=0)
+    return neural_dynamics(f"tpush-mpc 7-96x3-5 (residual), {samples} action samples, H={H}", base.W, base.b, n, k,
+                           lo, hi, actions, residual=True)
+
+
 def random_problem(seed: int, widths, D: int, H: int, eps: float = 0.1, mode: int = MODE_CHORD,
                    f32: bool = True, rho: float = 0.97, b_scale: float = 0.1, out_gain: float = 0.5) -> Problem:
     """Small random closed loop for tests: random boxes of radius ~eps around U[-1,1]^n centres."""
@@ -426,4 +498,6 @@ WORKLOADS = {
     "cartpole_diff": cartpole_diff,
     "quadrotor_branch": quadrotor_branch,
     "large16": large16,
+    "tpush_dt": tpush_dt,
+    "tpush_mpc": tpush_mpc,
 }

@@ -448,3 +448,74 @@ def test_planted_adaptive_tie_takes_zero(monkeypatch):
     _mutate(monkeypatch, "relax", [("a = torch.where(u >= -l, one, zero)", "a = torch.where(u > -l, one, zero)")])
     g, r = _adaptive_tie_box()
     assert (r["lo"][0, 1, 0].item(), r["hi"][0, 1, 0].item()) == pytest.approx(tuple(g["box1_if_tie_took_zero"]))
+
+
+# ---------------------------------------------------------------------------------------------
+# per-step offsets: DT neural dynamics with planned inputs (Alg. 2), MPC action samples (Sec. V-B)
+# ---------------------------------------------------------------------------------------------
+
+def _linear_dt(seed=0, D=3, H=5):
+    """x_{t+1} = W [x; u_t] + b with planned inputs: the network is affine, so the TM is exact."""
+    rng = np.random.default_rng(seed)
+    n, k = 3, 2
+    W = [rng.normal(size=(n, n + k)) * 0.5]
+    b = [rng.normal(size=n) * 0.1]
+    xhat = rng.uniform(-1, 1, size=(D, n))
+    r = rng.uniform(0.05, 0.2, size=(D, n))
+    acts = rng.uniform(-1, 1, size=(D, H, k))
+    return wl.neural_dynamics("lin-dt", W, b, n, k, xhat - r, xhat + r, acts), acts
+
+
+def test_offsets_closed_form_linear_dynamics():
+    p, acts = _linear_dt()
+    n = 3
+    r = orc.reach(p)
+    for d in range(p.D):
+        X = wl.box_vertices(p.lo[d, :n], p.hi[d, :n])
+        for t in range(p.H):
+            X = np.concatenate([X, np.repeat(acts[d, t][None], len(X), 0)], 1) @ p.W[0].T + p.b[0]
+            np.testing.assert_allclose(r["lo"][d, t + 1, :n].numpy(), X.min(0), rtol=1e-12, atol=1e-12)
+            np.testing.assert_allclose(r["hi"][d, t + 1, :n].numpy(), X.max(0), rtol=1e-12, atol=1e-12)
+            if t + 1 < p.H:  # the action rows carry the next planned input exactly
+                np.testing.assert_allclose(r["lo"][d, t + 1, n:].numpy(), acts[d, t + 1], atol=1e-15)
+                np.testing.assert_allclose(r["hi"][d, t + 1, n:].numpy(), acts[d, t + 1], atol=1e-15)
+
+
+def test_constant_offsets_equal_the_affine_term():
+    p = wl.random_problem(91, [3, 12, 2], D=5, H=4, eps=0.2)
+    e = np.array([0.3, -0.2, 0.1])
+    q = wl.random_problem(91, [3, 12, 2], D=5, H=4, eps=0.2)
+    q.eoff = np.broadcast_to(e, (q.D, q.H, 3)).copy()
+    p.e = e
+    a, b = orc.reach(p), orc.reach(q)
+    np.testing.assert_array_equal(a["lo"].numpy(), b["lo"].numpy())
+    np.testing.assert_array_equal(a["hi"].numpy(), b["hi"].numpy())
+
+
+def test_tpush_dt_trajectories_contained():
+    p = wl.tpush_dt(D=16)
+    r = orc.reach(p)
+    ok, n = _contained(p, r, 10000, 5)
+    assert ok and n == 10000
+
+
+def test_shift_gradient_matches_finite_differences():
+    p = wl.tpush_dt(D=2, H=4)
+    res, g = orc.value_and_shift_grad(p)
+    n = 5
+    flat = g.reshape(-1)
+    # action rows (dV/du_t) and state rows, at steps 0 (initial centre) and later
+    coords = [np.ravel_multi_index((d, t, i), g.shape) for d in range(2) for t in (0, 1, 3) for i in (0, 2, n, n + 1)]
+    base = torch.zeros(p.D, p.H + 1, p.n, dtype=torch.float64)
+    h = 1e-6
+    fd = []
+    for c in coords:
+        vals = []
+        for sg in (1.0, -1.0):
+            sh = base.clone().reshape(-1)
+            sh[c] += sg * h
+            vals.append(float(orc.reach(p, shift=sh.reshape(base.shape))["V"].sum()))
+        fd.append((vals[0] - vals[1]) / (2 * h))
+    an = flat.numpy()[coords]
+    assert np.abs(an).max() > 0
+    np.testing.assert_allclose(fd, an, rtol=1e-5, atol=1e-6 * np.abs(an).max())
