@@ -342,6 +342,46 @@ def measure_quad6(local, steps=10, warmup=3):
                          "peak_basis": "148 SMs x 128 FP32 lanes x 2 FLOP x 2032 MHz (FMA issue rate at max SM clock)"}}
 
 
+def measure_tpush(local, reps=5):
+    """DT neural dynamics with planned inputs (the T-pushing-shaped 7-96x3-5 residual model, H = 10):
+    bounds over 128 initial boxes and over 1024 MPC action samples, and the gradient dV/du of every
+    sample (forward pass with tape plus reverse sweep), batched vs one sample per call."""
+    from paper_2605_25346_b300 import api
+    out = {}
+    for name, prob in (("tpush_dt 128 boxes x action sequences", wl.tpush_dt()),
+                       ("tpush_mpc 1024 action samples", wl.tpush_mpc())):
+        t, _, _ = _time_passes(local, prob, reps)
+        out[name] = {"domain_steps_per_s": prob.D * prob.H / t, "ms_per_pass": 1e3 * t}
+    prob = wl.tpush_mpc()
+    r = api.Reach(local).load(prob)
+    r.backward()  # warm-up: tape and gradient buffers
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        r.backward()
+        g = r.shift_gradient()
+    tb = (time.perf_counter() - t0) / reps
+    r.close()
+    n = prob.meta["state_dims"]
+    sample = 8
+    tp = 0.0
+    for d in range(sample):
+        rr = api.Reach(local).load(prob.subset([d]))
+        rr.backward()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        rr.backward()
+        gp = rr.shift_gradient()
+        tp += time.perf_counter() - t1
+        assert np.allclose(gp[0], g[d], rtol=1e-6, atol=1e-9 * np.abs(g[d]).max())
+        rr.close()
+    out["tpush_mpc dV/du"] = {"samples_per_s_batched": prob.D / tb, "ms_per_gradient_batched": 1e3 * tb,
+                              "samples_per_s_plain": sample / tp, "plain_sample": sample,
+                              "batched_over_plain": (prob.D / tb) / (sample / tp),
+                              "max_abs_dV_du": float(np.abs(g[:, :prob.H, n:]).max())}
+    return out
+
+
 def _time_passes(local, prob, reps):
     """Seconds per dr_compute_bounds pass (CUDA events; graph replays after two warm calls), the
     last output and the replay count."""
@@ -681,6 +721,7 @@ def main():
             roof["pass_frac_of_measured_tf32_over_3_sustained"] = roof["pass_fp32eq_tflops"] / (tf32["tf32_tflops_sustained"] / 3.0)
             extras["quad6"] = measure_quad6(local)
             extras["branch12_full"] = measure_branch12_full(local)
+            extras["tpush_dt_mpc"] = measure_tpush(local)
             extras["refinement"] = measure_refinement(local)
             extras["wide"] = measure_wide(local, tf32=tf32)
             extras["wide_refinement"] = measure_wide_refinement(local)
@@ -695,6 +736,7 @@ def main():
                         "d2h_bytes_per_step": d2h, "steps": e2e_steps},
                 "gpu_launches": int(launches),
                 "cuda_graph_replays": int(replays),
+                "gemm_autotuner_picks": api.gemm_tuning_report().strip().split("\n"),
                 "wall_ms_per_step_incl_flush": 1e3 * t_wall / args.steps,
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(), "extras": extras}
         print(json.dumps(line), flush=True)

@@ -93,10 +93,16 @@ typedef struct dr_options {
                               into the Taylor model)                                        */
     int32_t tuning;        /* 0 = pick the fused kernel's launch shape by timing the candidates on
                               first use (cached per architecture and widths; file DR_TUNE_CACHE
-                              if set), 1 = no search (first candidate that fits), 2 + v = use
+                              if set), and the tensor-core GEMM's launch shape per GEMM shape
+                              (persistent or one tile per CTA, 128/64/32 columns; timed on the
+                              first pass outside a graph capture, cached per process; see
+                              dr_gemm_tuning_report), 1 = no search (first candidate that fits;
+                              the GEMM heuristic), 2 + v = use
                               candidate v (0..9; DR_ERR_SHAPE if it does not fit the controller):
                               0..2 one warp per domain (16/8/4 warps per CTA; two hidden layers,
-                              n, m <= 8, hidden widths <= 128), 3..9 several domains per CTA   */
+                              n, m <= 8, hidden widths <= 128), 3..9 several domains per CTA;
+                              100 + g = the tensor-core GEMM's launch shape g (1..4, see
+                              dr_gemm_tuning_report) for every GEMM, the fused kernels untuned */
     int32_t graphs;        /* 0 = dr_compute_bounds captures its launch sequence in a CUDA graph on
                               the second call with unchanged buffers, options and slope mode, and
                               replays it afterwards (needs a stream other than the legacy default
@@ -313,6 +319,13 @@ int dr_kernel_timing(dr_ctx* ctx, int which, int64_t min_rows, int64_t* launches
  * Number of dr_compute_bounds calls and dr_optimize_slopes steps served by replaying a captured CUDA
  * graph (dr_options.graphs). */
 int64_t dr_graph_replays(const dr_ctx* ctx);
+
+/* Paper: no passage (accounting).  The tensor-core GEMM autotuner's choices so far in this process
+ * (dr_options.tuning = 0), one line per shape: "epi<e> R<rows> K<k> N<n> sm<SMs>: variant <v> (ms:
+ * v<i>=<time> ...)", variants 1 = persistent 128 x 128 tiles, 2 / 3 / 4 = one 128 x 128 / 64 / 32 tile
+ * per CTA.  Writes at most cap bytes including the terminating NUL into buf (truncating; buf may
+ * be NULL) and returns the length the whole report needs. */
+int64_t dr_gemm_tuning_report(char* buf, int64_t cap);
 
 /* Paper: no passage (error reporting).
  * Message of the last failing call on ctx (or of the last failing dr_create when ctx is

@@ -21,7 +21,7 @@ DR_KT_GEMM_ALL, DR_KT_GEMM_CHAIN, DR_KT_GEMM_FINAL, DR_KT_GEMM_OTHER = 0, 1, 2, 
 EXPORTS = [
     "dr_create", "dr_destroy", "dr_load_controller", "dr_load_dynamics", "dr_set_boxes", "dr_set_splits",
     "dr_set_horizon", "dr_set_step_offsets", "dr_get_shift_gradient", "dr_set_options", "dr_compute_bounds", "dr_get_objective", "dr_optimize_slopes",
-    "dr_backward", "dr_get_alpha", "dr_set_alpha", "dr_get_beta", "dr_set_beta", "dr_kernel_launches", "dr_graph_replays", "dr_kernel_timing", "dr_last_error",
+    "dr_backward", "dr_get_alpha", "dr_set_alpha", "dr_get_beta", "dr_set_beta", "dr_kernel_launches", "dr_graph_replays", "dr_kernel_timing", "dr_gemm_tuning_report", "dr_last_error",
     "dr_slope_gradient_static", "dr_tf32x3_gemm", "dr_check_wait_expiry",
 ]
 
@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dr_set_beta": (i32, [vp, fp, i32]),
         "dr_kernel_launches": (i64, [vp]),
         "dr_graph_replays": (i64, [vp]),
+        "dr_gemm_tuning_report": (i64, [ctypes.c_char_p, i64]),
         "dr_kernel_timing": (i32, [vp, i32, i64, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double)]),
         "dr_last_error": (ctypes.c_char_p, [vp]),

@@ -216,6 +216,15 @@ class Reach:
         return int(nl.value), float(ms.value), float(fl.value)
 
 
+def gemm_tuning_report() -> str:
+    """The tensor-core GEMM autotuner's choices so far in this process (one line per GEMM shape)."""
+    lib = _lib.load()
+    need = int(lib.dr_gemm_tuning_report(None, 0))
+    buf = ctypes.create_string_buffer(max(need, 1))
+    lib.dr_gemm_tuning_report(buf, need)
+    return buf.value.decode()
+
+
 class BoundsFunction(torch.autograd.Function):
     """Differentiable bounds: (alpha, beta) -> (lo, hi), backward through the library's adjoint.
 

@@ -559,8 +559,15 @@ static int launch_tc_gemm_persistent(dr_ctx* c, const CUtensorMap* m, float* C, 
     return DR_OK;
 }
 
+// Launch shapes of the tensor-core GEMM (dr_options.tuning = 0 picks one per shape by timing them):
+// 0 = the heuristic (the persistent kernel for 128-column tiles with at least two tiles per SM, else
+// one 128 x tc_bn(N) tile per CTA), 1 = persistent 128 x 128, 2 = one 128 x 128 tile per CTA,
+// 3 = one 128 x 64 tile per CTA, 4 = one 128 x 32 tile per CTA.
+enum { kGemmHeuristic = 0, kGemmPersistent = 1, kGemmTile128 = 2, kGemmTile64 = 3, kGemmTile32 = 4 };
+
 static int tc_gemm_launch(dr_ctx* c, const float* Ah, const float* Al, const float* BTh, const float* BTl, float* C, int R,
-                          int K, int N, int ldk, int ldc, int* err, cudaStream_t st, const tc::ChainEpi* epi, int* cls);
+                          int K, int N, int ldk, int ldc, int* err, cudaStream_t st, const tc::ChainEpi* epi, int* cls,
+                          int variant, int* bn_used);
 
 static cudaEvent_t kt_event(dr_ctx* c) {
     cudaEvent_t e = nullptr;
@@ -574,16 +581,103 @@ static cudaEvent_t kt_event(dr_ctx* c) {
     return e;
 }
 
+// Autotuner of the tensor-core GEMM's launch shape: the first time a shape (epilogue kind, R, K, N,
+// SM count) is met outside a graph capture, every candidate runs twice on the real operands (each
+// run writes the same outputs from the same inputs) and the second run is timed with CUDA events;
+// the fastest is cached for the process and, if it was not the last one run, runs once more so that
+// the outputs are its own.  Captured and later calls reuse the cached choice; an uncached shape met
+// while capturing takes the heuristic.
+static std::mutex g_gemm_mu;
+static std::map<std::string, int> g_gemm_choice;
+static std::map<std::string, std::string> g_gemm_report;
+
+static std::string gemm_key(const tc::ChainEpi* epi, int R, int K, int N) {
+    char buf[96];
+    snprintf(buf, sizeof(buf), "epi%d R%d K%d N%d sm%d", !epi ? 0 : (epi->W1 ? 2 : 1), R, K, N, sm_count());
+    return buf;
+}
+
+static int tuned_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* BTh, const float* BTl, float* C, int R, int K,
+                      int N, int ldk, int ldc, int* err, cudaStream_t st, const tc::ChainEpi* epi, int* variant) {
+    const std::string key = gemm_key(epi, R, K, N);
+    {
+        std::lock_guard<std::mutex> lock(g_gemm_mu);
+        auto it = g_gemm_choice.find(key);
+        if (it != g_gemm_choice.end()) {
+            *variant = it->second;
+            return DR_OK;
+        }
+    }
+    if (c->capturing) return DR_OK;  // heuristic
+    int cand[4], nc = 0;
+    if (tc_bn(N) == 128) {
+        if (persistent_gemm_usable<0>() && persistent_gemm_usable<1>() && persistent_gemm_usable<2>()) cand[nc++] = kGemmPersistent;
+        cand[nc++] = kGemmTile128;
+    }
+    if (N > 32) cand[nc++] = kGemmTile64;
+    if (N > 16 && N <= 64) cand[nc++] = kGemmTile32;
+    if (nc <= 1) {
+        *variant = nc ? cand[0] : kGemmHeuristic;
+        return DR_OK;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(c, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(c, DR_ERR_CUDA, "cudaEventCreate");
+    }
+    float best = 0.f, ms[4] = {};
+    int pick = cand[0], rc = DR_OK;
+    for (int q = 0; q < nc && rc == DR_OK; ++q) {
+        for (int rep = 0; rep < 2 && rc == DR_OK; ++rep) {
+            int cls = 0, bn = 0;
+            if (cudaEventRecord(e0, st) != cudaSuccess) rc = fail(c, DR_ERR_CUDA, "cudaEventRecord");
+            if (rc == DR_OK) rc = tc_gemm_launch(c, Ah, Al, BTh, BTl, C, R, K, N, ldk, ldc, err, st, epi, &cls, cand[q], &bn);
+            if (rc == DR_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                cudaEventElapsedTime(&ms[q], e0, e1) != cudaSuccess))
+                rc = fail(c, DR_ERR_CUDA, "GEMM tuning: %s", cudaGetErrorString(cudaGetLastError()));
+        }
+        if (rc == DR_OK && (q == 0 || ms[q] < best)) {
+            best = ms[q];
+            pick = cand[q];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    TRY(rc);
+    int herr = 0;  // a bounded pipeline wait that expired during the trials
+    CUDA_TRY(c, cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) return fail(c, DR_ERR_TIMEOUT, "a tensor-core pipeline wait timed out while tuning");
+    {
+        std::lock_guard<std::mutex> lock(g_gemm_mu);
+        g_gemm_choice[key] = pick;
+        std::string rep = "variant " + std::to_string(pick) + " (ms:";
+        for (int q = 0; q < nc; ++q) {
+            char b[48];
+            snprintf(b, sizeof(b), " v%d=%.3f", cand[q], ms[q]);
+            rep += b;
+        }
+        g_gemm_report[key] = rep + ")";
+    }
+    *variant = pick;  // the caller then launches the pick, so the outputs are its own
+    return DR_OK;
+}
+
 // C [R x N] (ld ldc) = A B with A given as TF32 parts Ah/Al (blocked layout, tc::blk_index, ldk
 // columns) and B as BTh/BTl [N][ldk]; with `epi` the chain epilogue replaces the store of C.  With
 // dr_options.timing set (and not capturing a graph) the launch is bracketed by two CUDA events on `st`.
 static int tc_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* BTh, const float* BTl, float* C, int R, int K,
-                   int N, int ldk, int ldc, int* err, cudaStream_t st, const tc::ChainEpi* epi = nullptr) {
+                   int N, int ldk, int ldc, int* err, cudaStream_t st, const tc::ChainEpi* epi = nullptr, int* bn_used = nullptr) {
+    int bn_dummy = 0;
+    if (!bn_used) bn_used = &bn_dummy;
+    int variant = kGemmHeuristic;
+    if (c && c->opt.tuning == 0) TRY(tuned_gemm(c, Ah, Al, BTh, BTl, C, R, K, N, ldk, ldc, err, st, epi, &variant));
+    if (c && c->opt.tuning >= 100) variant = c->opt.tuning - 100;  // forced launch shape
     const bool timed = c && c->opt.timing && !c->capturing;
     cudaEvent_t e0 = timed ? kt_event(c) : nullptr, e1 = timed ? kt_event(c) : nullptr;
     if (e0 && e1) CUDA_TRY(c, cudaEventRecord(e0, st));
     int cls = DR_KT_GEMM_OTHER;
-    const int rc = tc_gemm_launch(c, Ah, Al, BTh, BTl, C, R, K, N, ldk, ldc, err, st, epi, &cls);
+    const int rc = tc_gemm_launch(c, Ah, Al, BTh, BTl, C, R, K, N, ldk, ldc, err, st, epi, &cls, variant, bn_used);
     if (timed) {
         if (rc == DR_OK && e0 && e1) {
             CUDA_TRY(c, cudaEventRecord(e1, st));
@@ -599,9 +693,11 @@ static int tc_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* BTh
 }
 
 static int tc_gemm_launch(dr_ctx* c, const float* Ah, const float* Al, const float* BTh, const float* BTl, float* C, int R,
-                          int K, int N, int ldk, int ldc, int* err, cudaStream_t st, const tc::ChainEpi* epi, int* cls) {
+                          int K, int N, int ldk, int ldc, int* err, cudaStream_t st, const tc::ChainEpi* epi, int* cls,
+                          int variant, int* bn_used) {
     TRY(get_encoder(c));
-    const int BN = tc_bn(N);
+    const int BN = variant == kGemmTile64 ? 64 : variant == kGemmTile32 ? 32 : variant >= kGemmPersistent ? 128 : tc_bn(N);
+    *bn_used = BN;
     CUtensorMap m[6];
     TRY(make_map_blocked(c, &m[0], Ah, R, ldk));
     TRY(make_map_blocked(c, &m[1], Al, R, ldk));
@@ -619,10 +715,10 @@ static int tc_gemm_launch(dr_ctx* c, const float* Ah, const float* Al, const flo
     if (epi) e = *epi;
     if (epi && epi->W1 && (BN < 32 || epi->n0 > tc::kFinalCols))
         return fail(c, DR_ERR_SHAPE, "fused final chain level needs >= 32 columns and n <= %d", tc::kFinalCols);
-    if (BN == 128) {
+    if (BN == 128 && variant != kGemmTile128) {
         const int nsm = sm_count();
         const int64_t tiles = ((int64_t)(R + tc::BM - 1) / tc::BM) * ((N + 127) / 128);
-        if (tiles >= 2 * (int64_t)nsm && tiles <= 0x7fffffffll) {
+        if ((variant == kGemmPersistent || tiles >= 2 * (int64_t)nsm) && tiles <= 0x7fffffffll) {
             if (!epi && persistent_gemm_usable<0>())
                 return launch_tc_gemm_persistent<0>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm);
             if (epi && epi->W1 && persistent_gemm_usable<2>()) {
@@ -753,7 +849,7 @@ static void tune_file_store() {
 // stream), the winner is cached per (architecture, widths).  dr_options.tuning = 1 disables the
 // search and takes the first fitting variant with the largest group.
 static int tuned_variant(dr_ctx* c, const MultiArgs& a, int* out) {
-    if (c->opt.tuning >= 2) {
+    if (c->opt.tuning >= 2 && c->opt.tuning < 100) {
         const int v = c->opt.tuning - 2;
         if (v >= kNumMultiVariants || !variant_fits(a, v))
             return fail(c, DR_ERR_SHAPE, "launch variant %d does not fit this controller", v);
@@ -775,7 +871,7 @@ static int tuned_variant(dr_ctx* c, const MultiArgs& a, int* out) {
             break;
         }
     if (first_fit < 0) return fail(c, DR_ERR_SHAPE, "no grouped variant fits shared memory");
-    if (c->opt.tuning == 1 || c->D == 0) {
+    if (c->opt.tuning == 1 || c->opt.tuning >= 100 || c->D == 0) {
         *out = first_fit;
         return DR_OK;
     }
@@ -910,6 +1006,20 @@ int64_t dr_kernel_launches(const dr_ctx* c) { return c ? c->launches : 0; }
 
 int64_t dr_graph_replays(const dr_ctx* c) { return c ? c->graph_replays : 0; }
 
+int64_t dr_gemm_tuning_report(char* buf, int64_t cap) {
+    std::string out;
+    {
+        std::lock_guard<std::mutex> lock(g_gemm_mu);
+        for (const auto& kv : g_gemm_report) out += kv.first + ": " + kv.second + "\n";
+    }
+    if (buf && cap > 0) {
+        const int64_t k = std::min<int64_t>(cap - 1, (int64_t)out.size());
+        memcpy(buf, out.data(), (size_t)k);
+        buf[k] = 0;
+    }
+    return (int64_t)out.size() + 1;
+}
+
 int dr_set_options(dr_ctx* c, const dr_options* o) {
     if (!c) return DR_ERR_ARG;
     dr_options n = o ? *o : default_options();
@@ -921,6 +1031,8 @@ int dr_set_options(dr_ctx* c, const dr_options* o) {
     if (n.slope_mode == DR_SLOPE_USER && !c->alpha_set && c->D > 0)
         return fail(c, DR_ERR_STATE, "DR_SLOPE_USER requires dr_set_alpha first");
     if (n.timing < 0 || n.timing > 1) return fail(c, DR_ERR_ARG, "timing %d out of range", n.timing);
+    if (n.tuning < 0 || (n.tuning >= 2 + kNumMultiVariants && (n.tuning < 101 || n.tuning > 104)))
+        return fail(c, DR_ERR_ARG, "tuning %d out of range", n.tuning);
     if (n.timing && !c->opt.timing) c->kt_done.clear();  // timing switched on: the totals start from zero
     c->opt = n;
     c->epoch++;  // kernel arguments may change
@@ -1297,21 +1409,24 @@ static int64_t wide_lam_stride(const NetDesc& N) {
     return best;
 }
 
-static int64_t wide_part_per_domain(const NetDesc& N) {
-    int64_t best = 1;
-    for (int l = 2; l <= N.L; ++l)
-        for (int mm = l - 1; mm >= 2; --mm) {
-            const int NN = N.w[mm - 1], bn = tc_bn(NN);
-            best = std::max<int64_t>(best, (int64_t)N.w[l] * ((NN + bn - 1) / bn) * tc::epi_groups(bn));
-        }
+// Intercept partial sets per stacked row of a GEMM with NN output columns: (column tiles) x (column
+// groups per tile), the largest over the tile widths the GEMM autotuner may pick (128, 64, 32).
+static int64_t gemm_part_sets(int NN) {
+    int64_t best = 0;
+    for (int bn : {tc_bn(NN), 128, 64, 32}) best = std::max<int64_t>(best, (int64_t)((NN + bn - 1) / bn) * tc::epi_groups(bn));
     return best;
 }
 
-// Partial Lambda_x rows per stacked row when the last chain level is fused into the GEMM epilogue.
-static int wide_lx_parts(const NetDesc& N) {
-    const int bn = tc_bn(N.w[1]);
-    return (N.w[1] + bn - 1) / bn * tc::epi_groups(bn);
+static int64_t wide_part_per_domain(const NetDesc& N) {
+    int64_t best = 1;
+    for (int l = 2; l <= N.L; ++l)
+        for (int mm = l - 1; mm >= 2; --mm) best = std::max<int64_t>(best, (int64_t)N.w[l] * gemm_part_sets(N.w[mm - 1]));
+    return best;
 }
+
+// Partial Lambda_x rows per stacked row when the last chain level is fused into the GEMM epilogue
+// (one per column tile, for any tile width the autotuner may pick).
+static int wide_lx_parts(const NetDesc& N) { return (int)gemm_part_sets(N.w[1]); }
 
 static size_t wide_bytes_per_domain(const NetDesc& N) {
     const int n = N.n, m = N.m;
@@ -1559,9 +1674,10 @@ static int wide_step(dr_ctx* c, WideLane& w, int t, bool tcore) {
                             epi.n0 = N.n;
                             epi.lxpart = lxpart;
                         }
-                        TRY(tc_gemm(c, curh, curl, WTh, WTl, nullptr, R, K, NN, ldk, 0, c->derr, st, &epi));
-                        const int gx = (NN + tc_bn(NN) - 1) / tc_bn(NN);  // column tiles of the GEMM
-                        const int ntiles = gx * tc::epi_groups(tc_bn(NN));
+                        int bn = 0;
+                        TRY(tc_gemm(c, curh, curl, WTh, WTl, nullptr, R, K, NN, ldk, 0, c->derr, st, &epi, &bn));
+                        const int gx = (NN + bn - 1) / bn;  // column tiles of the GEMM as launched
+                        const int ntiles = gx * tc::epi_groups(bn);
                         if (fin) {
                             lx_parts = gx;        // one Lambda_x partial per column tile
                             fin_tiles = ntiles;   // its intercept partials are added by the projection

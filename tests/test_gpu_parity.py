@@ -381,3 +381,20 @@ def test_tensor_core_bounds_contain_trajectories():
     g = gpu_bounds(p)
     dom, xs, _ = wl.sample_trajectories(p, 4000, 11)
     assert ((xs >= g["lo"][dom]) & (xs <= g["hi"][dom])).all()
+
+
+# ---- the tensor-core GEMM's launch shapes: each shape the autotuner may pick, forced for every GEMM
+# of the staged path (dr_options.tuning = 100 + g: 1 persistent 128 x 128, 2 / 3 / 4 one 128 x 128 /
+# 64 / 32 tile per CTA), and the autotuner itself (tuning = 0) with its report
+@pytest.mark.parametrize("shape", [1, 2, 3, 4])
+def test_tensor_core_gemm_launch_shapes(shape):
+    p = wl.random_problem(77, [6, 256, 256, 256, 3], D=48, H=2, eps=0.15)
+    compare(p, gpu_bounds(p, precision=TCORE, chunk=24, tuning=100 + shape), orc.reach(p))
+
+
+def test_gemm_autotuner_picks_and_reports():
+    api = _api()
+    p = wl.random_problem(78, [6, 256, 256, 200, 3], D=64, H=2, eps=0.15)
+    compare(p, gpu_bounds(p, precision=TCORE), orc.reach(p))
+    rep = api.gemm_tuning_report()
+    assert "epi1" in rep and "epi2" in rep and "variant" in rep, rep
