@@ -382,6 +382,42 @@ def measure_tpush(local, reps=5):
     return out
 
 
+def measure_rigorous(local):
+    """Rigorous rounding mode (worst-case error bounds carried through the pass): how far its boxes
+    lie outside the FP64 oracle's (relative to max(|lo|, |hi|, width) of the oracle's box, the
+    default mode's 1e-5 parity scale) and its throughput next to the default mode."""
+    import dataclasses
+    from oracle import reach as orc
+    from paper_2605_25346_b300 import api
+    out = {}
+    for name, prob, sample in (("quad6 6-64-64-3, 4096 sub-boxes, H=10", wl.quad6_batched(), np.arange(0, 4096, 64)),
+                               ("cartpole 4-128-128-2, 1024 sub-boxes, H=20", wl.cartpole_diff(), np.arange(0, 1024, 16)),
+                               ("large16 16-512x4-8, 296 sub-boxes, H=50", dataclasses.replace(wl.large16().subset(
+                                   np.arange(0, 262144, 886)[:296]), H=50), np.arange(0, 296, 74))):
+        res = {}
+        for rig in (0, 1):
+            stream = torch.cuda.Stream()
+            r = api.Reach(local, stream=stream).load(prob)
+            r.set_options(mode=prob.mode, rigorous=rig)
+            with torch.cuda.stream(stream):
+                r.bounds(on_device=True)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                g = r.bounds(on_device=False)
+                t = time.perf_counter() - t0
+            r.close()
+            o = orc.reach(prob.subset(sample))
+            olo, ohi = o["lo"].numpy(), o["hi"].numpy()
+            scale = np.maximum(np.maximum(np.abs(olo), np.abs(ohi)), ohi - olo)
+            dev = np.maximum(olo - g["lo"][sample], g["hi"][sample] - ohi) / scale
+            res["rigorous" if rig else "default"] = {
+                "domain_steps_per_s": prob.D * prob.H / t, "max_outward_dev_rel": float(dev.max()),
+                "median_outward_dev_rel": float(np.median(dev)), "encloses_oracle": bool((dev >= 0).all()),
+                "sampled_domains": int(len(sample))}
+        out[name] = res
+    return out
+
+
 def _time_passes(local, prob, reps):
     """Seconds per dr_compute_bounds pass (CUDA events; graph replays after two warm calls), the
     last output and the replay count."""
@@ -722,6 +758,7 @@ def main():
             extras["quad6"] = measure_quad6(local)
             extras["branch12_full"] = measure_branch12_full(local)
             extras["tpush_dt_mpc"] = measure_tpush(local)
+            extras["rigorous"] = measure_rigorous(local)
             extras["refinement"] = measure_refinement(local)
             extras["wide"] = measure_wide(local, tf32=tf32)
             extras["wide_refinement"] = measure_wide_refinement(local)

@@ -83,7 +83,8 @@ typedef struct dr_options {
                               is widened by rho * S, S the L1 magnitude of its summed terms.
                               Default 0: such margins compound through the closed loop.      */
     int64_t chunk_domains; /* domains per device pass of the staged path (bounds its scratch);
-                              0 = automatic: as many as 16 GiB of scratch holds, at most a quarter
+                              0 = automatic: the fewest equal chunks per lane that 24 GiB of
+                              scratch holds, at most a quarter
                               of the free device memory and within mem_cap_bytes              */
     int64_t mem_cap_bytes; /* cap on library-owned device memory; 0 = no cap                    */
     double box_margin;     /* outward margin of every reported box: lo -= b*S_box, hi += b*S_box,
@@ -110,7 +111,18 @@ typedef struct dr_options {
     int32_t timing;        /* 1 = time every tensor-core GEMM launch with a pair of CUDA events on the
                               stream it is launched on (read with dr_kernel_timing); passes then run
                               as plain launches, not graph replays.  0 (default) = off            */
-    int32_t reserved[3];
+    int32_t rigorous;      /* 1 = rigorous rounding for dr_compute_bounds: every FP32 product and sum
+                              of the controller pass carries a worst-case error bound (gamma(K)
+                              times the sum of its terms' magnitudes, IEEE round-to-nearest), summed
+                              with the intercepts and added outward to the pre-activation bounds and
+                              the controller TM's remainder; intercepts round up; the FP64 dynamics
+                              widen the remainder by 2^-47 of their terms' magnitude.  The chain then
+                              runs on CUDA cores (the tensor cores' accumulation rounding is not
+                              documented) on the staged path.  The boxes enclose the reachable sets
+                              of the real-number closed loop; they are wider than FP64 arithmetic
+                              without error terms gives.  The reverse sweep and refinement ignore
+                              it.  0 (default) = the calibrated box_margin only                  */
+    int32_t reserved[2];
 } dr_options;
 
 /* Paper: no passage; the engine of Sec. IV runs batched on a single GPU (Sec. VI), and a context

@@ -42,7 +42,8 @@ class dr_options(ctypes.Structure):
     _fields_ = [("slope_mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("margin_rho", ctypes.c_double),
                 ("chunk_domains", ctypes.c_int64), ("mem_cap_bytes", ctypes.c_int64),
                 ("box_margin", ctypes.c_double), ("tuning", ctypes.c_int32),
-                ("graphs", ctypes.c_int32), ("timing", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("graphs", ctypes.c_int32), ("timing", ctypes.c_int32), ("rigorous", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 _lib = None

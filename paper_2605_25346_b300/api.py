@@ -55,11 +55,12 @@ class Reach:
     # ---- problem upload -------------------------------------------------------------------
     def set_options(self, mode: Optional[int] = None, precision: int = _lib.DR_PREC_AUTO, rho: Optional[float] = None,
                     chunk: int = 0, mem_cap: int = 0, box_margin: Optional[float] = None, tuning: int = 0,
-                    graphs: int = 0, timing: int = 0):
+                    graphs: int = 0, timing: int = 0, rigorous: int = 0):
         o = _lib.dr_options()
         o.tuning = tuning
         o.graphs = graphs
         o.timing = timing
+        o.rigorous = rigorous
         o.slope_mode = _MODE[mode] if mode is not None else _lib.DR_SLOPE_CHORD
         o.precision = precision
         o.margin_rho = 0.0 if rho is None else rho

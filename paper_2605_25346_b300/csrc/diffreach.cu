@@ -1031,6 +1031,7 @@ int dr_set_options(dr_ctx* c, const dr_options* o) {
     if (n.slope_mode == DR_SLOPE_USER && !c->alpha_set && c->D > 0)
         return fail(c, DR_ERR_STATE, "DR_SLOPE_USER requires dr_set_alpha first");
     if (n.timing < 0 || n.timing > 1) return fail(c, DR_ERR_ARG, "timing %d out of range", n.timing);
+    if (n.rigorous < 0 || n.rigorous > 1) return fail(c, DR_ERR_ARG, "rigorous %d out of range", n.rigorous);
     if (n.tuning < 0 || (n.tuning >= 2 + kNumMultiVariants && (n.tuning < 101 || n.tuning > 104)))
         return fail(c, DR_ERR_ARG, "tuning %d out of range", n.tuning);
     if (n.timing && !c->opt.timing) c->kt_done.clear();  // timing switched on: the totals start from zero
@@ -1436,6 +1437,7 @@ static size_t wide_bytes_per_domain(const NetDesc& N) {
     b += sizeof(float) * (n + n * n + n + n + n + 1);            // FP32 view
     b += sizeof(float) * 4 * std::max(N.hidden, 1);               // l, u, s, d
     b += sizeof(double) * 2 * N.maxw;                             // kappa (FP64)
+    b += sizeof(double) * N.maxw + sizeof(float) * (n + std::max(N.hidden, 1));  // rigorous mode: kerr, xmax, q
     b += sizeof(float) * ((size_t)N.maxw * n + 4 * N.maxw);       // G, a, R, S
     b += sizeof(double) * 3 * m;                                  // controller TM (FP64)
     b += sizeof(float) * 4 * wide_lam_stride(N);                  // Lambda buffers (two TF32 pairs)
@@ -1515,6 +1517,9 @@ static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, int lanes, int lane, float*
     a.cu = (double*)take(sizeof(double) * D * m);
     a.Iulo = (double*)take(sizeof(double) * D * m);
     a.Iuhi = (double*)take(sizeof(double) * D * m);
+    a.kerr = (double*)take(sizeof(double) * D * N.maxw);
+    a.xmax = (float*)take(sizeof(float) * D * n);
+    a.hq = (float*)take(sizeof(float) * D * hid);
     a.lam_stride = wide_lam_stride(N);
     const int64_t lam_pad = wide_lam_pad(N);
     *lamA = (float*)take(sizeof(float) * (D * a.lam_stride + lam_pad));
@@ -1537,15 +1542,16 @@ static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, int lanes, int lane, float*
     return DR_OK;
 }
 
-// Domains per lane chunk: the option if set, else as many as a scratch budget allows.  The budget is
-// 16 GiB (larger chunks mean longer GEMM launches with fewer partial waves), at most a quarter of the
-// free device memory and at most the memory cap left, and never below 1 GiB.
+// Domains per lane chunk: the option if set, else the fewest equal chunks per lane that a scratch
+// budget allows.  The budget is 24 GiB (larger chunks mean longer GEMM launches with fewer partial
+// waves), at most a quarter of the free device memory and at most the memory cap left, and never
+// below 1 GiB.
 static int wide_chunk(dr_ctx* c, const NetDesc& N, int lanes) {
     if (c->opt.chunk_domains > 0) return (int)std::min<int64_t>(std::min<int64_t>(c->opt.chunk_domains, c->D), 65535);
     // a captured pass repeats the plain pass before it: keep its chunk, and query no device state
     // while the stream is being captured
     if (c->capturing && c->wDc > 0 && c->wLanes == lanes) return c->wDc;
-    size_t total = size_t(16) << 30;
+    size_t total = size_t(24) << 30;
     size_t free_b = 0, all_b = 0;
     // the scratch this context already holds counts as free, so the choice is stable across calls
     if (cudaMemGetInfo(&free_b, &all_b) == cudaSuccess) total = std::min(total, (free_b + c->wscratch_bytes) / 4);
@@ -1553,8 +1559,12 @@ static int wide_chunk(dr_ctx* c, const NetDesc& N, int lanes) {
         total = std::min(total, (size_t)c->opt.mem_cap_bytes > c->owned ? (size_t)c->opt.mem_cap_bytes - c->owned : size_t(0));
     total = std::max(total, size_t(1) << 30);
     const size_t budget = total / lanes;
-    const int64_t dc = std::max<int64_t>(1, (int64_t)(budget / wide_bytes_per_domain(N)));
-    return (int)std::min<int64_t>(std::min<int64_t>(dc, c->D), 65535);
+    const int64_t dmax = std::min<int64_t>(std::max<int64_t>(1, (int64_t)(budget / wide_bytes_per_domain(N))), 65535);
+    // as few chunks per lane as the budget allows, all of (nearly) the same size: a small last chunk
+    // would run its GEMMs with few tiles per SM
+    const int64_t per_lane = (c->D + lanes - 1) / lanes;
+    const int64_t k = (per_lane + dmax - 1) / dmax;
+    return (int)std::max<int64_t>(1, (per_lane + k - 1) / k);
 }
 
 static inline unsigned blocks_for(int64_t threads, int bs) { return (unsigned)((threads + bs - 1) / bs); }
@@ -1604,6 +1614,10 @@ static int wide_step(dr_ctx* c, WideLane& w, int t, bool tcore) {
     const size_t dyn_smem = sizeof(double) * (n * n + 3 * n + 128);
     k_w_view<<<dc, 128, 0, st>>>(a);
     c->launches++;
+    if (a.rigorous && L >= 2) {  // q_1 = |W_1| xmax for the error bounds of the last chain level
+        k_r_q<<<blocks_for((int64_t)dc * N.w[1] * 32, 256), 256, 0, st>>>(a, 1);
+        c->launches++;
+    }
     for (int ell = 1; ell <= L; ++ell) {
         const int rows = N.w[ell];
         const int64_t warps = (int64_t)dc * rows;
@@ -1698,6 +1712,10 @@ static int wide_step(dr_ctx* c, WideLane& w, int t, bool tcore) {
         if (ell < L) {
             k_w_relax<<<dc, 256, 0, st>>>(a, ell, t);
             c->launches++;
+            if (a.rigorous && ell + 1 <= L - 1) {
+                k_r_q<<<blocks_for((int64_t)dc * N.w[ell + 1] * 32, 256), 256, 0, st>>>(a, ell + 1);
+                c->launches++;
+            }
         }
     }
     k_w_dyn<<<dc, 128, dyn_smem, st>>>(a, t);
@@ -1733,6 +1751,7 @@ static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
     a.V = c->dV;
     a.status = c->dstatus;
     a.alpha_used = alpha_used;
+    a.rigorous = c->opt.rigorous;
     // Domains are independent: two lanes of chunks advance on two streams, so that one lane's
     // memory-bound kernels overlap the other lane's tensor-core GEMMs.
     const int lanes = c->D >= 256 ? 2 : 1;
@@ -1744,7 +1763,9 @@ static int run_forward_wide(dr_ctx* c, int mode, float* alpha_used) {
                       &w[l].t2));
         w[l].st = c->stream;
     }
-    const bool tcore = c->opt.precision != DR_PREC_SIMT;
+    // rigorous mode runs the chain on CUDA cores: its error bounds use the IEEE FP32 round-to-nearest
+    // model, which the tensor cores' internal accumulation does not document
+    const bool tcore = c->opt.precision != DR_PREC_SIMT && !c->opt.rigorous;
     if (tcore) CUDA_TRY(c, cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream));
     if (lanes > 1) {
         if (!c->ev_fork) CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
@@ -1823,7 +1844,7 @@ static int slab_chunk(dr_ctx* c, size_t per_cta, int64_t* chunk) {
 // shared memory (DR_PREC_AUTO); DR_PREC_SIMT / DR_PREC_TF32X3 and wider controllers take the
 // staged path.
 static bool use_fused(const dr_ctx* c) {
-    return c->opt.precision == DR_PREC_AUTO && fused_fits(c->net);
+    return c->opt.precision == DR_PREC_AUTO && !c->opt.rigorous && fused_fits(c->net);
 }
 
 static int run_forward(dr_ctx* c, int mode, float* alpha_used, bool tape) {

@@ -54,7 +54,28 @@ struct WideArgs {
     float *G, *sa, *sRlo, *sRhi, *sS;   // [Dc][maxw][n], [Dc][maxw]
     double *cu, *Iulo, *Iuhi;           // [Dc][m] controller TM, FP64
     int64_t lam_stride;                 // floats per domain in a Lambda buffer
+    // rigorous mode (CUDA-core chain only): rounding-error bounds carried with the intercepts
+    int rigorous;
+    float* xmax;   // [Dc][n] bound on |x| over the Taylor model (rounded up)
+    float* hq;     // [Dc][hidden] q_m = |W_m| hmax_{m-1} per neuron of hidden layer m (rounded up)
+    double* kerr;  // [Dc][maxw] accumulated error bound of each target row's linear bound
 };
+
+// Rigorous mode.  For IEEE FP32 with round-to-nearest (the CUDA-core FMA chains used in this mode),
+// a sum or dot product of K terms computed in any order errs by at most gamma(K) times the sum of the
+// absolute values of its terms, gamma(K) = K u / (1 - K u), u = 2^-24 (the standard forward error
+// bound of recursive summation).  Each bound below takes K + 2 to also cover the rounding of the
+// operands' products and the final addition.
+__device__ __forceinline__ double gamma_k(int K) {
+    const double ku = (double)(K + 2) * 5.9604644775390625e-8;  // (K + 2) * 2^-24
+    return ku / (1.0 - ku);
+}
+// Absolute error weight of one column j of a chain level: the level's product Lambda_s W_m (K = n_m
+// terms per entry, each bounded by |Lambda_ij| s_j |W_m[j,k]| hmax_{m-1}[k], summed over k into q_j)
+// and its intercept sums (terms |Lambda_ij| d_j and |Lambda_ij| s_j |b_j|).
+__device__ __forceinline__ float err_weight(float s, float d, float b, float q, double gk) {
+    return (float)(gk * ((double)s * ((double)q + fabs((double)b)) + (double)d)) * 1.0009765625f;  // (1 + 2^-10): rounding of this product
+}
 
 __device__ __forceinline__ float warp_sum(float x) {
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -101,6 +122,12 @@ __global__ void k_w_view(const WideArgs a) {
         a.cf[(int64_t)d * n + i] = cf;
         a.Ilof[(int64_t)d * n + i] = __double2float_rd(a.Ilo[(int64_t)d * n + i] + dc - dev);
         a.Ihif[(int64_t)d * n + i] = __double2float_ru(a.Ihi[(int64_t)d * n + i] + dc + dev);
+        if (a.rigorous) {
+            // |x| <= |c_f| + sum |P_f| + max |I_f| over the FP32 view (whose remainder covers the cast)
+            double mag = fabs((double)cf) + fmax(fabs((double)a.Ilof[(int64_t)d * n + i]), fabs((double)a.Ihif[(int64_t)d * n + i]));
+            for (int k = 0; k < n; ++k) mag += fabs((double)(float)P[i * n + k]);
+            a.xmax[(int64_t)d * n + i] = __double2float_ru(mag * (1.0 + 1e-12));
+        }
     }
     if (threadIdx.x == 0) {
         double dv = 0.0;
@@ -128,6 +155,7 @@ __global__ void k_w_chain_init(const WideArgs a, int ell, float* __restrict__ Ao
         if (lane == 0) {
             a.klo[(int64_t)d * N.maxw + i] = (double)bi;
             a.khi[(int64_t)d * N.maxw + i] = (double)bi;
+            if (a.rigorous) a.kerr[(int64_t)d * N.maxw + i] = 0.0;
         }
         return;
     }
@@ -136,19 +164,24 @@ __global__ void k_w_chain_init(const WideArgs a, int ell, float* __restrict__ Ao
     const float* s = a.hs + (int64_t)d * N.hidden + N.hoff[ell - 1];
     const float* dd = a.hd + (int64_t)d * N.hidden + N.hoff[ell - 1];
     const float* bm = a.b + N.boff[ell - 2];
+    const float* q = a.rigorous ? a.hq + (int64_t)d * N.hidden + N.hoff[ell - 1] : nullptr;
+    const double gk = gamma_k(K);
     float* out = Aout + (int64_t)d * a.lam_stride + (int64_t)i * K;
-    float spos = 0.f, sneg = 0.f, sb = 0.f;
+    float spos = 0.f, sneg = 0.f, sb = 0.f, se = 0.f;
     for (int j = lane; j < K; j += 32) {
         const float x = Wrow[j];
         spos = fmaf(posf(x), dd[j], spos);
         sneg = fmaf(negf(x), dd[j], sneg);
         const float xs = x * s[j];
         sb = fmaf(xs, bm[j], sb);
+        if (q) se = __fmaf_ru(fabsf(x), err_weight(s[j], dd[j], bm[j], q[j], gk), se);
         out[j] = xs;
     }
     spos = warp_sum(spos);
     sneg = warp_sum(sneg);
     sb = warp_sum(sb);
+    if (q) se = warp_sum(se);
+    if (lane == 0 && q) a.kerr[(int64_t)d * N.maxw + i] = (double)se * 1.0009765625;
     if (lane == 0) {
         a.khi[(int64_t)d * N.maxw + i] = (double)bi + (double)spos + (double)sb;
         a.klo[(int64_t)d * N.maxw + i] = (double)bi + (double)sneg + (double)sb;
@@ -167,19 +200,24 @@ __global__ void k_w_level_epi(const WideArgs a, int ell, int mm, float* __restri
     const float* s = a.hs + (int64_t)d * N.hidden + N.hoff[mm];
     const float* dd = a.hd + (int64_t)d * N.hidden + N.hoff[mm];
     const float* bm = a.b + N.boff[mm - 1];
+    const float* q = a.rigorous ? a.hq + (int64_t)d * N.hidden + N.hoff[mm] : nullptr;
+    const double gk = gamma_k(K);
     float* row = buf + (int64_t)d * a.lam_stride + (int64_t)i * K;
-    float spos = 0.f, sneg = 0.f, sb = 0.f;
+    float spos = 0.f, sneg = 0.f, sb = 0.f, se = 0.f;
     for (int j = lane; j < K; j += 32) {
         const float x = row[j];
         spos = fmaf(posf(x), dd[j], spos);
         sneg = fmaf(negf(x), dd[j], sneg);
         const float xs = x * s[j];
         sb = fmaf(xs, bm[j], sb);
+        if (q) se = __fmaf_ru(fabsf(x), err_weight(s[j], dd[j], bm[j], q[j], gk), se);
         row[j] = xs;
     }
     spos = warp_sum(spos);
     sneg = warp_sum(sneg);
     sb = warp_sum(sb);
+    if (q) se = warp_sum(se);
+    if (lane == 0 && q) a.kerr[(int64_t)d * N.maxw + i] += (double)se * 1.0009765625;
     if (lane == 0) {
         a.khi[(int64_t)d * N.maxw + i] += (double)spos + (double)sb;
         a.klo[(int64_t)d * N.maxw + i] += (double)sneg + (double)sb;
@@ -237,17 +275,18 @@ __global__ void __launch_bounds__(256) k_w_gemm_simt(const float* __restrict__ A
 // |G -+ v|) and its FP64 intercepts: the terms are added in FP64; pre-activation bounds are rounded
 // to FP32 outward (they feed the FP32 relaxation), the controller TM stays FP64.
 __device__ __forceinline__ void concretise(const WideArgs& a, int ell, int d, int i, float av, float rlo, float rhi,
-                                           float g1, float gm, float gp, float wf, double klo, double khi) {
+                                           float g1, float gm, float gp, float wf, double klo, double khi, double err = 0.0) {
     const NetDesc& N = a.net;
     const float S = fabsf(av) + g1 + (float)fabs(klo) + (float)fabs(khi) + fabsf(rlo) + fabsf(rhi) + fabsf(wf);
-    const double mr = (double)a.rho * (double)S;
+    // rigorous mode: the row's error bound plus the FP64 rounding of the few additions below
+    const double mr = (double)a.rho * (double)S + (a.rigorous ? err + 1e-15 * (double)S : 0.0);
     if (ell < N.L) {
         a.hl[(int64_t)d * N.hidden + N.hoff[ell] + i] = __double2float_rd((double)av + klo + (double)rlo - (double)gm - (double)wf - mr);
         a.hu[(int64_t)d * N.hidden + N.hoff[ell] + i] = __double2float_ru((double)av + khi + (double)rhi + (double)gp + (double)wf + mr);
         a.sa[(int64_t)d * N.maxw + i] = av;
         a.sRlo[(int64_t)d * N.maxw + i] = rlo;
         a.sRhi[(int64_t)d * N.maxw + i] = rhi;
-        a.sS[(int64_t)d * N.maxw + i] = S;
+        a.sS[(int64_t)d * N.maxw + i] = __double2float_ru(mr);  // the outward margin applied (split records reuse it)
     } else {
         a.cu[(int64_t)d * N.m + i] = (double)av + 0.5 * (klo + khi);
         a.Iulo[(int64_t)d * N.m + i] = 0.5 * (klo - khi) + (double)rlo - mr;
@@ -259,7 +298,7 @@ __device__ __forceinline__ void concretise(const WideArgs& a, int ell, int d, in
 // domain's Lambda_x (rows x n, ld n) or, for ell == 1, the shared W_1.
 __global__ void k_w_project(const WideArgs a, int ell, const float* __restrict__ Lxb, int shared_lx) {
     const NetDesc& N = a.net;
-    const int n = N.n, L = N.L, rows = N.w[ell];
+    const int n = N.n, rows = N.w[ell];
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (wid >= (int64_t)a.Dc * rows) return;
@@ -293,9 +332,41 @@ __global__ void k_w_project(const WideArgs a, int ell, const float* __restrict__
     av = warp_sum(av);
     rlo = warp_sum(rlo);
     rhi = warp_sum(rhi);
+    // rigorous mode: bound of this row's own rounding (G, the centre and remainder terms, the |G -+ v|
+    // sums; n terms each, every term at most |Lambda_x j| xmax_j or |G_k| + |v_k|) plus the chain's
+    float re = 0.f;
+    if (a.rigorous) {
+        const float* xm = a.xmax + (int64_t)d * n;
+        for (int j = lane; j < n; j += 32) re = __fmaf_ru(fabsf(Lx[j]), xm[j], re);
+        float vs = 0.f;
+        for (int k = lane; k < n; k += 32) vs += fabsf(vf[k]);
+        re = __fadd_ru(re, __fadd_ru(g1, vs));
+        re = warp_sum(re);
+    }
     if (lane != 0) return;
     const double klo = a.klo[(int64_t)d * N.maxw + i], khi = a.khi[(int64_t)d * N.maxw + i];
-    concretise(a, ell, d, i, av, rlo, rhi, g1, gm, gp, vf[n], klo, khi);
+    double err = 0.0;
+    if (a.rigorous)
+        err = a.kerr[(int64_t)d * N.maxw + i] + 4.0 * gamma_k(n) * (double)re * 1.0009765625;
+    concretise(a, ell, d, i, av, rlo, rhi, g1, gm, gp, vf[n], klo, khi, err);
+}
+
+// Rigorous mode: q_m = |W_m| hmax_{m-1} for hidden layer m (hmax_0 = xmax, else max(u_{m-1}, 0)), the
+// magnitude each level's product error is measured in.  One warp per (domain, neuron of layer m); the
+// FP32 sum of non-negative terms is rounded up and enlarged by 2^-10, far above its relative error.
+__global__ void k_r_q(const WideArgs a, int mm) {
+    const NetDesc& N = a.net;
+    const int rows = N.w[mm], K = N.w[mm - 1];
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= (int64_t)a.Dc * rows) return;
+    const int d = (int)(wid / rows), j = (int)(wid - (int64_t)d * rows);
+    const float* Wrow = a.W + N.Woff[mm - 1] + (int64_t)j * K;
+    const float* hu = mm == 1 ? a.xmax + (int64_t)d * N.n : a.hu + (int64_t)d * N.hidden + N.hoff[mm - 1];
+    float acc = 0.f;
+    for (int k = lane; k < K; k += 32) acc = __fmaf_ru(fabsf(Wrow[k]), mm == 1 ? hu[k] : fmaxf(hu[k], 0.f), acc);
+    acc = warp_sum(acc);
+    if (lane == 0) a.hq[(int64_t)d * N.hidden + N.hoff[mm] + j] = __fmul_ru(acc, 1.0009765625f);
 }
 
 // Splits of (t, ell) and the shared-slope relaxation of hidden layer ell; one block per domain.
@@ -316,8 +387,8 @@ __global__ void k_w_relax(const WideArgs a, int ell, int t) {
                 const int j = r.neuron;
                 const int64_t q = (int64_t)d * N.maxw + j;
                 const float bt = a.beta ? a.beta[cpos] : 0.f;
-                const double hh = r.sign > 0 ? ((double)a.sa[q] + a.khi[q] + (double)a.sRhi[q] + (double)a.rho * a.sS[q])
-                                             : (-((double)a.sa[q] + a.klo[q] + (double)a.sRlo[q]) + (double)a.rho * a.sS[q]);
+                const double hh = r.sign > 0 ? ((double)a.sa[q] + a.khi[q] + (double)a.sRhi[q] + (double)a.sS[q])
+                                             : (-((double)a.sa[q] + a.klo[q] + (double)a.sRlo[q]) + (double)a.sS[q]);
                 if (r.sign > 0) {
                     if (lh[j] < 0.f) lh[j] = 0.f;
                 } else {
@@ -355,7 +426,8 @@ __global__ void k_w_relax(const WideArgs a, int ell, int t) {
             else if (a.mode == DR_SLOPE_ADAPTIVE_K) al = (u >= -l) ? 1.f : 0.f;
             else if (a.mode == DR_SLOPE_ZERO_K) al = 0.f;
             else al = a.alpha[(dom * H + t) * (int64_t)N.hidden + N.hoff[ell] + j];
-            const float b1 = -al * l, b2 = (1.f - al) * u;
+            const float b1 = a.rigorous ? __fmul_ru(-al, l) : -al * l;
+            const float b2 = a.rigorous ? __fmul_ru(__fadd_ru(1.f, -al), u) : (1.f - al) * u;
             sl = al;
             dd = (b1 >= b2) ? b1 : b2;
         }
@@ -405,6 +477,23 @@ __global__ void k_w_dyn(const WideArgs a, int t) {
             acc = fma(x, cu[j], acc);
             lo_ += posd(x) * Iulo[j] + negd(x) * Iuhi[j];
             hi_ += posd(x) * Iuhi[j] + negd(x) * Iulo[j];
+        }
+        if (a.rigorous) {
+            // FP64 rounding of c', P' and the interval products (<= 34 terms each): 2^-47 of their
+            // magnitude (>= (34 + 2) 2^-53), folded into the remainder
+            double mag = fabs(a.e ? a.e[i] : 0.0) + fabs(a.eoff ? a.eoff[(dom * H + t) * n + i] : 0.0);
+            for (int j = 0; j < n; ++j) {
+                double pj = 0.0;
+                for (int k = 0; k < n; ++k) pj += fabs(P[j * n + k]);
+                mag += fabs(a.A[i * n + j]) * (fabs(c[j]) + pj + fmax(fabs(Ilo[j]), fabs(Ihi[j])));
+            }
+            for (int j = 0; j < m; ++j) {
+                double gj = 0.0;
+                for (int k = 0; k < n; ++k) gj += fabs((double)G[j * n + k]);
+                mag += fabs(a.B[i * m + j]) * (fabs(cu[j]) + gj + fmax(fabs(Iulo[j]), fabs(Iuhi[j])));
+            }
+            lo_ -= 7.105427357601002e-15 * mag;
+            hi_ += 7.105427357601002e-15 * mag;
         }
         cn[i] = acc;
         Ilon[i] = lo_;
