@@ -17,13 +17,15 @@
 //
 // The three TF32 products and their order are those of k_tc_gemm_p.  Accumulation is promoted per
 // fill: the tensor core sums kPromote chunks of 32 into a partial buffer, which the epilogue then
-// adds into FP32 registers.  kPromote = 1, as in k_tc_gemm_p: the tensor core's accumulation
-// rounds toward zero relative to the running sum, and over 50 closed-loop steps two chunks per
-// fill used up to 86 % of the reported boxes' outward margin (one chunk: 53 %, plain FP32 41 %),
-// four chunks exceeded it.  The intercept partials keep the two 64-column sets
-// per tile.  The final level's (x*s) W_1 product is taken with FP32 FMAs (the TMEM is all partial
-// buffers), not with 3xTF32 MMAs.  The next operand (chain levels) leaves through a per-warp
-// staging tile in shared memory, so its global stores cover whole 64-byte row segments.
+// adds into FP32 registers.  The tensor core's accumulation rounds toward zero relative to the running
+// sum, so longer fills err more.  kPromote = 2 (every 64 of K): with the intercepts summed in FP64
+// across the chain levels (wide.cuh), the boxes of the 16-512x4-8 workload over 50 steps use at
+// most 4 % of their outward margin against the FP64 oracle (7 % on the branch workload), against
+// 1 % (0.4 %) with one chunk per fill, and a pass is 3.6 % faster; four chunks per fill made a lower
+// bound of the branch workload tighter than the oracle's.  The intercept partials keep the two
+// 64-column sets per tile.  The final level's (x*s) W_1 product is taken with FP32 FMAs (the TMEM is
+// all partial buffers), not with 3xTF32 MMAs.  The next operand (chain levels) leaves through a
+// per-warp staging tile in shared memory, so its global stores cover whole 64-byte row segments.
 //
 // Every wait is bounded.  On expiry the error flag is raised and each role runs through its
 // remaining loop structure without waiting (group barriers stay matched), so the CTA always exits.
@@ -36,7 +38,7 @@ constexpr int kPersistThreads = 128 + 2 * 128;
 constexpr int kRegsLaunch = 168, kRegsCtl = 56, kRegsEpi = 224;
 static_assert(128 * (kRegsLaunch - kRegsCtl) >= 256 * (kRegsEpi - kRegsLaunch), "register split exceeds the launch's registers");
 constexpr int kPS = 3;                              // ring stages
-constexpr int kPromote = 1;                         // K chunks (of 32) per partial buffer fill
+constexpr int kPromote = 2;                         // K chunks (of 32) per partial buffer fill
 constexpr int kPSB = stage_bytes(128);              // 64 KB per stage
 __host__ __device__ constexpr int pp_coltab_offset() { return kPS * kPSB + 256; }
 __host__ __device__ constexpr int pp_w1tab_offset() { return pp_coltab_offset() + 2 * 128 * 16; }
