@@ -45,7 +45,7 @@ FUSED_TRAFFIC_BYTES = 548864
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch over R = 65,536 rows (ncu, small case),
 # divided by R.  The traffic grows with R (the left operand is read once; the chain level also writes
 # the next one once), so a full launch's traffic is this times its rows.
-GEMM_TRAFFIC_PER_ROW = {"final": (271.5e6 + 18.6e6) / 65536, "chain": (271.4e6 + 227.1e6) / 65536}
+GEMM_TRAFFIC_PER_ROW = {"final": (271.4e6 + 18.45e6) / 65536, "chain": (271.2e6 + 226.25e6) / 65536}
 # launches of at least this many stacked rows are the full-size ones (hidden-layer targets:
 # domains x 512 rows); the controller-output target's launches have domains x 8 rows
 BIG_GEMM_ROWS = 65536
@@ -750,6 +750,8 @@ def main():
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak_sus, "unit": "TFLOP/s",
             "frac": (achieved / peak_sus) if achieved else None,
             "traffic": GEMM_TRAFFIC_PER_ROW["final"] * rows_per_launch, "traffic_unit": "B per launch",
+            "traffic_basis": "dram read + write of one launch over 65,536 rows (ncu, profiles/k_tc_gemm_pp_large16.md) "
+                             "scaled by the launch's rows",
             "kernel": "tc::k_tc_gemm_pp<2> (persistent 3xTF32 GEMM of the last chain level, x W_1 in the epilogue; "
                       "launches of the hidden-layer targets)",
             "kernel_launches_timed": fin["launches"], "kernel_ms_avg": fin["ms"] / max(1, fin["launches"]),
