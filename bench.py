@@ -642,7 +642,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    from paper_2605_25346_b300 import _lib, api
+    from paper_2605_25346_b300 import _lib, api, shard
 
     prob = workload(rank)
     D, H, n = prob.D, prob.H, prob.n
@@ -659,6 +659,9 @@ def main():
 
     def step():
         r._c(r.lib.dr_compute_bounds(r.ctx, P(lo), P(hi), P(hl), P(hh), P(st), 1))
+        if world > 1:
+            # the path's only exchange: the hull over every rank's domains (a9), min/max over ranks
+            shard.merge_hull(hl, hh)
 
     with torch.cuda.stream(stream), ClockSampler(local) as clk:
         for _ in range(args.warmup):
@@ -799,7 +802,8 @@ def main():
                 "config": {"workload": f"large16 16-512x4-8, chunk of {D} of 262,144 sub-boxes per GPU, H={H}, "
                                        "chord slopes", "domains_per_gpu": D, "horizon": H,
                            "l2": "flushed between timed steps (working set 16 GiB, also above L2)",
-                           "parallelism": f"domains sharded, {world} independent shard(s)"},
+                           "parallelism": f"domains sharded over {world} rank(s); per step one min/max all-reduce of "
+                                          "the (H+1) x n hull when N > 1"},
                 "e2e": {"value": world * D * H / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "steps": e2e_steps},
                 "gpu_launches": int(launches),

@@ -9,7 +9,8 @@
   not depend on which other domains share the launch.
 * Soundness of the GPU machines themselves: 10^4 simulated trajectories per workload (FP64, initial
   states uniform in the union of the domain boxes) stay inside the boxes of their domain at every
-  step; for branch domains only trajectories that satisfy all of the domain's split signs count.
+  step; for branch domains only trajectories that satisfy all of the domain's split signs count, and
+  draws continue until 10^4 of those have been checked.
 
 Tolerance: the same 1e-5 relative per box entry and zero-slack containment of the oracle's box as
 the other parity tests.
@@ -108,8 +109,14 @@ def test_branch12_all_domains():
                                     rng.choice(65536, size=12, replace=False)]))
     assert len(idx) >= 16
     compare(p.subset(idx), _sampled(g, idx), orc.reach(p.subset(idx)), check_hull=False)
-    ok, n = _enclosed(p, g, 10000, 22, keep=_split_filter(p))
-    assert ok and n >= 300
+    # 10^4 trajectories that satisfy all of their domain's split signs (about 6 % of uniform draws do)
+    kept, seed = 0, 100
+    while kept < 10000 and seed < 140:
+        ok, n = _enclosed(p, g, 10000, seed, keep=_split_filter(p))
+        assert ok
+        kept += n
+        seed += 1
+    assert kept >= 10000
 
 
 def test_double_integrator_grid_enclosed():
