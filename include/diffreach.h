@@ -62,6 +62,11 @@ extern "C" {
 /* per-domain status bits written by dr_compute_bounds */
 #define DR_STATUS_NONFINITE 1u  /* some bound is inf/nan                                     */
 #define DR_STATUS_INFEASIBLE 2u /* a split left l > u: the domain is empty, bounds vacuous   */
+#define DR_STATUS_MARGIN 4u     /* a row of the controller pass summed terms of more than 256x
+                                   the Taylor model's scale (max_i |c_i| + sum_k |P_ik| + max |I_i|):
+                                   beyond the range the default box_margin was calibrated on, so
+                                   its FP32 rounding may exceed the margin; dr_options.rigorous
+                                   gives guaranteed boxes (never set in rigorous mode)          */
 
 typedef struct dr_ctx dr_ctx;
 

@@ -14,7 +14,7 @@ DR_ERR_ARG, DR_ERR_SHAPE, DR_ERR_STATE, DR_ERR_OOM, DR_ERR_CUDA, DR_ERR_TIMEOUT,
 DR_F32, DR_F64 = 0, 1
 DR_SLOPE_ADAPTIVE, DR_SLOPE_CHORD, DR_SLOPE_ZERO, DR_SLOPE_USER = 0, 1, 2, 3
 DR_PREC_AUTO, DR_PREC_SIMT, DR_PREC_TF32X3 = 0, 1, 2
-DR_STATUS_NONFINITE, DR_STATUS_INFEASIBLE = 1, 2
+DR_STATUS_NONFINITE, DR_STATUS_INFEASIBLE, DR_STATUS_MARGIN = 1, 2, 4
 DR_KT_GEMM_ALL, DR_KT_GEMM_CHAIN, DR_KT_GEMM_FINAL, DR_KT_GEMM_OTHER = 0, 1, 2, 3
 
 # every symbol the header declares

@@ -34,6 +34,25 @@ __host__ __device__ __forceinline__ int odd_ld(int x) { return x | 1; }
 
 #define DR_STATUS_NONFINITE_BIT 1u
 #define DR_STATUS_INFEASIBLE_BIT 2u
+#define DR_STATUS_MARGIN_BIT 4u
+
+// The default outward box margin is calibrated on passes whose rows' summed term magnitudes S stay
+// within this factor of the Taylor model's scale max_i (|c_i| + sum_k |P_ik| + max |I_i|) (measured:
+// at most 18 on the workloads and 126 with first-layer biases shifted by +-6; 362 and more with
+// shifts of +-50, where the margin no longer covers the FP32 rounding).  A row beyond it raises
+// DR_STATUS_MARGIN_BIT.
+#define DR_MARGIN_RATIO 256.0f
+
+// max_i (|c_i| + sum_k |P_ik| + max(|Ilo_i|, |Ihi_i|)) of an FP64 Taylor model, as FP32.
+__device__ __forceinline__ float tm_scale(const double* c, const double* P, const double* Ilo, const double* Ihi, int n) {
+    float s = 0.f;
+    for (int i = 0; i < n; ++i) {
+        float r = fabsf((float)c[i]) + fmaxf(fabsf((float)Ilo[i]), fabsf((float)Ihi[i]));
+        for (int k = 0; k < n; ++k) r += fabsf((float)P[i * n + k]);
+        s = fmaxf(s, r);
+    }
+    return s;
+}
 
 #define DR_SLOPE_ADAPTIVE_K 0
 #define DR_SLOPE_CHORD_K 1

@@ -450,7 +450,7 @@ static WarpLayout warp_layout(const NetDesc& N, int WPC, bool splits) {
     Y.sRhi = dtake(sizeof(float) * hm);
     Y.sS = dtake(sizeof(float) * hm);
     Y.Gs = dtake(sizeof(float) * hm * kWarpNX);
-    Y.misc = dtake(sizeof(int) * 2);
+    Y.misc = dtake(sizeof(int) * 4);
     Y.stride = (int)((d + 15) & ~size_t(15));
     Y.total = Y.dom0 + WPC * Y.stride;
     return Y;
@@ -1438,6 +1438,7 @@ static size_t wide_bytes_per_domain(const NetDesc& N) {
     b += sizeof(float) * 4 * std::max(N.hidden, 1);               // l, u, s, d
     b += sizeof(double) * 2 * N.maxw;                             // kappa (FP64)
     b += sizeof(double) * N.maxw + sizeof(float) * (n + std::max(N.hidden, 1));  // rigorous mode: kerr, xmax, q
+    b += sizeof(float);                                                           // Taylor-model scale
     b += sizeof(float) * ((size_t)N.maxw * n + 4 * N.maxw);       // G, a, R, S
     b += sizeof(double) * 3 * m;                                  // controller TM (FP64)
     b += sizeof(float) * 4 * wide_lam_stride(N);                  // Lambda buffers (two TF32 pairs)
@@ -1520,6 +1521,7 @@ static int wide_bind(dr_ctx* c, WideArgs& a, int Dc, int lanes, int lane, float*
     a.kerr = (double*)take(sizeof(double) * D * N.maxw);
     a.xmax = (float*)take(sizeof(float) * D * n);
     a.hq = (float*)take(sizeof(float) * D * hid);
+    a.xscale = (float*)take(sizeof(float) * D);
     a.lam_stride = wide_lam_stride(N);
     const int64_t lam_pad = wide_lam_pad(N);
     *lamA = (float*)take(sizeof(float) * (D * a.lam_stride + lam_pad));

@@ -186,6 +186,7 @@ __device__ void tm_view(const Dom& s, int n) {
             dv += fabs(s.v[k] - (double)s.vf[k]);
         }
         s.vf[n] = __double2float_ru(s.wv[0] + dv);
+        s.misc[2] = __float_as_int(tm_scale(s.c, s.P, s.Ilo, s.Ihi, n));  // for DR_STATUS_MARGIN_BIT
     }
     __syncthreads();
 }
@@ -321,6 +322,7 @@ __device__ void project(const Dom& s, const NetDesc& N, int ell, const float* cu
         }
         const float wf = s.vf[n];
         const float S = fabsf(av) + g1 + fabsf(s.klo[i]) + fabsf(s.khi[i]) + fabsf(rlo) + fabsf(rhi) + fabsf(wf);
+        if (S > DR_MARGIN_RATIO * __int_as_float(s.misc[2])) atomicOr(reinterpret_cast<unsigned int*>(&s.misc[1]), DR_STATUS_MARGIN_BIT);
         if (ell < L) {
             const float lb = av + s.klo[i] + rlo - gm - wf - rho * S;
             const float ub = av + s.khi[i] + rhi + gp + wf + rho * S;

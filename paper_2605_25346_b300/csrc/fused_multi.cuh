@@ -153,6 +153,7 @@ __global__ void __launch_bounds__(NT) k_fused_forward_multi(const MultiArgs a) {
                 dv += fabs(v[k] - (double)vf[k]);
             }
             vf[n] = __double2float_ru(MD(g, Y.w)[0] + dv);
+            MI(g, Y.misc)[2] = __float_as_int(tm_scale(MD(g, Y.c), MD(g, Y.P), MD(g, Y.Ilo), MD(g, Y.Ihi), n));
         }
         __syncthreads();
 
@@ -340,6 +341,8 @@ __global__ void __launch_bounds__(NT) k_fused_forward_multi(const MultiArgs a) {
                 const float klo = MF(g, Y.klo)[i], khi = MF(g, Y.khi)[i];
                 const float wf = vf[n];
                 const float S = fabsf(av) + g1 + fabsf(klo) + fabsf(khi) + fabsf(rlo) + fabsf(rhi) + fabsf(wf);
+                if (S > DR_MARGIN_RATIO * __int_as_float(MI(g, Y.misc)[2]))
+                    atomicOr(reinterpret_cast<unsigned int*>(MI(g, Y.misc) + 1), DR_STATUS_MARGIN_BIT);
                 if (ell < L) {
                     MF(g, Y.hl)[N.hoff[ell] + i] = av + klo + rlo - gm - wf - rho * S;
                     MF(g, Y.hu)[N.hoff[ell] + i] = av + khi + rhi + gp + wf + rho * S;

@@ -33,7 +33,7 @@ struct WarpLayout {  // shared: byte offsets from the CTA base; per warp: from t
     int Lx3;             // [m][n]
     int Pu, cu, Iulo, Iuhi;
     int sa, klo, khi, sRlo, sRhi, sS, Gs;  // split data of the current target (with splits only)
-    int misc;            // ints: [0] split cursor, [1] status
+    int misc;            // ints: [0] split cursor, [1] status, [2] Taylor-model scale (FP32 bits)
     int total;
 };
 
@@ -221,6 +221,7 @@ __global__ void __launch_bounds__(32 * WPC, (24 + WPC - 1) / WPC) k_fused_warp(c
     auto hidden_row = [&](int ell, int i, const RowOut& o, float klo, float khi, const float* G) {
         const float wf = vf[n];
         const float S = fabsf(o.av) + o.g1 + fabsf(klo) + fabsf(khi) + fabsf(o.rlo) + fabsf(o.rhi) + fabsf(wf);
+        if (S > DR_MARGIN_RATIO * __int_as_float(misc[2])) atomicOr(reinterpret_cast<unsigned int*>(misc + 1), DR_STATUS_MARGIN_BIT);
         hl[N.hoff[ell] + i] = o.av + klo + o.rlo - o.gm - wf - rho * S;
         hu[N.hoff[ell] + i] = o.av + khi + o.rhi + o.gp + wf + rho * S;
         if (has_splits) {
@@ -255,6 +256,7 @@ __global__ void __launch_bounds__(32 * WPC, (24 + WPC - 1) / WPC) k_fused_warp(c
                 dv += fabs(v[k] - (double)vf[k]);
             }
             vf[n] = __double2float_ru(wv[0] + dv);
+            misc[2] = __float_as_int(tm_scale(c, P, Ilo, Ihi, n));
         }
         __syncwarp();
 
@@ -392,6 +394,8 @@ __global__ void __launch_bounds__(32 * WPC, (24 + WPC - 1) / WPC) k_fused_warp(c
                 const RowOut o = concretise_row(x, n, Pf, cf, Ilof, Ihif, vf, G);
                 const float klo = kl3, khi = kh3, wf = vf[n];
                 const float S = fabsf(o.av) + o.g1 + fabsf(klo) + fabsf(khi) + fabsf(o.rlo) + fabsf(o.rhi) + fabsf(wf);
+                if (S > DR_MARGIN_RATIO * __int_as_float(misc[2]))
+                    atomicOr(reinterpret_cast<unsigned int*>(misc + 1), DR_STATUS_MARGIN_BIT);
                 cu[r] = o.av + 0.5f * (klo + khi);
                 Iulo[r] = 0.5f * (klo - khi) + o.rlo - rho * S;
                 Iuhi[r] = 0.5f * (khi - klo) + o.rhi + rho * S;

@@ -58,6 +58,7 @@ struct WideArgs {
     int rigorous;
     float* xmax;   // [Dc][n] bound on |x| over the Taylor model (rounded up)
     float* hq;     // [Dc][hidden] q_m = |W_m| hmax_{m-1} per neuron of hidden layer m (rounded up)
+    float* xscale; // [Dc] Taylor-model scale of the step (DR_STATUS_MARGIN_BIT)
     double* kerr;  // [Dc][maxw] accumulated error bound of each target row's linear bound
 };
 
@@ -137,6 +138,7 @@ __global__ void k_w_view(const WideArgs a) {
             dv += fabs(a.v[(int64_t)d * n + k] - (double)vf[k]);
         }
         vf[n] = __double2float_ru(a.w[d] + dv);
+        a.xscale[d] = tm_scale(a.c + (int64_t)d * n, P, a.Ilo + (int64_t)d * n, a.Ihi + (int64_t)d * n, n);
     }
 }
 
@@ -278,6 +280,7 @@ __device__ __forceinline__ void concretise(const WideArgs& a, int ell, int d, in
                                            float g1, float gm, float gp, float wf, double klo, double khi, double err = 0.0) {
     const NetDesc& N = a.net;
     const float S = fabsf(av) + g1 + (float)fabs(klo) + (float)fabs(khi) + fabsf(rlo) + fabsf(rhi) + fabsf(wf);
+    if (!a.rigorous && S > DR_MARGIN_RATIO * a.xscale[d]) atomicOr(&a.st[d], DR_STATUS_MARGIN_BIT);
     // rigorous mode: the row's error bound plus the FP64 rounding of the few additions below
     const double mr = (double)a.rho * (double)S + (a.rigorous ? err + 1e-15 * (double)S : 0.0);
     if (ell < N.L) {
