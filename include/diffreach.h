@@ -87,7 +87,8 @@ typedef struct dr_options {
                               (pre-activation bounds, controller remainder, split constraint)
                               is widened by rho * S, S the L1 magnitude of its summed terms.
                               Default 0: such margins compound through the closed loop.      */
-    int64_t chunk_domains; /* domains per device pass of the staged path (bounds its scratch);
+    int64_t chunk_domains; /* domains per device pass of the staged path (bounds its scratch) and
+                              at most this many per launch of the reverse sweep;
                               0 = automatic: the fewest equal chunks per lane that 24 GiB of
                               scratch holds, at most a quarter
                               of the free device memory and within mem_cap_bytes              */
@@ -127,7 +128,12 @@ typedef struct dr_options {
                               of the real-number closed loop; they are wider than FP64 arithmetic
                               without error terms gives.  The reverse sweep and refinement ignore
                               it.  0 (default) = the calibrated box_margin only                  */
-    int32_t reserved[2];
+    int32_t weight_grad;   /* 1 = dr_backward also forms the gradient with respect to the controller's
+                              weights and biases (read with dr_get_weight_gradient); costs about one
+                              more product per chain level in the reverse sweep and a per-domain
+                              slice of the parameters (at most 512 MiB, the sweep runs in chunks of
+                              domains).  0 (default) = off                                        */
+    int32_t reserved[1];
 } dr_options;
 
 /* Paper: no passage; the engine of Sec. IV runs batched on a single GPU (Sec. VI), and a context
@@ -239,6 +245,18 @@ int dr_optimize_slopes(dr_ctx* ctx, int steps, double lr_alpha, double lr_beta, 
  * shared memory run the same kernels out of library-owned per-CTA global-memory slabs (up to 2 GiB). */
 int dr_backward(dr_ctx* ctx, const double* dV_dlo, const double* dV_dhi, float* dalpha, float* dbeta,
                 int on_device);
+
+/* Paper: the certified-training loss of Sec. V-A differentiates the reachable-set objective with
+ * respect to the model's parameters; here the controller's parameters theta = (W_l, b_l).
+ * The gradient of the same scalar as the last dr_backward (which must have run with
+ * dr_options.weight_grad = 1), summed over all domains, with respect to the FP32 weights and biases
+ * the device computes with, through every path: the controller TM of each step, the pre-activation
+ * bounds that set the relaxation offsets (and, outside DR_SLOPE_USER, the slopes), and the split
+ * constraints.  dW [sum_l n_{l+1} n_l] FP64 packed as dr_static_args.W (layer after layer, row-major
+ * n_{l+1} x n_l), db [sum_l n_{l+1}] FP64 packed likewise; either may be NULL.  Host memory unless
+ * on_device != 0.  DR_ERR_STATE when no such dr_backward ran since the controller, dynamics, domains,
+ * horizon or splits changed. */
+int dr_get_weight_gradient(dr_ctx* ctx, double* dW, double* db, int on_device);
 
 /* Paper: the shared slope of each unstable ReLU under the shared-slope constraint (Sec. IV-C).
  * Slopes alpha [D x H x hidden] FP32 (hidden = n_1 + ... + n_{L-1}, layers concatenated);

@@ -138,13 +138,15 @@ class _SplitIndex:
 
 def reach(prob, alpha: Optional[torch.Tensor] = None, beta: Optional[torch.Tensor] = None,
           mode: Optional[int] = None, record: Optional[list] = None, keep_intermediate: bool = False,
-          shift: Optional[torch.Tensor] = None):
+          shift: Optional[torch.Tensor] = None, params: Optional[tuple] = None):
     """Bounds for every domain, step and coordinate (Alg. 2 with the closed loop of Sec. IV-E).
 
     alpha: [D, H, hidden] (MODE_USER only); beta: [nnz] split multipliers (>= 0) or None.
     shift: optional [D, H+1, n] shift of the TM centre, added to c_0 (entry 0) and to c_{t+1} after
     the dynamics of step t (entry t+1), on top of the problem's offsets; used to differentiate V
     with respect to the initial centre and the per-step offsets.
+    params: optional (W list, b list) of FP64 tensors replacing the controller's weights and biases
+    (to differentiate V with respect to them).
     Returns a dict with lo/hi [D, H+1, n], V [D], status [D] (int64), hull_lo/hull_hi [H+1, n],
     alpha_used [D, H, hidden] (the slopes in effect; zeros at stable neurons),
     and optionally the intermediate pre-activation bounds l/u [D, H, hidden].
@@ -152,8 +154,8 @@ def reach(prob, alpha: Optional[torch.Tensor] = None, beta: Optional[torch.Tenso
     mode = prob.mode if mode is None else mode
     D, n, H, L = prob.D, prob.n, prob.H, prob.L
     widths = prob.widths
-    W = [_t(w) for w in prob.W]
-    b = [_t(x) for x in prob.b]
+    W = [_t(w) for w in prob.W] if params is None else list(params[0])
+    b = [_t(x) for x in prob.b] if params is None else list(params[1])
     A, B, e = _t(prob.A), _t(prob.B), _t(prob.e)
     offs = np.concatenate([[0], np.cumsum(widths[1:-1])]).astype(int)
     if mode == MODE_USER and alpha is None:
@@ -342,6 +344,18 @@ def value_and_shift_grad(prob, alpha: Optional[torch.Tensor] = None, beta: Optio
     res = reach(prob, beta=beta, shift=sh, **kw)
     res["V"].sum().backward()
     return res, sh.grad
+
+
+def value_and_weight_grad(prob, alpha: Optional[torch.Tensor] = None, beta: Optional[torch.Tensor] = None):
+    """V per domain and dV/dW_l, dV/db_l of the controller (V summed over domains; the certified-training
+    loss of Sec. V-A differentiates the tube proxy with respect to the model's parameters), by
+    reverse-mode AD of the FP64 forward pass (user slopes held fixed when alpha is given)."""
+    W = [_t(w).clone().requires_grad_(True) for w in prob.W]
+    b = [_t(x).clone().requires_grad_(True) for x in prob.b]
+    kw = dict(mode=MODE_USER, alpha=alpha) if alpha is not None else {}
+    res = reach(prob, beta=beta, params=(W, b), **kw)
+    res["V"].sum().backward()
+    return res, [w.grad for w in W], [x.grad for x in b]
 
 
 def chord_alpha(prob) -> torch.Tensor:

@@ -21,7 +21,7 @@ DR_KT_GEMM_ALL, DR_KT_GEMM_CHAIN, DR_KT_GEMM_FINAL, DR_KT_GEMM_OTHER = 0, 1, 2, 
 EXPORTS = [
     "dr_create", "dr_destroy", "dr_load_controller", "dr_load_dynamics", "dr_set_boxes", "dr_set_splits",
     "dr_set_horizon", "dr_set_step_offsets", "dr_get_shift_gradient", "dr_set_options", "dr_compute_bounds", "dr_get_objective", "dr_optimize_slopes",
-    "dr_backward", "dr_get_alpha", "dr_set_alpha", "dr_get_beta", "dr_set_beta", "dr_kernel_launches", "dr_graph_replays", "dr_kernel_timing", "dr_gemm_tuning_report", "dr_last_error",
+    "dr_backward", "dr_get_weight_gradient", "dr_get_alpha", "dr_set_alpha", "dr_get_beta", "dr_set_beta", "dr_kernel_launches", "dr_graph_replays", "dr_kernel_timing", "dr_gemm_tuning_report", "dr_last_error",
     "dr_slope_gradient_static", "dr_tf32x3_gemm", "dr_check_wait_expiry",
 ]
 
@@ -43,7 +43,7 @@ class dr_options(ctypes.Structure):
                 ("chunk_domains", ctypes.c_int64), ("mem_cap_bytes", ctypes.c_int64),
                 ("box_margin", ctypes.c_double), ("tuning", ctypes.c_int32),
                 ("graphs", ctypes.c_int32), ("timing", ctypes.c_int32), ("rigorous", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("weight_grad", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 _lib = None
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dr_get_objective": (i32, [vp, dp, i32]),
         "dr_optimize_slopes": (i32, [vp, i32, ctypes.c_double, ctypes.c_double, dp]),
         "dr_backward": (i32, [vp, dp, dp, fp, fp, i32]),
+        "dr_get_weight_gradient": (i32, [vp, dp, dp, i32]),
         "dr_get_alpha": (i32, [vp, fp, i32]),
         "dr_set_alpha": (i32, [vp, fp, i32]),
         "dr_get_beta": (i32, [vp, fp, i32]),

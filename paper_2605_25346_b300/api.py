@@ -55,8 +55,9 @@ class Reach:
     # ---- problem upload -------------------------------------------------------------------
     def set_options(self, mode: Optional[int] = None, precision: int = _lib.DR_PREC_AUTO, rho: Optional[float] = None,
                     chunk: int = 0, mem_cap: int = 0, box_margin: Optional[float] = None, tuning: int = 0,
-                    graphs: int = 0, timing: int = 0, rigorous: int = 0):
+                    graphs: int = 0, timing: int = 0, rigorous: int = 0, weight_grad: int = 0):
         o = _lib.dr_options()
+        o.weight_grad = weight_grad
         o.tuning = tuning
         o.graphs = graphs
         o.timing = timing
@@ -133,6 +134,25 @@ class Reach:
         g = np.empty((p.D, p.H + 1, p.n))
         self._c(self.lib.dr_get_shift_gradient(self.ctx, _ptr(g), 0))
         return g
+
+    def weight_gradient(self):
+        """dV/dW_l, dV/db_l of the controller (lists of numpy arrays shaped like the problem's W, b),
+        summed over domains, of the last backward() call made with set_options(weight_grad=1)."""
+        p = self.prob
+        w = p.widths
+        nW = sum(int(w[l + 1]) * int(w[l]) for l in range(p.L))
+        nb = sum(int(w[l + 1]) for l in range(p.L))
+        gW = np.empty(nW)
+        gb = np.empty(nb)
+        self._c(self.lib.dr_get_weight_gradient(self.ctx, _ptr(gW), _ptr(gb), 0))
+        outW, outb, oW, ob = [], [], 0, 0
+        for l in range(p.L):
+            r, k = int(w[l + 1]), int(w[l])
+            outW.append(gW[oW:oW + r * k].reshape(r, k))
+            outb.append(gb[ob:ob + r])
+            oW += r * k
+            ob += r
+        return outW, outb
 
     # ---- computation ---------------------------------------------------------------------
     def bounds(self, on_device: bool = True, hull: bool = True):

@@ -58,6 +58,11 @@ struct dr_ctx {
     double* deoff = nullptr;    // [D][H][n] per-step offsets of the dynamics (null: none)
     double* dgshift = nullptr;  // [D][H+1][n] shift gradient written by the last dr_backward
     bool gshift_valid = false;
+    float* dgth = nullptr;       // per-domain slices of dV/dtheta of one backward chunk
+    size_t gth_bytes = 0;
+    double* dgth_part = nullptr; // [kThetaGroups][nparams] partial sums over the slices
+    double* dgtheta = nullptr;   // [nparams] dV/dtheta (W packed, then b) of the last dr_backward
+    bool gtheta_valid = false;
 
     // library-owned outputs / scratch
     double* dout_lo = nullptr;
@@ -196,7 +201,10 @@ static dr_options default_options() {
 
 static const int kMaxSmem = 227 * 1024;
 
-static FusedLayout fused_layout(const NetDesc& N, bool backward = false) {
+// top_adjoint: the Lambda-adjoint buffers also hold each target's top chain level (n_l x n_{l-1}),
+// which the weight gradient reads and the slab kernels' tiled products use as scratch; a backward
+// layout that does not fit shared memory (slab mode) always includes it.
+static FusedLayout fused_layout(const NetDesc& N, bool backward = false, bool top_adjoint = false) {
     FusedLayout Y;
     memset(&Y, 0, sizeof(Y));
     size_t off = 0;
@@ -263,7 +271,7 @@ static FusedLayout fused_layout(const NetDesc& N, bool backward = false) {
         size_t lv = 1, gl = (size_t)N.maxw * odd_ld(n);
         for (int l = 2; l <= N.L; ++l) {
             lv = std::max(lv, (size_t)lev_offset(N, l, l - 1));
-            for (int k = 1; k <= l - 2; ++k) gl = std::max(gl, (size_t)N.w[l] * odd_ld(N.w[k]));
+            for (int k = 1; k <= l - (top_adjoint ? 1 : 2); ++k) gl = std::max(gl, (size_t)N.w[l] * odd_ld(N.w[k]));
         }
         Y.lev = take(sizeof(float) * lv);
         Y.gc = take(sizeof(double) * n);
@@ -299,6 +307,7 @@ static FusedLayout fused_layout(const NetDesc& N, bool backward = false) {
         }
     }
     Y.total = (int)((off + 15) & ~size_t(15));
+    if (backward && !top_adjoint && Y.total > kMaxSmem) return fused_layout(N, true, true);
     return Y;
 }
 
@@ -951,6 +960,11 @@ static void free_outputs(dr_ctx* c) {
     dev_free(c, (void*&)c->dwhi, 0);
     dev_free(c, (void*&)c->dgshift, 0);
     c->gshift_valid = false;
+    dev_free(c, (void*&)c->dgth, c->gth_bytes);
+    c->gth_bytes = 0;
+    dev_free(c, (void*&)c->dgth_part, 0);
+    dev_free(c, (void*&)c->dgtheta, 0);
+    c->gtheta_valid = false;
     dev_free(c, c->wscratch, c->wscratch_bytes);
     c->wscratch_bytes = 0;
     dev_free(c, (void*&)c->gslab, c->gslab_bytes);
@@ -1032,6 +1046,7 @@ int dr_set_options(dr_ctx* c, const dr_options* o) {
         return fail(c, DR_ERR_STATE, "DR_SLOPE_USER requires dr_set_alpha first");
     if (n.timing < 0 || n.timing > 1) return fail(c, DR_ERR_ARG, "timing %d out of range", n.timing);
     if (n.rigorous < 0 || n.rigorous > 1) return fail(c, DR_ERR_ARG, "rigorous %d out of range", n.rigorous);
+    if (n.weight_grad < 0 || n.weight_grad > 1) return fail(c, DR_ERR_ARG, "weight_grad %d out of range", n.weight_grad);
     if (n.tuning < 0 || (n.tuning >= 2 + kNumMultiVariants && (n.tuning < 101 || n.tuning > 104)))
         return fail(c, DR_ERR_ARG, "tuning %d out of range", n.tuning);
     if (n.timing && !c->opt.timing) c->kt_done.clear();  // timing switched on: the totals start from zero
@@ -1130,6 +1145,8 @@ int dr_load_controller(dr_ctx* c, int L, const int32_t* widths, const void* cons
     dev_free(c, (void*&)c->dWpad, 0);
     TRY(dev_alloc(c, c->dW, nw));
     TRY(dev_alloc(c, c->db, nb));
+    c->gshift_valid = false;  // gradients of the previous controller
+    c->gtheta_valid = false;
     CUDA_TRY(c, cudaMemcpyAsync(c->dW, hw.data(), nw * sizeof(float), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->db, hb.data(), nb * sizeof(float), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -1237,6 +1254,8 @@ int dr_load_dynamics(dr_ctx* c, int n, int m, const double* A, const double* B, 
     dev_free(c, (void*&)c->dA, 0);
     dev_free(c, (void*&)c->dB, 0);
     dev_free(c, (void*&)c->de, 0);
+    c->gshift_valid = false;  // gradients of the previous dynamics
+    c->gtheta_valid = false;
     TRY(dev_alloc(c, c->dA, (size_t)n * n));
     TRY(dev_alloc(c, c->dB, (size_t)n * m));
     TRY(dev_alloc(c, c->de, (size_t)n));
@@ -2094,15 +2113,25 @@ int dr_set_beta(dr_ctx* c, const float* beta, int on_device) {
     return DR_OK;
 }
 
+// Controller parameter counts: packed weights (layer after layer, row-major) and packed biases.
+static int64_t theta_weights(const NetDesc& N) {
+    return N.Woff[N.L - 1] + (int64_t)N.w[N.L] * N.w[N.L - 1];
+}
+static int64_t theta_biases(const NetDesc& N) {
+    return N.boff[N.L - 1] + N.w[N.L];
+}
+constexpr int kThetaGroups = 64;                        // partial sums of the slice reduction
+constexpr size_t kThetaSliceBytes = size_t(512) << 20;  // per-domain slices of one backward chunk
+
 static int launch_backward(dr_ctx* c, int mode, const double* wlo, const double* whi, float* galpha, float* gbeta,
-                           double* gshift = nullptr) {
+                           double* gshift = nullptr, bool wgrad = false) {
     NetDesc N = c->net;
     N.H = c->H;
     if (c->D == 0) return DR_OK;
     FusedArgs a;
     memset(&a, 0, sizeof(a));
     a.net = N;
-    a.lay = fused_layout(N, true);
+    a.lay = fused_layout(N, true, wgrad);
     const bool slab = a.lay.total > kMaxSmem;
     a.W = c->dW;
     a.b = c->db;
@@ -2136,9 +2165,32 @@ static int launch_backward(dr_ctx* c, int mode, const double* wlo, const double*
         a.gwpad = c->dWpad;
         smem = nt == 256 ? (int)(sizeof(float) * kSlabTileFloats) : 0;  // the chain products' tiles
     }
+    if (c->opt.chunk_domains > 0) chunk = std::min<int64_t>(chunk, c->opt.chunk_domains);
+    const int64_t nth = theta_weights(N) + theta_biases(N);
+    if (wgrad) {
+        // one slice of dV/dtheta per domain (the kernel runs a CTA per domain), summed after each chunk
+        a.gth_boff = theta_weights(N);
+        a.gth_stride = (nth + 63) & ~int64_t(63);
+        chunk = std::max<int64_t>(1, std::min<int64_t>(chunk, (int64_t)(kThetaSliceBytes / (sizeof(float) * a.gth_stride))));
+        const size_t need = sizeof(float) * (size_t)std::min(chunk, c->D) * a.gth_stride;
+        if (c->gth_bytes < need) {
+            dev_free(c, (void*&)c->dgth, c->gth_bytes);
+            c->gth_bytes = 0;
+            TRY(dev_alloc(c, c->dgth, need / sizeof(float)));
+            c->gth_bytes = need;
+        }
+        dev_free(c, (void*&)c->dgth_part, 0);
+        TRY(dev_alloc(c, c->dgth_part, (size_t)kThetaGroups * nth));
+        if (!c->dgtheta) TRY(dev_alloc(c, c->dgtheta, (size_t)nth));
+        CUDA_TRY(c, cudaMemsetAsync(c->dgtheta, 0, sizeof(double) * nth, c->stream));
+    }
     for (int64_t d0 = 0; d0 < c->D; d0 += chunk) {
         a.d0 = d0;
         const int64_t nd = std::min(chunk, c->D - d0);
+        if (wgrad) {
+            a.gth = c->dgth;
+            CUDA_TRY(c, cudaMemsetAsync(c->dgth, 0, sizeof(float) * nd * a.gth_stride, c->stream));
+        }
         if (nt == 128) {
             CUDA_TRY(c, cudaFuncSetAttribute(k_fused_backward<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             k_fused_backward<128><<<(unsigned)nd, 128, smem, c->stream>>>(a);
@@ -2148,6 +2200,14 @@ static int launch_backward(dr_ctx* c, int mode, const double* wlo, const double*
         }
         CUDA_TRY(c, cudaGetLastError());
         c->launches++;
+        if (wgrad) {
+            const int groups = (int)std::min<int64_t>(kThetaGroups, nd);
+            const unsigned gx = (unsigned)((nth + 255) / 256);
+            k_theta_partial<<<dim3(gx, (unsigned)groups), 256, 0, c->stream>>>(c->dgth, nd, a.gth_stride, nth, c->dgth_part);
+            k_theta_finish<<<gx, 256, 0, c->stream>>>(c->dgth_part, groups, nth, c->dgtheta);
+            CUDA_TRY(c, cudaGetLastError());
+            c->launches += 2;
+        }
     }
     return DR_OK;
 }
@@ -2182,9 +2242,11 @@ int dr_backward(dr_ctx* c, const double* dV_dlo, const double* dV_dhi, float* da
     }
     if (!c->dgshift) TRY(dev_alloc(c, c->dgshift, nw));
     c->gshift_valid = false;
+    c->gtheta_valid = false;
     TRY(run_forward(c, mode, nullptr, true));
-    TRY(launch_backward(c, mode, wlo, whi, c->dgalpha, c->dgbeta, c->dgshift));
+    TRY(launch_backward(c, mode, wlo, whi, c->dgalpha, c->dgbeta, c->dgshift, c->opt.weight_grad != 0));
     c->gshift_valid = true;
+    c->gtheta_valid = c->opt.weight_grad != 0;
     const size_t na = (size_t)c->D * c->H * c->net.hidden;
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (dalpha && na) CUDA_TRY(c, cudaMemcpyAsync(dalpha, c->dgalpha, sizeof(float) * na, k, c->stream));
@@ -2220,6 +2282,19 @@ int dr_get_shift_gradient(dr_ctx* c, double* g, int on_device) {
     const size_t cnt = (size_t)c->D * (c->H + 1) * c->net.n;
     CUDA_TRY(c, cudaMemcpyAsync(g, c->dgshift, sizeof(double) * cnt, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                 c->stream));
+    if (!on_device) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return DR_OK;
+}
+
+int dr_get_weight_gradient(dr_ctx* c, double* dW, double* db, int on_device) {
+    if (!c || (!dW && !db)) return fail(c, DR_ERR_ARG, "dr_get_weight_gradient: NULL");
+    if (!c->gtheta_valid || !c->dgtheta)
+        return fail(c, DR_ERR_STATE, "no dr_backward with dr_options.weight_grad = 1 since the problem changed");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const int64_t nW = theta_weights(c->net), nb = theta_biases(c->net);
+    if (dW) CUDA_TRY(c, cudaMemcpyAsync(dW, c->dgtheta, sizeof(double) * nW, k, c->stream));
+    if (db) CUDA_TRY(c, cudaMemcpyAsync(db, c->dgtheta + nW, sizeof(double) * nb, k, c->stream));
     if (!on_device) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return DR_OK;
 }

@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused_backward(const FusedArgs a) {
             }
             float* gLprev = SMF(Y.gL0);  // adjoint of Lambda^(0) = Lambda_x
             const int xld = odd_ld(n);
-            if (ell > 1) {
+            if (ell > 1 || a.gth) {
                 for (int idx = tid; idx < rows * n; idx += NT) {
                     const int i = idx / n, j = idx - i * n;
                     const float x = cur[i * ld + j];
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused_backward(const FusedArgs a) {
                             const float x = Lm[i * lmld + j];
                             acc_s = fmaf(gls, x, acc_s);
                             acc_d += gkhi[i] * posf(x) + gklo[i] * negf(x);
-                            if (mm < ell - 1)
+                            if (mm < ell - 1 || a.gth)
                                 gLnext[i * lmld + j] = gls * sl[j] + gkhi[i] * (x > 0.f ? dl[j] : 0.f) + gklo[i] * (x < 0.f ? dl[j] : 0.f);
                         }
                         gs[N.hoff[mm] + j] += acc_s;
@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused_backward(const FusedArgs a) {
                                     const float x = Lm[i * lmld + j];
                                     acc_s[q] = fmaf(g[r][q], x, acc_s[q]);
                                     acc_d[q] += gkhi[i] * posf(x) + gklo[i] * negf(x);
-                                    if (mm < ell - 1)
+                                    if (mm < ell - 1 || a.gth)
                                         gLnext[i * lmld + j] = g[r][q] * sl[j] + gkhi[i] * (x > 0.f ? dl[j] : 0.f) +
                                                                gklo[i] * (x < 0.f ? dl[j] : 0.f);
                                 }
@@ -462,17 +462,50 @@ __global__ void __launch_bounds__(NT, 2) k_fused_backward(const FusedArgs a) {
                         const float x = Lm[i * lmld + j];
                         acc_s = fmaf(gls, x, acc_s);
                         acc_d += gkhi[i] * posf(x) + gklo[i] * negf(x);
-                        if (mm < ell - 1) {
+                        if (mm < ell - 1 || a.gth) {
                             gLnext[i * lmld + j] = gls * sl[j] + gkhi[i] * (x > 0.f ? dl[j] : 0.f) + gklo[i] * (x < 0.f ? dl[j] : 0.f);
                         }
                     }
                     gs[N.hoff[mm] + j] += acc_s;
                     gd[N.hoff[mm] + j] += acc_d;
                 }
+                if (a.gth) {
+                    // dV/dW_mm += (Lambda diag(s_mm))^T gLprev and dV/db_mm += (Lambda diag(s_mm))^T (gklo + gkhi):
+                    // the level's product Lambda_s W_mm and its intercept Lambda_s b_mm
+                    float* th = a.gth + (int64_t)blockIdx.x * a.gth_stride;
+                    float* gWm = th + N.Woff[mm - 1];
+                    for (int e = tid; e < K * NN; e += NT) {
+                        const int j = e / NN, k = e - j * NN;
+                        const float sj = sl[j];
+                        if (sj == 0.f) continue;
+                        float acc = 0.f;
+                        for (int i = 0; i < rows; ++i) acc = fmaf(Lm[i * lmld + j], gLprev[i * prev_ld + k], acc);
+                        gWm[e] += sj * acc;
+                    }
+                    float* gbm = th + a.gth_boff + N.boff[mm - 1];
+                    for (int j = tid; j < K; j += NT) {
+                        float acc = 0.f;
+                        for (int i = 0; i < rows; ++i) acc = fmaf(Lm[i * lmld + j], gklo[i] + gkhi[i], acc);
+                        gbm[j] += sl[j] * acc;
+                    }
+                }
                 __syncthreads();
                 gLprev = gLnext;
                 prev_ld = lmld;
                 buf ^= 1;
+            }
+            if (a.gth) {
+                // the target's own layer: Lambda starts as W_ell (its adjoint is now gLprev) and kappa as b_ell
+                float* th = a.gth + (int64_t)blockIdx.x * a.gth_stride;
+                float* gWl = th + N.Woff[ell - 1];
+                const int cols = N.w[ell - 1];
+                for (int e = tid; e < rows * cols; e += NT) {
+                    const int i = e / cols, j = e - i * cols;
+                    gWl[e] += gLprev[i * prev_ld + j];
+                }
+                float* gbl = th + a.gth_boff + N.boff[ell - 1];
+                for (int i = tid; i < rows; i += NT) gbl[i] += gklo[i] + gkhi[i];
+                __syncthreads();
             }
         }
         // ---- TM_t adjoint becomes the incoming adjoint of the previous step
@@ -512,7 +545,6 @@ __global__ void k_pgd(float* __restrict__ x, const float* __restrict__ g, int64_
         x[i] = fminf(fmaxf(x[i] - lr * g[i], lo), hi);
 }
 
-// Sum of D values into out[0] (single block, deterministic order per thread then tree).
 // Sum of v[0..D) into hist[*slot], then *slot += 1: the slot index lives on the device, so one
 // captured refinement step (CUDA graph) writes the next history entry on every replay.
 __global__ void k_sum_hist(const double* __restrict__ v, int64_t D, double* __restrict__ hist, int* __restrict__ slot) {
@@ -532,6 +564,7 @@ __global__ void k_sum_hist(const double* __restrict__ v, int64_t D, double* __re
     }
 }
 
+// Sum of D values into out[0] (single block, deterministic order per thread then tree).
 __global__ void k_sum(const double* __restrict__ v, int64_t D, double* __restrict__ out) {
     __shared__ double red[256];
     double acc = 0.0;
@@ -543,4 +576,25 @@ __global__ void k_sum(const double* __restrict__ v, int64_t D, double* __restric
         __syncthreads();
     }
     if (threadIdx.x == 0) out[0] = red[0];
+}
+
+// Weight gradient, first half of the reduction over the per-domain slices: part[g][e] = sum of
+// slice[s][e] over s = g, g + G, ... (G = gridDim.y).  Threads of a warp read consecutive e of one
+// slice; the fixed order makes the sum deterministic.
+__global__ void k_theta_partial(const float* __restrict__ slices, int64_t nslices, int64_t stride, int64_t count,
+                                double* __restrict__ part) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    double acc = 0.0;
+    for (int64_t s = blockIdx.y; s < nslices; s += gridDim.y) acc += (double)slices[s * stride + e];
+    part[(int64_t)blockIdx.y * count + e] = acc;
+}
+
+// Second half: out[e] += sum over the G partial sums (out accumulates over the backward chunks).
+__global__ void k_theta_finish(const double* __restrict__ part, int groups, int64_t count, double* __restrict__ out) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    double acc = 0.0;
+    for (int g = 0; g < groups; ++g) acc += part[(int64_t)g * count + e];
+    out[e] += acc;
 }

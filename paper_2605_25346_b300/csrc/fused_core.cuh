@@ -77,6 +77,11 @@ struct FusedArgs {
     const double* whi;  // [D][H+1][n] upstream gradient of hi (null: +1 on steps 1..H)
     float* dalpha;      // [D][H][hidden] or null
     float* dbeta;       // [nnz] or null
+    // weight gradient: per-CTA slices gth + blockIdx.x * gth_stride of dV/dW (packed as NetDesc::Woff)
+    // followed at gth_boff by dV/db (packed as NetDesc::boff), accumulated by the CTA; null = off
+    float* gth;
+    int64_t gth_stride;
+    int64_t gth_boff;
 };
 
 #define SMF(off) reinterpret_cast<float*>(sm + (off))

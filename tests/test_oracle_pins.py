@@ -519,3 +519,28 @@ def test_shift_gradient_matches_finite_differences():
     an = flat.numpy()[coords]
     assert np.abs(an).max() > 0
     np.testing.assert_allclose(fd, an, rtol=1e-5, atol=1e-6 * np.abs(an).max())
+
+
+def test_weight_gradient_matches_finite_differences():
+    # dV/dtheta of the controller (certified training, Sec. V-A) at fixed interior slopes
+    p = wl.random_problem(47, [3, 8, 8, 2], D=3, H=3, eps=0.3)
+    alpha = _interior_alpha(p, 4)
+    _, gW, gb = orc.value_and_weight_grad(p, alpha)
+    rng = np.random.default_rng(1)
+    h = 1e-6
+    checked = 0
+    for layer in range(p.L):
+        for which, grads, arrays in (("W", gW, p.W), ("b", gb, p.b)):
+            flat = grads[layer].reshape(-1).numpy()
+            for idx in rng.choice(flat.size, size=min(4, flat.size), replace=False):
+                vals = []
+                for sg in (1.0, -1.0):
+                    Ws = [torch.as_tensor(w).clone() for w in p.W]
+                    bs = [torch.as_tensor(x).clone() for x in p.b]
+                    tgt = Ws if which == "W" else bs
+                    tgt[layer].view(-1)[idx] += sg * h
+                    vals.append(float(orc.reach(p, alpha=alpha, mode=orc.MODE_USER, params=(Ws, bs))["V"].sum()))
+                fd = (vals[0] - vals[1]) / (2 * h)
+                assert abs(fd - flat[idx]) <= 1e-5 * max(1.0, abs(flat[idx])), (layer, which, idx, fd, flat[idx])
+                checked += 1
+    assert checked >= 10 and max(float(g.abs().max()) for g in gW) > 0
