@@ -133,7 +133,16 @@ typedef struct dr_options {
                               more product per chain level in the reverse sweep and a per-domain
                               slice of the parameters (at most 512 MiB, the sweep runs in chunks of
                               domains).  0 (default) = off                                        */
-    int32_t reserved[1];
+    int32_t reverse;       /* engine of the reverse sweep (dr_backward, dr_optimize_slopes) for controllers
+                              too wide for the fused kernels' shared memory: 0 (default) = staged: the
+                              forward pass of a chunk of domains keeps every step's chain levels,
+                              bounds and Taylor models in device memory (chunks sized to a memory
+                              budget), and the reverse chain products run on the tensor cores (3xTF32;
+                              targets of width not a multiple of 32, and DR_PREC_SIMT, on CUDA cores);
+                              1 = the fused kernels (out of per-domain global-memory slabs for wide
+                              controllers, levels recomputed per step); 2 = the staged sweep for any
+                              controller width.  The weight gradient always uses the fused kernels;
+                              under 0, narrow controllers use them too.                           */
 } dr_options;
 
 /* Paper: no passage; the engine of Sec. IV runs batched on a single GPU (Sec. VI), and a context
@@ -342,6 +351,8 @@ int64_t dr_kernel_launches(const dr_ctx* ctx);
 #define DR_KT_GEMM_CHAIN 1 /* persistent chain-level GEMM, next left operand formed in the epilogue     */
 #define DR_KT_GEMM_FINAL 2 /* persistent GEMM whose epilogue also multiplies by W_1 (last chain level) */
 #define DR_KT_GEMM_OTHER 3 /* the remaining GEMMs (one tile per CTA; target-2 products)                */
+#define DR_KT_GEMM_REVERSE 4 /* persistent reverse chain-level GEMM of the staged reverse sweep: adjoint
+                                times W_m^T, slope/intercept column sums and the next adjoint operand */
 /* Totals over the launches of class `which` with at least `min_rows` rows R (stacked Lambda rows, the
  * M dimension) timed since timing was switched on by dr_set_options (options.timing = 1):
  * *launches, *ms (sum of the per-launch CUDA-event durations, each measured on the stream the launch

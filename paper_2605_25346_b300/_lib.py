@@ -15,7 +15,7 @@ DR_F32, DR_F64 = 0, 1
 DR_SLOPE_ADAPTIVE, DR_SLOPE_CHORD, DR_SLOPE_ZERO, DR_SLOPE_USER = 0, 1, 2, 3
 DR_PREC_AUTO, DR_PREC_SIMT, DR_PREC_TF32X3 = 0, 1, 2
 DR_STATUS_NONFINITE, DR_STATUS_INFEASIBLE, DR_STATUS_MARGIN = 1, 2, 4
-DR_KT_GEMM_ALL, DR_KT_GEMM_CHAIN, DR_KT_GEMM_FINAL, DR_KT_GEMM_OTHER = 0, 1, 2, 3
+DR_KT_GEMM_ALL, DR_KT_GEMM_CHAIN, DR_KT_GEMM_FINAL, DR_KT_GEMM_OTHER, DR_KT_GEMM_REVERSE = 0, 1, 2, 3, 4
 
 # every symbol the header declares
 EXPORTS = [
@@ -43,7 +43,7 @@ class dr_options(ctypes.Structure):
                 ("chunk_domains", ctypes.c_int64), ("mem_cap_bytes", ctypes.c_int64),
                 ("box_margin", ctypes.c_double), ("tuning", ctypes.c_int32),
                 ("graphs", ctypes.c_int32), ("timing", ctypes.c_int32), ("rigorous", ctypes.c_int32),
-                ("weight_grad", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("weight_grad", ctypes.c_int32), ("reverse", ctypes.c_int32)]
 
 
 _lib = None

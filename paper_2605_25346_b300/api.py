@@ -55,9 +55,10 @@ class Reach:
     # ---- problem upload -------------------------------------------------------------------
     def set_options(self, mode: Optional[int] = None, precision: int = _lib.DR_PREC_AUTO, rho: Optional[float] = None,
                     chunk: int = 0, mem_cap: int = 0, box_margin: Optional[float] = None, tuning: int = 0,
-                    graphs: int = 0, timing: int = 0, rigorous: int = 0, weight_grad: int = 0):
+                    graphs: int = 0, timing: int = 0, rigorous: int = 0, weight_grad: int = 0, reverse: int = 0):
         o = _lib.dr_options()
         o.weight_grad = weight_grad
+        o.reverse = reverse
         o.tuning = tuning
         o.graphs = graphs
         o.timing = timing

@@ -21,6 +21,7 @@
 #include "tc_gemm.cuh"
 #include "tc_gemm_persistent.cuh"
 #include "wide.cuh"
+#include "wide_bwd.cuh"
 
 
 struct dr_ctx {
@@ -90,6 +91,15 @@ struct dr_ctx {
     // W_2 and [W_2^+; W_2^-] as blocked TF32 parts (left operands of the target-2 GEMMs), rows
     // padded to 128, K = ru32(n_1); null for a one-layer controller
     float *dA2h = nullptr, *dA2l = nullptr, *dA2ph = nullptr, *dA2pl = nullptr;
+    // for the staged reverse sweep: every layer W_l as TF32 parts [n_l][ru32(n_{l-1})] (right operand
+    // of the reverse chain GEMMs) and in the kept-level layout (lev_index, the shared top level)
+    float *dWRh = nullptr, *dWRl = nullptr, *dWlev = nullptr;
+    int64_t WRoff[DR_MAXL] = {}, WLoff[DR_MAXL] = {};
+    // staged reverse sweep: keep store and adjoint scratch of one chunk, split values h
+    void* kscratch = nullptr;
+    size_t kscratch_bytes = 0;
+    float* dsph = nullptr;
+    int64_t sph_n = 0;
     int* derr = nullptr;
     // per-CTA global slabs for the fused kernels on wide controllers (tape runs), and the one padded
     // weight copy they share
@@ -680,7 +690,7 @@ static int tc_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* BTh
     int bn_dummy = 0;
     if (!bn_used) bn_used = &bn_dummy;
     int variant = kGemmHeuristic;
-    if (c && c->opt.tuning == 0) TRY(tuned_gemm(c, Ah, Al, BTh, BTl, C, R, K, N, ldk, ldc, err, st, epi, &variant));
+    if (c && c->opt.tuning == 0 && !(epi && epi->colpart)) TRY(tuned_gemm(c, Ah, Al, BTh, BTl, C, R, K, N, ldk, ldc, err, st, epi, &variant));
     if (c && c->opt.tuning >= 100) variant = c->opt.tuning - 100;  // forced launch shape
     const bool timed = c && c->opt.timing && !c->capturing;
     cudaEvent_t e0 = timed ? kt_event(c) : nullptr, e1 = timed ? kt_event(c) : nullptr;
@@ -705,14 +715,19 @@ static int tc_gemm_launch(dr_ctx* c, const float* Ah, const float* Al, const flo
                           int K, int N, int ldk, int ldc, int* err, cudaStream_t st, const tc::ChainEpi* epi, int* cls,
                           int variant, int* bn_used) {
     TRY(get_encoder(c));
-    const int BN = variant == kGemmTile64 ? 64 : variant == kGemmTile32 ? 32 : variant >= kGemmPersistent ? 128 : tc_bn(N);
+    // the reverse chain level runs only on the persistent kernel, whose stages hold 128-row B boxes
+    const int BN = (epi && epi->colpart) ? 128
+                   : variant == kGemmTile64 ? 64 : variant == kGemmTile32 ? 32 : variant >= kGemmPersistent ? 128 : tc_bn(N);
     *bn_used = BN;
     CUtensorMap m[6];
     TRY(make_map_blocked(c, &m[0], Ah, R, ldk));
     TRY(make_map_blocked(c, &m[1], Al, R, ldk));
     TRY(make_map(c, &m[2], BTh, N, ldk, BN));
     TRY(make_map(c, &m[3], BTl, N, ldk, BN));
-    if (epi && !epi->W1) {
+    if (epi && epi->colpart) {
+        m[4] = m[0];
+        m[5] = m[1];
+    } else if (epi && !epi->W1) {
         // the chain epilogue stores the next left operand (blocked, epi->ldk columns) by TMA
         TRY(make_map_blocked(c, &m[4], epi->Ah, R, epi->ldk));
         TRY(make_map_blocked(c, &m[5], epi->Al, R, epi->ldk));
@@ -724,6 +739,15 @@ static int tc_gemm_launch(dr_ctx* c, const float* Ah, const float* Al, const flo
     if (epi) e = *epi;
     if (epi && epi->W1 && (BN < 32 || epi->n0 > tc::kFinalCols))
         return fail(c, DR_ERR_SHAPE, "fused final chain level needs >= 32 columns and n <= %d", tc::kFinalCols);
+    if (epi && epi->colpart) {
+        // reverse chain level: the persistent kernel's reverse epilogue (the only launch shape)
+        if (!persistent_gemm_usable<3>()) return fail(c, DR_ERR_STATE, "the reverse chain GEMM is unavailable in this build");
+        const int64_t tiles = ((int64_t)(R + tc::BM - 1) / tc::BM) * ((N + 127) / 128);
+        if (tiles > 0x7fffffffll) return fail(c, DR_ERR_SHAPE, "too many tiles for one reverse GEMM");
+        *bn_used = 128;
+        *cls = DR_KT_GEMM_REVERSE;
+        return launch_tc_gemm_persistent<3>(c, m, C, R, K, N, ldc, err, st, e, tiles, sm_count());
+    }
     if (BN == 128 && variant != kGemmTile128) {
         const int nsm = sm_count();
         const int64_t tiles = ((int64_t)(R + tc::BM - 1) / tc::BM) * ((N + 127) / 128);
@@ -970,6 +994,9 @@ static void free_outputs(dr_ctx* c) {
     dev_free(c, (void*&)c->gslab, c->gslab_bytes);
     c->gslab_bytes = 0;
     dev_free(c, (void*&)c->dWpad, 0);
+    dev_free(c, c->kscratch, c->kscratch_bytes);
+    c->kscratch_bytes = 0;
+    dev_free(c, (void*&)c->dsph, 0);
     c->wDc = 0;
     c->out_bytes = 0;
     c->tape_bytes = 0;
@@ -999,6 +1026,9 @@ void dr_destroy(dr_ctx* c) {
     cudaFree(c->dA2l);
     cudaFree(c->dA2ph);
     cudaFree(c->dA2pl);
+    cudaFree(c->dWRh);
+    cudaFree(c->dWRl);
+    cudaFree(c->dWlev);
     cudaFree(c->derr);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     for (int l = 0; l < dr_ctx::kMaxLanes; ++l) {
@@ -1047,6 +1077,7 @@ int dr_set_options(dr_ctx* c, const dr_options* o) {
     if (n.timing < 0 || n.timing > 1) return fail(c, DR_ERR_ARG, "timing %d out of range", n.timing);
     if (n.rigorous < 0 || n.rigorous > 1) return fail(c, DR_ERR_ARG, "rigorous %d out of range", n.rigorous);
     if (n.weight_grad < 0 || n.weight_grad > 1) return fail(c, DR_ERR_ARG, "weight_grad %d out of range", n.weight_grad);
+    if (n.reverse < 0 || n.reverse > 2) return fail(c, DR_ERR_ARG, "reverse %d out of range", n.reverse);
     if (n.tuning < 0 || (n.tuning >= 2 + kNumMultiVariants && (n.tuning < 101 || n.tuning > 104)))
         return fail(c, DR_ERR_ARG, "tuning %d out of range", n.tuning);
     if (n.timing && !c->opt.timing) c->kt_done.clear();  // timing switched on: the totals start from zero
@@ -1077,7 +1108,7 @@ static int kt_drain(dr_ctx* c) {
 
 int dr_kernel_timing(dr_ctx* c, int which, int64_t min_rows, int64_t* launches, double* ms, double* flop) {
     if (!c) return DR_ERR_ARG;
-    if (which < DR_KT_GEMM_ALL || which > DR_KT_GEMM_OTHER) return fail(c, DR_ERR_ARG, "timing class %d", which);
+    if (which < DR_KT_GEMM_ALL || which > DR_KT_GEMM_REVERSE) return fail(c, DR_ERR_ARG, "timing class %d", which);
     CUDA_TRY(c, cudaSetDevice(c->device));
     TRY(kt_drain(c));
     int64_t n = 0;
@@ -1217,6 +1248,39 @@ int dr_load_controller(dr_ctx* c, int L, const int32_t* widths, const void* cons
             CUDA_TRY(c, cudaMemcpyAsync(c->dA2l, a2l.data(), a2l.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
             CUDA_TRY(c, cudaMemcpyAsync(c->dA2ph, a2ph.data(), a2ph.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
             CUDA_TRY(c, cudaMemcpyAsync(c->dA2pl, a2pl.data(), a2pl.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        }
+        {
+            // reverse-sweep copies: W_l row-major with K = n_{l-1} padded to 32 (TF32 parts), and W_l in
+            // the kept-level layout (rows padded to 32)
+            int64_t rt = 0, lt = 0;
+            for (int l = 0; l < L; ++l) {
+                c->WRoff[l] = rt;
+                c->WLoff[l] = lt;
+                rt += (int64_t)widths[l + 1] * ((widths[l] + 31) & ~31);
+                lt += (int64_t)((widths[l + 1] + 31) & ~31) * widths[l];
+            }
+            std::vector<float> rh(rt, 0.f), rl(rt, 0.f), lv(lt, 0.f);
+            for (int l = 0; l < L; ++l) {
+                const int rows = widths[l + 1], K = widths[l], ldk = (K + 31) & ~31;
+                for (int i = 0; i < rows; ++i)
+                    for (int k = 0; k < K; ++k) {
+                        const float x = hw[N.Woff[l] + (int64_t)i * K + k];
+                        const float h = tf32(x);
+                        rh[c->WRoff[l] + (int64_t)i * ldk + k] = h;
+                        rl[c->WRoff[l] + (int64_t)i * ldk + k] = tf32(x - h);
+                        lv[c->WLoff[l] + lev_index(i, k, K)] = x;
+                    }
+            }
+            dev_free(c, (void*&)c->dWRh, 0);
+            dev_free(c, (void*&)c->dWRl, 0);
+            dev_free(c, (void*&)c->dWlev, 0);
+            TRY(dev_alloc(c, c->dWRh, rt));
+            TRY(dev_alloc(c, c->dWRl, rt));
+            TRY(dev_alloc(c, c->dWlev, lt));
+            CUDA_TRY(c, cudaMemcpyAsync(c->dWRh, rh.data(), rt * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+            CUDA_TRY(c, cudaMemcpyAsync(c->dWRl, rl.data(), rt * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+            CUDA_TRY(c, cudaMemcpyAsync(c->dWlev, lv.data(), lt * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+            CUDA_TRY(c, cudaStreamSynchronize(c->stream));
         }
         if (!c->derr) TRY(dev_alloc(c, c->derr, 1));
         CUDA_TRY(c, cudaMemcpyAsync(c->dWTh, th.data(), tot * sizeof(float), cudaMemcpyHostToDevice, c->stream));
@@ -1624,8 +1688,18 @@ struct WideLane {
     bool active;
 };
 
+// Keep mode of the staged forward pass: where one step's chain levels go.  Level Lambda^(m) of target
+// ell (m = 1 .. ell-2, the levels a chain GEMM produces) sits at base + off[ell][m] in the lev_index
+// layout over the chunk's stacked rows with n_m columns.
+struct KeepLevels {
+    float* base;
+    int64_t off[DR_MAXL + 1][DR_MAXL + 1];
+};
+
 // Every kernel of time step t of one lane's chunk (layers, chain, concretisation, relaxation, dynamics).
-static int wide_step(dr_ctx* c, WideLane& w, int t, bool tcore) {
+// With kl set (keep mode; w.a's keep fields set by the caller) the step also keeps what the staged
+// reverse sweep reads.
+static int wide_step(dr_ctx* c, WideLane& w, int t, bool tcore, const KeepLevels* kl = nullptr) {
     const NetDesc& N = w.a.net;
     const int n = N.n, L = N.L;
     WideArgs& a = w.a;
@@ -1639,12 +1713,15 @@ static int wide_step(dr_ctx* c, WideLane& w, int t, bool tcore) {
         k_r_q<<<blocks_for((int64_t)dc * N.w[1] * 32, 256), 256, 0, st>>>(a, 1);
         c->launches++;
     }
+    auto levp = [&](int ell, int mm) -> float* { return kl ? kl->base + kl->off[ell][mm] : nullptr; };
     for (int ell = 1; ell <= L; ++ell) {
         const int rows = N.w[ell];
         const int64_t warps = (int64_t)dc * rows;
+        WideArgs ap = a;  // the projection's copy: keep-mode row offset of this target
+        ap.koff = ell < L ? N.hoff[ell] : N.hidden;
         if (tcore && ell == 1) {
             // layer 1: Lambda_x = W_1, shared by every domain
-            launch_t_project(c, a, 1, c->dW + N.Woff[0], 1, (int64_t)dc * rows, 0, st);
+            launch_t_project(c, ap, 1, c->dW + N.Woff[0], 1, (int64_t)dc * rows, 0, st);
         } else if (!tcore || ell == 1) {
             k_w_chain_init<<<blocks_for(warps * 32, 256), 256, 0, st>>>(a, ell, lamA);
             c->launches++;
@@ -1657,13 +1734,13 @@ static int wide_step(dr_ctx* c, WideLane& w, int t, bool tcore) {
                 k_w_gemm_simt<<<grid, 256, 0, st>>>(cur, Wm, nxt, rows, K, NN, a.lam_stride);
                 c->launches++;
                 if (mm - 1 >= 1) {
-                    k_w_level_epi<<<blocks_for(warps * 32, 256), 256, 0, st>>>(a, ell, mm - 1, nxt);
+                    k_w_level_epi<<<blocks_for(warps * 32, 256), 256, 0, st>>>(a, ell, mm - 1, nxt, levp(ell, mm - 1));
                     c->launches++;
                 }
                 std::swap(cur, nxt);
             }
-            if (ell == 1) k_w_project<<<blocks_for(warps * 32, 256), 256, 0, st>>>(a, 1, c->dW + N.Woff[0], 1);
-            else k_w_project<<<blocks_for(warps * 32, 256), 256, 0, st>>>(a, ell, cur, 0);
+            if (ell == 1) k_w_project<<<blocks_for(warps * 32, 256), 256, 0, st>>>(ap, 1, c->dW + N.Woff[0], 1);
+            else k_w_project<<<blocks_for(warps * 32, 256), 256, 0, st>>>(ap, ell, cur, 0);
             c->launches++;
         } else {
             // tensor-core chain: rows of all domains stacked, A as TF32 parts, shared W^T parts;
@@ -1680,7 +1757,7 @@ static int wide_step(dr_ctx* c, WideLane& w, int t, bool tcore) {
                 TRY(tc_gemm(c, c->dA2ph, c->dA2pl, w.t2.Dh, w.t2.Dl, w.t2.C2, 2 * rows, N.w[1], dc, ldk1, dc, c->derr, st));
                 k_t2_finish<<<blocks_for((int64_t)R, 256), 256, 0, st>>>(a, w.t2.C1, w.t2.C2, lamC);
                 c->launches++;
-                launch_t_project(c, a, ell, lamC, 0, R, 0, st);
+                launch_t_project(c, ap, ell, lamC, 0, R, 0, st);
             } else {
                 int ldk = round_up32(N.w[ell - 1]);
                 k_t_chain_init<<<blocks_for(warps * 32, 256), 256, 0, st>>>(a, ell, lamA, lamB, ldk);
@@ -1704,6 +1781,7 @@ static int wide_step(dr_ctx* c, WideLane& w, int t, bool tcore) {
                         epi.Al = nxtl;
                         epi.ldk = round_up32(NN);
                         epi.part = part;
+                        epi.lev = levp(ell, mm - 1);
                         if (fin) {
                             epi.W1 = c->dW + N.Woff[0];
                             epi.n0 = N.n;
@@ -1727,7 +1805,7 @@ static int wide_step(dr_ctx* c, WideLane& w, int t, bool tcore) {
                         TRY(tc_gemm(c, curh, curl, WTh, WTl, nxth, R, K, NN, ldk, NN, c->derr, st));
                     }
                 }
-                launch_t_project(c, a, ell, lx_parts ? lxpart : nxth, 0, R, lx_parts, st, part, fin_tiles);
+                launch_t_project(c, ap, ell, lx_parts ? lxpart : nxth, 0, R, lx_parts, st, part, fin_tiles);
             }
         }
         if (ell < L) {
@@ -2212,6 +2290,396 @@ static int launch_backward(dr_ctx* c, int mode, const double* wlo, const double*
     return DR_OK;
 }
 
+// ------------------------------------------------------------------------------------------------
+// staged reverse sweep (wide controllers): keep-mode forward pass of a chunk, then the reverse
+// ------------------------------------------------------------------------------------------------
+
+// The keep store (one slot per step) and the adjoint scratch of one chunk of Dc domains, carved from
+// one allocation.  With base == nullptr only the size is computed.
+struct RevStore {
+    // keep slots: array x at x + t * sx
+    float *Pf, *cf, *Ilof, *Ihif, *vsnap, *hl, *hu, *hs, *hd, *hl0, *hu0, *Gk, *LXk, *lev;
+    int64_t sPf, sn, svs, shid, sG, slev;
+    KeepLevels kl;  // level offsets inside a slot (base unset)
+    double* tape;   // [Dc][H+1][ts]
+    // adjoint state
+    double *gcn, *gPn, *gIlon, *gIhin, *gv, *gw;  // carried across steps (contiguous, zeroed per chunk)
+    size_t carried_bytes;
+    double *gc, *gP, *gIlo, *gIhi, *gcu, *gPu, *gIulo, *gIuhi;
+    float *gs, *gd, *ga, *gklo, *gkhi, *gRlo, *gRhi, *gG, *gLx, *gLxh, *gLxl, *gLa, *gLb, *colpart;
+    float *Lh[2], *Ll[2];
+    int ldw;
+};
+
+// Shared memory limit of the few-rows CUDA-core chain reverse (k_rv_chain_rows).
+constexpr size_t kRevRowsSmem = 96 * 1024;
+
+// Targets whose chain reverse runs on the tensor cores: the reverse epilogue sums columns over row
+// segments inside one domain, 32 rows each or a whole domain of 2, 4, 8 or 16 rows.
+static bool rev_tc_rows(int rows) { return rows % 32 == 0 || (rows >= 2 && rows < 32 && (rows & (rows - 1)) == 0); }
+
+// Row count of the widest target whose chain reverse runs on CUDA cores (0 if none).
+static int rev_simt_rows(const NetDesc& N, bool tc_rev) {
+    int r = 0;
+    for (int ell = 2; ell <= N.L; ++ell)
+        if (!tc_rev || !rev_tc_rows(N.w[ell])) r = std::max(r, N.w[ell]);
+    return r;
+}
+
+static size_t rev_store(const NetDesc& N, int Dc, bool tc_rev, RevStore* S, unsigned char* base) {
+    const int n = N.n, m = N.m, L = N.L, H = N.H;
+    const int64_t D = Dc, hid = std::max(N.hidden, 1), krows = N.hidden + m;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void* {
+        off = (off + 255) & ~size_t(255);
+        void* r = base ? base + off : nullptr;
+        off += bytes;
+        return r;
+    };
+    S->sPf = D * n * n;
+    S->sn = D * n;
+    S->svs = D * L * (n + 1);
+    S->shid = D * hid;
+    S->sG = D * krows * n;
+    int64_t lt = 0;
+    for (int ell = 0; ell <= DR_MAXL; ++ell)
+        for (int mm = 0; mm <= DR_MAXL; ++mm) S->kl.off[ell][mm] = 0;
+    for (int ell = 3; ell <= L; ++ell)
+        for (int mm = 1; mm <= ell - 2; ++mm) {
+            S->kl.off[ell][mm] = lt;
+            lt += (((D * N.w[ell]) + 31) & ~int64_t(31)) * N.w[mm];
+        }
+    S->slev = std::max<int64_t>(lt, 1);
+    S->kl.base = nullptr;
+    const size_t f = sizeof(float);
+    S->Pf = (float*)take(f * H * S->sPf);
+    S->cf = (float*)take(f * H * S->sn);
+    S->Ilof = (float*)take(f * H * S->sn);
+    S->Ihif = (float*)take(f * H * S->sn);
+    S->vsnap = (float*)take(f * H * S->svs);
+    S->hl = (float*)take(f * H * S->shid);
+    S->hu = (float*)take(f * H * S->shid);
+    S->hs = (float*)take(f * H * S->shid);
+    S->hd = (float*)take(f * H * S->shid);
+    S->hl0 = (float*)take(f * H * S->shid);
+    S->hu0 = (float*)take(f * H * S->shid);
+    S->Gk = (float*)take(f * H * S->sG);
+    S->LXk = (float*)take(f * H * S->sG);
+    S->lev = (float*)take(f * H * S->slev);
+    const int ts = tape_stride(N);
+    S->tape = (double*)take(sizeof(double) * D * (H + 1) * ts);
+    // carried adjoints: one contiguous block
+    off = (off + 255) & ~size_t(255);
+    const size_t c0 = off;
+    double* cb = (double*)(base ? base + off : nullptr);
+    off += sizeof(double) * D * (4 * n + n * n + n + 1);
+    S->carried_bytes = off - c0;
+    S->gcn = cb;
+    S->gPn = cb ? cb + D * n : nullptr;
+    S->gIlon = cb ? S->gPn + D * n * n : nullptr;
+    S->gIhin = cb ? S->gIlon + D * n : nullptr;
+    S->gv = cb ? S->gIhin + D * n : nullptr;
+    S->gw = cb ? S->gv + D * n : nullptr;
+    const size_t dd = sizeof(double);
+    S->gc = (double*)take(dd * D * n);
+    S->gP = (double*)take(dd * D * n * n);
+    S->gIlo = (double*)take(dd * D * n);
+    S->gIhi = (double*)take(dd * D * n);
+    S->gcu = (double*)take(dd * D * m);
+    S->gPu = (double*)take(dd * D * m * n);
+    S->gIulo = (double*)take(dd * D * m);
+    S->gIuhi = (double*)take(dd * D * m);
+    S->gs = (float*)take(f * D * hid);
+    S->gd = (float*)take(f * D * hid);
+    S->ga = (float*)take(f * D * N.maxw);
+    S->gklo = (float*)take(f * D * N.maxw);
+    S->gkhi = (float*)take(f * D * N.maxw);
+    S->gRlo = (float*)take(f * D * N.maxw);
+    S->gRhi = (float*)take(f * D * N.maxw);
+    S->gG = (float*)take(f * D * N.maxw * n);
+    S->gLx = (float*)take(f * D * N.maxw * n);
+    const int64_t rpad = ((D * N.maxw + tc::BM - 1) / tc::BM) * tc::BM;
+    const int ldkx = (n + 31) & ~31;
+    int ldkw = 32;
+    for (int l = 1; l < L; ++l) ldkw = std::max(ldkw, (N.w[l] + 31) & ~31);
+    S->gLxh = (float*)take(f * rpad * ldkx);
+    S->gLxl = (float*)take(f * rpad * ldkx);
+    for (int q = 0; q < 2; ++q) {
+        S->Lh[q] = (float*)take(f * rpad * ldkw);
+        S->Ll[q] = (float*)take(f * rpad * ldkw);
+    }
+    S->colpart = (float*)take(f * D * std::max(1, (N.maxw + 31) / 32) * 2 * N.maxw);  // [segments][2][n_m]
+    S->ldw = std::max(N.maxw, n);
+    const int sr = rev_simt_rows(N, tc_rev);
+    S->gLa = (float*)take(f * D * std::max(sr, 1) * S->ldw);
+    S->gLb = (float*)take(f * D * std::max(sr, 1) * S->ldw);
+    return off + 256;
+}
+
+// Domains per chunk of the staged reverse sweep: the keep store, the adjoint scratch and the forward
+// scratch of a chunk within min(48 GiB, half the free memory, the memory cap left), at least one.
+static int rev_chunk(dr_ctx* c, const NetDesc& N, bool tc_rev) {
+    if (c->opt.chunk_domains > 0) return (int)std::min<int64_t>(std::min<int64_t>(c->opt.chunk_domains, c->D), 65535);
+    if (c->capturing && c->wDc > 0) return c->wDc;  // a captured step repeats the plain step before it
+    RevStore S;
+    const size_t per = rev_store(N, 64, tc_rev, &S, nullptr) / 64 + wide_bytes_per_domain(N) + 4096;
+    size_t budget = size_t(48) << 30;
+    size_t free_b = 0, all_b = 0;
+    if (cudaMemGetInfo(&free_b, &all_b) == cudaSuccess) budget = std::min(budget, (free_b + c->kscratch_bytes + c->wscratch_bytes) / 2);
+    if (c->opt.mem_cap_bytes > 0)
+        budget = std::min(budget, (size_t)c->opt.mem_cap_bytes > c->owned ? (size_t)c->opt.mem_cap_bytes - c->owned : size_t(0));
+    const int64_t dmax = std::min<int64_t>(std::max<int64_t>(1, (int64_t)(budget / per)), 65535);
+    const int64_t k = (c->D + dmax - 1) / dmax;  // equal chunks
+    return (int)std::max<int64_t>(1, (c->D + k - 1) / k);
+}
+
+static bool use_staged_reverse(const dr_ctx* c, bool wgrad) {
+    NetDesc N = c->net;
+    N.H = c->H;
+    if (wgrad || c->opt.reverse == 1) return false;
+    return c->opt.reverse == 2 || fused_layout(N, true, false).total > kMaxSmem;
+}
+
+// Forward pass with the slopes of `mode` (outputs lo/hi/V/status as dr_compute_bounds writes them)
+// and the reverse sweep, chunk by chunk, for controllers too wide for the fused kernels.
+static int run_staged_backward(dr_ctx* c, int mode, const double* wlo, const double* whi, float* galpha, float* gbeta,
+                               double* gshift) {
+    NetDesc N = c->net;
+    N.H = c->H;
+    const int n = N.n, L = N.L, H = N.H;
+    if (c->D == 0) return DR_OK;
+    if (mode == DR_SLOPE_USER && !c->dalpha) return fail(c, DR_ERR_STATE, "no slopes set");
+    const bool tcore = c->opt.precision != DR_PREC_SIMT;
+    const bool tc_rev = tcore && persistent_gemm_usable<3>();
+    const int Dc = rev_chunk(c, N, tc_rev);
+    WideArgs a;
+    memset(&a, 0, sizeof(a));
+    a.net = N;
+    a.W = c->dW;
+    a.b = c->db;
+    a.A = c->dA;
+    a.B = c->dB;
+    a.e = c->de;
+    a.eoff = c->deoff;
+    a.lo0 = c->dlo0;
+    a.hi0 = c->dhi0;
+    a.sp_row = c->nnz ? c->dsp_row : nullptr;
+    a.sp = c->dsp;
+    a.beta = c->dbeta;
+    a.alpha = c->dalpha;
+    a.mode = mode;
+    a.rho = (float)c->opt.margin_rho;
+    a.box_margin = c->opt.box_margin;
+    a.lo = c->dout_lo;
+    a.hi = c->dout_hi;
+    a.V = c->dV;
+    a.status = c->dstatus;
+    WideLane w;
+    w.a = a;
+    TRY(wide_bind(c, w.a, Dc, 1, 0, &w.lamA, &w.lamB, &w.lamC, &w.lamD, &w.part, &w.lxpart, &w.t2));
+    w.st = c->stream;
+    RevStore S;
+    const size_t need = rev_store(N, Dc, tc_rev, &S, nullptr);
+    if (!c->kscratch || c->kscratch_bytes < need) {
+        dev_free(c, c->kscratch, c->kscratch_bytes);
+        c->kscratch_bytes = 0;
+        unsigned char* p = nullptr;
+        TRY(dev_alloc(c, p, need));
+        c->kscratch = p;
+        c->kscratch_bytes = need;
+    }
+    rev_store(N, Dc, tc_rev, &S, reinterpret_cast<unsigned char*>(c->kscratch));
+    if (c->nnz && (!c->dsph || c->sph_n != c->nnz)) {
+        dev_free(c, (void*&)c->dsph, 0);
+        TRY(dev_alloc(c, c->dsph, (size_t)c->nnz));
+        c->sph_n = c->nnz;
+    }
+    const cudaStream_t st = c->stream;
+    if (tcore) CUDA_TRY(c, cudaMemsetAsync(c->derr, 0, sizeof(int), st));
+    {
+        // the first reverse GEMM's left operand: its K padding columns (n .. 31) stay zero
+        const size_t gx = sizeof(float) * (size_t)(((int64_t)Dc * N.maxw + tc::BM - 1) / tc::BM * tc::BM) * round_up32(n);
+        CUDA_TRY(c, cudaMemsetAsync(S.gLxh, 0, gx, st));
+        CUDA_TRY(c, cudaMemsetAsync(S.gLxl, 0, gx, st));
+    }
+    const int krows = N.hidden + N.m;
+    RevArgs r;
+    memset(&r, 0, sizeof(r));
+    r.net = N;
+    r.W = c->dW;
+    r.b = c->db;
+    r.A = c->dA;
+    r.B = c->dB;
+    r.sp_row = a.sp_row;
+    r.sp = c->dsp;
+    r.beta = c->dbeta;
+    r.sph = c->dsph;
+    r.alpha = c->dalpha;
+    r.mode = mode;
+    r.wlo = wlo;
+    r.whi = whi;
+    r.dalpha = galpha;
+    r.dbeta = gbeta;
+    r.gshift = gshift;
+    r.tape = S.tape;
+    r.krows = krows;
+    r.gcn = S.gcn;
+    r.gPn = S.gPn;
+    r.gIlon = S.gIlon;
+    r.gIhin = S.gIhin;
+    r.gv = S.gv;
+    r.gw = S.gw;
+    r.gc = S.gc;
+    r.gP = S.gP;
+    r.gIlo = S.gIlo;
+    r.gIhi = S.gIhi;
+    r.gcu = S.gcu;
+    r.gPu = S.gPu;
+    r.gIulo = S.gIulo;
+    r.gIuhi = S.gIuhi;
+    r.gs = S.gs;
+    r.gd = S.gd;
+    r.ga = S.ga;
+    r.gklo = S.gklo;
+    r.gkhi = S.gkhi;
+    r.gRlo = S.gRlo;
+    r.gRhi = S.gRhi;
+    r.gG = S.gG;
+    r.gLa = S.gLa;
+    r.gLb = S.gLb;
+    r.ldw = S.ldw;
+    for (int64_t d0 = 0; d0 < c->D; d0 += Dc) {
+        const int nd = (int)std::min<int64_t>(Dc, c->D - d0);
+        w.a.d0 = d0;
+        w.a.Dc = nd;
+        k_w_seed<<<blocks_for((int64_t)nd * n, 256), 256, 0, st>>>(w.a);
+        c->launches++;
+        // ---- forward pass of the chunk, keeping every step
+        for (int t = 0; t < H; ++t) {
+            WideLane ws = w;
+            WideArgs& k = ws.a;
+            k.Pf = S.Pf + t * S.sPf;
+            k.cf = S.cf + t * S.sn;
+            k.Ilof = S.Ilof + t * S.sn;
+            k.Ihif = S.Ihif + t * S.sn;
+            k.hl = S.hl + t * S.shid;
+            k.hu = S.hu + t * S.shid;
+            k.hs = S.hs + t * S.shid;
+            k.hd = S.hd + t * S.shid;
+            k.hl0 = S.hl0 + t * S.shid;
+            k.hu0 = S.hu0 + t * S.shid;
+            k.vsnap = S.vsnap + t * S.svs;
+            k.Gk = S.Gk + t * S.sG;
+            k.LXk = S.LXk + t * S.sG;
+            k.krows = krows;
+            k.sph = c->dsph;
+            k.tape = S.tape;
+            KeepLevels kl = S.kl;
+            kl.base = S.lev + t * S.slev;
+            k_w_tape<<<nd, 128, 0, st>>>(k, t);
+            c->launches++;
+            TRY(wide_step(c, ws, t, tcore, &kl));
+        }
+        {
+            WideArgs k = w.a;
+            k.tape = S.tape;
+            k_w_tape<<<nd, 128, 0, st>>>(k, H);
+            c->launches++;
+        }
+        // ---- reverse sweep
+        CUDA_TRY(c, cudaMemsetAsync(S.gcn, 0, S.carried_bytes, st));
+        r.d0 = d0;
+        r.Dc = nd;
+        for (int t = H - 1; t >= 0; --t) {
+            r.Pf = S.Pf + t * S.sPf;
+            r.cf = S.cf + t * S.sn;
+            r.Ilof = S.Ilof + t * S.sn;
+            r.Ihif = S.Ihif + t * S.sn;
+            r.hl = S.hl + t * S.shid;
+            r.hu = S.hu + t * S.shid;
+            r.hs = S.hs + t * S.shid;
+            r.hd = S.hd + t * S.shid;
+            r.hl0 = S.hl0 + t * S.shid;
+            r.hu0 = S.hu0 + t * S.shid;
+            r.vsnap = S.vsnap + t * S.svs;
+            r.Gk = S.Gk + t * S.sG;
+            r.LXk = S.LXk + t * S.sG;
+            float* levt = S.lev + t * S.slev;
+            k_rv_dyn<<<nd, 128, 0, st>>>(r, t);
+            c->launches++;
+            for (int ell = L; ell >= 1; --ell) {
+                const int rows = N.w[ell];
+                const bool use_tc = tc_rev && ell >= 2 && rev_tc_rows(rows);
+                RevArgs rt = r;
+                rt.gLx = use_tc ? nullptr : S.gLx;
+                rt.gLxh = use_tc ? S.gLxh : nullptr;
+                rt.gLxl = use_tc ? S.gLxl : nullptr;
+                const size_t tsm = sizeof(float) * (size_t)rv_target_smem_floats(rows, n);
+                if (rv_items_per_thread(n) <= 2) {
+                    if (tsm > 48 * 1024) CUDA_TRY(c, cudaFuncSetAttribute(k_rv_target<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+                    k_rv_target<2><<<nd, 256, tsm, st>>>(rt, ell, t);
+                } else {
+                    if (tsm > 48 * 1024) CUDA_TRY(c, cudaFuncSetAttribute(k_rv_target<18>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+                    k_rv_target<18><<<nd, 256, tsm, st>>>(rt, ell, t);
+                }
+                c->launches++;
+                if (ell < 2) continue;
+                if (use_tc) {
+                    const int R = nd * rows;
+                    const float* Ah = S.gLxh;
+                    const float* Al = S.gLxl;
+                    int ldkA = round_up32(n);
+                    for (int mm = 1; mm <= ell - 1; ++mm) {
+                        const int Kc = N.w[mm - 1], Nc = N.w[mm];
+                        const bool top = mm == ell - 1;
+                        tc::ChainEpi e{};
+                        e.hs = r.hs;
+                        e.hd = r.hd;
+                        e.bias = c->db + N.boff[mm - 1];
+                        e.hidden = N.hidden;
+                        e.hoff = N.hoff[mm];
+                        e.rows_per_dom = rows;
+                        e.Ah = top ? nullptr : S.Lh[mm & 1];
+                        e.Al = top ? nullptr : S.Ll[mm & 1];
+                        e.ldk = round_up32(Nc);
+                        e.rklo = S.gklo;
+                        e.rkhi = S.gkhi;
+                        e.kld = N.maxw;
+                        e.rlev = top ? c->dWlev + c->WLoff[ell - 1] : levt + S.kl.off[ell][mm];
+                        e.rlev_shared = top ? 1 : 0;
+                        e.colpart = S.colpart;
+                        TRY(tc_gemm(c, Ah, Al, c->dWRh + c->WRoff[mm - 1], c->dWRl + c->WRoff[mm - 1], nullptr, R, Kc, Nc, ldkA,
+                                    0, c->derr, st, &e));
+                        k_rv_colsum<<<blocks_for((int64_t)nd * Nc, 256), 256, 0, st>>>(r, ell, mm, S.colpart);
+                        c->launches++;
+                        Ah = e.Ah;
+                        Al = e.Al;
+                        ldkA = e.ldk;
+                    }
+                } else {
+                    RevArgs rc = rt;
+                    for (int mm = 0; mm <= DR_MAXL; ++mm) rc.tlev[mm] = nullptr;
+                    for (int mm = 1; mm <= ell - 2; ++mm) rc.tlev[mm] = levt + S.kl.off[ell][mm];
+                    const size_t rsmem = sizeof(float) * 2 * (size_t)rows * S.ldw;
+                    if (rows <= 32 && rsmem <= kRevRowsSmem) {
+                        if (rsmem > 48 * 1024)
+                            CUDA_TRY(c, cudaFuncSetAttribute(k_rv_chain_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem));
+                        k_rv_chain_rows<<<nd, 256, rsmem, st>>>(rc, ell);
+                    } else {
+                        k_rv_chain_simt<<<nd, 256, 0, st>>>(rc, ell);
+                    }
+                    c->launches++;
+                }
+            }
+            k_rv_carry<<<blocks_for((int64_t)nd * n, 256), 256, 0, st>>>(r, t);
+            c->launches++;
+        }
+    }
+    CUDA_TRY(c, cudaGetLastError());
+    if (tcore && !c->capturing) TRY(check_tc_error(c));
+    return DR_OK;
+}
+
 static int ensure_grad_buffers(dr_ctx* c) {
     const size_t na = (size_t)c->D * c->H * std::max(c->net.hidden, 1);
     if (!c->dgalpha) TRY(dev_alloc(c, c->dgalpha, na));
@@ -2243,8 +2711,12 @@ int dr_backward(dr_ctx* c, const double* dV_dlo, const double* dV_dhi, float* da
     if (!c->dgshift) TRY(dev_alloc(c, c->dgshift, nw));
     c->gshift_valid = false;
     c->gtheta_valid = false;
-    TRY(run_forward(c, mode, nullptr, true));
-    TRY(launch_backward(c, mode, wlo, whi, c->dgalpha, c->dgbeta, c->dgshift, c->opt.weight_grad != 0));
+    if (use_staged_reverse(c, c->opt.weight_grad != 0)) {
+        TRY(run_staged_backward(c, mode, wlo, whi, c->dgalpha, c->dgbeta, c->dgshift));
+    } else {
+        TRY(run_forward(c, mode, nullptr, true));
+        TRY(launch_backward(c, mode, wlo, whi, c->dgalpha, c->dgbeta, c->dgshift, c->opt.weight_grad != 0));
+    }
     c->gshift_valid = true;
     c->gtheta_valid = c->opt.weight_grad != 0;
     const size_t na = (size_t)c->D * c->H * c->net.hidden;
@@ -2338,10 +2810,21 @@ int dr_optimize_slopes(dr_ctx* c, int steps, double lr_alpha, double lr_beta, do
         c->launches += 2;
         return DR_OK;
     };
-    // one projected-gradient step: evaluate with the tape, reverse sweep, projected updates
+    // one projected-gradient step: evaluate with the tape, reverse sweep, projected updates (the staged
+    // reverse sweep runs its own forward pass, whose objective the keep-best step then reads)
+    const bool staged = use_staged_reverse(c, false);
     auto step = [&]() -> int {
-        TRY(evaluate(true));
-        TRY(launch_backward(c, DR_SLOPE_USER, nullptr, nullptr, c->dgalpha, c->dgbeta));
+        if (staged) {
+            TRY(run_staged_backward(c, DR_SLOPE_USER, nullptr, nullptr, c->dgalpha, c->dgbeta, nullptr));
+            k_keep_best<<<(unsigned)c->D, 128, 0, c->stream>>>(c->dV, c->dbestV, c->dalpha, c->dbest_alpha, c->dbeta,
+                                                              c->dbest_beta, sp_row, per_dom);
+            k_sum_hist<<<1, 256, 0, c->stream>>>(c->dbestV, c->D, c->dVhist, c->dhist_slot);
+            CUDA_TRY(c, cudaGetLastError());
+            c->launches += 2;
+        } else {
+            TRY(evaluate(true));
+            TRY(launch_backward(c, DR_SLOPE_USER, nullptr, nullptr, c->dgalpha, c->dgbeta));
+        }
         if (na) {
             k_pgd<<<1184, 256, 0, c->stream>>>(c->dalpha, c->dgalpha, (int64_t)na, (float)lr_alpha, 0.f, 1.f);
             c->launches++;

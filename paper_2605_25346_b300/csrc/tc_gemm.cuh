@@ -17,6 +17,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cstdint>
+#include "common.cuh"
 
 namespace tc {
 
@@ -172,7 +173,17 @@ struct ChainEpi {
     const float* W1;   // final level: W_1 [N][n0] (row-major), else null
     int n0;            // columns of W_1 (<= kFinalCols)
     float* lxpart;     // final level: [column tiles][n0][R] partial Lambda_x entries
+    float* lev;        // keep mode: the level Lambda (before the slopes) at lev_index(row, col, N), or null
+    // reverse chain level (EPI 3, see pp_row_epilogue_rev): the per-row intercept adjoints of the
+    // target, the forward level read back, and the per-warp column sums
+    const float* rklo;  // [domains][kld]
+    const float* rkhi;
+    int kld;
+    const float* rlev;  // forward level at lev_index(row, col, N); with rlev_shared, lev_index(row % rows_per_dom, ...)
+    int rlev_shared;
+    float* colpart;     // [R / 32][2][N]: sums over each warp's 32 rows of lev*g (slope) and of the intercept term
 };
+
 constexpr int kFinalCols = 16;  // widest input layer the fused final level handles
 // Shared memory: pipeline stages, 256 B of barriers, the epilogue's per-column table, then (1 KB
 // aligned) the final level's right operand W_1^T as TF32 parts in the 128-byte swizzle layout
@@ -404,6 +415,11 @@ __global__ void __launch_bounds__(gemm_threads(BN), 1) k_tc_gemm_p(const __grid_
             float spos = 0.f, sneg = 0.f, sb = 0.f;
             if (uniform) {
                 // padding columns carry (0, 0, 0): x*s = 0 and no intercept contribution
+                if (epi.lev && live) {
+#pragma unroll
+                    for (int j = 0; j < BNH; ++j)
+                        if (n0 + cofs + j < N) epi.lev[lev_index(row, n0 + cofs + j, N)] = acc[j];
+                }
 #pragma unroll
                 for (int j = 0; j < BNH; ++j) {
                     const float4 q = coltab[cofs + j];
@@ -420,6 +436,7 @@ __global__ void __launch_bounds__(gemm_threads(BN), 1) k_tc_gemm_p(const __grid_
                     float xs = 0.f;
                     if (col < N) {
                         const float x = acc[j], dj = dl[col];
+                        if (epi.lev && live) epi.lev[lev_index(row, col, N)] = x;
                         xs = x * sl[col];
                         spos = fmaf(fmaxf(x, 0.f), dj, spos);
                         sneg = fmaf(fminf(x, 0.f), dj, sneg);

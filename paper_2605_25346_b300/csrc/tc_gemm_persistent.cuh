@@ -86,6 +86,7 @@ __device__ __forceinline__ void pp_row_epilogue(float* acc, const float4* coltab
     const int enk = epi.ldk >> 5;
     const int nch = min(BN, epi.ldk - n0) >> 5;  // 32-column chunks of this tile inside the operand
     const int row0 = row - lane;                 // first row of this warp
+    float* levrow = (epi.lev && live) ? epi.lev + lev_index(row, 0, N) : nullptr;  // keep mode: the level itself
     constexpr int CB = EPI == 1 ? 16 : 4;  // columns per block (EPI 1: one staging tile)
 #pragma unroll
     for (int hc = 0; hc < BN / CB; ++hc) {
@@ -94,6 +95,7 @@ __device__ __forceinline__ void pp_row_epilogue(float* acc, const float4* coltab
         for (int e = 0; e < CB; ++e) {
             const int j = CB * hc + e, h = j >> 6;
             const float x = acc[j];
+            if (levrow && n0 + j < N) levrow[(int64_t)(n0 + j) << 5] = x;
             float xs = 0.f;
             if constexpr (U) {
                 // padding columns carry (0, 0, 0): x*s = 0 and no intercept contribution
@@ -177,6 +179,135 @@ __device__ __forceinline__ void pp_row_epilogue(float* acc, const float4* coltab
 #pragma unroll
             for (int c = 0; c < kFinalCols; ++c)
                 if (c < epi.n0) o[(int64_t)c * R] = px[c];
+        }
+    }
+}
+
+// Warp reduce-scatter of 32 values per lane over segments of lanes: with G = 32, after five rounds of
+// pairwise exchange (31 shuffles) v[0] of lane L is the sum over the warp of the lanes' value L.
+// The same over segments of G lanes (G a power of two, at most 32; uniform across the warp): each
+// round halves the live values and pairs lanes inside the segment, so that afterwards lane L holds in
+// v[0 .. 32/G) the segment's sums of the values (L mod G) * 32/G + q.
+template <int HALF>
+__device__ __forceinline__ void bfly_masked(float* v, int lane, int mask) {
+    const bool up = (lane & mask) != 0;
+#pragma unroll
+    for (int q = 0; q < HALF; ++q) {
+        const float send = up ? v[q] : v[q + HALF];
+        const float keep = up ? v[q + HALF] : v[q];
+        v[q] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
+    }
+}
+__device__ __forceinline__ void seg_reduce_scatter32(float* v, int lane, int G) {
+    if (G >= 2) bfly_masked<16>(v, lane, G >> 1);
+    if (G >= 4) bfly_masked<8>(v, lane, G >> 2);
+    if (G >= 8) bfly_masked<4>(v, lane, G >> 3);
+    if (G >= 16) bfly_masked<2>(v, lane, G >> 4);
+    if (G >= 32) bfly_masked<1>(v, lane, 1);
+}
+
+// Reverse chain level (EPI 3) of one row over the tile's 128 columns, the neurons j of hidden layer
+// m: acc = (adjoint of the level below) W_m^T.  Per entry, g = acc + (gklo_i + gkhi_i) b_j adds the
+// adjoint through the level's intercept term Lambda_s b_m; with lam = Lambda^(m)_ij of the forward
+// pass, the warp sums lam g (the adjoint of the slope s_j) and gkhi_i lam^+ + gklo_i lam^- (the
+// adjoint of the relaxation intercept d_j) over each row segment into colpart, and the adjoint of
+// Lambda^(m), g s_j + d_j (gkhi_i [lam > 0] + gklo_i [lam < 0]), becomes the next reverse level's
+// left operand (TF32 parts through the staging tile, as in EPI 1) unless epi.Ah is null (the
+// target's top level).  Segments lie inside one domain: 32 rows when n_ell is a multiple of 32, else
+// the domain's n_ell rows (2, 4, 8 or 16).
+template <bool U, bool SEG32>
+__device__ __forceinline__ void pp_row_epilogue_rev(float* acc, const float4* coltab, float* stg, const ChainEpi& epi, int row,
+                                                    bool ok, int n0, int N, int R) {
+    constexpr int BN = 128, CB = 16;
+    const int lane = threadIdx.x & 31;
+    const bool live = ok && row < R;
+    const int rr = live ? row : (R > 0 ? R - 1 : 0);
+    const int dom = rr / epi.rows_per_dom, i = rr - dom * epi.rows_per_dom;
+    const float* sl = epi.hs + (int64_t)dom * epi.hidden + epi.hoff;
+    const float* dl = epi.hd + (int64_t)dom * epi.hidden + epi.hoff;
+    const float kl = live ? epi.rklo[(int64_t)dom * epi.kld + i] : 0.f;
+    const float kh = live ? epi.rkhi[(int64_t)dom * epi.kld + i] : 0.f;
+    const float kb = kl + kh;
+    const float* lrow = epi.rlev + lev_index(epi.rlev_shared ? i : rr, 0, N);
+    const int enk = epi.ldk >> 5;
+    const int nch = epi.Ah ? (min(BN, epi.ldk - n0) >> 5) : 0;  // 32-column chunks of the next operand in this tile
+    const int row0 = row - lane;
+    const int G = SEG32 ? 32 : epi.rows_per_dom;  // row segment of the column sums
+#pragma unroll
+    for (int hc = 0; hc < BN / CB; ++hc) {
+        float v[32], xv[CB];
+#pragma unroll
+        for (int e = 0; e < CB; ++e) {
+            const int j = CB * hc + e, col = n0 + j;
+            float sj = 0.f, dj = 0.f, bj = 0.f;
+            if constexpr (U) {
+                const float4 qv = coltab[j];  // padding columns carry (0, 0, 0)
+                sj = qv.x;
+                dj = qv.y;
+                bj = qv.z;
+            } else if (col < N) {
+                sj = sl[col];
+                dj = dl[col];
+                bj = epi.bias[col];
+            }
+            const bool in = live && col < N;
+            const float lam = in ? lrow[(int64_t)col << 5] : 0.f;
+            const float g = in ? fmaf(kb, bj, acc[j]) : 0.f;
+            const float kv = lam > 0.f ? kh : kl;  // the intercept adjoint of lam's sign (lam = 0 adds nothing)
+            v[e] = lam * g;
+            v[CB + e] = lam * kv;
+            xv[e] = fmaf(g, sj, lam != 0.f ? dj * kv : 0.f);
+        }
+        if constexpr (SEG32) {
+            bfly_masked<16>(v, lane, 16);
+            bfly_masked<8>(v, lane, 8);
+            bfly_masked<4>(v, lane, 4);
+            bfly_masked<2>(v, lane, 2);
+            bfly_masked<1>(v, lane, 1);
+        } else {
+            seg_reduce_scatter32(v, lane, G);
+        }
+        // value index x < 16: slope sum of column CB*hc + x; x >= 16: intercept sum of column CB*hc + x - 16
+        if constexpr (SEG32) {
+            const int col = n0 + CB * hc + (lane & 15);
+            if (ok && row0 < R && col < N) epi.colpart[((int64_t)(row0 >> 5) * 2 + (lane >> 4)) * N + col] = v[0];
+        } else {
+            const int cnt = 32 / G, seg = (row0 + lane) / G;
+            const bool seg_live = ok && row0 + (lane & ~(G - 1)) < R;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                if (q < cnt) {
+                    const int x = (lane & (G - 1)) * cnt + q;
+                    const int col = n0 + CB * hc + (x & 15);
+                    if (seg_live && col < N) epi.colpart[((int64_t)seg * 2 + (x >> 4)) * N + col] = v[q];
+                }
+            }
+        }
+        const int c = hc >> 1;
+        if (c < nch) {  // uniform across the warp
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {
+                float w4[CB];
+#pragma unroll
+                for (int e = 0; e < CB; ++e) {
+                    const float hi = tf32_part_rna(xv[e]);
+                    w4[e] = part == 0 ? hi : tf32_part_rna(xv[e] - hi);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    *reinterpret_cast<float4*>(stg + lane * 16 + ((u ^ ((lane >> 1) & 3)) << 2)) =
+                        make_float4(w4[4 * u], w4[4 * u + 1], w4[4 * u + 2], w4[4 * u + 3]);
+                __syncwarp();
+                float* dst = part == 0 ? epi.Ah : epi.Al;
+                const int u = lane & 3;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int r = (lane >> 2) + 8 * q;
+                    const float4 w = *reinterpret_cast<const float4*>(stg + r * 16 + ((u ^ ((r >> 1) & 3)) << 2));
+                    if (ok && row0 + r < R) *reinterpret_cast<float4*>(dst + blk_index(row0 + r, n0 + 16 * hc + 4 * u, enk)) = w;
+                }
+                __syncwarp();
+            }
         }
     }
 }
@@ -340,6 +471,20 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
                 }
                 group_bar(g);
             }
+            if constexpr (EPI == 3) {
+                // the forward level this warp's rows read in the epilogue: into L2 while the tile's MMAs
+                // run (one 128-byte line per column of the 32-row block; lane L takes columns L + 32 q)
+                const int r0 = m0 + sub * 32;
+                if (r0 < R) {
+                    const int rl = epi.rlev_shared ? (r0 % epi.rows_per_dom) : r0;
+                    const float* lb = epi.rlev + lev_index(rl, 0, N);
+#pragma unroll
+                    for (int q = 0; q < BN / 32; ++q) {
+                        const int col = n0 + lane + 32 * q;
+                        if (col < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(lb + ((int64_t)col << 5)));
+                    }
+                }
+            }
             float acc[BN];
 #pragma unroll
             for (int j = 0; j < BN; ++j) acc[j] = 0.f;
@@ -374,8 +519,14 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
             } else {
                 // EPI 1 has no W_1 table: its per-warp staging tiles (2 KB each) take that space
                 float* stg = w1tab + sub * 512;
-                if (uniform) pp_row_epilogue<EPI, true>(acc, coltab, w1tab, stg, epi, row, ok, n0, N, R);
-                else pp_row_epilogue<EPI, false>(acc, coltab, w1tab, stg, epi, row, ok, n0, N, R);
+                if constexpr (EPI == 3) {
+                    if (epi.rows_per_dom % 32 != 0) pp_row_epilogue_rev<false, false>(acc, coltab, stg, epi, row, ok, n0, N, R);
+                    else if (uniform) pp_row_epilogue_rev<true, true>(acc, coltab, stg, epi, row, ok, n0, N, R);
+                    else pp_row_epilogue_rev<false, true>(acc, coltab, stg, epi, row, ok, n0, N, R);
+                } else {
+                    if (uniform) pp_row_epilogue<EPI, true>(acc, coltab, w1tab, stg, epi, row, ok, n0, N, R);
+                    else pp_row_epilogue<EPI, false>(acc, coltab, w1tab, stg, epi, row, ok, n0, N, R);
+                }
             }
         }
     }

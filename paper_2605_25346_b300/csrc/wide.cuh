@@ -60,6 +60,14 @@ struct WideArgs {
     float* hq;     // [Dc][hidden] q_m = |W_m| hmax_{m-1} per neuron of hidden layer m (rounded up)
     float* xscale; // [Dc] Taylor-model scale of the step (DR_STATUS_MARGIN_BIT)
     double* kerr;  // [Dc][maxw] accumulated error bound of each target row's linear bound
+    // keep mode (the staged reverse sweep reads these back; null otherwise).  The host points
+    // cf/Pf/Ilof/Ihif and hl/hu/hs/hd at the step's slot of the keep store as well.
+    float* vsnap;        // [Dc][L][n+1] dual vector (and w) seen by target l's concretisation
+    float *hl0, *hu0;    // [Dc][hidden] pre-activation bounds before the split clipping
+    float* sph;          // [nnz] value h of every split constraint recorded in this pass
+    float *Gk, *LXk;     // [Dc][krows][n] G = Lambda_x P and Lambda_x of every target
+    int krows, koff;     // krows = hidden + m; koff = row offset of the target being projected
+    double* tape;        // [Dc][H+1][n*n + 4n + 2] FP64 TM (P, c, Ilo, Ihi, v, w, cursor) per step
 };
 
 // Rigorous mode.  For IEEE FP32 with round-to-nearest (the CUDA-core FMA chains used in this mode),
@@ -139,6 +147,27 @@ __global__ void k_w_view(const WideArgs a) {
         }
         vf[n] = __double2float_ru(a.w[d] + dv);
         a.xscale[d] = tm_scale(a.c + (int64_t)d * n, P, a.Ilo + (int64_t)d * n, a.Ihi + (int64_t)d * n, n);
+        if (a.vsnap)
+            for (int k = 0; k <= n; ++k) a.vsnap[(int64_t)d * a.net.L * (n + 1) + k] = vf[k];
+    }
+}
+
+// Keep mode: the FP64 TM of every domain of the chunk at the start of step t (t = H: after the
+// last step) into the chunk's tape, laid out as P, c, Ilo, Ihi, v, w, split cursor.
+__global__ void k_w_tape(const WideArgs a, int t) {
+    const int n = a.net.n, d = blockIdx.x, H = a.net.H;
+    const int ts = n * n + 4 * n + 2;
+    double* tp = a.tape + ((int64_t)d * (H + 1) + t) * ts;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) tp[idx] = a.P[(int64_t)d * n * n + idx];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        tp[n * n + i] = a.c[(int64_t)d * n + i];
+        tp[n * n + n + i] = a.Ilo[(int64_t)d * n + i];
+        tp[n * n + 2 * n + i] = a.Ihi[(int64_t)d * n + i];
+        tp[n * n + 3 * n + i] = a.v[(int64_t)d * n + i];
+    }
+    if (threadIdx.x == 0) {
+        tp[n * n + 4 * n] = a.w[d];
+        tp[n * n + 4 * n + 1] = (double)a.cursor[d];
     }
 }
 
@@ -191,8 +220,9 @@ __global__ void k_w_chain_init(const WideArgs a, int ell, float* __restrict__ Ao
 }
 
 // After a GEMM level produced Lambda^(mm) (mm >= 1) in buf [d][i][k], k < n_mm: the intercepts of the
-// relaxation of layer mm and, in place, A = Lambda diag(s_mm).  One warp per (domain, row).
-__global__ void k_w_level_epi(const WideArgs a, int ell, int mm, float* __restrict__ buf) {
+// relaxation of layer mm and, in place, A = Lambda diag(s_mm).  One warp per (domain, row).  With
+// lev set, Lambda^(mm) itself is also kept (keep mode).
+__global__ void k_w_level_epi(const WideArgs a, int ell, int mm, float* __restrict__ buf, float* __restrict__ lev) {
     const NetDesc& N = a.net;
     const int rows = N.w[ell], K = N.w[mm];
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -213,6 +243,7 @@ __global__ void k_w_level_epi(const WideArgs a, int ell, int mm, float* __restri
         const float xs = x * s[j];
         sb = fmaf(xs, bm[j], sb);
         if (q) se = __fmaf_ru(fabsf(x), err_weight(s[j], dd[j], bm[j], q[j], gk), se);
+        if (lev) lev[lev_index(wid, j, K)] = x;
         row[j] = xs;
     }
     spos = warp_sum(spos);
@@ -314,10 +345,15 @@ __global__ void k_w_project(const WideArgs a, int ell, const float* __restrict__
     const float* vf = a.vf + (int64_t)d * (n + 1);
     float* G = a.G + ((int64_t)d * N.maxw + i) * n;
     float g1 = 0.f, gm = 0.f, gp = 0.f;
+    float* Gk = a.Gk ? a.Gk + ((int64_t)d * a.krows + a.koff + i) * n : nullptr;
     for (int k = lane; k < n; k += 32) {
         float acc = 0.f;
         for (int j = 0; j < n; ++j) acc = fmaf(Lx[j], Pf[j * n + k], acc);
         G[k] = acc;
+        if (Gk) {
+            Gk[k] = acc;
+            a.LXk[((int64_t)d * a.krows + a.koff + i) * n + k] = Lx[k];
+        }
         g1 += fabsf(acc);
         gm += fabsf(acc - vf[k]);
         gp += fabsf(acc + vf[k]);
@@ -379,6 +415,14 @@ __global__ void k_w_relax(const WideArgs a, int ell, int t) {
     const int64_t dom = a.d0 + d;
     float* lh = a.hl + (int64_t)d * N.hidden + N.hoff[ell];
     float* uh = a.hu + (int64_t)d * N.hidden + N.hoff[ell];
+    if (a.hl0) {
+        // keep mode: the bounds before the clipping below
+        for (int j = threadIdx.x; j < rows; j += blockDim.x) {
+            a.hl0[(int64_t)d * N.hidden + N.hoff[ell] + j] = lh[j];
+            a.hu0[(int64_t)d * N.hidden + N.hoff[ell] + j] = uh[j];
+        }
+        __syncthreads();
+    }
     if (threadIdx.x == 0 && a.sp_row) {
         const int64_t sp_end = a.sp_row[dom + 1];
         int cpos = a.cursor[d];
@@ -392,6 +436,7 @@ __global__ void k_w_relax(const WideArgs a, int ell, int t) {
                 const float bt = a.beta ? a.beta[cpos] : 0.f;
                 const double hh = r.sign > 0 ? ((double)a.sa[q] + a.khi[q] + (double)a.sRhi[q] + (double)a.sS[q])
                                              : (-((double)a.sa[q] + a.klo[q] + (double)a.sRlo[q]) + (double)a.sS[q]);
+                if (a.sph) a.sph[cpos] = (float)hh;
                 if (r.sign > 0) {
                     if (lh[j] < 0.f) lh[j] = 0.f;
                 } else {
@@ -416,6 +461,12 @@ __global__ void k_w_relax(const WideArgs a, int ell, int t) {
             }
             vf[n] = __double2float_ru(a.w[d] + dv);
         }
+    }
+    if (threadIdx.x == 0 && a.vsnap && ell + 1 <= N.L) {
+        // keep mode: the dual vector the next target's concretisation sees
+        const float* vf = a.vf + (int64_t)d * (n + 1);
+        float* vs = a.vsnap + ((int64_t)d * N.L + ell) * (n + 1);
+        for (int k = 0; k <= n; ++k) vs[k] = vf[k];
     }
     __syncthreads();
     for (int j = threadIdx.x; j < rows; j += blockDim.x) {
@@ -791,6 +842,15 @@ __global__ void __launch_bounds__(256, 3) k_t_project4(const WideArgs a, int ell
             sb += __shfl_xor_sync(0xffffffffu, sb, o);
         }
         if (!live) continue;
+        if (a.Gk && k0 < n) {
+            const int64_t ko = ((int64_t)d * a.krows + a.koff + i) * n + k0;
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (k0 + e < n) {
+                    a.Gk[ko + e] = gr[e];
+                    a.LXk[ko + e] = xl[e];
+                }
+        }
         if (k0 < n && (ell == L || a.sp_row != nullptr)) {  // G rows nobody reads are not stored
             float* G = a.G + ((int64_t)d * N.maxw + i) * n + k0;
             if constexpr (VEC) {
@@ -926,6 +986,20 @@ __global__ void __launch_bounds__(128) k_t_project(const WideArgs a, int ell, co
                 g1 += fabsf(acc);
                 gm += fabsf(acc - vf[k]);
                 gp += fabsf(acc + vf[k]);
+            }
+        }
+        if (a.Gk) {
+            // keep mode: Lambda_x and G of this row (G recomputed in the same order as above)
+            const int64_t ko = ((int64_t)d * a.krows + a.koff + i) * n;
+#pragma unroll
+            for (int j = 0; j < NMAX; ++j)
+                if (j < n) a.LXk[ko + j] = x[j];
+            for (int k = 0; k < n; ++k) {
+                float acc = 0.f;
+#pragma unroll
+                for (int j = 0; j < NMAX; ++j)
+                    if (j < n) acc = fmaf(x[j], Pf[j * n + k], acc);
+                a.Gk[ko + k] = acc;
             }
         }
         // layer 1 has no chain: its intercepts are the bias (and kappa is recorded for the splits)
