@@ -58,10 +58,3 @@ __device__ __forceinline__ float tm_scale(const double* c, const double* P, cons
 #define DR_SLOPE_CHORD_K 1
 #define DR_SLOPE_ZERO_K 2
 #define DR_SLOPE_USER_K 3
-
-// Layout in which the staged path keeps a chain level Lambda (stacked rows r = d * n_ell + i, ncols
-// columns) for the reverse sweep: 32-row blocks, column-major inside a block, so the 32 rows of a
-// warp at one column are 128 contiguous bytes.
-__host__ __device__ __forceinline__ int64_t lev_index(int64_t r, int j, int ncols) {
-    return (((r >> 5) * ncols + j) << 5) + (r & 31);
-}

@@ -92,7 +92,8 @@ struct dr_ctx {
     // padded to 128, K = ru32(n_1); null for a one-layer controller
     float *dA2h = nullptr, *dA2l = nullptr, *dA2ph = nullptr, *dA2pl = nullptr;
     // for the staged reverse sweep: every layer W_l as TF32 parts [n_l][ru32(n_{l-1})] (right operand
-    // of the reverse chain GEMMs) and in the kept-level layout (lev_index, the shared top level)
+    // of the reverse chain GEMMs) and in the kept-level layout (blocked as the operands, rows padded to
+    // 128: the shared top level of the reverse chain)
     float *dWRh = nullptr, *dWRl = nullptr, *dWlev = nullptr;
     int64_t WRoff[DR_MAXL] = {}, WLoff[DR_MAXL] = {};
     // staged reverse sweep: keep store and adjoint scratch of one chunk, split values h
@@ -1257,7 +1258,7 @@ int dr_load_controller(dr_ctx* c, int L, const int32_t* widths, const void* cons
                 c->WRoff[l] = rt;
                 c->WLoff[l] = lt;
                 rt += (int64_t)widths[l + 1] * ((widths[l] + 31) & ~31);
-                lt += (int64_t)((widths[l + 1] + 31) & ~31) * widths[l];
+                lt += (int64_t)((widths[l + 1] + 127) & ~127) * ((widths[l] + 31) & ~31);
             }
             std::vector<float> rh(rt, 0.f), rl(rt, 0.f), lv(lt, 0.f);
             for (int l = 0; l < L; ++l) {
@@ -1268,7 +1269,7 @@ int dr_load_controller(dr_ctx* c, int L, const int32_t* widths, const void* cons
                         const float h = tf32(x);
                         rh[c->WRoff[l] + (int64_t)i * ldk + k] = h;
                         rl[c->WRoff[l] + (int64_t)i * ldk + k] = tf32(x - h);
-                        lv[c->WLoff[l] + lev_index(i, k, K)] = x;
+                        lv[c->WLoff[l] + tc::blk_index(i, k, ldk >> 5)] = x;
                     }
             }
             dev_free(c, (void*&)c->dWRh, 0);
@@ -1689,8 +1690,8 @@ struct WideLane {
 };
 
 // Keep mode of the staged forward pass: where one step's chain levels go.  Level Lambda^(m) of target
-// ell (m = 1 .. ell-2, the levels a chain GEMM produces) sits at base + off[ell][m] in the lev_index
-// layout over the chunk's stacked rows with n_m columns.
+// ell (m = 1 .. ell-2, the levels a chain GEMM produces) sits at base + off[ell][m], blocked like the
+// GEMM operands (tc::blk_index over the chunk's stacked rows, ru32(n_m) columns).
 struct KeepLevels {
     float* base;
     int64_t off[DR_MAXL + 1][DR_MAXL + 1];
@@ -2347,7 +2348,7 @@ static size_t rev_store(const NetDesc& N, int Dc, bool tc_rev, RevStore* S, unsi
     for (int ell = 3; ell <= L; ++ell)
         for (int mm = 1; mm <= ell - 2; ++mm) {
             S->kl.off[ell][mm] = lt;
-            lt += (((D * N.w[ell]) + 31) & ~int64_t(31)) * N.w[mm];
+            lt += (((D * N.w[ell]) + tc::BM - 1) / tc::BM * tc::BM) * ((N.w[mm] + 31) & ~31);
         }
     S->slev = std::max<int64_t>(lt, 1);
     S->kl.base = nullptr;

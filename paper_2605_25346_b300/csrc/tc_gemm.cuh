@@ -173,13 +173,14 @@ struct ChainEpi {
     const float* W1;   // final level: W_1 [N][n0] (row-major), else null
     int n0;            // columns of W_1 (<= kFinalCols)
     float* lxpart;     // final level: [column tiles][n0][R] partial Lambda_x entries
-    float* lev;        // keep mode: the level Lambda (before the slopes) at lev_index(row, col, N), or null
+    float* lev;        // keep mode: the level Lambda (before the slopes), blocked like the operands (blk_index,
+                       // ru32(N) columns), or null
     // reverse chain level (EPI 3, see pp_row_epilogue_rev): the per-row intercept adjoints of the
     // target, the forward level read back, and the per-warp column sums
     const float* rklo;  // [domains][kld]
     const float* rkhi;
     int kld;
-    const float* rlev;  // forward level at lev_index(row, col, N); with rlev_shared, lev_index(row % rows_per_dom, ...)
+    const float* rlev;  // forward level, blocked (blk_index, ru32(N) columns); with rlev_shared the rows are row % rows_per_dom
     int rlev_shared;
     float* colpart;     // [R / 32][2][N]: sums over each warp's 32 rows of lev*g (slope) and of the intercept term
 };
@@ -418,7 +419,7 @@ __global__ void __launch_bounds__(gemm_threads(BN), 1) k_tc_gemm_p(const __grid_
                 if (epi.lev && live) {
 #pragma unroll
                     for (int j = 0; j < BNH; ++j)
-                        if (n0 + cofs + j < N) epi.lev[lev_index(row, n0 + cofs + j, N)] = acc[j];
+                        if (n0 + cofs + j < N) epi.lev[blk_index(row, n0 + cofs + j, (N + 31) >> 5)] = acc[j];
                 }
 #pragma unroll
                 for (int j = 0; j < BNH; ++j) {
@@ -436,7 +437,7 @@ __global__ void __launch_bounds__(gemm_threads(BN), 1) k_tc_gemm_p(const __grid_
                     float xs = 0.f;
                     if (col < N) {
                         const float x = acc[j], dj = dl[col];
-                        if (epi.lev && live) epi.lev[lev_index(row, col, N)] = x;
+                        if (epi.lev && live) epi.lev[blk_index(row, col, (N + 31) >> 5)] = x;
                         xs = x * sl[col];
                         spos = fmaf(fmaxf(x, 0.f), dj, spos);
                         sneg = fmaf(fminf(x, 0.f), dj, sneg);

@@ -86,7 +86,8 @@ __device__ __forceinline__ void pp_row_epilogue(float* acc, const float4* coltab
     const int enk = epi.ldk >> 5;
     const int nch = min(BN, epi.ldk - n0) >> 5;  // 32-column chunks of this tile inside the operand
     const int row0 = row - lane;                 // first row of this warp
-    float* levrow = (epi.lev && live) ? epi.lev + lev_index(row, 0, N) : nullptr;  // keep mode: the level itself
+    float* levp = live ? epi.lev : nullptr;  // keep mode: the level itself, blocked with ru32(N) columns
+    const int ldl = (N + 31) & ~31;
     constexpr int CB = EPI == 1 ? 16 : 4;  // columns per block (EPI 1: one staging tile)
 #pragma unroll
     for (int hc = 0; hc < BN / CB; ++hc) {
@@ -95,7 +96,6 @@ __device__ __forceinline__ void pp_row_epilogue(float* acc, const float4* coltab
         for (int e = 0; e < CB; ++e) {
             const int j = CB * hc + e, h = j >> 6;
             const float x = acc[j];
-            if (levrow && n0 + j < N) levrow[(int64_t)(n0 + j) << 5] = x;
             float xs = 0.f;
             if constexpr (U) {
                 // padding columns carry (0, 0, 0): x*s = 0 and no intercept contribution
@@ -115,6 +115,15 @@ __device__ __forceinline__ void pp_row_epilogue(float* acc, const float4* coltab
                 }
             }
             xv[e] = xs;
+        }
+        if (levp) {
+#pragma unroll
+            for (int u = 0; u < CB / 4; ++u) {
+                const int c0 = n0 + CB * hc + 4 * u;
+                if (c0 < ldl)
+                    *reinterpret_cast<float4*>(levp + blk_index(row, c0, ldl >> 5)) =
+                        make_float4(acc[CB * hc + 4 * u], acc[CB * hc + 4 * u + 1], acc[CB * hc + 4 * u + 2], acc[CB * hc + 4 * u + 3]);
+            }
         }
         if constexpr (EPI == 1) {
             const int c = hc >> 1;
@@ -215,27 +224,64 @@ __device__ __forceinline__ void seg_reduce_scatter32(float* v, int lane, int G) 
 // left operand (TF32 parts through the staging tile, as in EPI 1) unless epi.Ah is null (the
 // target's top level).  Segments lie inside one domain: 32 rows when n_ell is a multiple of 32, else
 // the domain's n_ell rows (2, 4, 8 or 16).
+// The row's intercept adjoints, read by the reverse epilogue.
+struct RevPre {
+    float kl, kh;
+};
+__device__ __forceinline__ int64_t rev_level_row(const ChainEpi& epi, int row, int R) {
+    const int rr = row < R ? row : (R > 0 ? R - 1 : 0);
+    return epi.rlev_shared ? (int64_t)(rr % epi.rows_per_dom) : (int64_t)rr;
+}
+__device__ __forceinline__ void rev_level_load(const ChainEpi& epi, int64_t lrow, bool in, int c0, int N, float4* l) {
+    const int nkl = (N + 31) >> 5;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        l[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (in && c0 + 4 * u < N) l[u] = *reinterpret_cast<const float4*>(epi.rlev + blk_index(lrow, c0 + 4 * u, nkl));
+    }
+}
+__device__ __forceinline__ RevPre rev_preload(const ChainEpi& epi, int row, int R) {
+    RevPre p;
+    const bool in = row < R;
+    const int rr = in ? row : (R > 0 ? R - 1 : 0);
+    const int dom = rr / epi.rows_per_dom, i = rr - dom * epi.rows_per_dom;
+    p.kl = in ? epi.rklo[(int64_t)dom * epi.kld + i] : 0.f;
+    p.kh = in ? epi.rkhi[(int64_t)dom * epi.kld + i] : 0.f;
+    return p;
+}
+
 template <bool U, bool SEG32>
 __device__ __forceinline__ void pp_row_epilogue_rev(float* acc, const float4* coltab, float* stg, const ChainEpi& epi, int row,
-                                                    bool ok, int n0, int N, int R) {
+                                                    bool ok, int n0, int N, int R, const RevPre& pre) {
     constexpr int BN = 128, CB = 16;
     const int lane = threadIdx.x & 31;
     const bool live = ok && row < R;
     const int rr = live ? row : (R > 0 ? R - 1 : 0);
-    const int dom = rr / epi.rows_per_dom, i = rr - dom * epi.rows_per_dom;
+    const int dom = rr / epi.rows_per_dom;
     const float* sl = epi.hs + (int64_t)dom * epi.hidden + epi.hoff;
     const float* dl = epi.hd + (int64_t)dom * epi.hidden + epi.hoff;
-    const float kl = live ? epi.rklo[(int64_t)dom * epi.kld + i] : 0.f;
-    const float kh = live ? epi.rkhi[(int64_t)dom * epi.kld + i] : 0.f;
+    const float kl = live ? pre.kl : 0.f;
+    const float kh = live ? pre.kh : 0.f;
     const float kb = kl + kh;
-    const float* lrow = epi.rlev + lev_index(epi.rlev_shared ? i : rr, 0, N);
+    const int64_t lrow = rev_level_row(epi, row, R);  // row of the forward level read
     const int enk = epi.ldk >> 5;
     const int nch = epi.Ah ? (min(BN, epi.ldk - n0) >> 5) : 0;  // 32-column chunks of the next operand in this tile
     const int row0 = row - lane;
     const int G = SEG32 ? 32 : epi.rows_per_dom;  // row segment of the column sums
 #pragma unroll
     for (int hc = 0; hc < BN / CB; ++hc) {
-        float v[32], xv[CB];
+        float v[32], xv[CB], lv[CB];
+        {
+            float4 q4[4];
+            rev_level_load(epi, lrow, live, n0 + CB * hc, N, q4);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                lv[4 * u] = q4[u].x;
+                lv[4 * u + 1] = q4[u].y;
+                lv[4 * u + 2] = q4[u].z;
+                lv[4 * u + 3] = q4[u].w;
+            }
+        }
 #pragma unroll
         for (int e = 0; e < CB; ++e) {
             const int j = CB * hc + e, col = n0 + j;
@@ -251,12 +297,12 @@ __device__ __forceinline__ void pp_row_epilogue_rev(float* acc, const float4* co
                 bj = epi.bias[col];
             }
             const bool in = live && col < N;
-            const float lam = in ? lrow[(int64_t)col << 5] : 0.f;
+            const float lam = in ? lv[e] : 0.f;
             const float g = in ? fmaf(kb, bj, acc[j]) : 0.f;
             const float kv = lam > 0.f ? kh : kl;  // the intercept adjoint of lam's sign (lam = 0 adds nothing)
             v[e] = lam * g;
             v[CB + e] = lam * kv;
-            xv[e] = fmaf(g, sj, lam != 0.f ? dj * kv : 0.f);
+            xv[e] = fmaf(g, sj, lam != 0.f ? dj * kv : 0.f);  // the adjoint of Lambda^(m): the next operand
         }
         if constexpr (SEG32) {
             bfly_masked<16>(v, lane, 16);
@@ -476,12 +522,13 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
                 // run (one 128-byte line per column of the 32-row block; lane L takes columns L + 32 q)
                 const int r0 = m0 + sub * 32;
                 if (r0 < R) {
+                    // blocked layout: the warp's 32 rows of one 32-column chunk are 4 KB contiguous
                     const int rl = epi.rlev_shared ? (r0 % epi.rows_per_dom) : r0;
-                    const float* lb = epi.rlev + lev_index(rl, 0, N);
+                    const int nkl = (N + 31) >> 5;
 #pragma unroll
                     for (int q = 0; q < BN / 32; ++q) {
-                        const int col = n0 + lane + 32 * q;
-                        if (col < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(lb + ((int64_t)col << 5)));
+                        const int c0 = n0 + 32 * q;
+                        if (c0 < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(epi.rlev + blk_index(rl, c0, nkl) + 32 * lane));
                     }
                 }
             }
@@ -520,9 +567,10 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
                 // EPI 1 has no W_1 table: its per-warp staging tiles (2 KB each) take that space
                 float* stg = w1tab + sub * 512;
                 if constexpr (EPI == 3) {
-                    if (epi.rows_per_dom % 32 != 0) pp_row_epilogue_rev<false, false>(acc, coltab, stg, epi, row, ok, n0, N, R);
-                    else if (uniform) pp_row_epilogue_rev<true, true>(acc, coltab, stg, epi, row, ok, n0, N, R);
-                    else pp_row_epilogue_rev<false, true>(acc, coltab, stg, epi, row, ok, n0, N, R);
+                    const RevPre pre = rev_preload(epi, row, R);
+                    if (epi.rows_per_dom % 32 != 0) pp_row_epilogue_rev<false, false>(acc, coltab, stg, epi, row, ok, n0, N, R, pre);
+                    else if (uniform) pp_row_epilogue_rev<true, true>(acc, coltab, stg, epi, row, ok, n0, N, R, pre);
+                    else pp_row_epilogue_rev<false, true>(acc, coltab, stg, epi, row, ok, n0, N, R, pre);
                 } else {
                     if (uniform) pp_row_epilogue<EPI, true>(acc, coltab, w1tab, stg, epi, row, ok, n0, N, R);
                     else pp_row_epilogue<EPI, false>(acc, coltab, w1tab, stg, epi, row, ok, n0, N, R);

@@ -243,7 +243,7 @@ __global__ void k_w_level_epi(const WideArgs a, int ell, int mm, float* __restri
         const float xs = x * s[j];
         sb = fmaf(xs, bm[j], sb);
         if (q) se = __fmaf_ru(fabsf(x), err_weight(s[j], dd[j], bm[j], q[j], gk), se);
-        if (lev) lev[lev_index(wid, j, K)] = x;
+        if (lev) lev[tc::blk_index(wid, j, (K + 31) >> 5)] = x;
         row[j] = xs;
     }
     spos = warp_sum(spos);

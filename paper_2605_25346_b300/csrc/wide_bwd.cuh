@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(256) k_rv_chain_simt(const RevArgs a, int ell)
                 float g = (gklo[i] + gkhi[i]) * bm[j];
                 const float* pr = prev + (int64_t)i * pld;
                 for (int k = 0; k < NN; ++k) g = fmaf(pr[k], wrow[k], g);
-                const float lam = lev ? lev[lev_index((int64_t)d * rows + i, j, K)] : Wl[(int64_t)i * K + j];
+                const float lam = lev ? lev[tc::blk_index((int64_t)d * rows + i, j, (K + 31) >> 5)] : Wl[(int64_t)i * K + j];
                 acc_s = fmaf(lam, g, acc_s);
                 acc_d += gkhi[i] * posf(lam) + gklo[i] * negf(lam);
                 if (mm < ell - 1)
@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(256) k_rv_chain_rows(const RevArgs a, int ell)
                 if (lane < 8 && i < rows) {
                     const float kl = gklo[i], kh = gkhi[i];
                     const float g = fmaf(kl + kh, bj, mine);
-                    const float lam = lev ? lev[lev_index((int64_t)d * rows + i, j, K)] : Wl[(int64_t)i * K + j];
+                    const float lam = lev ? lev[tc::blk_index((int64_t)d * rows + i, j, (K + 31) >> 5)] : Wl[(int64_t)i * K + j];
                     ps = lam * g;
                     pd = kh * posf(lam) + kl * negf(lam);
                     if (!top) next[i * a.ldw + j] = g * sj + kh * (lam > 0.f ? dj : 0.f) + kl * (lam < 0.f ? dj : 0.f);
