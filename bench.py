@@ -136,47 +136,88 @@ def measure_refinement(local):
     return out
 
 
-def measure_wide_refinement(local):
-    """Slope (and split multiplier) refinement on samples of the two wide workloads, whose fused
-    forward/reverse kernels keep their working set in per-CTA global slabs."""
+def measure_wide_refinement(local, forward_rate=None):
+    """Slope (and split multiplier) refinement on the two wide workloads through the staged reverse
+    sweep: per chunk of domains a keep-mode forward pass, then the reverse sweep with its chain
+    products on the tensor cores; steps after the first replay one captured step (a context stream of
+    its own).  The 16-512x4-8 workload runs at its full horizon (H = 50) on 1024 sub-boxes, from the
+    chord slopes (a local minimum of V: V barely moves) and from slopes 0.05 off them; the branch
+    workload on 4096 of its domains with split multipliers, batched vs the plain per-domain form.
+    `forward_rate`: the bounds pass's domain-steps/s on the same workload, for the ratio."""
     import dataclasses
     from paper_2605_25346_b300 import api
-    out = {}
-    for name, prob, steps, lrb in (
-            ("branch12 12-256x3-4, 256 of 65536 branch domains, H=30, alpha+beta", wl.quadrotor_branch(only=np.arange(256)),
-             2, 0.005),
-            ("large16 16-512x4-8, 148 of 262144 sub-boxes, H=10 (one domain per SM), alpha",
-             dataclasses.replace(wl.large16().subset(np.arange(148)), H=10), 2, 0.0),
-            ("large16 16-512x4-8, 296 of 262144 sub-boxes, H=10 (two domains per SM), alpha",
-             dataclasses.replace(wl.large16().subset(np.arange(296)), H=10), 2, 0.0)):
-        r = api.Reach(local).load(prob)
-        r.optimize(1, 0.1, lrb)  # warm-up: slabs, tape and gradient buffers
+
+    def run(prob, steps, lrb, start=None, reverse=0):
+        r = api.Reach(local, stream=torch.cuda.Stream()).load(prob)
+        r.set_options(reverse=reverse)
+        if start is not None:
+            r.set_alpha(start)
+        r.optimize(1, 0.1, lrb)  # warm-up: keep store, scratch and the GEMM tuning
         r.close()
-        r = api.Reach(local).load(prob)
+        r = api.Reach(local, stream=torch.cuda.Stream()).load(prob)
+        r.set_options(reverse=reverse)
+        if start is not None:
+            r.set_alpha(start)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         hist = r.optimize(steps, 0.1, lrb)
+        torch.cuda.synchronize()
         t = time.perf_counter() - t0
-        out[name] = {"alpha_opt_steps_per_s": steps / t, "domain_steps_per_s": prob.D * prob.H * steps / t,
-                     "V_first": float(hist[0]), "V_best": float(hist[-1])}
-        if name.startswith("branch12"):
-            # batched vs plain (one domain per call, same steps and rates) on a sample of the domains
-            Vb = r.objective()
-            sample = 4
-            tp, Vp = 0.0, []
-            for d in range(sample):
-                rr = api.Reach(local).load(prob.subset([d]))
-                torch.cuda.synchronize()
-                t1 = time.perf_counter()
-                rr.optimize(steps, 0.1, lrb)
-                tp += time.perf_counter() - t1
-                Vp.append(rr.objective()[0])
-                rr.close()
-            out[name].update({"batched_domains_per_s": prob.D / t, "plain_domains_per_s": sample / tp,
-                              "plain_sample_domains": sample, "batched_over_plain": (prob.D / t) / (sample / tp),
-                              "max_rel_V_gap_batched_vs_plain": float(np.max(np.abs(np.array(Vp) - Vb[:sample]) /
-                                                                              np.abs(Vb[:sample])))})
-        r.close()
+        res = {"alpha_opt_steps_per_s": steps / t, "domain_steps_per_s": prob.D * prob.H * steps / t,
+               "V_first": float(hist[0]), "V_best": float(hist[-1]), "V_reduction": 1.0 - float(hist[-1]) / float(hist[0]),
+               "graph_replays": r.graph_replays()}
+        return r, res, t
+
+    out = {}
+    L16 = wl.large16()
+    name = "large16 16-512x4-8, 1024 of 262144 sub-boxes, H=50, alpha from the chord slopes (staged reverse sweep)"
+    prob = dataclasses.replace(L16.subset(np.arange(1024)), H=50)
+    r, res, _ = run(prob, 2, 0.0)
+    r.close()
+    if forward_rate:
+        res["forward_domain_steps_per_s"] = forward_rate
+        res["alpha_step_over_forward"] = res["domain_steps_per_s"] / forward_rate
+    out[name] = res
+    # from slopes 0.05 off the chord point, where the gradient moves V (over 50 steps the looser start
+    # makes the tube diverge, so this runs at H = 10)
+    p10 = dataclasses.replace(L16.subset(np.arange(1024)), H=10)
+    r = api.Reach(local).load(p10)
+    a0 = r.get_alpha()
+    r.close()
+    start = np.where((a0 > 0) & (a0 < 1), np.clip(a0 + 0.05, 0.0, 1.0), a0).astype(np.float32)
+    r, pert, _ = run(p10, 3, 0.0, start=start)
+    r.close()
+    out["large16 16-512x4-8, 1024 sub-boxes, H=10, alpha from chord slopes + 0.05 on unstable neurons"] = pert
+    # the previous engine, the fused reverse kernels out of global slabs, against the staged sweep
+    small = dataclasses.replace(L16.subset(np.arange(148)), H=10)
+    r, slab, _ = run(small, 2, 0.0, reverse=1)
+    r.close()
+    r, stg, _ = run(small, 2, 0.0)
+    r.close()
+    out["large16 16-512x4-8, 148 sub-boxes, H=10: staged vs fused slab reverse"] = {
+        "staged_domain_steps_per_s": stg["domain_steps_per_s"], "slab_domain_steps_per_s": slab["domain_steps_per_s"],
+        "staged_over_slab": stg["domain_steps_per_s"] / slab["domain_steps_per_s"]}
+    # branch domains with split multipliers (alpha + beta), batched vs one domain per call
+    name = "branch12 12-256x3-4, 4096 of 65536 branch domains, H=30, alpha+beta (staged reverse sweep)"
+    prob = wl.quadrotor_branch(only=np.arange(4096))
+    steps, lrb = 2, 0.005
+    r, res, t = run(prob, steps, lrb)
+    Vb = r.objective()
+    r.close()
+    sample = 4
+    tp, Vp = 0.0, []
+    for d in range(sample):
+        rr = api.Reach(local).load(prob.subset([d]))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        rr.optimize(steps, 0.1, lrb)
+        tp += time.perf_counter() - t1
+        Vp.append(rr.objective()[0])
+        rr.close()
+    res.update({"batched_domains_per_s": prob.D / t, "plain_domains_per_s": sample / tp, "plain_sample_domains": sample,
+                "batched_over_plain": (prob.D / t) / (sample / tp),
+                "max_rel_V_gap_batched_vs_plain": float(np.max(np.abs(np.array(Vp) - Vb[:sample]) / np.abs(Vb[:sample])))})
+    out[name] = res
     return out
 
 
@@ -282,12 +323,14 @@ def full_large16():
 
 
 def wide_refine(domains, horizon):
-    """One projected-gradient slope step (forward with tape, reverse sweep, update) on the first
-    `domains` sub-boxes of the 16-512x4-8 workload with horizon `horizon` (a profiling case)."""
+    """One projected-gradient slope step (keep-mode forward pass and staged reverse sweep, update) on
+    the first `domains` sub-boxes of the 16-512x4-8 workload with horizon `horizon` (a profiling case:
+    the GEMM launch shapes are the heuristic's, so no tuning trials appear in a launch list)."""
     import dataclasses
     from paper_2605_25346_b300 import api
     prob = dataclasses.replace(wl.large16().subset(np.arange(domains)), H=horizon)
     r = api.Reach(0).load(prob)
+    r.set_options(tuning=1)
     t0 = time.perf_counter()
     hist = r.optimize(1, 0.1, 0.0)
     torch.cuda.synchronize()
@@ -402,7 +445,9 @@ def measure_tpush(local, reps=5):
         rr.backward()
         gp = rr.shift_gradient()
         tp += time.perf_counter() - t1
-        assert np.allclose(gp[0], g[d], rtol=1e-6, atol=1e-9 * np.abs(g[d]).max())
+        # the same gradient (the staged sweep's GEMM launch shapes differ with the batch, which moves
+        # FP32 rounding by ~1e-7; the parity tolerance of gradients is 1e-4 of the largest entry)
+        assert np.abs(gp[0] - g[d]).max() <= 1e-4 * np.abs(g[d]).max()
         rr.close()
     out["tpush_mpc dV/du"] = {"samples_per_s_batched": prob.D / tb, "ms_per_gradient_batched": 1e3 * tb,
                               "samples_per_s_plain": sample / tp, "plain_sample": sample,
@@ -795,7 +840,7 @@ def main():
             extras["rigorous"] = measure_rigorous(local)
             extras["refinement"] = measure_refinement(local)
             extras["wide"] = measure_wide(local, tf32=tf32)
-            extras["wide_refinement"] = measure_wide_refinement(local)
+            extras["wide_refinement"] = measure_wide_refinement(local, forward_rate=value / world)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32(3xtf32)+f64", "data": "synthetic",

@@ -2418,13 +2418,13 @@ static size_t rev_store(const NetDesc& N, int Dc, bool tc_rev, RevStore* S, unsi
 }
 
 // Domains per chunk of the staged reverse sweep: the keep store, the adjoint scratch and the forward
-// scratch of a chunk within min(48 GiB, half the free memory, the memory cap left), at least one.
+// scratch of a chunk within min(96 GiB, half the free memory, the memory cap left), at least one.
 static int rev_chunk(dr_ctx* c, const NetDesc& N, bool tc_rev) {
     if (c->opt.chunk_domains > 0) return (int)std::min<int64_t>(std::min<int64_t>(c->opt.chunk_domains, c->D), 65535);
     if (c->capturing && c->wDc > 0) return c->wDc;  // a captured step repeats the plain step before it
     RevStore S;
     const size_t per = rev_store(N, 64, tc_rev, &S, nullptr) / 64 + wide_bytes_per_domain(N) + 4096;
-    size_t budget = size_t(48) << 30;
+    size_t budget = size_t(96) << 30;
     size_t free_b = 0, all_b = 0;
     if (cudaMemGetInfo(&free_b, &all_b) == cudaSuccess) budget = std::min(budget, (free_b + c->kscratch_bytes + c->wscratch_bytes) / 2);
     if (c->opt.mem_cap_bytes > 0)
