@@ -567,23 +567,65 @@ static bool persistent_gemm_usable() {
 
 // 128-column GEMMs with at least two tiles per SM run persistently (one CTA per SM, the epilogue of
 // one tile overlapped with the main loop of the next).
+// Clusters of `cs` CTAs (1 or 2): the CTAs of a cluster share the right operand's tile through a TMA
+// multicast (tc_gemm_persistent.cuh).  The grid is at most the co-resident clusters (queried once per
+// epilogue kind), so the kernel stays persistent.
 template <int EPI>
 static int launch_tc_gemm_persistent(dr_ctx* c, const CUtensorMap* m, float* C, int R, int K, int N, int ldc, int* err,
-                                     cudaStream_t st, const tc::ChainEpi& epi, int64_t tiles, int nsm) {
+                                     cudaStream_t st, const tc::ChainEpi& epi, int64_t tiles, int nsm, int cs = 2) {
     const int smem = tc::pp_smem_bytes();
     CUDA_TRY(c, cudaFuncSetAttribute(tc::k_tc_gemm_pp<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    const int grid = (int)std::min<int64_t>(tiles, nsm);
-    tc::k_tc_gemm_pp<EPI><<<grid, tc::kPersistThreads, smem, st>>>(m[0], m[1], m[2], m[3], C, R, K, N, ldc, err, epi);
-    CUDA_TRY(c, cudaGetLastError());
+    static int max_clusters = 0;  // co-resident clusters of two (-1: none)
+    if (cs == 2 && max_clusters == 0) {
+        if (c && c->capturing) {
+            cs = 1;  // never queried outside a capture: no query inside one
+        } else {
+            cudaLaunchConfig_t q = {};
+            q.gridDim = dim3((unsigned)(nsm & ~1));
+            q.blockDim = dim3(tc::kPersistThreads);
+            q.dynamicSmemBytes = smem;
+            cudaLaunchAttribute qa[1];
+            qa[0].id = cudaLaunchAttributeClusterDimension;
+            qa[0].val.clusterDim.x = 2;
+            qa[0].val.clusterDim.y = 1;
+            qa[0].val.clusterDim.z = 1;
+            q.attrs = qa;
+            q.numAttrs = 1;
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, tc::k_tc_gemm_pp<EPI>, &q) != cudaSuccess || n < 1) n = -1;
+            cudaGetLastError();
+            max_clusters = n;
+        }
+    }
+    if (cs == 2 && max_clusters < 1) cs = 1;  // no cluster launch here: every CTA loads both operands
+    const int64_t mtn = (R + tc::BM - 1) / tc::BM, ntn = (N + 127) / 128;
+    const int64_t ctiles = ((mtn + cs - 1) / cs) * ntn;
+    int64_t nclu = std::min<int64_t>(ctiles, cs == 2 ? max_clusters : nsm);
+    if (nclu < 1) nclu = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nclu * cs));
+    cfg.blockDim = dim3(tc::kPersistThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    CUDA_TRY(c, cudaLaunchKernelEx(&cfg, tc::k_tc_gemm_pp<EPI>, m[0], m[1], m[2], m[3], C, R, K, N, ldc, err, epi));
     if (c) c->launches++;
+    (void)tiles;
     return DR_OK;
 }
 
 // Launch shapes of the tensor-core GEMM (dr_options.tuning = 0 picks one per shape by timing them):
 // 0 = the heuristic (the persistent kernel for 128-column tiles with at least two tiles per SM, else
-// one 128 x tc_bn(N) tile per CTA), 1 = persistent 128 x 128, 2 = one 128 x 128 tile per CTA,
-// 3 = one 128 x 64 tile per CTA, 4 = one 128 x 32 tile per CTA.
-enum { kGemmHeuristic = 0, kGemmPersistent = 1, kGemmTile128 = 2, kGemmTile64 = 3, kGemmTile32 = 4 };
+// one 128 x tc_bn(N) tile per CTA), 1 = persistent 128 x 128 in clusters of two CTAs sharing the
+// right operand's tiles, 2 = one 128 x 128 tile per CTA, 3 = one 128 x 64 tile per CTA, 4 = one
+// 128 x 32 tile per CTA, 5 = persistent 128 x 128 without clusters.
+enum { kGemmHeuristic = 0, kGemmPersistent = 1, kGemmTile128 = 2, kGemmTile64 = 3, kGemmTile32 = 4, kGemmPersistent1 = 5 };
 
 static int tc_gemm_launch(dr_ctx* c, const float* Ah, const float* Al, const float* BTh, const float* BTl, float* C, int R,
                           int K, int N, int ldk, int ldc, int* err, cudaStream_t st, const tc::ChainEpi* epi, int* cls,
@@ -629,9 +671,12 @@ static int tuned_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* 
         }
     }
     if (c->capturing) return DR_OK;  // heuristic
-    int cand[4], nc = 0;
+    int cand[5], nc = 0;
     if (tc_bn(N) == 128) {
-        if (persistent_gemm_usable<0>() && persistent_gemm_usable<1>() && persistent_gemm_usable<2>()) cand[nc++] = kGemmPersistent;
+        if (persistent_gemm_usable<0>() && persistent_gemm_usable<1>() && persistent_gemm_usable<2>()) {
+            cand[nc++] = kGemmPersistent;
+            cand[nc++] = kGemmPersistent1;
+        }
         cand[nc++] = kGemmTile128;
     }
     if (N > 32) cand[nc++] = kGemmTile64;
@@ -646,7 +691,7 @@ static int tuned_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* 
         cudaEventDestroy(e0);
         return fail(c, DR_ERR_CUDA, "cudaEventCreate");
     }
-    float best = 0.f, ms[4] = {};
+    float best = 0.f, ms[5] = {};
     int pick = cand[0], rc = DR_OK;
     for (int q = 0; q < nc && rc == DR_OK; ++q) {
         for (int rep = 0; rep < 2 && rc == DR_OK; ++rep) {
@@ -719,6 +764,7 @@ static int tc_gemm_launch(dr_ctx* c, const float* Ah, const float* Al, const flo
     // the reverse chain level runs only on the persistent kernel, whose stages hold 128-row B boxes
     const int BN = (epi && epi->colpart) ? 128
                    : variant == kGemmTile64 ? 64 : variant == kGemmTile32 ? 32 : variant >= kGemmPersistent ? 128 : tc_bn(N);
+    const int ccs = variant == kGemmPersistent1 ? 1 : 2;  // cluster size of a persistent launch
     *bn_used = BN;
     CUtensorMap m[6];
     TRY(make_map_blocked(c, &m[0], Ah, R, ldk));
@@ -747,21 +793,21 @@ static int tc_gemm_launch(dr_ctx* c, const float* Ah, const float* Al, const flo
         if (tiles > 0x7fffffffll) return fail(c, DR_ERR_SHAPE, "too many tiles for one reverse GEMM");
         *bn_used = 128;
         *cls = DR_KT_GEMM_REVERSE;
-        return launch_tc_gemm_persistent<3>(c, m, C, R, K, N, ldc, err, st, e, tiles, sm_count());
+        return launch_tc_gemm_persistent<3>(c, m, C, R, K, N, ldc, err, st, e, tiles, sm_count(), ccs);
     }
     if (BN == 128 && variant != kGemmTile128) {
         const int nsm = sm_count();
         const int64_t tiles = ((int64_t)(R + tc::BM - 1) / tc::BM) * ((N + 127) / 128);
-        if ((variant == kGemmPersistent || tiles >= 2 * (int64_t)nsm) && tiles <= 0x7fffffffll) {
+        if ((variant == kGemmPersistent || variant == kGemmPersistent1 || tiles >= 2 * (int64_t)nsm) && tiles <= 0x7fffffffll) {
             if (!epi && persistent_gemm_usable<0>())
-                return launch_tc_gemm_persistent<0>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm);
+                return launch_tc_gemm_persistent<0>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm, ccs);
             if (epi && epi->W1 && persistent_gemm_usable<2>()) {
                 *cls = DR_KT_GEMM_FINAL;
-                return launch_tc_gemm_persistent<2>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm);
+                return launch_tc_gemm_persistent<2>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm, ccs);
             }
             if (epi && !epi->W1 && persistent_gemm_usable<1>()) {
                 *cls = DR_KT_GEMM_CHAIN;
-                return launch_tc_gemm_persistent<1>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm);
+                return launch_tc_gemm_persistent<1>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm, ccs);
             }
         }
     }
@@ -1079,7 +1125,7 @@ int dr_set_options(dr_ctx* c, const dr_options* o) {
     if (n.rigorous < 0 || n.rigorous > 1) return fail(c, DR_ERR_ARG, "rigorous %d out of range", n.rigorous);
     if (n.weight_grad < 0 || n.weight_grad > 1) return fail(c, DR_ERR_ARG, "weight_grad %d out of range", n.weight_grad);
     if (n.reverse < 0 || n.reverse > 2) return fail(c, DR_ERR_ARG, "reverse %d out of range", n.reverse);
-    if (n.tuning < 0 || (n.tuning >= 2 + kNumMultiVariants && (n.tuning < 101 || n.tuning > 104)))
+    if (n.tuning < 0 || (n.tuning >= 2 + kNumMultiVariants && (n.tuning < 101 || n.tuning > 105)))
         return fail(c, DR_ERR_ARG, "tuning %d out of range", n.tuning);
     if (n.timing && !c->opt.timing) c->kt_done.clear();  // timing switched on: the totals start from zero
     c->opt = n;

@@ -377,12 +377,21 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
     const int nk = (K + BK - 1) / BK;
     const int npc = (nk + kPromote - 1) / kPromote;  // partial buffer fills per tile
     const int ntn = (N + BN - 1) / BN;
-    const int tiles = ((R + BM - 1) / BM) * ntn;
+    // Launched in clusters of cs CTAs (cs = 1 or 2), the CTAs of a cluster take cs consecutive row
+    // tiles of the same column tile at the same time: the leader loads the shared right-operand tile
+    // once and multicasts it into every CTA's stage (half the right operand's traffic per SM at
+    // cs = 2), each CTA loads its own left-operand rows.  A stage is free again when every CTA of the
+    // cluster has consumed it: each MMA issuer's commit arrives on every CTA's `empty` barrier.
+    const int cs = (int)cluster_size(), crank = (int)cluster_rank();
+    const int nclu = gridDim.x / cs, cid = blockIdx.x / cs;
+    const uint16_t cmask = (uint16_t)((1u << cs) - 1u);
+    const int mtc = ((R + BM - 1) / BM + cs - 1) / cs;  // row-tile groups of the cluster
+    const int tiles = mtc * ntn;                          // cluster tiles (row-tile group, column tile)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], cs);
         }
         for (int p = 0; p < 4; ++p) {
             mbar_init(&pfull[p], 1);
@@ -400,7 +409,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     fence_before();
-    __syncthreads();
+    if (cs > 1) cluster_sync_all();  // every CTA's barriers exist before a peer signals them
+    else __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_holder;
     if (warp < 4) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsCtl));
@@ -410,8 +420,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
         // ---- TMA producer
         int q = 0;
         bool ok = true;
-        for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
-            const int mt = tile / ntn, n0 = (tile - mt * ntn) * BN;
+        for (int tile = cid; tile < tiles && ok; tile += nclu) {
+            const int mg = tile / ntn, n0 = (tile - mg * ntn) * BN, mt = mg * cs + crank;
             for (int kc = 0; kc < nk; ++kc, ++q) {
                 const int s = q % S;
                 if (q >= S && !mbar_wait(&empty[s], ((q / S) - 1) & 1)) {
@@ -427,10 +437,15 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
                 unsigned char* st = base + s * SB;
                 mbar_expect_tx(&full[s], SB);
                 const int ay = (mt * nk + kc) * BM;
-                tma_load_2d(st, &mAh, &full[s], 0, ay);
+                tma_load_2d(st, &mAh, &full[s], 0, ay);  // row tiles past R read zeros
                 tma_load_2d(st + BM * BK * 4, &mAl, &full[s], 0, ay);
-                tma_load_2d(st + 2 * BM * BK * 4, &mBh, &full[s], kc * BK, n0);
-                tma_load_2d(st + 2 * BM * BK * 4 + BN * BK * 4, &mBl, &full[s], kc * BK, n0);
+                if (cs == 1) {
+                    tma_load_2d(st + 2 * BM * BK * 4, &mBh, &full[s], kc * BK, n0);
+                    tma_load_2d(st + 2 * BM * BK * 4 + BN * BK * 4, &mBl, &full[s], kc * BK, n0);
+                } else if (crank == 0) {
+                    tma_load_2d_mc(st + 2 * BM * BK * 4, &mBh, &full[s], kc * BK, n0, cmask);
+                    tma_load_2d_mc(st + 2 * BM * BK * 4 + BN * BK * 4, &mBl, &full[s], kc * BK, n0, cmask);
+                }
             }
         }
         for (int k = (q > S ? q - S : 0); k < q; ++k) {  // every issued stage lands before exit
@@ -439,11 +454,21 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
                 break;
             }
         }
+        if (cs > 1) {
+            // every CTA's release of the last use of each stage has arrived here, so no peer signals
+            // this CTA's barriers after it exits
+            for (int k = (q > S ? q - S : 0); k < q; ++k) {
+                if (!mbar_wait(&empty[k % S], (k / S) & 1)) {
+                    atomicExch(err, 1);
+                    break;
+                }
+            }
+        }
     } else if (threadIdx.x == 32) {
         // ---- MMA issuer
         int q = 0, lt = 0;
         bool ok = true;
-        for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++lt) {
+        for (int tile = cid; tile < tiles && ok; tile += nclu, ++lt) {
             const int g = lt & 1, kg = lt >> 1;
             for (int kc = 0; kc < nk; ++kc, ++q) {
                 const int s = q % S, ps = kc / kPromote, r = ps & 1, p = 2 * g + r;
@@ -472,7 +497,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
                     const uint64_t o = (uint64_t)(kk * 32) >> 4;
                     mma_tf32(d, ah + o, bh + o, IDESC, 1u);
                 }
-                mma_commit(&empty[s]);
+                if (cs == 1) mma_commit(&empty[s]);
+                else mma_commit_mc(&empty[s], cmask);
                 if (last) mma_commit(&pfull[p]);
             }
         }
@@ -485,9 +511,9 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
         const uint32_t lane_base = (uint32_t)(sub * 32) << 16;
         bool ok = true;
         int lt = g;
-        for (int tile = blockIdx.x + g * gridDim.x; tile < tiles; tile += 2 * gridDim.x, lt += 2) {
+        for (int tile = cid + g * nclu; tile < tiles; tile += 2 * nclu, lt += 2) {
             const int kg = lt >> 1;
-            const int mt = tile / ntn, m0 = mt * BM, n0 = (tile - mt * ntn) * BN;
+            const int mg = tile / ntn, mt = mg * cs + crank, m0 = mt * BM, n0 = (tile - mg * ntn) * BN;
             bool uniform = false;
             if constexpr (EPI != 0) {
                 group_bar(g);  // the group's previous tile no longer reads the tables
@@ -579,7 +605,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
         }
     }
     fence_before();
-    __syncthreads();
+    if (cs > 1) cluster_sync_all();  // no CTA leaves while a peer may still write its stages
+    else __syncthreads();
     if (warp == 1) {
         __syncwarp();
         fence_after();
