@@ -175,7 +175,7 @@ def measure_wide_refinement(local, forward_rate=None):
     # 10-step and a 2-step call
     name = "large16 16-512x4-8, 1024 of 262144 sub-boxes, H=50, 10 alpha steps from the chord slopes (staged reverse sweep)"
     prob = dataclasses.replace(L16.subset(np.arange(1024)), H=50)
-    r, res, t10 = run(prob, 10, 0.0)
+    r, res, t10 = run(prob, 10, 0.0)  # the chord slopes are a local minimum of V here: V barely moves
     r.close()
     r, _, t2 = run(prob, 2, 0.0)
     r.close()
@@ -190,16 +190,6 @@ def measure_wide_refinement(local, forward_rate=None):
         res["forward_domain_steps_per_s"] = forward_rate
         res["alpha_step_over_forward"] = res["domain_steps_per_s"] / forward_rate
     out[name] = res
-    # from slopes 0.05 off the chord point, where the gradient moves V (over 50 steps the looser start
-    # makes the tube diverge, so this runs at H = 10)
-    p10 = dataclasses.replace(L16.subset(np.arange(1024)), H=10)
-    r = api.Reach(local).load(p10)
-    a0 = r.get_alpha()
-    r.close()
-    start = np.where((a0 > 0) & (a0 < 1), np.clip(a0 + 0.05, 0.0, 1.0), a0).astype(np.float32)
-    r, pert, _ = run(p10, 3, 0.0, start=start)
-    r.close()
-    out["large16 16-512x4-8, 1024 sub-boxes, H=10, alpha from chord slopes + 0.05 on unstable neurons"] = pert
     # the previous engine, the fused reverse kernels out of global slabs, against the staged sweep
     small = dataclasses.replace(L16.subset(np.arange(148)), H=10)
     r, slab, _ = run(small, 2, 0.0, reverse=1)
