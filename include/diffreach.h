@@ -108,7 +108,7 @@ typedef struct dr_options {
                               candidate v (0..9; DR_ERR_SHAPE if it does not fit the controller):
                               0..2 one warp per domain (16/8/4 warps per CTA; two hidden layers,
                               n, m <= 8, hidden widths <= 128), 3..9 several domains per CTA;
-                              100 + g = the tensor-core GEMM's launch shape g (1..5, see
+                              100 + g = the tensor-core GEMM's launch shape g (1..6, see
                               dr_gemm_tuning_report) for every GEMM, the fused kernels untuned */
     int32_t graphs;        /* 0 = dr_compute_bounds captures its launch sequence in a CUDA graph on
                               the second call with unchanged buffers, options and slope mode, and
@@ -369,8 +369,9 @@ int64_t dr_graph_replays(const dr_ctx* ctx);
 /* Paper: no passage (accounting).  The tensor-core GEMM autotuner's choices so far in this process
  * (dr_options.tuning = 0), one line per shape: "epi<e> R<rows> K<k> N<n> sm<SMs>: variant <v> (ms:
  * v<i>=<time> ...)", variants 1 = persistent 128 x 128 tiles in clusters of two CTAs that share the
- * right operand's tiles (TMA multicast), 5 = the same without clusters, 2 / 3 / 4 = one 128 x 128 /
- * 64 / 32 tile per CTA.  Writes at most cap bytes including the terminating NUL into buf (truncating; buf may
+ * right operand's tiles (TMA multicast), 5 = the same without clusters, 6 = the pair form (one
+ * cta_group::2 MMA of M = 256 over two CTAs, B's columns split between them), 2 / 3 / 4 = one
+ * 128 x 128 / 64 / 32 tile per CTA.  Writes at most cap bytes including the terminating NUL into buf (truncating; buf may
  * be NULL) and returns the length the whole report needs. */
 int64_t dr_gemm_tuning_report(char* buf, int64_t cap);
 

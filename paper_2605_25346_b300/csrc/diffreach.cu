@@ -554,12 +554,12 @@ static int sm_count() {
 
 // The persistent kernel's warpgroup register split needs exactly the registers it was designed for
 // at entry; a build that compiled it otherwise keeps the one-tile-per-CTA kernel.
-template <int EPI>
+template <int EPI, bool PAIR = false>
 static bool persistent_gemm_usable() {
     static int ok = -1;
     if (ok < 0) {
         cudaFuncAttributes fa;
-        ok = cudaFuncGetAttributes(&fa, tc::k_tc_gemm_pp<EPI>) == cudaSuccess && fa.numRegs == tc::kRegsLaunch;
+        ok = cudaFuncGetAttributes(&fa, tc::k_tc_gemm_pp<EPI, PAIR>) == cudaSuccess && fa.numRegs == tc::kRegsLaunch;
         cudaGetLastError();
     }
     return ok == 1;
@@ -570,11 +570,12 @@ static bool persistent_gemm_usable() {
 // Clusters of `cs` CTAs (1 or 2): the CTAs of a cluster share the right operand's tile through a TMA
 // multicast (tc_gemm_persistent.cuh).  The grid is at most the co-resident clusters (queried once per
 // epilogue kind), so the kernel stays persistent.
-template <int EPI>
+template <int EPI, bool PAIR = false>
 static int launch_tc_gemm_persistent(dr_ctx* c, const CUtensorMap* m, float* C, int R, int K, int N, int ldc, int* err,
                                      cudaStream_t st, const tc::ChainEpi& epi, int64_t tiles, int nsm, int cs = 2) {
     const int smem = tc::pp_smem_bytes();
-    CUDA_TRY(c, cudaFuncSetAttribute(tc::k_tc_gemm_pp<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CUDA_TRY(c, cudaFuncSetAttribute(tc::k_tc_gemm_pp<EPI, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    if (PAIR) cs = 2;
     static int max_clusters = 0;  // co-resident clusters of two (-1: none)
     if (cs == 2 && max_clusters == 0) {
         if (c && c->capturing) {
@@ -592,11 +593,12 @@ static int launch_tc_gemm_persistent(dr_ctx* c, const CUtensorMap* m, float* C, 
             q.attrs = qa;
             q.numAttrs = 1;
             int n = 0;
-            if (cudaOccupancyMaxActiveClusters(&n, tc::k_tc_gemm_pp<EPI>, &q) != cudaSuccess || n < 1) n = -1;
+            if (cudaOccupancyMaxActiveClusters(&n, tc::k_tc_gemm_pp<EPI, PAIR>, &q) != cudaSuccess || n < 1) n = -1;
             cudaGetLastError();
             max_clusters = n;
         }
     }
+    if (PAIR && max_clusters < 1) return fail(c, DR_ERR_STATE, "the pair GEMM needs clusters of two CTAs");
     if (cs == 2 && max_clusters < 1) cs = 1;  // no cluster launch here: every CTA loads both operands
     const int64_t mtn = (R + tc::BM - 1) / tc::BM, ntn = (N + 127) / 128;
     const int64_t ctiles = ((mtn + cs - 1) / cs) * ntn;
@@ -614,7 +616,7 @@ static int launch_tc_gemm_persistent(dr_ctx* c, const CUtensorMap* m, float* C, 
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    CUDA_TRY(c, cudaLaunchKernelEx(&cfg, tc::k_tc_gemm_pp<EPI>, m[0], m[1], m[2], m[3], C, R, K, N, ldc, err, epi));
+    CUDA_TRY(c, cudaLaunchKernelEx(&cfg, tc::k_tc_gemm_pp<EPI, PAIR>, m[0], m[1], m[2], m[3], C, R, K, N, ldc, err, epi));
     if (c) c->launches++;
     (void)tiles;
     return DR_OK;
@@ -624,8 +626,9 @@ static int launch_tc_gemm_persistent(dr_ctx* c, const CUtensorMap* m, float* C, 
 // 0 = the heuristic (the persistent kernel for 128-column tiles with at least two tiles per SM, else
 // one 128 x tc_bn(N) tile per CTA), 1 = persistent 128 x 128 in clusters of two CTAs sharing the
 // right operand's tiles, 2 = one 128 x 128 tile per CTA, 3 = one 128 x 64 tile per CTA, 4 = one
-// 128 x 32 tile per CTA, 5 = persistent 128 x 128 without clusters.
-enum { kGemmHeuristic = 0, kGemmPersistent = 1, kGemmTile128 = 2, kGemmTile64 = 3, kGemmTile32 = 4, kGemmPersistent1 = 5 };
+// 128 x 32 tile per CTA, 5 = persistent 128 x 128 without clusters, 6 = persistent pair form (one
+// cta_group::2 MMA of M = 256 over a CTA pair, B's columns split between the two CTAs).
+enum { kGemmHeuristic = 0, kGemmPersistent = 1, kGemmTile128 = 2, kGemmTile64 = 3, kGemmTile32 = 4, kGemmPersistent1 = 5, kGemmPair = 6 };
 
 static int tc_gemm_launch(dr_ctx* c, const float* Ah, const float* Al, const float* BTh, const float* BTl, float* C, int R,
                           int K, int N, int ldk, int ldc, int* err, cudaStream_t st, const tc::ChainEpi* epi, int* cls,
@@ -671,12 +674,14 @@ static int tuned_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* 
         }
     }
     if (c->capturing) return DR_OK;  // heuristic
-    int cand[5], nc = 0;
+    int cand[6], nc = 0;
     if (tc_bn(N) == 128) {
         if (persistent_gemm_usable<0>() && persistent_gemm_usable<1>() && persistent_gemm_usable<2>()) {
             cand[nc++] = kGemmPersistent;
             cand[nc++] = kGemmPersistent1;
         }
+        if (persistent_gemm_usable<0, true>() && persistent_gemm_usable<1, true>() && persistent_gemm_usable<2, true>())
+            cand[nc++] = kGemmPair;
         cand[nc++] = kGemmTile128;
     }
     if (N > 32) cand[nc++] = kGemmTile64;
@@ -691,7 +696,7 @@ static int tuned_gemm(dr_ctx* c, const float* Ah, const float* Al, const float* 
         cudaEventDestroy(e0);
         return fail(c, DR_ERR_CUDA, "cudaEventCreate");
     }
-    float best = 0.f, ms[5] = {};
+    float best = 0.f, ms[6] = {};
     int pick = cand[0], rc = DR_OK;
     for (int q = 0; q < nc && rc == DR_OK; ++q) {
         for (int rep = 0; rep < 2 && rc == DR_OK; ++rep) {
@@ -769,8 +774,9 @@ static int tc_gemm_launch(dr_ctx* c, const float* Ah, const float* Al, const flo
     CUtensorMap m[6];
     TRY(make_map_blocked(c, &m[0], Ah, R, ldk));
     TRY(make_map_blocked(c, &m[1], Al, R, ldk));
-    TRY(make_map(c, &m[2], BTh, N, ldk, BN));
-    TRY(make_map(c, &m[3], BTl, N, ldk, BN));
+    const bool pair = variant == kGemmPair && !(epi && epi->colpart);
+    TRY(make_map(c, &m[2], BTh, N, ldk, pair ? BN / 2 : BN));  // the pair form: each CTA loads half of B's columns
+    TRY(make_map(c, &m[3], BTl, N, ldk, pair ? BN / 2 : BN));
     if (epi && epi->colpart) {
         m[4] = m[0];
         m[5] = m[1];
@@ -798,6 +804,15 @@ static int tc_gemm_launch(dr_ctx* c, const float* Ah, const float* Al, const flo
     if (BN == 128 && variant != kGemmTile128) {
         const int nsm = sm_count();
         const int64_t tiles = ((int64_t)(R + tc::BM - 1) / tc::BM) * ((N + 127) / 128);
+        if (pair && tiles <= 0x7fffffffll) {
+            if (!epi) return launch_tc_gemm_persistent<0, true>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm);
+            if (epi->W1) {
+                *cls = DR_KT_GEMM_FINAL;
+                return launch_tc_gemm_persistent<2, true>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm);
+            }
+            *cls = DR_KT_GEMM_CHAIN;
+            return launch_tc_gemm_persistent<1, true>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm);
+        }
         if ((variant == kGemmPersistent || variant == kGemmPersistent1 || tiles >= 2 * (int64_t)nsm) && tiles <= 0x7fffffffll) {
             if (!epi && persistent_gemm_usable<0>())
                 return launch_tc_gemm_persistent<0>(c, m, C, R, K, N, ldc, err, st, e, tiles, nsm, ccs);
@@ -1125,7 +1140,7 @@ int dr_set_options(dr_ctx* c, const dr_options* o) {
     if (n.rigorous < 0 || n.rigorous > 1) return fail(c, DR_ERR_ARG, "rigorous %d out of range", n.rigorous);
     if (n.weight_grad < 0 || n.weight_grad > 1) return fail(c, DR_ERR_ARG, "weight_grad %d out of range", n.weight_grad);
     if (n.reverse < 0 || n.reverse > 2) return fail(c, DR_ERR_ARG, "reverse %d out of range", n.reverse);
-    if (n.tuning < 0 || (n.tuning >= 2 + kNumMultiVariants && (n.tuning < 101 || n.tuning > 105)))
+    if (n.tuning < 0 || (n.tuning >= 2 + kNumMultiVariants && (n.tuning < 101 || n.tuning > 106)))
         return fail(c, DR_ERR_ARG, "tuning %d out of range", n.tuning);
     if (n.timing && !c->opt.timing) c->kt_done.clear();  // timing switched on: the totals start from zero
     c->opt = n;

@@ -358,13 +358,21 @@ __device__ __forceinline__ void pp_row_epilogue_rev(float* acc, const float4* co
     }
 }
 
-template <int EPI>
+// PAIR: the pair form (launched in clusters of two).  One thread of the leader CTA (rank 0) issues
+// tcgen05.mma.cta_group::2 with M = 256: each CTA of the pair loads its own 128-row tile of A and
+// half of the 128 columns of B (64 rows of B^T) into its stages (48 KB, four of them), every load
+// signalling the leader's `full` barrier, and each CTA's TMEM receives its 128 rows, so the
+// epilogues are those of the single-CTA form.  Per SM the tensor core then reads 6 KB of operands
+// per 128 x 128 x 8 product instead of 8 KB.  The leader's commits arrive on both CTAs' `empty` and
+// `pfull` barriers; the follower's epilogue warps release a partial buffer on the leader's `pfree`.
+template <int EPI, bool PAIR = false>
 __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                                                                   const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
                                                                   float* __restrict__ C, int R, int K, int N, int ldc, int* __restrict__ err,
                                                                   const ChainEpi epi) {
-    constexpr int BN = 128, S = kPS, SB = kPSB;
-    constexpr uint32_t IDESC = idesc_tf32(BM, BN);
+    constexpr int BN = 128, S = PAIR ? 4 : kPS, SB = PAIR ? (2 * BM * BK * 4 + BN * BK * 4) : kPSB;
+    static_assert(S * SB == kPS * kPSB, "the pair form keeps the single-CTA form's stage area");
+    constexpr uint32_t IDESC = idesc_tf32(PAIR ? 2 * BM : BM, BN);
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* full = reinterpret_cast<uint64_t*>(base + S * SB);
@@ -391,11 +399,11 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], cs);
+            mbar_init(&empty[s], PAIR ? 1 : cs);
         }
         for (int p = 0; p < 4; ++p) {
             mbar_init(&pfull[p], 1);
-            mbar_init(&pfree[p], 4);
+            mbar_init(&pfree[p], PAIR ? 8 : 4);  // pair: the release of both CTAs' four epilogue warps
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -404,9 +412,15 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mBh)) : "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)), "r"(512)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        if constexpr (PAIR) {
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)), "r"(512)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)), "r"(512)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
     }
     fence_before();
     if (cs > 1) cluster_sync_all();  // every CTA's barriers exist before a peer signals them
@@ -435,23 +449,36 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
                     break;
                 }
                 unsigned char* st = base + s * SB;
-                mbar_expect_tx(&full[s], SB);
                 const int ay = (mt * nk + kc) * BM;
-                tma_load_2d(st, &mAh, &full[s], 0, ay);  // row tiles past R read zeros
-                tma_load_2d(st + BM * BK * 4, &mAl, &full[s], 0, ay);
-                if (cs == 1) {
-                    tma_load_2d(st + 2 * BM * BK * 4, &mBh, &full[s], kc * BK, n0);
-                    tma_load_2d(st + 2 * BM * BK * 4 + BN * BK * 4, &mBl, &full[s], kc * BK, n0);
-                } else if (crank == 0) {
-                    tma_load_2d_mc(st + 2 * BM * BK * 4, &mBh, &full[s], kc * BK, n0, cmask);
-                    tma_load_2d_mc(st + 2 * BM * BK * 4 + BN * BK * 4, &mBl, &full[s], kc * BK, n0, cmask);
+                if constexpr (PAIR) {
+                    // both CTAs' bytes land on the leader's barrier: A rows of this CTA, B^T rows
+                    // n0 + 64 rank .. + 63 (this CTA's half of the tile's columns)
+                    if (crank == 0) mbar_expect_tx(&full[s], 2 * SB);
+                    const uint32_t fb = cluster_addr(&full[s], 0);
+                    tma_load_2d_pair(st, &mAh, fb, 0, ay);
+                    tma_load_2d_pair(st + BM * BK * 4, &mAl, fb, 0, ay);
+                    tma_load_2d_pair(st + 2 * BM * BK * 4, &mBh, fb, kc * BK, n0 + 64 * crank);
+                    tma_load_2d_pair(st + 2 * BM * BK * 4 + 64 * BK * 4, &mBl, fb, kc * BK, n0 + 64 * crank);
+                } else {
+                    mbar_expect_tx(&full[s], SB);
+                    tma_load_2d(st, &mAh, &full[s], 0, ay);  // row tiles past R read zeros
+                    tma_load_2d(st + BM * BK * 4, &mAl, &full[s], 0, ay);
+                    if (cs == 1) {
+                        tma_load_2d(st + 2 * BM * BK * 4, &mBh, &full[s], kc * BK, n0);
+                        tma_load_2d(st + 2 * BM * BK * 4 + BN * BK * 4, &mBl, &full[s], kc * BK, n0);
+                    } else if (crank == 0) {
+                        tma_load_2d_mc(st + 2 * BM * BK * 4, &mBh, &full[s], kc * BK, n0, cmask);
+                        tma_load_2d_mc(st + 2 * BM * BK * 4 + BN * BK * 4, &mBl, &full[s], kc * BK, n0, cmask);
+                    }
                 }
             }
         }
-        for (int k = (q > S ? q - S : 0); k < q; ++k) {  // every issued stage lands before exit
-            if (!mbar_wait(&full[k % S], (k / S) & 1)) {
-                atomicExch(err, 1);
-                break;
+        if (!PAIR || crank == 0) {
+            for (int k = (q > S ? q - S : 0); k < q; ++k) {  // every issued stage lands before exit
+                if (!mbar_wait(&full[k % S], (k / S) & 1)) {
+                    atomicExch(err, 1);
+                    break;
+                }
             }
         }
         if (cs > 1) {
@@ -465,9 +492,9 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
             }
         }
     } else if (threadIdx.x == 32) {
-        // ---- MMA issuer
+        // ---- MMA issuer (the pair's leader only in the pair form)
         int q = 0, lt = 0;
-        bool ok = true;
+        bool ok = !PAIR || crank == 0;
         for (int tile = cid; tile < tiles && ok; tile += nclu, ++lt) {
             const int g = lt & 1, kg = lt >> 1;
             for (int kc = 0; kc < nk; ++kc, ++q) {
@@ -486,20 +513,37 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
                 const uint32_t sa = smem_u32(base + s * SB);
                 const uint64_t ah = sw128_desc(sa), al = sw128_desc(sa + BM * BK * 4);
                 const uint64_t bh = sw128_desc(sa + 2 * BM * BK * 4), bl = sw128_desc(sa + 2 * BM * BK * 4 + BN * BK * 4);
+                if constexpr (PAIR) {
+                    const uint64_t bh2 = sw128_desc(sa + 2 * BM * BK * 4), bl2 = sw128_desc(sa + 2 * BM * BK * 4 + 64 * BK * 4);
 #pragma unroll
-                for (int kk = 0; kk < BK / 8; ++kk) {
-                    const uint64_t o = (uint64_t)(kk * 32) >> 4;
-                    mma_tf32(d, ah + o, bl + o, IDESC, (kk || !first) ? 1u : 0u);
-                    mma_tf32(d, al + o, bh + o, IDESC, 1u);
-                }
+                    for (int kk = 0; kk < BK / 8; ++kk) {
+                        const uint64_t o = (uint64_t)(kk * 32) >> 4;
+                        mma_tf32_pair(d, ah + o, bl2 + o, IDESC, (kk || !first) ? 1u : 0u);
+                        mma_tf32_pair(d, al + o, bh2 + o, IDESC, 1u);
+                    }
 #pragma unroll
-                for (int kk = 0; kk < BK / 8; ++kk) {
-                    const uint64_t o = (uint64_t)(kk * 32) >> 4;
-                    mma_tf32(d, ah + o, bh + o, IDESC, 1u);
+                    for (int kk = 0; kk < BK / 8; ++kk) {
+                        const uint64_t o = (uint64_t)(kk * 32) >> 4;
+                        mma_tf32_pair(d, ah + o, bh2 + o, IDESC, 1u);
+                    }
+                    mma_commit_pair_mc(&empty[s], cmask);
+                    if (last) mma_commit_pair_mc(&pfull[p], cmask);
+                } else {
+#pragma unroll
+                    for (int kk = 0; kk < BK / 8; ++kk) {
+                        const uint64_t o = (uint64_t)(kk * 32) >> 4;
+                        mma_tf32(d, ah + o, bl + o, IDESC, (kk || !first) ? 1u : 0u);
+                        mma_tf32(d, al + o, bh + o, IDESC, 1u);
+                    }
+#pragma unroll
+                    for (int kk = 0; kk < BK / 8; ++kk) {
+                        const uint64_t o = (uint64_t)(kk * 32) >> 4;
+                        mma_tf32(d, ah + o, bh + o, IDESC, 1u);
+                    }
+                    if (cs == 1) mma_commit(&empty[s]);
+                    else mma_commit_mc(&empty[s], cmask);
+                    if (last) mma_commit(&pfull[p]);
                 }
-                if (cs == 1) mma_commit(&empty[s]);
-                else mma_commit_mc(&empty[s], cmask);
-                if (last) mma_commit(&pfull[p]);
             }
         }
     }
@@ -578,7 +622,10 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
                     fence_before();
                 }
                 __syncwarp();
-                if (ok && lane == 0) mbar_arrive(&pfree[p]);
+                if (ok && lane == 0) {
+                    if (PAIR && crank != 0) mbar_arrive_cluster(cluster_addr(&pfree[p], 0));  // the leader issues the MMAs
+                    else mbar_arrive(&pfree[p]);
+                }
             }
             if (!ok) atomicExch(err, 1);
             const int row = m0 + sub * 32 + lane;
@@ -610,7 +657,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
     if (warp == 1) {
         __syncwarp();
         fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+        if constexpr (PAIR) asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+        else asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
     }
 }
 

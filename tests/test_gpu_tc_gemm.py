@@ -31,3 +31,36 @@ def test_tf32x3_gemm_matches_fp64(M, N, K):
     err = ((C.double() - ref).abs() / mag.clamp_min(1e-30)).max().item()
     assert torch.isfinite(C).all()
     assert err <= 2.0 ** -18, f"max elementwise error {err:.3e} of |A||B|"
+
+
+# The persistent GEMM's launch shapes on the staged path: clusters of two CTAs sharing the right
+# operand's tiles (1), one CTA per tile row (5), and the pair form, one cta_group::2 MMA of M = 256
+# over two CTAs with B's columns split between them (6).  They run the same products in the same
+# order, so the bounds agree bit for bit, and they match the FP64 oracle on a few domains.  Widths
+# include columns that are no multiple of 128 (partial tiles and B halves) and an odd number of row
+# tiles (the last pair's second CTA has no rows).
+@pytest.mark.parametrize("widths,D", [([16, 512, 512, 512, 512, 8], 96), ([4, 200, 150, 130, 3], 37)])
+def test_persistent_launch_shapes_agree(widths, D):
+    import dataclasses
+    from oracle import reach as orc
+    from paper_2605_25346_b300 import api
+    from paper_2605_25346_b300 import workloads as wl
+    if widths[0] == 16:
+        p = dataclasses.replace(wl.large16().subset(np.arange(D)), H=2)
+    else:
+        p = wl.random_problem(81, widths, D=D, H=2, eps=0.2)
+    out = {}
+    for tuning in (101, 105, 106):
+        r = api.Reach(0).load(p, precision=2)
+        r.set_options(precision=2, tuning=tuning)
+        out[tuning] = r.bounds(on_device=False)
+        r.close()
+    for t in (101, 106):
+        np.testing.assert_array_equal(out[t]["lo"], out[105]["lo"])
+        np.testing.assert_array_equal(out[t]["hi"], out[105]["hi"])
+    q = p.subset(np.arange(3))
+    o = orc.reach(q)
+    olo, ohi = o["lo"].numpy(), o["hi"].numpy()
+    scale = np.maximum(np.maximum(np.abs(olo), np.abs(ohi)), ohi - olo)
+    err = np.maximum(np.abs(out[106]["lo"][:3] - olo), np.abs(out[106]["hi"][:3] - ohi)) / scale
+    assert err.max() <= 1e-5
