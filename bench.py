@@ -45,7 +45,7 @@ FUSED_TRAFFIC_BYTES = 548864
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch over R = 65,536 rows (ncu, small case),
 # divided by R.  The traffic grows with R (the left operand is read once; the chain level also writes
 # the next one once), so a full launch's traffic is this times its rows.
-GEMM_TRAFFIC_PER_ROW = {"final": (271.4e6 + 18.45e6) / 65536, "chain": (271.2e6 + 226.25e6) / 65536}
+GEMM_TRAFFIC_PER_ROW = {"final": (271.52e6 + 19.82e6) / 65536, "chain": (271.67e6 + 227.17e6) / 65536}
 # launches of at least this many stacked rows are the full-size ones (hidden-layer targets:
 # domains x 512 rows); the controller-output target's launches have domains x 8 rows
 BIG_GEMM_ROWS = 65536
@@ -341,13 +341,16 @@ def wide_refine(domains, horizon):
     r.close()
 
 
-def wide_pass(domains, horizon):
+def wide_pass(domains, horizon, gemm_shape=0):
     """Two bounds passes of the staged path on the first `domains` sub-boxes of the 16-512x4-8
-    workload with horizon `horizon` (a small case for kernel profiling)."""
+    workload with horizon `horizon` (a small case for kernel profiling); `gemm_shape` > 0 forces the
+    tensor-core GEMM's launch shape (dr_options.tuning = 100 + shape)."""
     import dataclasses
     from paper_2605_25346_b300 import api
     prob = dataclasses.replace(wl.large16().subset(np.arange(domains)), H=horizon)
     r = api.Reach(0).load(prob)
+    if gemm_shape:
+        r.set_options(tuning=100 + gemm_shape)
     for _ in range(2):
         r.bounds(on_device=True)
     torch.cuda.synchronize()
@@ -665,11 +668,13 @@ def main():
                     help="one staged pass over all 262,144 sub-boxes of the 16-512x4-8 workload (H = 50)")
     ap.add_argument("--tf32-probe", action="store_true",
                     help="only the cuBLAS TF32 8192^3 throughput probe (the denominator of the 3xTF32 path)")
+    ap.add_argument("--gemm-shape", type=int, default=0, choices=range(0, 7),
+                    help="with --wide-pass: force the tensor-core GEMM launch shape (1..6, see dr_gemm_tuning_report)")
     ap.add_argument("--wide-pass", nargs=2, type=int, metavar=("DOMAINS", "H"), default=None,
                     help="profiling aid: run two staged tensor-core passes on a 16-512x4-8 sample and exit")
     args = ap.parse_args()
     if args.wide_pass:
-        return wide_pass(*args.wide_pass)
+        return wide_pass(*args.wide_pass, gemm_shape=args.gemm_shape)
     if args.wide_refine:
         return wide_refine(*args.wide_refine)
     if args.full_large16:
