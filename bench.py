@@ -45,7 +45,7 @@ FUSED_TRAFFIC_BYTES = 548864
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch over R = 65,536 rows (ncu, small case),
 # divided by R.  The traffic grows with R (the left operand is read once; the chain level also writes
 # the next one once), so a full launch's traffic is this times its rows.
-GEMM_TRAFFIC_PER_ROW = {"final": (271.52e6 + 19.82e6) / 65536, "chain": (271.67e6 + 227.17e6) / 65536}
+GEMM_TRAFFIC_PER_ROW = {"final": (271.55e6 + 19.45e6) / 65536, "chain": (271.54e6 + 226.41e6) / 65536}
 # launches of at least this many stacked rows are the full-size ones (hidden-layer targets:
 # domains x 512 rows); the controller-output target's launches have domains x 8 rows
 BIG_GEMM_ROWS = 65536

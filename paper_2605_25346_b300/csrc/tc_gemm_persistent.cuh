@@ -4,9 +4,20 @@
 // the tensor cores already work on the next tile for the other group.
 //
 //   warp 0 lane 0  TMA producer over all tiles' 32-wide K chunks (three-stage ring)
-//   warp 1         TMEM owner (512 columns = 2 groups x 2 partial buffers x 128); lane 0 issues the
-//                  MMAs, tile j into group j % 2's buffers, alternating per fill (kPromote chunks)
-//   warps 2, 3     idle (they complete the first warpgroup for the register split)
+//   warp 1         TMEM owner (512 columns = 2 groups x 2 partial buffers x 128)
+//   warps 1, 2     lane 0 of each issues MMAs: tile j goes into group j % 2's buffers, alternating
+//                  per fill (kPromote chunks); warp 1 issues the even fills, warp 2 the odd ones
+//   warp 3         idle (it completes the first warpgroup for the register split)
+//
+// Two issuers: a tcgen05.mma of 128 x 128 x 8 (TF32) keeps the tensor pipe busy for only 64 cycles,
+// and the pipe holds almost no queued work behind it, so any time the issuing thread spends between
+// MMAs (a barrier test, index arithmetic, losing issue slots to the epilogue warps on its
+// sub-partition) is idle tensor time.  With the fills split between two threads in different
+// warps, one thread's MMAs run while the other waits for its next stage; each thread owns its own
+// partial buffers (fill parity), and its commits track only its own MMAs.  Each stage has one
+// `full` barrier per issuer, signalled by the chunks that issuer consumes: a thread then tests only
+// phases of its own chunks, in order, and no barrier can run two phases ahead of the thread waiting
+// on it (one barrier shared by both would, whenever one thread lags the other).
 //   warps 4..7     epilogue group 0 (tiles 0, 2, 4, ... of this CTA), warps 8..11 group 1; warp w
 //                  reads TMEM lane quadrant w % 4 and holds that quadrant's rows x 128 columns
 //
@@ -375,12 +386,13 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
     constexpr uint32_t IDESC = idesc_tf32(PAIR ? 2 * BM : BM, BN);
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* full = reinterpret_cast<uint64_t*>(base + S * SB);
-    uint64_t* empty = full + S;
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + S * SB);  // [2][S] stage landed, per MMA issuer
+    uint64_t* empty = full + 2 * S;
     uint64_t* pfull = empty + S;  // [4] buffer ready (MMA commit)
     uint64_t* pfree = pfull + 4;  // [4] buffer consumed (the owning group's 4 warps)
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(pfree + 4);
     int* abort_flag = reinterpret_cast<int*>(tmem_holder + 1);
+    static_assert((3 * S + 8) * 8 + 8 <= pp_coltab_offset() - kPS * kPSB, "barriers fit their area");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = (K + BK - 1) / BK;
     const int npc = (nk + kPromote - 1) / kPromote;  // partial buffer fills per tile
@@ -399,6 +411,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
+            mbar_init(&full[S + s], 1);
             mbar_init(&empty[s], PAIR ? 1 : cs);
         }
         for (int p = 0; p < 4; ++p) {
@@ -430,70 +443,10 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
     if (warp < 4) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsCtl));
     else asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsEpi));
 
-    if (threadIdx.x == 0) {
-        // ---- TMA producer
-        int q = 0;
-        bool ok = true;
-        for (int tile = cid; tile < tiles && ok; tile += nclu) {
-            const int mg = tile / ntn, n0 = (tile - mg * ntn) * BN, mt = mg * cs + crank;
-            for (int kc = 0; kc < nk; ++kc, ++q) {
-                const int s = q % S;
-                if (q >= S && !mbar_wait(&empty[s], ((q / S) - 1) & 1)) {
-                    atomicExch(err, 1);
-                    *(volatile int*)abort_flag = 1;
-                    ok = false;
-                    break;
-                }
-                if (*(volatile int*)abort_flag) {
-                    ok = false;
-                    break;
-                }
-                unsigned char* st = base + s * SB;
-                const int ay = (mt * nk + kc) * BM;
-                if constexpr (PAIR) {
-                    // both CTAs' bytes land on the leader's barrier: A rows of this CTA, B^T rows
-                    // n0 + 64 rank .. + 63 (this CTA's half of the tile's columns)
-                    if (crank == 0) mbar_expect_tx(&full[s], 2 * SB);
-                    const uint32_t fb = cluster_addr(&full[s], 0);
-                    tma_load_2d_pair(st, &mAh, fb, 0, ay);
-                    tma_load_2d_pair(st + BM * BK * 4, &mAl, fb, 0, ay);
-                    tma_load_2d_pair(st + 2 * BM * BK * 4, &mBh, fb, kc * BK, n0 + 64 * crank);
-                    tma_load_2d_pair(st + 2 * BM * BK * 4 + 64 * BK * 4, &mBl, fb, kc * BK, n0 + 64 * crank);
-                } else {
-                    mbar_expect_tx(&full[s], SB);
-                    tma_load_2d(st, &mAh, &full[s], 0, ay);  // row tiles past R read zeros
-                    tma_load_2d(st + BM * BK * 4, &mAl, &full[s], 0, ay);
-                    if (cs == 1) {
-                        tma_load_2d(st + 2 * BM * BK * 4, &mBh, &full[s], kc * BK, n0);
-                        tma_load_2d(st + 2 * BM * BK * 4 + BN * BK * 4, &mBl, &full[s], kc * BK, n0);
-                    } else if (crank == 0) {
-                        tma_load_2d_mc(st + 2 * BM * BK * 4, &mBh, &full[s], kc * BK, n0, cmask);
-                        tma_load_2d_mc(st + 2 * BM * BK * 4 + BN * BK * 4, &mBl, &full[s], kc * BK, n0, cmask);
-                    }
-                }
-            }
-        }
-        if (!PAIR || crank == 0) {
-            for (int k = (q > S ? q - S : 0); k < q; ++k) {  // every issued stage lands before exit
-                if (!mbar_wait(&full[k % S], (k / S) & 1)) {
-                    atomicExch(err, 1);
-                    break;
-                }
-            }
-        }
-        if (cs > 1) {
-            // every CTA's release of the last use of each stage has arrived here, so no peer signals
-            // this CTA's barriers after it exits
-            for (int k = (q > S ? q - S : 0); k < q; ++k) {
-                if (!mbar_wait(&empty[k % S], (k / S) & 1)) {
-                    atomicExch(err, 1);
-                    break;
-                }
-            }
-        }
-    } else if (threadIdx.x == 32) {
-        // ---- MMA issuer (the pair's leader only in the pair form)
+    // ---- MMA issuers (in the pair's leader only in the pair form): fills of parity `own`
+    auto issue_fills = [&](const int own) {
         int q = 0, lt = 0;
+        uint32_t par = 0;  // bit s: parity of the next phase of full[own][s]
         bool ok = !PAIR || crank == 0;
         for (int tile = cid; tile < tiles && ok; tile += nclu, ++lt) {
             const int g = lt & 1, kg = lt >> 1;
@@ -502,7 +455,10 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
                 const int uses = kg * ((npc + 1 - r) >> 1) + (ps >> 1);  // earlier fills of buffer p
                 const bool first = kc % kPromote == 0;                    // this chunk starts a fill
                 const bool last = kc % kPromote == kPromote - 1 || kc == nk - 1;
-                if (!mbar_wait(&full[s], (q / S) & 1) || (first && uses >= 1 && !mbar_wait(&pfree[p], (uses - 1) & 1))) {
+                if (r != own) continue;  // the other issuer's chunk
+                const uint32_t ph = (par >> s) & 1u;
+                par ^= 1u << s;
+                if (!mbar_wait(&full[own * S + s], ph) || (first && uses >= 1 && !mbar_wait(&pfree[p], (uses - 1) & 1))) {
                     atomicExch(err, 1);
                     *(volatile int*)abort_flag = 1;
                     ok = false;
@@ -546,6 +502,79 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_tc_gemm_pp(const __grid_
                 }
             }
         }
+    };
+
+    if (threadIdx.x == 0) {
+        // ---- TMA producer
+        int q = 0;
+        bool ok = true;
+        uint32_t fpar = 0, lastr = 0;  // phases begun on full[r][s] (bit r S + s, mod 2); owner of stage s's last chunk
+        for (int tile = cid; tile < tiles && ok; tile += nclu) {
+            const int mg = tile / ntn, n0 = (tile - mg * ntn) * BN, mt = mg * cs + crank;
+            for (int kc = 0; kc < nk; ++kc, ++q) {
+                const int s = q % S, r = (kc / kPromote) & 1;
+                if (q >= S && !mbar_wait(&empty[s], ((q / S) - 1) & 1)) {
+                    atomicExch(err, 1);
+                    *(volatile int*)abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+                if (*(volatile int*)abort_flag) {
+                    ok = false;
+                    break;
+                }
+                unsigned char* st = base + s * SB;
+                const int ay = (mt * nk + kc) * BM;
+                uint64_t* fb0 = &full[r * S + s];  // the barrier of the issuer that consumes this chunk
+                fpar ^= 1u << (r * S + s);
+                lastr = (lastr & ~(1u << s)) | ((uint32_t)r << s);
+                if constexpr (PAIR) {
+                    // both CTAs' bytes land on the leader's barrier: A rows of this CTA, B^T rows
+                    // n0 + 64 rank .. + 63 (this CTA's half of the tile's columns)
+                    if (crank == 0) mbar_expect_tx(fb0, 2 * SB);
+                    const uint32_t fb = cluster_addr(fb0, 0);
+                    tma_load_2d_pair(st, &mAh, fb, 0, ay);
+                    tma_load_2d_pair(st + BM * BK * 4, &mAl, fb, 0, ay);
+                    tma_load_2d_pair(st + 2 * BM * BK * 4, &mBh, fb, kc * BK, n0 + 64 * crank);
+                    tma_load_2d_pair(st + 2 * BM * BK * 4 + 64 * BK * 4, &mBl, fb, kc * BK, n0 + 64 * crank);
+                } else {
+                    mbar_expect_tx(fb0, SB);
+                    tma_load_2d(st, &mAh, fb0, 0, ay);  // row tiles past R read zeros
+                    tma_load_2d(st + BM * BK * 4, &mAl, fb0, 0, ay);
+                    if (cs == 1) {
+                        tma_load_2d(st + 2 * BM * BK * 4, &mBh, fb0, kc * BK, n0);
+                        tma_load_2d(st + 2 * BM * BK * 4 + BN * BK * 4, &mBl, fb0, kc * BK, n0);
+                    } else if (crank == 0) {
+                        // the same barrier offset in every CTA of the cluster: the chunk's owner is the same there
+                        tma_load_2d_mc(st + 2 * BM * BK * 4, &mBh, fb0, kc * BK, n0, cmask);
+                        tma_load_2d_mc(st + 2 * BM * BK * 4 + BN * BK * 4, &mBl, fb0, kc * BK, n0, cmask);
+                    }
+                }
+            }
+        }
+        if (!PAIR || crank == 0) {
+            for (int s = 0; s < S && s < q; ++s) {  // the last chunk of every stage lands before exit
+                const int r = (int)((lastr >> s) & 1u);
+                if (!mbar_wait(&full[r * S + s], ((fpar >> (r * S + s)) & 1u) ^ 1u)) {
+                    atomicExch(err, 1);
+                    break;
+                }
+            }
+        }
+        if (cs > 1) {
+            // every CTA's release of the last use of each stage has arrived here, so no peer signals
+            // this CTA's barriers after it exits
+            for (int k = (q > S ? q - S : 0); k < q; ++k) {
+                if (!mbar_wait(&empty[k % S], (k / S) & 1)) {
+                    atomicExch(err, 1);
+                    break;
+                }
+            }
+        }
+    } else if (threadIdx.x == 32) {
+        issue_fills(0);
+    } else if (threadIdx.x == 64) {
+        issue_fills(1);
     }
     if (warp >= 4) {
         // ---- epilogue groups
