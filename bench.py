@@ -654,6 +654,20 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def branch_pass(domains, horizon):
+    """Two bounds passes of the staged path on the first `domains` branch domains (with their split
+    lists) of the 12-256x3-4 workload with horizon `horizon` (a small case for kernel profiling)."""
+    import dataclasses
+    from paper_2605_25346_b300 import api
+    prob = dataclasses.replace(wl.quadrotor_branch(only=np.arange(domains)), H=horizon)
+    r = api.Reach(0).load(prob)
+    for _ in range(2):
+        r.bounds(on_device=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"branch_pass": {"domains": domains, "horizon": horizon, "launches": r.launches()}}), flush=True)
+    r.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -672,7 +686,11 @@ def main():
                     help="with --wide-pass: force the tensor-core GEMM launch shape (1..6, see dr_gemm_tuning_report)")
     ap.add_argument("--wide-pass", nargs=2, type=int, metavar=("DOMAINS", "H"), default=None,
                     help="profiling aid: run two staged tensor-core passes on a 16-512x4-8 sample and exit")
+    ap.add_argument("--branch-pass", nargs=2, type=int, metavar=("DOMAINS", "H"), default=None,
+                    help="profiling aid: run two staged tensor-core passes on a 12-256x3-4 branch sample and exit")
     args = ap.parse_args()
+    if args.branch_pass:
+        return branch_pass(*args.branch_pass)
     if args.wide_pass:
         return wide_pass(*args.wide_pass, gemm_shape=args.gemm_shape)
     if args.wide_refine:

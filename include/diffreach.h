@@ -102,8 +102,9 @@ typedef struct dr_options {
                               first use (cached per architecture and widths; file DR_TUNE_CACHE
                               if set), and the tensor-core GEMM's launch shape per GEMM shape
                               (persistent or one tile per CTA, 128/64/32 columns; timed on the
-                              first pass outside a graph capture, cached per process; see
-                              dr_gemm_tuning_report), 1 = no search (first candidate that fits;
+                              first pass outside a graph capture, cached per process and in the
+                              file DR_GEMM_TUNE_CACHE if set; see dr_gemm_tuning_report),
+                              1 = no search (first candidate that fits;
                               the GEMM heuristic), 2 + v = use
                               candidate v (0..9; DR_ERR_SHAPE if it does not fit the controller):
                               0..2 one warp per domain (16/8/4 warps per CTA; two hidden layers,

@@ -118,11 +118,19 @@ __global__ void k_w_seed(const WideArgs a) {
 
 // FP32 view of each domain's TM; one block per domain.
 __global__ void k_w_view(const WideArgs a) {
+    __shared__ unsigned int xs_bits;  // max over rows of the TM scale's row sums (non-negative floats)
     const int n = a.net.n, d = blockIdx.x;
     const double* P = a.P + (int64_t)d * n * n;
     float* Pf = a.Pf + (int64_t)d * n * n;
+    if (threadIdx.x == 0) xs_bits = 0u;
+    __syncthreads();
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) Pf[idx] = (float)P[idx];
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        // row i of tm_scale (common.cuh), in its order; the rows' maximum is taken below
+        float rs = fabsf((float)a.c[(int64_t)d * n + i]) +
+                   fmaxf(fabsf((float)a.Ilo[(int64_t)d * n + i]), fabsf((float)a.Ihi[(int64_t)d * n + i]));
+        for (int k = 0; k < n; ++k) rs += fabsf((float)P[i * n + k]);
+        if (!isnan(rs)) atomicMax(&xs_bits, __float_as_uint(rs));  // as fmaxf: a NaN row is skipped
         const double ci = a.c[(int64_t)d * n + i];
         const float cf = (float)ci;
         double dev = 0.0;
@@ -138,6 +146,7 @@ __global__ void k_w_view(const WideArgs a) {
             a.xmax[(int64_t)d * n + i] = __double2float_ru(mag * (1.0 + 1e-12));
         }
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
         double dv = 0.0;
         float* vf = a.vf + (int64_t)d * (n + 1);
@@ -146,7 +155,9 @@ __global__ void k_w_view(const WideArgs a) {
             dv += fabs(a.v[(int64_t)d * n + k] - (double)vf[k]);
         }
         vf[n] = __double2float_ru(a.w[d] + dv);
-        a.xscale[d] = tm_scale(a.c + (int64_t)d * n, P, a.Ilo + (int64_t)d * n, a.Ihi + (int64_t)d * n, n);
+        // tm_scale of the TM with its rows spread over the threads: this GPU's FP64 pipe (which
+        // also converts FP64 to FP32) takes as long for one thread's instruction as for a warp's
+        a.xscale[d] = __uint_as_float(xs_bits);
         if (a.vsnap)
             for (int k = 0; k <= n; ++k) a.vsnap[(int64_t)d * a.net.L * (n + 1) + k] = vf[k];
     }
@@ -602,14 +613,19 @@ __device__ __forceinline__ float tf32_part(float x) {
 // First chain level of target ell >= 2 from the shared W_ell, writing A = W_ell diag(s_{ell-1}) as
 // TF32 parts Ah/Al in the blocked left-operand layout (rows Dc*n_ell, ldk zero-padded columns; see
 // tc::blk_index) plus kappa.  One warp per (domain, row).
-__global__ void k_t_chain_init(const WideArgs a, int ell, float* __restrict__ Ah, float* __restrict__ Al, int ldk) {
+//
+// kappa = b + (row sums) is formed in FP64.  The FP64 pipe of this GPU takes about as long for one
+// warp instruction as for 32 active lanes' worth of work, and runs at a small fraction of the FP32
+// rate, so the warps' three sums go through shared memory and one lane per row of the block does
+// the FP64 additions: one set of FP64 instructions per block instead of one per row (with K = 256
+// the per-row sets were what bound this kernel, not its HBM writes).
+constexpr int kChainInitThreads = 256;
+// One row of k_t_chain_init: the operand's TF32 parts, and the row's three FP32 sums into `sums`.
+__device__ __forceinline__ void k_t_chain_init_row(const WideArgs& a, int ell, float* __restrict__ Ah, float* __restrict__ Al,
+                                                   int ldk, int64_t wid, int lane, float (*sums)[kChainInitThreads / 32]) {
     const NetDesc& N = a.net;
     const int rows = N.w[ell];
-    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (wid >= (int64_t)a.Dc * rows) return;
     const int d = (int)(wid / rows), i = (int)(wid - (int64_t)d * rows);
-    const float bi = a.b[N.boff[ell - 1] + i];
     const int K = N.w[ell - 1];
     const float* Wrow = a.W + N.Woff[ell - 1] + (int64_t)i * K;
     const float* s = a.hs + (int64_t)d * N.hidden + N.hoff[ell - 1];
@@ -662,8 +678,120 @@ __global__ void k_t_chain_init(const WideArgs a, int ell, float* __restrict__ Ah
     sneg = warp_sum(sneg);
     sb = warp_sum(sb);
     if (lane == 0) {
-        a.khi[(int64_t)d * N.maxw + i] = (double)bi + (double)spos + (double)sb;
-        a.klo[(int64_t)d * N.maxw + i] = (double)bi + (double)sneg + (double)sb;
+        const int w = (threadIdx.x >> 5);
+        sums[0][w] = spos;
+        sums[1][w] = sneg;
+        sums[2][w] = sb;
+    }
+}
+
+__global__ void __launch_bounds__(kChainInitThreads) k_t_chain_init(const WideArgs a, int ell, float* __restrict__ Ah,
+                                                                   float* __restrict__ Al, int ldk) {
+    __shared__ float sums[3][kChainInitThreads / 32];
+    const NetDesc& N = a.net;
+    const int rows = N.w[ell];
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t nrows = (int64_t)a.Dc * rows;
+    if (wid < nrows) {
+        k_t_chain_init_row(a, ell, Ah, Al, ldk, wid, lane, sums);
+    }
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    const int64_t r = (blockIdx.x * (int64_t)blockDim.x >> 5) + threadIdx.x;
+    if (threadIdx.x < nw && r < nrows) {
+        const int d = (int)(r / rows), i = (int)(r - (int64_t)d * rows);
+        const float bi = a.b[N.boff[ell - 1] + i];
+        a.khi[(int64_t)d * N.maxw + i] = (double)bi + (double)sums[0][threadIdx.x] + (double)sums[2][threadIdx.x];
+        a.klo[(int64_t)d * N.maxw + i] = (double)bi + (double)sums[1][threadIdx.x] + (double)sums[2][threadIdx.x];
+    }
+}
+
+// The same first chain level with the domain's per-column vectors held in registers: a warp takes
+// kChainRowsPerWarp consecutive rows (of one domain, mostly), loads s, d (per domain) and the bias
+// b_{ell-1} once, and then reads only the W_ell row per row.  For K = 128 KV columns, K = ldk, and
+// 16-byte aligned rows and vectors (the host checks).  Per row the arithmetic and its order are
+// k_t_chain_init_row's, so the outputs are identical; the instruction count per row falls about
+// four-fold (no per-row index divisions or vector loads), which makes the kernel bound by its
+// HBM writes also for K = 256.
+constexpr int kChainRowsPerWarp = 16;
+template <int KV>
+__global__ void __launch_bounds__(kChainInitThreads) k_t_chain_init_rc(const WideArgs a, int ell, float* __restrict__ Ah,
+                                                                      float* __restrict__ Al, int ldk) {
+    constexpr int kRowsPerBlock = kChainInitThreads / 32 * kChainRowsPerWarp;
+    __shared__ float sums[3][kRowsPerBlock];
+    const NetDesc& N = a.net;
+    const int rows = N.w[ell];
+    const int K = N.w[ell - 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t nrows = (int64_t)a.Dc * rows;
+    const int64_t rb0 = (int64_t)blockIdx.x * kRowsPerBlock;
+    const int64_t r0 = rb0 + (int64_t)warp * kChainRowsPerWarp;
+    const int nk = ldk >> 5;
+    const float* Wl = a.W + N.Woff[ell - 1];
+    const float* bm = a.b + N.boff[ell - 2];
+    float4 bv[KV], sv[KV], dv[KV];
+#pragma unroll
+    for (int v = 0; v < KV; ++v) bv[v] = *reinterpret_cast<const float4*>(bm + 4 * lane + 128 * v);
+    int d = (int)(r0 / rows), i = (int)(r0 - (int64_t)d * rows), dl = -1;
+    for (int q = 0; q < kChainRowsPerWarp; ++q, ++i) {
+        const int64_t r = r0 + q;
+        if (r >= nrows) break;  // uniform across the warp
+        if (i == rows) {
+            i = 0;
+            ++d;
+        }
+        if (d != dl) {
+            const float* sd = a.hs + (int64_t)d * N.hidden + N.hoff[ell - 1];
+            const float* dd = a.hd + (int64_t)d * N.hidden + N.hoff[ell - 1];
+#pragma unroll
+            for (int v = 0; v < KV; ++v) {
+                sv[v] = *reinterpret_cast<const float4*>(sd + 4 * lane + 128 * v);
+                dv[v] = *reinterpret_cast<const float4*>(dd + 4 * lane + 128 * v);
+            }
+            dl = d;
+        }
+        const float* Wrow = Wl + (int64_t)i * K;
+        float spos = 0.f, sneg = 0.f, sb = 0.f;
+#pragma unroll
+        for (int v = 0; v < KV; ++v) {
+            const int j = 4 * lane + 128 * v;
+            const float4 x = *reinterpret_cast<const float4*>(Wrow + j);
+            const float xa[4] = {x.x, x.y, x.z, x.w}, da[4] = {dv[v].x, dv[v].y, dv[v].z, dv[v].w};
+            const float sa[4] = {sv[v].x, sv[v].y, sv[v].z, sv[v].w}, ba[4] = {bv[v].x, bv[v].y, bv[v].z, bv[v].w};
+            float h[4], l[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                spos = fmaf(posf(xa[e]), da[e], spos);
+                sneg = fmaf(negf(xa[e]), da[e], sneg);
+                const float xs = xa[e] * sa[e];
+                sb = fmaf(xs, ba[e], sb);
+                h[e] = tf32_part(xs);
+                l[e] = tf32_part(xs - h[e]);
+            }
+            const int64_t o = tc::blk_index(r, j, nk);
+            *reinterpret_cast<float4*>(Ah + o) = make_float4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<float4*>(Al + o) = make_float4(l[0], l[1], l[2], l[3]);
+        }
+        spos = warp_sum(spos);
+        sneg = warp_sum(sneg);
+        sb = warp_sum(sb);
+        if (lane == 0) {
+            const int t = warp * kChainRowsPerWarp + q;
+            sums[0][t] = spos;
+            sums[1][t] = sneg;
+            sums[2][t] = sb;
+        }
+    }
+    __syncthreads();
+    // kappa in FP64, one thread per row of the block (see k_t_chain_init)
+    for (int t = threadIdx.x; t < kRowsPerBlock; t += blockDim.x) {
+        const int64_t r = rb0 + t;
+        if (r >= nrows) break;
+        const int dr = (int)(r / rows), ir = (int)(r - (int64_t)dr * rows);
+        const float bi = a.b[N.boff[ell - 1] + ir];
+        a.khi[(int64_t)dr * N.maxw + ir] = (double)bi + (double)sums[0][t] + (double)sums[2][t];
+        a.klo[(int64_t)dr * N.maxw + ir] = (double)bi + (double)sums[1][t] + (double)sums[2][t];
     }
 }
 
