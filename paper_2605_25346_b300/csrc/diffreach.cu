@@ -1764,7 +1764,9 @@ static void launch_t_project(dr_ctx* c, const WideArgs& a, int ell, const float*
         if (a.net.n % 4 == 0) k_t_project4<true><<<blocks, 256, 0, st>>>(a, ell, Lx, shared_lx, lx_parts, part, ntiles);
         else k_t_project4<false><<<blocks, 256, 0, st>>>(a, ell, Lx, shared_lx, lx_parts, part, ntiles);
     } else {
-        const unsigned blocks = (unsigned)std::min<int64_t>((R + 127) / 128, (int64_t)148 * 16);
+        // one row per thread (no grid-stride tail); seven blocks of 128 threads per SM at 72 registers
+        // (k_t_project's launch bounds): 1.3x the earlier 96-register, 16-blocks-per-SM grid
+        const unsigned blocks = (unsigned)std::min<int64_t>((R + 127) / 128, (int64_t)1 << 30);
         if (a.net.n <= 16) k_t_project<16><<<blocks, 128, 0, st>>>(a, ell, Lx, shared_lx, lx_parts, part, ntiles);
         else k_t_project<64><<<blocks, 128, 0, st>>>(a, ell, Lx, shared_lx, lx_parts, part, ntiles);
     }

@@ -1009,8 +1009,11 @@ __global__ void __launch_bounds__(256, 3) k_t_project4(const WideArgs a, int ell
 // so that the row lives in registers and the loops unroll.
 // With lx_parts > 0 the row is the sum, in order, of lx_parts partial rows stored entry-major:
 // entry j of part t at Lxb[(t*n + j)*R + r].
+// The row's work is a few hundred FP64 and FP32 operations with long FP64 latencies: the launch
+// bounds ask for seven resident blocks per SM (72 registers for NMAX = 16, a few spilled bytes),
+// which measured faster than 96 registers (five blocks) or 64 (eight blocks, 400 bytes spilled).
 template <int NMAX>
-__global__ void __launch_bounds__(128) k_t_project(const WideArgs a, int ell, const float* __restrict__ Lxb, int shared_lx,
+__global__ void __launch_bounds__(128, NMAX <= 16 ? 7 : 1) k_t_project(const WideArgs a, int ell, const float* __restrict__ Lxb, int shared_lx,
                                                    int lx_parts, const float* __restrict__ part, int ntiles) {
     const NetDesc& N = a.net;
     const int n = N.n, L = N.L, rows = N.w[ell];
