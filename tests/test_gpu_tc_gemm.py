@@ -64,3 +64,40 @@ def test_persistent_launch_shapes_agree(widths, D):
     scale = np.maximum(np.maximum(np.abs(olo), np.abs(ohi)), ohi - olo)
     err = np.maximum(np.abs(out[106]["lo"][:3] - olo), np.abs(out[106]["hi"][:3] - ohi)) / scale
     assert err.max() <= 1e-5
+
+
+# The GEMM autotuner's choices persist in the file DR_GEMM_TUNE_CACHE: the first process times the
+# candidates and writes one "key variant" line per GEMM shape; a second process takes the file's
+# choices without trials (its report says so) and computes the same bounds.
+_CACHE_SCRIPT = """
+import sys
+import numpy as np
+from paper_2605_25346_b300 import api
+from paper_2605_25346_b300 import workloads as wl
+p = wl.random_problem(79, [6, 256, 256, 200, 3], D=64, H=2, eps=0.15)
+r = api.Reach(0).load(p, precision=2)
+b = r.bounds(on_device=False)
+np.save(sys.argv[1], np.concatenate([b["lo"].ravel(), b["hi"].ravel()]))
+r.close()
+print(api.gemm_tuning_report())
+"""
+
+
+def test_gemm_tuning_cache_file(tmp_path):
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, DR_GEMM_TUNE_CACHE=str(tmp_path / "gemm_cache.txt"))
+    runs = []
+    for k in range(2):
+        out = subprocess.run([sys.executable, "-c", _CACHE_SCRIPT, str(tmp_path / f"b{k}.npy")], cwd=root, env=env,
+                             capture_output=True, text=True, timeout=600)
+        assert out.returncode == 0, out.stderr[-2000:]
+        runs.append(out.stdout)
+    lines = (tmp_path / "gemm_cache.txt").read_text().split("\n")
+    entries = [ln.split() for ln in lines if ln.strip()]
+    assert entries and all(len(e) == 2 and e[0].startswith("epi") and 1 <= int(e[1]) <= 6 for e in entries), lines
+    assert "(ms:" in runs[0] and "from DR_GEMM_TUNE_CACHE" in runs[1], runs
+    assert "(ms:" not in runs[1], runs[1]
+    np.testing.assert_array_equal(np.load(tmp_path / "b0.npy"), np.load(tmp_path / "b1.npy"))
