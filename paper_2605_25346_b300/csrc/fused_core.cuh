@@ -174,9 +174,16 @@ __device__ void load_params(const Dom& s, const FusedArgs& a) {
 template <int NT>
 __device__ void tm_view(const Dom& s, int n) {
     const int tid = threadIdx.x;
+    if (tid == 0) s.misc[2] = 0;  // the previous step's projections are done (the step ended with a barrier)
+    __syncthreads();
     for (int idx = tid; idx < n * n; idx += NT) s.Pf[idx] = (float)s.P[idx];
     for (int i = tid; i < n; i += NT) {
         const float ci = (float)s.c[i];
+        // row i of tm_scale (common.cuh), in its order; the maximum over rows by atomicMax on the
+        // float's bits (a NaN row is skipped, as fmaxf skips it), instead of one thread doing all rows
+        float rs = fabsf(ci) + fmaxf(fabsf((float)s.Ilo[i]), fabsf((float)s.Ihi[i]));
+        for (int k = 0; k < n; ++k) rs += fabsf((float)s.P[i * n + k]);
+        if (!isnan(rs)) atomicMax(reinterpret_cast<unsigned int*>(s.misc + 2), __float_as_uint(rs));
         double dev = 0.0;
         for (int k = 0; k < n; ++k) dev += fabs(s.P[i * n + k] - (double)(float)s.P[i * n + k]);
         const double dc = s.c[i] - (double)ci;
@@ -191,7 +198,6 @@ __device__ void tm_view(const Dom& s, int n) {
             dv += fabs(s.v[k] - (double)s.vf[k]);
         }
         s.vf[n] = __double2float_ru(s.wv[0] + dv);
-        s.misc[2] = __float_as_int(tm_scale(s.c, s.P, s.Ilo, s.Ihi, n));  // for DR_STATUS_MARGIN_BIT
     }
     __syncthreads();
 }

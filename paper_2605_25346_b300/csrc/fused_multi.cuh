@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(NT) k_fused_forward_multi(const MultiArgs a) {
         for (int i = 0; i <= n; ++i) MD(g, Y.red)[i] = 0.0;
         MI(g, Y.misc)[0] = a.sp_row ? (int)a.sp_row[dbase + g] : 0;
         MI(g, Y.misc)[1] = 0;
+        MI(g, Y.misc)[2] = 0;  // the TM scale (bits of a non-negative float), built by atomicMax per step
     }
     __syncthreads();
 
@@ -137,6 +138,13 @@ __global__ void __launch_bounds__(NT) k_fused_forward_multi(const MultiArgs a) {
             const double* P = MD(g, Y.P);
             const double ci = MD(g, Y.c)[i];
             const float cf = (float)ci;
+            // row i of tm_scale (common.cuh), in its order; the maximum over rows by atomicMax on the
+            // float's bits (a NaN row is skipped, as fmaxf skips it).  One thread per domain doing all
+            // rows cost 9 % of this kernel: its FP64-to-FP32 conversions each take the FP64 pipe's time
+            // of a whole warp instruction
+            float rs = fabsf(cf) + fmaxf(fabsf((float)MD(g, Y.Ilo)[i]), fabsf((float)MD(g, Y.Ihi)[i]));
+            for (int k = 0; k < n; ++k) rs += fabsf((float)P[i * n + k]);
+            if (!isnan(rs)) atomicMax(reinterpret_cast<unsigned int*>(MI(g, Y.misc) + 2), __float_as_uint(rs));
             double dev = 0.0;
             for (int k = 0; k < n; ++k) dev += fabs(P[i * n + k] - (double)(float)P[i * n + k]);
             const double dc = ci - (double)cf;
@@ -153,7 +161,6 @@ __global__ void __launch_bounds__(NT) k_fused_forward_multi(const MultiArgs a) {
                 dv += fabs(v[k] - (double)vf[k]);
             }
             vf[n] = __double2float_ru(MD(g, Y.w)[0] + dv);
-            MI(g, Y.misc)[2] = __float_as_int(tm_scale(MD(g, Y.c), MD(g, Y.P), MD(g, Y.Ilo), MD(g, Y.Ihi), n));
         }
         __syncthreads();
 
@@ -426,7 +433,8 @@ __global__ void __launch_bounds__(NT) k_fused_forward_multi(const MultiArgs a) {
                 __syncthreads();
             }
         }
-        // ---- a7 dynamics (FP64)
+        // ---- a7 dynamics (FP64); the step's projections no longer read the TM scale: reset it
+        for (int g = tid; g < gcount; g += NT) MI(g, Y.misc)[2] = 0;
         for (int idx = tid; idx < gcount * n * n; idx += NT) {
             const int g = idx / (n * n), r = idx - g * n * n, i = r / n, k = r - i * n;
             const double* P = MD(g, Y.P);

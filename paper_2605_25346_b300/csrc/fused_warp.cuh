@@ -240,8 +240,11 @@ __global__ void __launch_bounds__(32 * WPC, (24 + WPC - 1) / WPC) k_fused_warp(c
     for (int t = 0; t < H; ++t) {
         // ---- FP32 view of the TM (remainder absorbs the casts of c and P; wf those of v)
         for (int idx = lane; idx < n * n; idx += 32) Pf[idx] = (float)P[idx];
+        float rs = 0.f;  // row `lane` of tm_scale (common.cuh) in its order; lanes past n hold 0
         for (int i = lane; i < n; i += 32) {
             const float ci = (float)c[i];
+            rs = fabsf(ci) + fmaxf(fabsf((float)Ilo[i]), fabsf((float)Ihi[i]));
+            for (int k = 0; k < n; ++k) rs += fabsf((float)P[i * n + k]);
             double dev = 0.0;
             for (int k = 0; k < n; ++k) dev += fabs(P[i * n + k] - (double)(float)P[i * n + k]);
             const double dc = c[i] - (double)ci;
@@ -256,8 +259,11 @@ __global__ void __launch_bounds__(32 * WPC, (24 + WPC - 1) / WPC) k_fused_warp(c
                 dv += fabs(v[k] - (double)vf[k]);
             }
             vf[n] = __double2float_ru(wv[0] + dv);
-            misc[2] = __float_as_int(tm_scale(c, P, Ilo, Ihi, n));
         }
+        // the rows' maximum (fmaxf skips a NaN row; n <= kWarpNX < 32, so some lane holds 0)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rs = fmaxf(rs, __shfl_xor_sync(0xffffffffu, rs, o));
+        if (lane == 0) misc[2] = __float_as_int(rs);
         __syncwarp();
 
         // ---- target 1: Lambda_x = W_1, kappa = b_1
