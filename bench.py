@@ -419,6 +419,25 @@ def measure_quad6(local, steps=10, warmup=3):
                          "peak_basis": "148 SMs x 128 FP32 lanes x 2 FLOP x 2032 MHz (FMA issue rate at max SM clock)"}}
 
 
+def measure_quad6_fresh(local):
+    """measure_quad6 in a fresh process: the short fused launches measured 10-40 % slower inside this
+    process after the large staged workload and the TF32 probe had run (same kernel variant, same
+    stream setup), and 1.04-1.07 ms per pass in a process of their own."""
+    try:
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--quad6"], capture_output=True, text=True,
+                             timeout=600, env=dict(os.environ, LOCAL_RANK=str(local)))
+        for ln in out.stdout.splitlines()[::-1]:
+            if ln.startswith("{"):
+                res = json.loads(ln)["quad6"]
+                res["process"] = "fresh"
+                return res
+    except (OSError, subprocess.SubprocessError, ValueError, KeyError):
+        pass
+    res = measure_quad6(local)
+    res["process"] = "benchmark process (the fresh-process run failed)"
+    return res
+
+
 def measure_tpush(local, reps=5):
     """DT neural dynamics with planned inputs (the T-pushing-shaped 7-96x3-5 residual model, H = 10):
     bounds over 128 initial boxes and over 1024 MPC action samples, and the gradient dV/du of every
@@ -686,9 +705,14 @@ def main():
                     help="with --wide-pass: force the tensor-core GEMM launch shape (1..6, see dr_gemm_tuning_report)")
     ap.add_argument("--wide-pass", nargs=2, type=int, metavar=("DOMAINS", "H"), default=None,
                     help="profiling aid: run two staged tensor-core passes on a 16-512x4-8 sample and exit")
+    ap.add_argument("--quad6", action="store_true",
+                    help="only the 6-64-64-3 fused-kernel measurement (one JSON line), in a process of its own")
     ap.add_argument("--branch-pass", nargs=2, type=int, metavar=("DOMAINS", "H"), default=None,
                     help="profiling aid: run two staged tensor-core passes on a 12-256x3-4 branch sample and exit")
     args = ap.parse_args()
+    if args.quad6:
+        print(json.dumps({"quad6": measure_quad6(int(os.environ.get("LOCAL_RANK", "0")))}), flush=True)
+        return
     if args.branch_pass:
         return branch_pass(*args.branch_pass)
     if args.wide_pass:
@@ -859,7 +883,7 @@ def main():
                 roof["frac_named"] = ("frac uses the bf16-derived sustained peak; frac_of_measured_tf32_over_3_* use "
                                       "the cuBLAS TF32 probe of this run")
             roof["pass_frac_of_measured_tf32_over_3_sustained"] = roof["pass_fp32eq_tflops"] / (tf32["tf32_tflops_sustained"] / 3.0)
-            extras["quad6"] = measure_quad6(local)
+            extras["quad6"] = measure_quad6_fresh(local)
             extras["branch12_full"] = measure_branch12_full(local)
             extras["tpush_dt_mpc"] = measure_tpush(local)
             extras["rigorous"] = measure_rigorous(local)
