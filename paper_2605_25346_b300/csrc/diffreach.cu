@@ -1865,7 +1865,12 @@ static int wide_step(dr_ctx* c, WideLane& w, int t, bool tcore, const KeepLevels
                 c->launches++;
                 TRY(tc_gemm(c, c->dA2h, c->dA2l, w.t2.Bh, w.t2.Bl, w.t2.C1, rows, N.w[1], dc * NB, ldk1, dc * NB, c->derr, st));
                 TRY(tc_gemm(c, c->dA2ph, c->dA2pl, w.t2.Dh, w.t2.Dl, w.t2.C2, 2 * rows, N.w[1], dc, ldk1, dc, c->derr, st));
-                k_t2_finish<<<blocks_for((int64_t)R, 256), 256, 0, st>>>(a, w.t2.C1, w.t2.C2, lamC);
+                if (NB <= kT2MaxNB) {
+                    const dim3 grid((unsigned)((dc + kT2TileDoms - 1) / kT2TileDoms), (unsigned)((rows + kT2TileRows - 1) / kT2TileRows));
+                    k_t2_finish_tiled<<<grid, 256, 0, st>>>(a, w.t2.C1, w.t2.C2, lamC);
+                } else {
+                    k_t2_finish<<<blocks_for((int64_t)R, 256), 256, 0, st>>>(a, w.t2.C1, w.t2.C2, lamC);
+                }
                 c->launches++;
                 launch_t_project(c, ap, ell, lamC, 0, R, 0, st);
             } else {

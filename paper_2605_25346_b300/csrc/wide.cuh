@@ -842,6 +842,38 @@ __global__ void k_t2_finish(const WideArgs a, const float* __restrict__ C1, cons
     }
 }
 
+// k_t2_finish through a shared-memory tile of 32 rows x 8 domains (n <= 16): C1 holds row i's
+// domains contiguously ([i][d][NB]) while Lambda_x wants each domain's rows contiguously ([d][i][n]),
+// so the one-thread-per-(domain, row) form reads or writes with a stride on one side.  Here the
+// block reads the tile's C1 rows with consecutive threads on consecutive addresses and writes each
+// domain's rows the same way.  Same values and the same FP64 additions for kappa.
+constexpr int kT2TileRows = 32, kT2TileDoms = 8, kT2MaxNB = 17;
+__global__ void __launch_bounds__(256) k_t2_finish_tiled(const WideArgs a, const float* __restrict__ C1,
+                                                         const float* __restrict__ C2, float* __restrict__ Lx) {
+    __shared__ float tile[kT2TileRows][kT2TileDoms * kT2MaxNB + 1];
+    const NetDesc& N = a.net;
+    const int n = N.n, rows = N.w[2], NB = n + 1, W = kT2TileDoms * NB;
+    const int64_t ld1 = (int64_t)a.Dc * NB, ld2 = a.Dc;
+    const int d0 = blockIdx.x * kT2TileDoms, i0 = blockIdx.y * kT2TileRows;
+    const int nd = min(kT2TileDoms, a.Dc - d0), ni = min(kT2TileRows, rows - i0);
+    for (int e = threadIdx.x; e < kT2TileRows * W; e += blockDim.x) {
+        const int ii = e / W, q = e - ii * W;
+        if (ii < ni && q < nd * NB) tile[ii][q] = C1[(int64_t)(i0 + ii) * ld1 + (int64_t)d0 * NB + q];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kT2TileDoms * kT2TileRows * n; e += blockDim.x) {
+        const int dd = e / (kT2TileRows * n), rem = e - dd * (kT2TileRows * n), ii = rem / n, c = rem - ii * n;
+        if (dd < nd && ii < ni) Lx[((int64_t)(d0 + dd) * rows + i0 + ii) * n + c] = tile[ii][dd * NB + c];
+    }
+    const int dd = threadIdx.x % kT2TileDoms, ii = threadIdx.x / kT2TileDoms;
+    if (dd < nd && ii < ni) {
+        const int d = d0 + dd, i = i0 + ii;
+        const double bi = a.b[N.boff[1] + i], sb = tile[ii][dd * NB + n];
+        a.khi[(int64_t)d * N.maxw + i] = bi + (double)C2[(int64_t)i * ld2 + d] + sb;
+        a.klo[(int64_t)d * N.maxw + i] = bi + (double)C2[(int64_t)(rows + i) * ld2 + d] + sb;
+    }
+}
+
 // Adds the per-column-tile intercept partials of a fused chain level into kappa (fixed order).
 __global__ void k_t_partials(const WideArgs a, int ell, const float* __restrict__ part, int ntiles) {
     const NetDesc& N = a.net;
