@@ -8,6 +8,8 @@
 //   warps 1, 2     lane 0 of each issues MMAs: tile j goes into group j % 2's buffers, alternating
 //                  per fill (kPromote chunks); warp 1 issues the even fills, warp 2 the odd ones
 //   warp 3         idle (it completes the first warpgroup for the register split)
+//   warps 4..7     epilogue group 0 (tiles 0, 2, 4, ... of this CTA), warps 8..11 group 1; warp w
+//                  reads TMEM lane quadrant w % 4 and holds that quadrant's rows x 128 columns
 //
 // Two issuers: a tcgen05.mma of 128 x 128 x 8 (TF32) keeps the tensor pipe busy for only 64 cycles,
 // and the pipe holds almost no queued work behind it, so any time the issuing thread spends between
@@ -18,8 +20,6 @@
 // `full` barrier per issuer, signalled by the chunks that issuer consumes: a thread then tests only
 // phases of its own chunks, in order, and no barrier can run two phases ahead of the thread waiting
 // on it (one barrier shared by both would, whenever one thread lags the other).
-//   warps 4..7     epilogue group 0 (tiles 0, 2, 4, ... of this CTA), warps 8..11 group 1; warp w
-//                  reads TMEM lane quadrant w % 4 and holds that quadrant's rows x 128 columns
 //
 // Registers: the launch gives 168 per thread (384 threads, one CTA per SM); the first warpgroup
 // drops to kRegsCtl and the two epilogue warpgroups rise to kRegsEpi, which the released registers
