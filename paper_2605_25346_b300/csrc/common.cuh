@@ -23,6 +23,27 @@ struct SplitRec {
 };
 
 __device__ __forceinline__ float posf(float x) { return x > 0.f ? x : 0.f; }
+
+// A running sum of FP32 terms kept as an unevaluated pair hi + lo: each term enters by TwoSum
+// (Knuth; error-free), so the pair holds the sum to about 2^-48 of its magnitude with FP32 adds only.
+// Summing FP32 partials this way and converting once replaces an FP64 conversion and add per term;
+// on a GPU whose FP64 rate is a small fraction of its FP32 rate that is the cheaper way to the same
+// FP64 value (the FP64 sum rounds to 2^-53 per add; both are far inside the outward margins).
+struct F32Pair {
+    float hi = 0.f, lo = 0.f;
+};
+__device__ __forceinline__ void pair_add(F32Pair& p, float x) {
+    const float s = __fadd_rn(p.hi, x);
+    const float bp = __fsub_rn(s, p.hi);
+    const float e = __fadd_rn(__fsub_rn(p.hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    p.hi = s;
+    p.lo = __fadd_rn(p.lo, e);
+}
+// The pair's value in FP64; a non-finite running sum (an infinite or NaN term, or FP32 overflow)
+// is returned as it is, so it stays non-finite (and is flagged downstream) rather than turning NaN.
+__device__ __forceinline__ double pair_value(const F32Pair& p) {
+    return isfinite(p.hi) ? (double)p.hi + (double)p.lo : (double)p.hi;
+}
 __device__ __forceinline__ float negf(float x) { return x < 0.f ? x : 0.f; }
 __device__ __forceinline__ double posd(double x) { return x > 0.0 ? x : 0.0; }
 __device__ __forceinline__ double negd(double x) { return x < 0.0 ? x : 0.0; }

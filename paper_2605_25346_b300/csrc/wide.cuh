@@ -881,12 +881,13 @@ __global__ void k_t_partials(const WideArgs a, int ell, const float* __restrict_
     const int64_t R = (int64_t)a.Dc * rows;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
         const int d = (int)(r / rows), i = (int)(r - (int64_t)d * rows);
-        double sp = 0.0, sn = 0.0, sb = 0.0;
+        F32Pair psp, psn, psb;
         for (int t = 0; t < ntiles; ++t) {
-            sp += part[((int64_t)t * 3 + 0) * R + r];
-            sn += part[((int64_t)t * 3 + 1) * R + r];
-            sb += part[((int64_t)t * 3 + 2) * R + r];
+            pair_add(psp, part[((int64_t)t * 3 + 0) * R + r]);
+            pair_add(psn, part[((int64_t)t * 3 + 1) * R + r]);
+            pair_add(psb, part[((int64_t)t * 3 + 2) * R + r]);
         }
+        const double sp = pair_value(psp), sn = pair_value(psn), sb = pair_value(psb);
         a.khi[(int64_t)d * N.maxw + i] += sp + sb;
         a.klo[(int64_t)d * N.maxw + i] += sn + sb;
     }
@@ -945,11 +946,15 @@ __global__ void __launch_bounds__(256, 3) k_t_project4(const WideArgs a, int ell
         }
         double sp = 0.0, sn = 0.0, sb = 0.0;
         if (!shared_lx && ntiles > 0) {
+            F32Pair psp, psn, psb;
             for (int t = q; t < ntiles; t += 4) {
-                sp += part[((int64_t)t * 3 + 0) * R + rc];
-                sn += part[((int64_t)t * 3 + 1) * R + rc];
-                sb += part[((int64_t)t * 3 + 2) * R + rc];
+                pair_add(psp, part[((int64_t)t * 3 + 0) * R + rc]);
+                pair_add(psn, part[((int64_t)t * 3 + 1) * R + rc]);
+                pair_add(psb, part[((int64_t)t * 3 + 2) * R + rc]);
             }
+            sp = pair_value(psp);
+            sn = pair_value(psn);
+            sb = pair_value(psb);
         }
         float av = 0.f, rlo = 0.f, rhi = 0.f;
 #pragma unroll
@@ -1061,12 +1066,13 @@ __global__ void __launch_bounds__(128, NMAX <= 16 ? 7 : 1) k_t_project(const Wid
             klo = a.klo[(int64_t)d * N.maxw + i];
             khi = a.khi[(int64_t)d * N.maxw + i];
             if (ntiles > 0) {
-                double sp = 0.0, sn = 0.0, sb = 0.0;
+                F32Pair psp, psn, psb;
                 for (int t = 0; t < ntiles; ++t) {
-                    sp += part[((int64_t)t * 3 + 0) * R + r];
-                    sn += part[((int64_t)t * 3 + 1) * R + r];
-                    sb += part[((int64_t)t * 3 + 2) * R + r];
+                    pair_add(psp, part[((int64_t)t * 3 + 0) * R + r]);
+                    pair_add(psn, part[((int64_t)t * 3 + 1) * R + r]);
+                    pair_add(psb, part[((int64_t)t * 3 + 2) * R + r]);
                 }
+                const double sp = pair_value(psp), sn = pair_value(psn), sb = pair_value(psb);
                 khi += sp + sb;
                 klo += sn + sb;
             }
